@@ -1,0 +1,472 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+rational weights, polynomial exactness, closed forms of Gaussian charge
+clouds, a dense direct solve assembled independently, spherical-harmonic
+multipoles, finite differences, invariances stated in the paper, and a
+second route to the FOD gradient (Eq. 9).
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2108_01186_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _cube(n, h, c=0.0):
+    o = c - 0.5 * h * (n - 1)
+    return (n, n, n, h, np.array([o, o, o]))
+
+
+def _coords(grid):
+    nx, ny, nz, h, o = grid
+    z, y, x = np.meshgrid(o[2] + h * np.arange(nz), o[1] + h * np.arange(ny),
+                          o[0] + h * np.arange(nx), indexing="ij")
+    return x.ravel(), y.ravel(), z.ravel()
+
+
+# --------------------------------------------------------------------------
+# c-0: stencil weights and Laplacian (Sec. II.A)
+# --------------------------------------------------------------------------
+
+def test_fd_weights_match_exact_rationals(orc):
+    w = orc.fd_weights(6)
+    gold = [l.split() for l in open(os.path.join(GOLD, "fd12_weights.txt")) if not l.startswith("#")]
+    for k, num, den in gold:
+        assert abs(w[int(k)] - int(num) / int(den)) < 1e-15
+
+
+def test_fd_weights_order_conditions(orc):
+    w = orc.fd_weights(6)
+    k = np.arange(7, dtype=float)
+    assert abs(w[0] + 2 * w[1:].sum()) < 1e-14                 # constants
+    assert abs(2 * np.sum(k[1:] ** 2 * w[1:]) - 2.0) < 1e-13   # u'' of x^2 / 2
+    for m in range(2, 7):                                       # x^4 .. x^12 exact
+        assert abs(2 * np.sum(k[1:] ** (2 * m) * w[1:])) < 1e-9 * 6 ** (2 * m)
+    assert abs(2 * np.sum(k[1:] ** 14 * w[1:])) > 1.0          # order exactly 12
+    # Nyquist symbol per dimension
+    sym = w[0] + 2 * np.sum(w[1:] * np.cos(np.pi * k[1:]))
+    assert abs(sym - (-7.0729)) < 1e-3
+    # lower orders reduce to the textbook stencils
+    assert np.allclose(orc.fd_weights(1), [-2.0, 1.0])
+    assert np.allclose(orc.fd_weights(2), [-2.5, 4.0 / 3.0, -1.0 / 12.0])
+
+
+def test_laplacian_exact_on_polynomials(orc):
+    grid = (17, 15, 14, 0.3, np.array([-1.0, 0.4, -0.2]))
+    x, y, z = _coords(grid)
+    u = x ** 5 * y ** 3 + 2 * y ** 2 * z ** 4 - z ** 7 + x * y * z
+    lap = 20 * x ** 3 * y ** 3 + 6 * x ** 5 * y + 4 * z ** 4 + 24 * y ** 2 * z ** 2 - 42 * z ** 5
+    out = orc.laplacian(u, grid).reshape(14, 15, 17)
+    ref = lap.reshape(14, 15, 17)
+    inner = (slice(6, -6), slice(6, -6), slice(6, -6))
+    assert np.max(np.abs(out[inner] - ref[inner])) < 1e-8 * np.max(np.abs(ref))
+
+
+def _dense_laplacian(nx, ny, nz, h, w):
+    def d1(n):
+        L = np.zeros((n, n))
+        for i in range(n):
+            L[i, i] = w[0]
+            for k in range(1, len(w)):
+                if i + k < n:
+                    L[i, i + k] = w[k]
+                if i - k >= 0:
+                    L[i, i - k] = w[k]
+        return L / h ** 2
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    return (np.kron(np.kron(Iz, Iy), d1(nx)) + np.kron(np.kron(Iz, d1(ny)), Ix)
+            + np.kron(np.kron(d1(nz), Iy), Ix))
+
+
+def _gold_weights():
+    rows = [l.split() for l in open(os.path.join(GOLD, "fd12_weights.txt")) if not l.startswith("#")]
+    return np.array([int(a) / int(b) for _, a, b in rows])
+
+
+def test_laplacian_matches_kronecker_operator(orc):
+    nx, ny, nz, h = 9, 8, 7, 0.35
+    grid = (nx, ny, nz, h, np.zeros(3))
+    A = _dense_laplacian(nx, ny, nz, h, _gold_weights())
+    u = np.random.default_rng(0).normal(size=nx * ny * nz)
+    assert np.max(np.abs(orc.laplacian(u, grid) - A @ u)) < 1e-10 * np.max(np.abs(A @ u))
+
+
+# --------------------------------------------------------------------------
+# c-5: multipole boundary values and the Poisson solve (Sec. II.A)
+# --------------------------------------------------------------------------
+
+def _sph_multipole(rho, grid, Rpts, lmax=2):
+    """Exterior multipole potential from complex spherical harmonics:
+    V(R) = sum_lm 4pi/(2l+1) q_lm Y_lm(R^)/|R|^{l+1}, q_lm = sum rho r^l Y*_lm dV."""
+    from scipy.special import sph_harm_y
+    nx, ny, nz, h, o = grid
+    c = o + 0.5 * h * (np.array([nx, ny, nz]) - 1)
+    x, y, z = _coords(grid)
+    X, Y, Z = x - c[0], y - c[1], z - c[2]
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    th = np.arccos(np.where(r > 0, Z / np.where(r > 0, r, 1), 1.0))
+    ph = np.arctan2(Y, X)
+    out = np.zeros(len(Rpts))
+    Rr = np.linalg.norm(Rpts, axis=1)
+    Rth = np.arccos(Rpts[:, 2] / Rr)
+    Rph = np.arctan2(Rpts[:, 1], Rpts[:, 0])
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            q = np.sum(rho * r ** l * np.conj(sph_harm_y(l, m, th, ph))) * h ** 3
+            out += np.real(4 * np.pi / (2 * l + 1) * q * sph_harm_y(l, m, Rth, Rph) / Rr ** (l + 1))
+    return out
+
+
+def test_multipole_matches_spherical_harmonics(orc):
+    grid = _cube(12, 0.4)
+    x, y, z = _coords(grid)
+    rng = np.random.default_rng(3)
+    rho = np.exp(-((x - 0.5) ** 2 + (y + 0.3) ** 2 + 2 * (z - 0.2) ** 2)) * (1 + 0.3 * rng.random(x.size))
+    mom = orc.multipole_moments(rho, grid)
+    R = rng.normal(size=(20, 3)) * 4.0
+    R *= (4.0 + rng.random((20, 1))) / np.linalg.norm(R, axis=1, keepdims=True)
+    ours = np.array([orc.multipole_value(mom, r) for r in R])
+    ref = _sph_multipole(rho, grid, R)
+    assert np.max(np.abs(ours - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_multipole_truncation_error_is_octupole_sized(orc):
+    # A displaced compact charge: l<=2 expansion differs from the exact
+    # Q/|R-d| by O(Q d^3/R^4); without the quadrupole it is O(Q d^2/R^3).
+    grid = _cube(20, 0.25)
+    x, y, z = _coords(grid)
+    d = np.array([0.4, -0.3, 0.25])
+    s = 0.35
+    rho = np.exp(-((x - d[0]) ** 2 + (y - d[1]) ** 2 + (z - d[2]) ** 2) / (2 * s * s))
+    mom = orc.multipole_moments(rho, grid)
+    Q = mom[0]
+    dn = np.linalg.norm(d)
+    for u in (np.eye(3)[0], np.eye(3)[2], np.array([1.0, 1.0, -1.0]) / np.sqrt(3)):
+        errs = []
+        for Rn in (8.0, 16.0):
+            R = Rn * u
+            exact = Q / np.linalg.norm(R - d)
+            err = abs(orc.multipole_value(mom, R) - exact)
+            assert err < 1.5 * Q * dn ** 3 / (Rn - dn) ** 4
+            errs.append(err)
+        # the remainder falls like R^-4 (octupole), not R^-3 (quadrupole)
+        assert errs[0] / errs[1] > 12.0
+
+
+def _dense_poisson(rho, grid, w):
+    """Dense direct solve of the interior system with the ghost values taken
+    from the spherical-harmonic multipole (assembled here, not by the oracle)."""
+    nx, ny, nz, h, o = grid
+    c = o + 0.5 * h * (np.array([nx, ny, nz]) - 1)
+    A = -_dense_laplacian(nx, ny, nz, h, w)
+    b = 4 * np.pi * rho.copy()
+    ghosts, owners, wts = [], [], []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                g = (k * ny + j) * nx + i
+                for d in range(3):
+                    for m in range(1, 7):
+                        for sgn in (-1, 1):
+                            q = [i, j, k]
+                            q[d] += sgn * m
+                            if 0 <= q[d] < (nx, ny, nz)[d]:
+                                continue
+                            ghosts.append(o + h * np.array(q) - c)
+                            owners.append(g)
+                            wts.append(w[m] / h ** 2)
+    Vb = _sph_multipole(rho, grid, np.array(ghosts))
+    np.add.at(b, owners, np.array(wts) * Vb)
+    return np.linalg.solve(A, b)
+
+
+def test_poisson_matches_dense_direct_solve(orc):
+    grid = (9, 8, 10, 0.5, np.array([-2.0, -1.75, -2.25]))
+    x, y, z = _coords(grid)
+    rho = np.exp(-1.5 * ((x - 0.3) ** 2 + (y + 0.2) ** 2 + z ** 2)) * (1 + 0.5 * x * y)
+    V, it = orc.poisson(rho[None], grid, tol=1e-14)
+    assert it[0] > 0
+    ref = _dense_poisson(rho, grid, _gold_weights())
+    assert np.max(np.abs(V[0] - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_gaussian_hartree_converges_to_closed_form(orc):
+    gold = np.loadtxt(os.path.join(GOLD, "gaussian_closed_forms.txt"))
+    sigma, U_exact = gold[2, 0], gold[2, 1]          # sigma = 1
+    errs = []
+    for n, h in ((24, 0.7), (32, 0.5), (48, 1.0 / 3.0)):
+        grid = _cube(n, h)
+        x, y, z = _coords(grid)
+        r2 = x * x + y * y + z * z
+        rho = (2 * np.pi * sigma ** 2) ** -1.5 * np.exp(-r2 / (2 * sigma ** 2))
+        V, _ = orc.poisson(rho[None], grid, tol=1e-12)
+        U = 0.5 * h ** 3 * np.sum(rho * V[0])
+        errs.append(abs(U - U_exact))
+        r = np.sqrt(r2)
+        far = r > 4.0
+        from scipy.special import erf
+        Vex = erf(r[far] / (np.sqrt(2) * sigma)) / r[far]
+        if n == 48:
+            assert np.max(np.abs(V[0][far] - Vex)) < 1e-5
+    assert errs[-1] < 2e-6
+    assert errs[0] > errs[1] > errs[2]
+
+
+# --------------------------------------------------------------------------
+# c-1: cubic interpolation at FODs (Sec. II.B)
+# --------------------------------------------------------------------------
+
+def test_interp_exact_on_tricubic_polynomials(orc):
+    grid = (10, 9, 8, 0.4, np.array([-1.8, -1.6, -1.4]))
+    x, y, z = _coords(grid)
+    f = lambda x, y, z: (x ** 3 - 2 * x) * (y ** 2 + y ** 3) * (1 + z - z ** 3)
+    df = lambda x, y, z: np.array([(3 * x ** 2 - 2) * (y ** 2 + y ** 3) * (1 + z - z ** 3),
+                                   (x ** 3 - 2 * x) * (2 * y + 3 * y ** 2) * (1 + z - z ** 3),
+                                   (x ** 3 - 2 * x) * (y ** 2 + y ** 3) * (1 - 3 * z ** 2)])
+    u = f(x, y, z)
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        a = np.array([-0.5, -0.4, -0.3]) + rng.random(3) * 1.0
+        val, grad = orc.interp(u[None], grid, a)
+        assert abs(val[0] - f(*a)) < 1e-11
+        assert np.max(np.abs(grad[0] - df(*a))) < 1e-10
+
+
+def test_interp_brute_force_lagrange_and_nodes(orc):
+    grid = (6, 6, 6, 0.5, np.zeros(3))
+    u = np.random.default_rng(2).normal(size=216)
+    U3 = u.reshape(6, 6, 6)
+    a = np.array([1.23, 0.71, 1.9])
+    # independent: 1-D Lagrange polynomials through 4 nodes via polyfit
+    idx = [int(np.floor(a[d] / 0.5)) for d in range(3)]
+    def weights(d):
+        nodes = np.arange(idx[d] - 1, idx[d] + 3)
+        ws = []
+        for q in nodes:
+            y = (nodes == q).astype(float)
+            ws.append(np.polyval(np.polyfit(nodes * 0.5, y, 3), a[d]))
+        return nodes, ws
+    (nx_, wx), (ny_, wy), (nz_, wz) = weights(0), weights(1), weights(2)
+    ref = 0.0
+    for c, kz in zip(wz, nz_):
+        for b, jy in zip(wy, ny_):
+            for e, ix in zip(wx, nx_):
+                if 0 <= ix < 6 and 0 <= jy < 6 and 0 <= kz < 6:
+                    ref += c * b * e * U3[kz, jy, ix]
+    val, _ = orc.interp(u[None], grid, a)
+    assert abs(val[0] - ref) < 1e-12
+    node = np.array([1.0, 1.5, 2.0])
+    val, _ = orc.interp(u[None], grid, node)
+    assert abs(val[0] - U3[4, 3, 2]) < 1e-14
+
+
+def test_interp_scatter_is_adjoint(orc):
+    grid = (7, 8, 6, 0.3, np.array([0.1, -0.2, 0.0]))
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=7 * 8 * 6)
+    a = np.array([0.05, 0.0, 0.2])                # cell touches the boundary
+    out = np.zeros_like(u)
+    orc.interp_scatter(grid, a, 1.7, out)
+    val, _ = orc.interp(u[None], grid, a)
+    assert abs(out @ u - 1.7 * val[0]) < 1e-12
+
+
+def test_grad_central_scheme(orc):
+    grid = (8, 7, 6, 0.25, np.zeros(3))
+    x, y, z = _coords(grid)
+    u = 3 * x + x * x - y * z
+    g = orc.grad_central(u, grid).reshape(3, 6, 7, 8)
+    # central differences are exact on quadratics at inner points
+    gx = (3 + 2 * x).reshape(6, 7, 8)
+    assert np.max(np.abs(g[0][:, :, 1:-1] - gx[:, :, 1:-1])) < 1e-12
+    # one-sided at the first point: (u_1 - u_0)/h = 3 + 2 x_0 + h
+    assert np.max(np.abs(g[0][:, :, 0] - (3 + 2 * x.reshape(6, 7, 8)[:, :, 0] + 0.25))) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# c-6: fully polarised LSDA (Eq. 1 with E_xc[rho_i, 0]; Sec. III)
+# --------------------------------------------------------------------------
+
+def test_slater_exchange_of_gaussian_closed_form(orc):
+    gold = np.loadtxt(os.path.join(GOLD, "gaussian_closed_forms.txt"))
+    for sigma, _, Ex in gold:
+        n, h = 64, sigma / 5.0
+        grid = _cube(n, h)
+        x, y, z = _coords(grid)
+        rho = (2 * np.pi * sigma ** 2) ** -1.5 * np.exp(-(x * x + y * y + z * z) / (2 * sigma ** 2))
+        # exchange part alone: eps_x = -(3/4)(6 rho/pi)^{1/3}
+        eps, _ = orc.lsda_pol(rho)
+        ec = np.array([orc.pw92_ferro((3 / (4 * np.pi * r)) ** (1 / 3))[0] if r > 1e-30 else 0.0 for r in rho])
+        Ex_num = h ** 3 * np.sum(rho * (eps - ec))
+        assert abs(Ex_num - Ex) < 1e-6 * abs(Ex)
+
+
+def test_lsda_potential_is_density_derivative(orc):
+    n = np.logspace(-6, 2, 40)
+    _, v = orc.lsda_pol(n)
+    d = 1e-6 * n
+    ep, _ = orc.lsda_pol(n + d)
+    em, _ = orc.lsda_pol(n - d)
+    fd = ((n + d) * ep - (n - d) * em) / (2 * d)
+    assert np.max(np.abs(fd - v) / np.abs(v)) < 1e-7
+
+
+def test_pw92_ferro_limits(orc):
+    A, b1, b2 = 0.015545, 14.1189, 6.1977
+    # the PW92 fit ties beta_2 to A and beta_1: beta_2 = 2 A beta_1^2
+    assert abs(2 * A * b1 ** 2 - b2) < 1e-3
+    # high density: d eps_c / d ln rs -> A
+    for rs in (1e-6, 1e-8):
+        _, dec = orc.pw92_ferro(rs)
+        assert abs(rs * dec - A) < 3e-3 * A
+    # values decrease in magnitude with rs, correlation negative
+    e1, _ = orc.pw92_ferro(1.0)
+    e5, _ = orc.pw92_ferro(5.0)
+    assert e1 < e5 < 0
+    # below rho_min everything vanishes
+    eps, v = orc.lsda_pol(np.array([1e-31, 0.0]), rho_min=1e-30)
+    assert np.all(eps == 0) and np.all(v == 0)
+
+
+# --------------------------------------------------------------------------
+# c-2..c-4: Fermi orbitals and Loewdin (Eqs. 6-8; Sec. I.B)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_sys():
+    return synth.make_system(20, 0.45, 2, [4], seed=11)
+
+
+def test_flos_orthonormal_and_span(orc, small_sys):
+    s = small_sys
+    fl = orc.build_flos(s.psi[0], s.fods[0], s.grid)
+    dV = s.h ** 3
+    assert np.max(np.abs(dV * fl["phi"] @ fl["phi"].T - np.eye(4))) < 1e-12
+    assert np.max(np.abs(np.sum(fl["phi"] ** 2, 0) - np.sum(s.psi[0] ** 2, 0))) < 1e-12 * np.max(s.psi[0] ** 2)
+    # FOs are normalised when psi is orthonormal: diag(S) = 1
+    assert np.max(np.abs(np.diag(fl["S"]) - 1)) < 1e-12
+    # S = T (dV psi psi^T) T^T
+    M = dV * s.psi[0] @ s.psi[0].T
+    assert np.max(np.abs(fl["S"] - fl["T"] @ M @ fl["T"].T)) < 1e-12
+
+
+def test_single_orbital_flo_is_signed_psi(orc):
+    s = synth.make_system(18, 0.5, 1, [1], seed=3)
+    fl = orc.build_flos(s.psi[0], s.fods[0], s.grid)
+    sgn = np.sign(fl["vals"][0, 0])
+    assert np.max(np.abs(fl["phi"][0] - sgn * s.psi[0][0])) < 1e-12
+
+
+def test_coincident_fods_are_rejected(orc, small_sys):
+    s = small_sys
+    f = s.fods[0].copy()
+    f[1] = f[0]
+    with pytest.raises(ValueError):
+        orc.build_flos(s.psi[0], f, s.grid)
+
+
+def test_esic_unitary_invariance(orc, small_sys):
+    s = small_sys
+    E0 = orc.sic_forward(s.psi, s.fods, s.grid, tol=1e-13)["E_sic"]
+    Qr, _ = np.linalg.qr(np.random.default_rng(9).normal(size=(4, 4)))
+    E1 = orc.sic_forward([Qr @ s.psi[0]], s.fods, s.grid, tol=1e-13)["E_sic"]
+    assert abs(E1 - E0) < 1e-11 * abs(E0)
+
+
+# --------------------------------------------------------------------------
+# c-7: energy and averaged potential (Eqs. 1, 5, 13)
+# --------------------------------------------------------------------------
+
+def test_one_electron_gaussian_energy_and_potential(orc):
+    gold = np.loadtxt(os.path.join(GOLD, "gaussian_closed_forms.txt"))
+    sigma, U_ex, Ex_ex = gold[0]
+    n, h = 48, 0.2
+    grid = _cube(n, h)
+    x, y, z = _coords(grid)
+    rho = (2 * np.pi * sigma ** 2) ** -1.5 * np.exp(-(x * x + y * y + z * z) / (2 * sigma ** 2))
+    psi = np.sqrt(rho)
+    psi /= np.sqrt(h ** 3 * np.sum(psi ** 2))
+    fod = np.array([[0.13, -0.07, 0.21]])
+    out = orc.sic_forward([psi[None]], [fod], grid, scale=0.5)
+    b = out["blocks"][0]
+    # E_SIC = -(U + E_x + E_c); compare U and E_x with the closed forms
+    assert abs(b["U"][0] - U_ex) < 1e-6
+    ec = np.array([orc.pw92_ferro((3 / (4 * np.pi * r)) ** (1 / 3))[0] if r > 1e-30 else 0 for r in b["rho"][0]])
+    Ec = h ** 3 * np.sum(b["rho"][0] * ec)
+    assert abs(b["Exc"][0] - Ec - Ex_ex) < 1e-5
+    assert abs(out["E_sic"] + b["U"][0] + b["Exc"][0]) < 1e-15
+    # one orbital: V_avg = s * V^SIC wherever the density is above the cutoff
+    m = b["rho_s"] > 1e-12
+    assert np.max(np.abs(b["Vavg"][m] - 0.5 * b["Vsic"][0][m])) < 1e-12
+    # and the SIC energy does not depend on where the single FOD sits
+    out2 = orc.sic_forward([psi[None]], [fod + 0.3], grid, scale=0.5)
+    assert abs(out2["E_sic"] - out["E_sic"]) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# c-8: backward (Eqs. 9-11)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def fd_sys():
+    return synth.make_system(22, 0.42, 2, [3], seed=5)
+
+
+def test_fod_gradient_two_routes_agree(orc, fd_sys):
+    s = fd_sys
+    f = orc.sic_forward(s.psi, s.fods, s.grid, tol=1e-13)
+    _, g = orc.sic_backward(f, s.grid)
+    p = orc.pederson_fod_gradient(f, s.grid)
+    assert np.max(np.abs(g[0] - p[0])) < 1e-10 * np.max(np.abs(p[0]))
+
+
+def test_fod_gradient_matches_central_differences(orc, fd_sys):
+    s = fd_sys
+    f = orc.sic_forward(s.psi, s.fods, s.grid, tol=1e-13)
+    _, g = orc.sic_backward(f, s.grid, adjoint="exact", tol=1e-13)
+    eps = 1e-4
+    for i, d in ((0, 0), (1, 2), (2, 1)):
+        fp = s.fods[0].copy(); fp[i, d] += eps
+        fm = s.fods[0].copy(); fm[i, d] -= eps
+        Ep = orc.sic_forward(s.psi, [fp], s.grid, tol=1e-13)["E_sic"]
+        Em = orc.sic_forward(s.psi, [fm], s.grid, tol=1e-13)["E_sic"]
+        assert abs((Ep - Em) / (2 * eps) - g[0][i, d]) < 1e-6
+
+
+def test_psi_gradient_matches_directional_difference(orc, fd_sys):
+    s = fd_sys
+    f = orc.sic_forward(s.psi, s.fods, s.grid, tol=1e-13)
+    dpsi, _ = orc.sic_backward(f, s.grid, adjoint="exact", tol=1e-13)
+    D = np.random.default_rng(7).normal(size=s.psi[0].shape) * np.abs(s.psi[0]).max()
+    e = 1e-5
+    Ep = orc.sic_forward([s.psi[0] + e * D], s.fods, s.grid, tol=1e-13)["E_sic"]
+    Em = orc.sic_forward([s.psi[0] - e * D], s.fods, s.grid, tol=1e-13)["E_sic"]
+    ref = (Ep - Em) / (2 * e)
+    assert abs(ref - np.sum(dpsi[0] * D)) < 1e-6 * max(1.0, abs(ref))
+
+
+def test_single_electron_fod_gradient_vanishes(orc):
+    s = synth.make_system(18, 0.5, 1, [1], seed=8)
+    f = orc.sic_forward(s.psi, s.fods, s.grid)
+    _, g = orc.sic_backward(f, s.grid)
+    assert np.max(np.abs(g[0])) < 1e-13
+
+
+def test_paper_central_gradient_converges_to_exact(orc):
+    # The paper's scheme (central-difference grid gradient, then cubic
+    # interpolation) approximates the interpolant's derivative to O(h^2):
+    # halving h on the same box shrinks the gap about fourfold.
+    gaps = []
+    for n, h in ((36, 0.3), (72, 0.15)):
+        s = synth.make_system(n, h, 2, [3], seed=21)
+        f = orc.sic_forward(s.psi, s.fods, s.grid, tol=1e-11)
+        _, g = orc.sic_backward(f, s.grid)
+        _, gc = orc.sic_backward(f, s.grid, grad_mode="paper_central")
+        gaps.append(np.max(np.abs(g[0] - gc[0])))
+    assert gaps[1] < gaps[0] / 3.0
