@@ -1,0 +1,180 @@
+/*
+ * flosic.h -- C ABI of the GB300 (sm_103a) real-space FLO-SIC orbital-SIC step.
+ *
+ * Method: Diaz, Suryanarayana, Xu, Baruah, Pask, Zope, "Implementation of
+ * Perdew-Zunger self-interaction correction in real space using
+ * Fermi-Loewdin orbitals" (arXiv 2108.01186).  One step takes Kohn-Sham
+ * orbitals psi on a uniform grid and Fermi-orbital descriptor (FOD)
+ * positions a_i, and returns the PZ-SIC energy (Eq. 1), the scaled averaged
+ * SIC potential (Eq. 13) and, in reverse mode, dE_SIC/dpsi and the FOD
+ * gradient dE_SIC/da (Eqs. 9-11).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller, except the
+ *    options/system descriptors and the pointers marked "host".
+ *  - A batch holds nsys independent systems.  System s has an nx*ny*nz
+ *    interior grid with spacing h (bohr); point (i,j,k) sits at
+ *    origin + h*(i,j,k) and has flat index (k*ny + j)*nx + i (x fastest).
+ *    G = nx*ny*nz.  Orbitals vanish outside the interior (zero Dirichlet).
+ *  - A "spin block" is one spin of one system with N = norb[spin] orbitals.
+ *    Blocks are ordered system-major, then spin.  Orbital-sized arrays
+ *    (psi, phi, V, dE_dpsi) are the blocks' [N][G] float64 arrays packed
+ *    back to back; FOD arrays are [N][3] float64 per block packed the same
+ *    way; N x N matrices (S, S_mhalf) are row-major per block, packed;
+ *    per-orbital scalars (U, Exc, iters, conv_flags) are packed per block;
+ *    V_avg is one [G] array per block; E_sic and gE hold one value per
+ *    system.  flosic_layout() returns every packed size.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, passed as
+ *    void*), except that calls whose result can fail on the device
+ *    (flosic_build_flos: ILLCOND/NONFINITE, flosic_orbital_poisson: NOCONV)
+ *    wait for the stream before they return the status.
+ *  - Every call returns an int status (flosic_status); nothing throws across
+ *    the ABI.  flosic_last_error() returns a message for the last failure.
+ *  - The context owns its device workspace (allocated in flosic_create,
+ *    freed in flosic_destroy).  A context must not be used by two streams
+ *    at once.
+ */
+#ifndef FLOSIC_H
+#define FLOSIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FLOSIC_OK = 0,
+    FLOSIC_ERR_ARG = 1,        /* bad argument or descriptor */
+    FLOSIC_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    FLOSIC_ERR_ILLCOND = 3,    /* FO overlap near singular (FODs too close) */
+    FLOSIC_ERR_NOCONV = 4,     /* a Poisson solve hit max_iter */
+    FLOSIC_ERR_NONFINITE = 5   /* NaN/Inf met in an input or result */
+} flosic_status;
+
+enum { FLOSIC_FP64 = 0, FLOSIC_MIXED = 1 };                 /* precision */
+enum { FLOSIC_GRAD_INTERP = 0, FLOSIC_GRAD_PAPER = 1 };     /* fod_grad_mode */
+enum { FLOSIC_ADJ_REUSE_V = 0, FLOSIC_ADJ_EXACT = 1 };      /* adjoint_mode */
+enum { FLOSIC_PC_NONE = 0, FLOSIC_PC_MG = 1 };              /* preconditioner */
+
+typedef struct {
+    int nx, ny, nz;       /* interior grid points per direction (>= 1) */
+    double h;             /* grid spacing, bohr (> 0) */
+    double origin[3];     /* position of point (0,0,0), bohr */
+    int nspin;            /* 1 or 2 */
+    int norb[2];          /* occupied orbitals = FODs per spin (>= 1) */
+} flosic_system;
+
+typedef struct {
+    int precision;        /* FLOSIC_FP64: every step in float64.
+                             FLOSIC_MIXED: Poisson CG in float32 with float64
+                             residual refinement; the rest float64. */
+    double cg_tol;        /* relative residual ||b - A V|| / ||b|| per solve */
+    int max_iter;         /* CG iteration cap per solve (all refinement
+                             sweeps together) */
+    int fod_grad_mode;    /* grad psi at the FODs: FLOSIC_GRAD_INTERP = exact
+                             derivative of the cubic interpolant (consistent
+                             with the energy); FLOSIC_GRAD_PAPER = central-
+                             difference grid gradient then cubic
+                             interpolation (Sec. II.B) */
+    int adjoint_mode;     /* dU/drho: FLOSIC_ADJ_REUSE_V uses V itself;
+                             FLOSIC_ADJ_EXACT adds the transpose of the
+                             multipole boundary map (one extra zero-boundary
+                             solve per orbital) */
+    double rho_min;       /* density cutoff of xc and of V_avg */
+    double illcond_tol;   /* ILLCOND when lambda_min(S) < tol*lambda_max(S) */
+    int preconditioner;   /* FLOSIC_PC_NONE or FLOSIC_PC_MG (multigrid
+                             V-cycle on the 7-point Laplacian) */
+} flosic_options;
+
+typedef struct flosic_ctx flosic_ctx;
+
+/* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
+ * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG.
+ * Returns FLOSIC_ERR_ARG if opt is NULL. */
+int flosic_default_options(flosic_options* opt);
+
+/* Creates a context for nsys systems (host array sys[nsys]) and allocates
+ * its device workspace on the current device.  opt may be NULL (defaults).
+ * Errors: ARG (bad descriptor), CUDA (allocation failed).  On error *ctx is
+ * NULL and the message is available from flosic_last_error(NULL). */
+int flosic_create(flosic_ctx** ctx, const flosic_system* sys, int nsys,
+                  const flosic_options* opt);
+
+/* Frees the context and its workspace.  NULL is a no-op. */
+int flosic_destroy(flosic_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failed
+ * flosic_create when ctx is NULL).  Owned by the library. */
+const char* flosic_last_error(const flosic_ctx* ctx);
+
+/* Packed sizes (host array out[6]): [0] orbitals in the batch, [1] elements
+ * of an orbital-sized array (sum N*G), [2] elements of V_avg (sum of G over
+ * blocks), [3] elements of the N x N matrix arrays (sum N*N), [4] spin
+ * blocks, [5] systems. */
+int flosic_layout(const flosic_ctx* ctx, int64_t* out);
+
+/* Steps a1-a5 (Sec. II.B, Eqs. 6-8, Loewdin of Sec. I.B):
+ *   psi_a(a_i), grad psi_a(a_i) by tricubic Lagrange interpolation,
+ *   rho(a_i) = sum_a psi_a(a_i)^2, T_ia = psi_a(a_i)/sqrt(rho(a_i)),
+ *   F = T psi, S = dV F F^T (summed over the grid), S = U L U^T,
+ *   S^{-1/2} = U L^{-1/2} U^T, phi = S^{-1/2} F.
+ * In:  psi [sum N*G] float64, fods [sum N*3] float64 (bohr).
+ * Out: phi [sum N*G] float64 (the FLOs), S and S_mhalf [sum N*N] float64.
+ *      S and S_mhalf may be NULL (not returned).
+ * The context keeps T, the eigen-pairs and the interpolation data for
+ * flosic_sic_backward.  Errors: ARG, CUDA, ILLCOND (some block's overlap is
+ * near singular; phi is then undefined), NONFINITE (NaN/Inf in psi or at a
+ * FOD).  Waits for `stream` before returning. */
+int flosic_build_flos(flosic_ctx* ctx, const double* psi, const double* fods,
+                      double* phi, double* S, double* S_mhalf, void* stream);
+
+/* Steps a6-a7 (Sec. II.A): per orbital, -Delta_h V_i = 4 pi phi_i^2 with the
+ * 12th-order centred Laplacian and Dirichlet values from the l <= 2
+ * multipole expansion of phi_i^2 about the box centre on the 6-layer ghost
+ * shell; conjugate gradients to ||b - A V|| <= cg_tol ||b||.
+ * In:  phi [sum N*G] float64.  In/out: V [sum N*G] float64 (in: warm start
+ * if warm_start != 0, ignored otherwise; out: the potentials).
+ * Out (may be NULL): iters [orbitals] int32 (CG iterations per orbital, all
+ * precisions summed), conv_flags [orbitals] int32 (1 = converged).
+ * Errors: ARG, CUDA, NOCONV (some orbital hit max_iter; V holds the last
+ * iterate).  Waits for `stream` before returning. */
+int flosic_orbital_poisson(flosic_ctx* ctx, const double* phi, double* V,
+                           int warm_start, int* iters, int* conv_flags,
+                           void* stream);
+
+/* Steps a8-a9 (Eq. 1, the bracketed term of Eq. 5, Eq. 13):
+ *   rho_i = phi_i^2, U_i = (dV/2) sum rho_i V_i,
+ *   E_xc,i = dV sum rho_i eps_xc(rho_i, 0) (LSDA exchange + PW92 at zeta=1),
+ *   E_sic = -sum_{i,spin} (U_i + E_xc,i) per system,
+ *   V_i^SIC = -(V_i + v_xc(rho_i)),
+ *   V_avg = scale * sum_i rho_i V_i^SIC / rho_spin with rho_spin =
+ *   sum_a psi_a^2 (0 where rho_spin < rho_min).
+ * In:  psi, phi, V [sum N*G] float64; scale (host scalar).
+ * Out (any may be NULL): U, Exc [orbitals], E_sic [nsys], V_avg [sum G].
+ * Errors: ARG, CUDA. */
+int flosic_sic_energy_potential(flosic_ctx* ctx, const double* psi,
+                                const double* phi, const double* V, double scale,
+                                double* U, double* Exc, double* E_sic,
+                                double* V_avg, void* stream);
+
+/* Step a10 (Eqs. 9-11, by reverse mode): gradients of sum_s gE[s]*E_sic[s]
+ * with respect to the grid values of psi and to the FOD positions.  Uses the
+ * data kept by the last flosic_build_flos on this context; psi, fods, phi
+ * and V must be the arrays of that forward step.
+ * In:  psi, phi, V [sum N*G], fods [sum N*3], gE [nsys] float64.
+ * Out: dE_dpsi [sum N*G] float64 (partial derivative with respect to each
+ *      grid value, i.e. the functional derivative times dV) and dE_dfod
+ *      [sum N*3] float64 (hartree/bohr); either may be NULL.
+ * Errors: ARG (no forward step recorded), CUDA, NOCONV (adjoint_mode EXACT
+ * and an extra solve hit max_iter). */
+int flosic_sic_backward(flosic_ctx* ctx, const double* psi, const double* fods,
+                        const double* phi, const double* V, const double* gE,
+                        double* dE_dpsi, double* dE_dfod, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOSIC_H */

@@ -1,0 +1,317 @@
+// C ABI of the FLO-SIC step: context, workspace and the four step calls.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+using namespace flosic;
+
+namespace {
+std::string g_create_error;   // message of the last failed flosic_create
+
+int fail(flosic_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <class T>
+cudaError_t alloc(flosic_ctx* c, T** p, long long n) {
+    *p = nullptr;
+    if (n <= 0) n = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (size_t)n);
+    if (e == cudaSuccess) {
+        c->allocations.push_back(q);
+        *p = (T*)q;
+    }
+    return e;
+}
+
+void release(flosic_ctx* c) {
+    for (void* p : c->allocations) cudaFree(p);
+    c->allocations.clear();
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    c->h_pinned = nullptr;
+}
+
+int validate_options(const flosic_options& o, std::string& why) {
+    if (o.precision != FLOSIC_FP64 && o.precision != FLOSIC_MIXED) why = "precision must be FP64 or MIXED";
+    else if (!(o.cg_tol > 0.0) || !(o.cg_tol < 1.0)) why = "cg_tol must be in (0, 1)";
+    else if (o.max_iter < 1) why = "max_iter must be >= 1";
+    else if (o.fod_grad_mode != FLOSIC_GRAD_INTERP && o.fod_grad_mode != FLOSIC_GRAD_PAPER) why = "bad fod_grad_mode";
+    else if (o.adjoint_mode != FLOSIC_ADJ_REUSE_V && o.adjoint_mode != FLOSIC_ADJ_EXACT) why = "bad adjoint_mode";
+    else if (!(o.rho_min >= 0.0)) why = "rho_min must be >= 0";
+    else if (!(o.illcond_tol >= 0.0) || !(o.illcond_tol < 1.0)) why = "illcond_tol must be in [0, 1)";
+    else if (o.preconditioner != FLOSIC_PC_NONE && o.preconditioner != FLOSIC_PC_MG) why = "bad preconditioner";
+    else return 0;
+    return 1;
+}
+
+// Waits for the stream and returns the device status words.
+int read_status(flosic_ctx* c, cudaStream_t s, int* st4) {
+    int rc = check_cuda(c, cudaGetLastError(), "kernel launch");
+    if (rc) return rc;
+    rc = check_cuda(c, cudaMemcpyAsync(c->h_pinned, c->ws.status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s),
+                    "cudaMemcpyAsync(status)");
+    if (rc) return rc;
+    rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (rc) return rc;
+    for (int k = 0; k < 4; ++k) st4[k] = c->h_pinned[k];
+    return FLOSIC_OK;
+}
+}  // namespace
+
+namespace flosic {
+int check_cuda(flosic_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return FLOSIC_OK;
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return FLOSIC_ERR_CUDA;
+}
+}  // namespace flosic
+
+extern "C" {
+
+int flosic_default_options(flosic_options* opt) {
+    if (!opt) return FLOSIC_ERR_ARG;
+    opt->precision = FLOSIC_MIXED;
+    opt->cg_tol = 1e-10;
+    opt->max_iter = 20000;
+    opt->fod_grad_mode = FLOSIC_GRAD_INTERP;
+    opt->adjoint_mode = FLOSIC_ADJ_REUSE_V;
+    opt->rho_min = 1e-30;
+    opt->illcond_tol = 1e-10;
+    opt->preconditioner = FLOSIC_PC_MG;
+    return FLOSIC_OK;
+}
+
+const char* flosic_last_error(const flosic_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const flosic_options* opt) {
+    if (!out) { g_create_error = "ctx pointer is NULL"; return FLOSIC_ERR_ARG; }
+    *out = nullptr;
+    if (!sys || nsys < 1) { g_create_error = "need at least one system"; return FLOSIC_ERR_ARG; }
+    flosic_options o;
+    if (opt) o = *opt; else flosic_default_options(&o);
+    std::string why;
+    if (validate_options(o, why)) { g_create_error = why; return FLOSIC_ERR_ARG; }
+    for (int s = 0; s < nsys; ++s) {
+        const flosic_system& y = sys[s];
+        char buf[160];
+        if (y.nx < 1 || y.ny < 1 || y.nz < 1 || !(y.h > 0.0) || !std::isfinite(y.h) ||
+            !std::isfinite(y.origin[0]) || !std::isfinite(y.origin[1]) || !std::isfinite(y.origin[2])) {
+            snprintf(buf, sizeof buf, "system %d: bad grid", s);
+            g_create_error = buf;
+            return FLOSIC_ERR_ARG;
+        }
+        if (y.nspin != 1 && y.nspin != 2) {
+            snprintf(buf, sizeof buf, "system %d: nspin must be 1 or 2", s);
+            g_create_error = buf;
+            return FLOSIC_ERR_ARG;
+        }
+        for (int sp = 0; sp < y.nspin; ++sp)
+            if (y.norb[sp] < 1 || y.norb[sp] > kMaxN) {
+                snprintf(buf, sizeof buf, "system %d spin %d: norb must be in [1, %d]", s, sp, kMaxN);
+                g_create_error = buf;
+                return FLOSIC_ERR_ARG;
+            }
+    }
+    flosic_ctx* c = new (std::nothrow) flosic_ctx();
+    if (!c) { g_create_error = "out of host memory"; return FLOSIC_ERR_ARG; }
+    c->opt = o;
+    c->sys.assign(sys, sys + nsys);
+    // spin blocks, packed offsets, chunk table
+    long long off = 0, moff = 0, voff = 0, fod = 0, chunk = 0;
+    int orb = 0;
+    std::vector<int> sys_orb0(nsys + 1, 0);
+    for (int s = 0; s < nsys; ++s) {
+        const flosic_system& y = sys[s];
+        sys_orb0[s] = orb;
+        for (int sp = 0; sp < y.nspin; ++sp) {
+            BlkDesc b{};
+            b.nx = y.nx; b.ny = y.ny; b.nz = y.nz; b.N = y.norb[sp];
+            b.h = y.h; b.dV = y.h * y.h * y.h;
+            b.ox = y.origin[0]; b.oy = y.origin[1]; b.oz = y.origin[2];
+            b.cx = y.origin[0] + 0.5 * y.h * (y.nx - 1);
+            b.cy = y.origin[1] + 0.5 * y.h * (y.ny - 1);
+            b.cz = y.origin[2] + 0.5 * y.h * (y.nz - 1);
+            b.G = (long long)y.nx * y.ny * y.nz;
+            b.off = off; b.moff = moff; b.voff = voff; b.fod_off = fod;
+            b.orb0 = orb; b.sys = s; b.spin = sp;
+            b.nchunk = (int)((b.G + kChunk - 1) / kChunk);
+            b.chunk0 = chunk;
+            c->blk.push_back(b);
+            for (int i = 0; i < b.N; ++i) c->h_orb_blk.push_back((int)c->blk.size() - 1);
+            off += b.N * b.G; moff += (long long)b.N * b.N; voff += b.G; fod += b.N;
+            chunk += (long long)b.N * b.nchunk; orb += b.N;
+        }
+    }
+    sys_orb0[nsys] = orb;
+    c->nblk = (int)c->blk.size();
+    c->norb = orb;
+    c->orb_elems = off;
+    c->vavg_elems = voff;
+    c->mat_elems = moff;
+    c->nchunk_total = chunk;
+    int kp = (608 + c->nblk - 1) / c->nblk;
+    c->kparts = kp < 1 ? 1 : (kp > 1024 ? 1024 : kp);
+    std::vector<int> chunk_orb((size_t)chunk);
+    for (const BlkDesc& b : c->blk)
+        for (int i = 0; i < b.N; ++i)
+            for (int k = 0; k < b.nchunk; ++k) chunk_orb[(size_t)(b.chunk0 + (long long)i * b.nchunk + k)] = b.orb0 + i;
+
+    Workspace& w = c->ws;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, long long n) { if (e == cudaSuccess) e = alloc(c, p, n); };
+    A(&c->d_blk, c->nblk);
+    A(&c->d_orb_blk, c->norb);
+    A(&c->d_chunk_orb, chunk);
+    A(&c->d_sys_orb0, nsys + 1);
+    const long long me = moff;
+    w.mat_elems = me;
+    A(&w.vals, me); A(&w.grads, 3 * me); A(&w.rho_a, orb); A(&w.T, me); A(&w.M, me);
+    A(&w.S, me); A(&w.Q, me); A(&w.C, me); A(&w.U, me); A(&w.lam, orb); A(&w.P, me);
+    A(&w.vbar, me); A(&w.tmp, 4 * me); A(&w.E2, 2 * me);
+    A(&w.mat_part, (long long)c->kparts * me);
+    A(&w.mom, 10LL * orb); A(&w.mom_part, 10 * chunk);
+    A(&w.e_part, 2 * chunk); A(&w.e_orb, 2LL * orb);
+    A(&w.status, 4);
+    A(&w.b64, off); A(&w.r64, off);
+    if (o.precision == FLOSIC_FP64) {
+        A(&w.p64, off); A(&w.q64, off);
+    } else {
+        A(&w.d32, off); A(&w.r32, off); A(&w.p32, off); A(&w.q32, off);
+    }
+    if (o.adjoint_mode == FLOSIC_ADJ_EXACT) A(&w.veff, off);
+    CgState& g = w.cg;
+    A(&g.rr, orb); A(&g.pq, orb); A(&g.bb, orb); A(&g.thr, orb); A(&g.beta, orb);
+    A(&g.part, chunk); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
+    A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_orb_blk, c->h_orb_blk.data(), sizeof(int) * c->norb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
+    if (e == cudaSuccess) e = upload_stencil_constants();
+    if (e == cudaSuccess) {
+        int nmax = 0;
+        for (const auto& b : c->blk) nmax = b.N > nmax ? b.N : nmax;
+        e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * nmax * nmax));
+    }
+    if (e != cudaSuccess) {
+        g_create_error = std::string("workspace set-up: ") + cudaGetErrorString(e);
+        release(c);
+        delete c;
+        return FLOSIC_ERR_CUDA;
+    }
+    *out = c;
+    return FLOSIC_OK;
+}
+
+int flosic_destroy(flosic_ctx* ctx) {
+    if (!ctx) return FLOSIC_OK;
+    release(ctx);
+    delete ctx;
+    return FLOSIC_OK;
+}
+
+int flosic_layout(const flosic_ctx* c, int64_t* out) {
+    if (!c || !out) return FLOSIC_ERR_ARG;
+    out[0] = c->norb;
+    out[1] = c->orb_elems;
+    out[2] = c->vavg_elems;
+    out[3] = c->mat_elems;
+    out[4] = c->nblk;
+    out[5] = (int64_t)c->sys.size();
+    return FLOSIC_OK;
+}
+
+int flosic_build_flos(flosic_ctx* c, const double* psi, const double* fods, double* phi, double* S,
+                      double* S_mhalf, void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!psi || !fods || !phi) return fail(c, FLOSIC_ERR_ARG, "psi, fods and phi are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->have_forward = false;
+    int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
+    if (rc) return rc;
+    launch_interp_fod(c, psi, fods, s);
+    launch_gram(c, psi, s);
+    launch_lowdin(c, S, S_mhalf, s);
+    launch_flo_apply(c, psi, phi, s);
+    int st[4];
+    rc = read_status(c, s, st);
+    if (rc) return rc;
+    if (st[0]) return fail(c, FLOSIC_ERR_NONFINITE, "non-finite value in psi or at a FOD");
+    if (st[2]) return fail(c, FLOSIC_ERR_ILLCOND, "Fermi-orbital overlap is near singular (FODs too close?)");
+    c->have_forward = true;
+    return FLOSIC_OK;
+}
+
+int flosic_orbital_poisson(flosic_ctx* c, const double* phi, double* V, int warm_start, int* iters,
+                           int* conv_flags, void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!phi || !V) return fail(c, FLOSIC_ERR_ARG, "phi and V are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
+    if (rc) return rc;
+    launch_moments(c, phi, true, s);
+    launch_rhs(c, phi, true, c->ws.b64, s);
+    rc = run_poisson(c, c->ws.b64, V, warm_start != 0, s);
+    if (rc) return rc;
+    finish_poisson(c, iters, conv_flags, s);
+    int st[4];
+    rc = read_status(c, s, st);
+    if (rc) return rc;
+    if (st[1]) return fail(c, FLOSIC_ERR_NOCONV, "a Poisson solve reached max_iter");
+    return FLOSIC_OK;
+}
+
+int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* phi, const double* V,
+                                double scale, double* U, double* Exc, double* E_sic, double* V_avg,
+                                void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!psi || !phi || !V) return fail(c, FLOSIC_ERR_ARG, "psi, phi and V are required");
+    if (!std::isfinite(scale)) return fail(c, FLOSIC_ERR_ARG, "scale must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_xc_energy(c, psi, phi, V, scale, V_avg, s);
+    launch_energy_reduce(c, U, Exc, E_sic, s);
+    return check_cuda(c, cudaGetLastError(), "energy kernels");
+}
+
+int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, const double* phi,
+                        const double* V, const double* gE, double* dE_dpsi, double* dE_dfod,
+                        void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!psi || !fods || !phi || !V || !gE) return fail(c, FLOSIC_ERR_ARG, "psi, fods, phi, V, gE are required");
+    if (!c->have_forward) return fail(c, FLOSIC_ERR_ARG, "no forward step recorded on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* Vsrc = V;
+    if (c->opt.adjoint_mode == FLOSIC_ADJ_EXACT) {
+        int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
+        if (rc) return rc;
+        launch_rhs(c, phi, false, c->ws.b64, s);                 // A W = rho (zero boundary)
+        rc = run_poisson(c, c->ws.b64, c->ws.veff, false, s);
+        if (rc) return rc;
+        finish_poisson(c, nullptr, nullptr, s);
+        launch_bc_adjoint(c, c->ws.veff, V, c->ws.veff, s);    // veff = (V + G^T rho)/2
+        Vsrc = c->ws.veff;
+    }
+    launch_backward_contract(c, psi, phi, Vsrc, gE, s);
+    launch_backward_small(c, dE_dfod, s);
+    if (dE_dpsi) launch_psibar(c, psi, phi, Vsrc, gE, fods, dE_dpsi, s);
+    if (c->opt.adjoint_mode == FLOSIC_ADJ_EXACT) {
+        int st[4];
+        int rc = read_status(c, s, st);
+        if (rc) return rc;
+        if (st[1]) return fail(c, FLOSIC_ERR_NOCONV, "adjoint Poisson solve reached max_iter");
+        return FLOSIC_OK;
+    }
+    return check_cuda(c, cudaGetLastError(), "backward kernels");
+}
+
+}  // extern "C"

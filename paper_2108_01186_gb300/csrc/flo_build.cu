@@ -1,0 +1,603 @@
+// Fermi-Loewdin orbitals (Sec. I.B, Eqs. 6-8; Sec. II.B) and the reverse
+// mode of that map for the FOD gradient (Eqs. 9-11).
+//
+// Forward, per spin block with N orbitals on G points:
+//   interpolation: v_ia = psi_a(a_i) and grad psi_a(a_i) (tricubic Lagrange)
+//   Gram:          M = dV psi psi^T            (grid contraction, K = G)
+//   small:         rho_i = sum_a v_ia^2, T = v / sqrt(rho), S = T M T^T
+//                  (= dV F F^T with F = T psi), S = U L U^T (Jacobi),
+//                  Q = S^{-1/2} = U L^{-1/2} U^T, C = Q T
+//   apply:         phi = C psi                 (N x N times N x G)
+// F itself is never stored: phi = Q F = (Q T) psi.
+//
+// Reverse, with Phibar_i = dE/dphi_i = 2 dV V_i^SIC phi_i (times gE):
+//   P = Phibar psi^T (grid contraction), Qbar = P T^T, Daleckii-Krein
+//   Sbar = U[(U^T Qbar U) o K]U^T with K_ij = -1/(a_i a_j (a_i + a_j)),
+//   a = sqrt(lambda); Tbar = Q P + (Sbar + Sbar^T) T M;
+//   vbar = Tbar/sqrt(rho) - v (Tbar.v)/rho^{3/2} (product form of Eq. 11);
+//   dE/da_i = sum_a vbar_ia grad psi_a(a_i);
+//   psibar = C^T Phibar + dV T^T (Sbar + Sbar^T) T psi + interpolation adjoint.
+#include "internal.cuh"
+#include "xc_device.cuh"
+
+namespace flosic {
+
+// ---------------------------------------------------------------------------
+// tricubic Lagrange interpolation at the FODs
+// ---------------------------------------------------------------------------
+// 4-point Lagrange basis on nodes -1, 0, 1, 2 at t and its derivative.
+__device__ __forceinline__ void lagrange4(double t, double* L, double* dL) {
+    const double tp = t + 1.0, tm = t - 1.0, t2 = t - 2.0;
+    L[0] = -t * tm * t2 * (1.0 / 6.0);
+    L[1] = tp * tm * t2 * 0.5;
+    L[2] = -tp * t * t2 * 0.5;
+    L[3] = tp * t * tm * (1.0 / 6.0);
+    dL[0] = -(3.0 * t * t - 6.0 * t + 2.0) * (1.0 / 6.0);
+    dL[1] = (3.0 * t * t - 4.0 * t - 1.0) * 0.5;
+    dL[2] = -(3.0 * t * t - 2.0 * t - 2.0) * 0.5;
+    dL[3] = (3.0 * t * t - 1.0) * (1.0 / 6.0);
+}
+
+struct Cell {
+    int i0[3];
+    double L[3][4], dL[3][4];
+};
+
+__device__ __forceinline__ Cell cell_of(const BlkDesc& B, const double* a) {
+    Cell c;
+    const double o[3] = {B.ox, B.oy, B.oz};
+    for (int d = 0; d < 3; ++d) {
+        const double u = (a[d] - o[d]) / B.h;
+        const double f = floor(u);
+        c.i0[d] = (int)f;
+        lagrange4(u - f, c.L[d], c.dL[d]);
+    }
+    return c;
+}
+
+// one of the paper's grid-gradient components at an interior node: central
+// difference inside, one-sided at the first and last point of the line
+__device__ __forceinline__ double grid_grad(const double* u, const BlkDesc& B, int x, int y, int z,
+                                            int d) {
+    const int p[3] = {x, y, z};
+    const int n[3] = {B.nx, B.ny, B.nz};
+    const long long st[3] = {1, B.nx, (long long)B.nx * B.ny};
+    const long long g = ((long long)z * B.ny + y) * B.nx + x;
+    if (n[d] == 1) return 0.0;
+    if (p[d] == 0) return (u[g + st[d]] - u[g]) / B.h;
+    if (p[d] == n[d] - 1) return (u[g] - u[g - st[d]]) / B.h;
+    return (u[g + st[d]] - u[g - st[d]]) / (2.0 * B.h);
+}
+
+// One warp per (block, FOD i, orbital a): vals[moff + i N + a] = psi_a(a_i)
+// and grads[3 (moff + i N + a) + d].
+__global__ void k_interp_fod(const BlkDesc* __restrict__ blk, int nblk, long long total,
+                             const double* __restrict__ psi, const double* __restrict__ fods,
+                             int mode, double* __restrict__ vals, double* __restrict__ grads,
+                             int* __restrict__ status) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= total) return;
+    int b = 0;
+    while (b + 1 < nblk && blk[b + 1].moff <= w) ++b;
+    const BlkDesc& B = blk[b];
+    const long long r = w - B.moff;
+    const int i = (int)(r / B.N), a = (int)(r % B.N);
+    const double* f = fods + (B.fod_off + i) * 3;
+    const double fa[3] = {f[0], f[1], f[2]};
+    const Cell c = cell_of(B, fa);
+    const double* u = psi + B.off + (long long)a * B.G;
+    double v = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int node = lane; node < 64; node += 32) {
+        const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
+        const int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+        if (qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz) continue;
+        const double uv = u[((long long)qz * B.ny + qy) * B.nx + qx];
+        const double wgt = c.L[0][e] * c.L[1][bb] * c.L[2][cc];
+        v += wgt * uv;
+        if (mode == FLOSIC_GRAD_INTERP) {
+            g0 += c.dL[0][e] * c.L[1][bb] * c.L[2][cc] * uv;
+            g1 += c.L[0][e] * c.dL[1][bb] * c.L[2][cc] * uv;
+            g2 += c.L[0][e] * c.L[1][bb] * c.dL[2][cc] * uv;
+        } else {
+            g0 += wgt * grid_grad(u, B, qx, qy, qz, 0);
+            g1 += wgt * grid_grad(u, B, qx, qy, qz, 1);
+            g2 += wgt * grid_grad(u, B, qx, qy, qz, 2);
+        }
+    }
+    v = warp_sum(v);
+    g0 = warp_sum(g0);
+    g1 = warp_sum(g1);
+    g2 = warp_sum(g2);
+    if (lane == 0) {
+        const double sc = (mode == FLOSIC_GRAD_INTERP) ? 1.0 / B.h : 1.0;
+        vals[w] = v;
+        grads[3 * w + 0] = g0 * sc;
+        grads[3 * w + 1] = g1 * sc;
+        grads[3 * w + 2] = g2 * sc;
+        if (!isfinite(v) || !isfinite(fa[0] + fa[1] + fa[2])) atomicOr(status + 0, 1);
+    }
+}
+
+void launch_interp_fod(const flosic_ctx* c, const double* psi, const double* fods, cudaStream_t s) {
+    const long long total = c->mat_elems;
+    const unsigned blocks = (unsigned)((total * 32 + 255) / 256);
+    k_interp_fod<<<blocks, 256, 0, s>>>(c->d_blk, c->nblk, total, psi, fods, c->opt.fod_grad_mode,
+                                        c->ws.vals, c->ws.grads, c->ws.status);
+}
+
+// ---------------------------------------------------------------------------
+// grid contractions C_ij = sum_g A_i(g) B_j(g) per block (K-split partials)
+// ---------------------------------------------------------------------------
+struct LoadPsi {
+    const double* p;
+    __device__ __forceinline__ double operator()(const BlkDesc& B, int i, long long g) const {
+        return p[B.off + (long long)i * B.G + g];
+    }
+};
+
+// Phibar_i(g) = gE * 2 dV * V_i^SIC(g) * phi_i(g), V^SIC = -(V + v_xc(phi^2)).
+struct LoadPhibar {
+    const double* phi;
+    const double* V;
+    const double* gE;
+    double rho_min;
+    __device__ __forceinline__ double operator()(const BlkDesc& B, int i, long long g) const {
+        const long long k = B.off + (long long)i * B.G + g;
+        const double f = phi[k];
+        double eps, vxc;
+        lsda_pol(f * f, rho_min, eps, vxc);
+        return gE[B.sys] * 2.0 * B.dV * (-(V[k] + vxc)) * f;
+    }
+};
+
+template <int RM, class LA, class LB>
+__global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ blk, int kparts, LA la,
+                                                  LB lb, double* __restrict__ part, long long mat_elems) {
+    constexpr int KT = 16;
+    constexpr int NP = 16 * RM;
+    __shared__ double As[KT][NP + 1];
+    __shared__ double Bs[KT][NP + 1];
+    const BlkDesc& B = blk[blockIdx.y];
+    const int N = B.N;
+    const long long G = B.G;
+    const int kp = blockIdx.x;
+    const long long kb = G * kp / kparts, ke = G * (kp + 1) / kparts;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[RM][RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < RM; ++q) acc[r][q] = 0.0;
+    for (long long k0 = kb; k0 < ke; k0 += KT) {
+        for (int idx = threadIdx.x; idx < KT * NP; idx += 256) {
+            const int i = idx / KT, kk = idx % KT;
+            const long long g = k0 + kk;
+            const bool ok = (i < N) && (g < ke);
+            As[kk][i] = ok ? la(B, i, g) : 0.0;
+            Bs[kk][i] = ok ? lb(B, i, g) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KT; ++kk) {
+            double a[RM], bv[RM];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+            for (int q = 0; q < RM; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < RM; ++q) acc[r][q] += a[r] * bv[q];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < RM; ++q) {
+            const int i = ty + 16 * r, j = tx + 16 * q;
+            if (i < N && j < N) part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = acc[r][q];
+        }
+}
+
+// out[e] = sum_kp part[kp][e] in a fixed order
+__global__ void k_sum_parts(const double* __restrict__ part, int kparts, long long n,
+                            double* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < kparts; ++k) s += part[(long long)k * n + e];
+    out[e] = s;
+}
+
+static int max_block_n(const flosic_ctx* c) {
+    int m = 0;
+    for (const auto& b : c->blk) m = b.N > m ? b.N : m;
+    return m;
+}
+
+template <class LA, class LB>
+static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_t s) {
+    const int nmax = max_block_n(c);
+    const dim3 grid(c->kparts, c->nblk);
+    double* part = c->ws.mat_part;
+    if (nmax <= 16)
+        k_contract<1><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    else if (nmax <= 32)
+        k_contract<2><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    else if (nmax <= 64)
+        k_contract<4><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    else
+        k_contract<8><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out);
+}
+
+void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s) {
+    contract(c, LoadPsi{psi}, LoadPsi{psi}, c->ws.M, s);
+}
+
+void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,
+                              const double* Vsrc, const double* gE, cudaStream_t s) {
+    contract(c, LoadPhibar{phi, Vsrc, gE, c->opt.rho_min}, LoadPsi{psi}, c->ws.P, s);
+}
+
+// ---------------------------------------------------------------------------
+// small dense algebra, one CTA per spin block
+// ---------------------------------------------------------------------------
+// Y = op(A) op(B) for row-major N x N matrices in global memory (ta/tb:
+// transpose).  All threads of the CTA take part; ends with __syncthreads.
+__device__ void mm(int N, const double* A, bool ta, const double* Bm, bool tb, double* Y) {
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i = e / N, j = e % N;
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) {
+            const double a = ta ? A[k * N + i] : A[i * N + k];
+            const double b = tb ? Bm[j * N + k] : Bm[k * N + j];
+            s += a * b;
+        }
+        Y[e] = s;
+    }
+    __syncthreads();
+}
+
+// Cyclic Jacobi eigen-decomposition of the symmetric matrix S (shared, N x N,
+// row-major), round-robin ordering so that the N/2 rotations of a round are
+// disjoint and run in parallel.  On exit S is diagonal (the eigenvalues) and
+// U (global) holds the eigenvectors as columns.
+__device__ void jacobi_eig(int N, double* S, double* U) {
+    __shared__ int rp[kMaxN / 2], rq[kMaxN / 2];
+    __shared__ double rc[kMaxN / 2], rs[kMaxN / 2];
+    __shared__ double scratch[32];
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[e] = (e / N == e % N) ? 1.0 : 0.0;
+    __syncthreads();
+    const int N2 = N + (N & 1);
+    const int m = N2 - 1;
+    for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const double v = S[e];
+            if (e / N == e % N) dg += v * v; else off += v * v;
+        }
+        off = block_sum(off, scratch);
+        dg = block_sum(dg, scratch);
+        if (off <= 1e-30 * dg) break;
+        for (int round = 0; round < m; ++round) {
+            if (threadIdx.x < N2 / 2) {
+                const int t = threadIdx.x;
+                int p, q;
+                if (t == 0) {
+                    p = 0;
+                    q = round % m + 1;
+                } else {
+                    p = (round + t) % m + 1;
+                    q = (round - t + m) % m + 1;
+                }
+                if (p > q) { const int tmp = p; p = q; q = tmp; }
+                double c = 1.0, s = 0.0;
+                if (q < N) {
+                    const double apq = S[p * N + q];
+                    if (fabs(apq) > 1e-300) {
+                        const double th = (S[q * N + q] - S[p * N + p]) / (2.0 * apq);
+                        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = rsqrt(tt * tt + 1.0);
+                        s = tt * c;
+                    }
+                }
+                rp[t] = p;
+                rq[t] = q < N ? q : p;   // dummy partner: identity rotation
+                rc[t] = c;
+                rs[t] = (q < N) ? s : 0.0;
+            }
+            __syncthreads();
+            const int np = N2 / 2;
+            for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // rows p, q
+                const int t = e / N, k = e % N;
+                const int p = rp[t], q = rq[t];
+                if (p == q) continue;
+                const double c = rc[t], s = rs[t];
+                const double a = S[p * N + k], b = S[q * N + k];
+                S[p * N + k] = c * a - s * b;
+                S[q * N + k] = s * a + c * b;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // columns p, q
+                const int t = e / N, k = e % N;
+                const int p = rp[t], q = rq[t];
+                if (p == q) continue;
+                const double c = rc[t], s = rs[t];
+                double a = S[k * N + p], b = S[k * N + q];
+                S[k * N + p] = c * a - s * b;
+                S[k * N + q] = s * a + c * b;
+                a = U[k * N + p];
+                b = U[k * N + q];
+                U[k * N + p] = c * a - s * b;
+                U[k * N + q] = s * a + c * b;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Per block: T, S, eigen-pairs, Q = S^{-1/2}, C = Q T; ILLCOND / NONFINITE.
+__global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk, Workspace w,
+                                                double illcond, double* S_out, double* Q_out) {
+    extern __shared__ double Ssh[];
+    __shared__ double scratch[32];
+    const BlkDesc& B = blk[blockIdx.x];
+    const int N = B.N;
+    const long long mo = B.moff;
+    const double* vals = w.vals + mo;
+    double* T = w.T + mo;
+    double* M = w.M + mo;
+    double* X = w.tmp + mo;
+    double* U = w.U + mo;
+    double* Q = w.Q + mo;
+    // M = dV * (raw Gram), finiteness of psi
+    double bad = 0.0;
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        M[e] *= B.dV;
+        if (!isfinite(M[e]) || !isfinite(vals[e])) bad = 1.0;
+    }
+    bad = block_sum(bad, scratch);
+    if (bad > 0.0) {
+        if (threadIdx.x == 0) atomicOr(w.status + 0, 1);
+        return;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double r = 0.0;
+        for (int a = 0; a < N; ++a) r += vals[i * N + a] * vals[i * N + a];
+        w.rho_a[B.orb0 + i] = r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) T[e] = vals[e] * rsqrt(w.rho_a[B.orb0 + e / N]);
+    __syncthreads();
+    mm(N, T, false, M, false, X);          // X = T M
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // S = X T^T
+        const int i = e / N, j = e % N;
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) s += X[i * N + k] * T[j * N + k];
+        Ssh[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // exact symmetry
+        const int i = e / N, j = e % N;
+        if (i < j) {
+            const double v = 0.5 * (Ssh[e] + Ssh[j * N + i]);
+            Ssh[e] = v;
+            Ssh[j * N + i] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        w.S[mo + e] = Ssh[e];
+        if (S_out) S_out[mo + e] = Ssh[e];
+    }
+    __syncthreads();
+    jacobi_eig(N, Ssh, U);
+    double* lam = w.lam + B.orb0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) lam[i] = Ssh[i * N + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double lmin = lam[0], lmax = lam[0];
+        for (int i = 1; i < N; ++i) {
+            lmin = fmin(lmin, lam[i]);
+            lmax = fmax(lmax, lam[i]);
+        }
+        if (!(lmin > illcond * lmax) || !(lmin > 0.0)) atomicOr(w.status + 2, 1);
+    }
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // Q = U L^{-1/2} U^T
+        const int i = e / N, j = e % N;
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) s += U[i * N + k] * U[j * N + k] * rsqrt(fmax(lam[k], 1e-300));
+        Q[e] = s;
+        if (Q_out) Q_out[mo + e] = s;
+    }
+    __syncthreads();
+    mm(N, Q, false, T, false, w.C + mo);   // C = Q T
+}
+
+void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s) {
+    const int nmax = max_block_n(c);
+    const size_t shm = sizeof(double) * nmax * nmax;
+    k_lowdin<<<c->nblk, 512, shm, s>>>(c->d_blk, c->ws, c->opt.illcond_tol, S_out, Q_out);
+}
+
+// ---------------------------------------------------------------------------
+// out_j(g) = sum_k E_jk X_k(g): small matrix times a tall operand, per block
+// ---------------------------------------------------------------------------
+struct LoadPhibarPsi {   // rows 0..N-1: Phibar; rows N..2N-1: psi
+    LoadPhibar pb;
+    const double* psi;
+    __device__ __forceinline__ double operator()(const BlkDesc& B, int k, long long g) const {
+        if (k < B.N) return pb(B, k, g);
+        return psi[B.off + (long long)(k - B.N) * B.G + g];
+    }
+};
+
+template <int RJ, class LX>
+__global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ blk,
+                                                  const double* __restrict__ E, int mult, LX lx,
+                                                  double* __restrict__ out) {
+    constexpr int TG = 32, KC = 32;
+    __shared__ double Es[8 * RJ][KC + 1];
+    __shared__ double Xs[KC][TG];
+    const BlkDesc& B = blk[blockIdx.y];
+    const int N = B.N, K = mult * N;
+    const double* Eb = E + mult * B.moff;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    for (long long tile = blockIdx.x; tile * TG < B.G; tile += gridDim.x) {
+        const long long g = tile * TG + lane;
+        double acc[RJ];
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) acc[r] = 0.0;
+        for (int kc = 0; kc < K; kc += KC) {
+            for (int e = threadIdx.x; e < 8 * RJ * KC; e += 256) {
+                const int j = e / KC, kk = e % KC;
+                Es[j][kk] = (j < N && kc + kk < K) ? Eb[(long long)j * K + kc + kk] : 0.0;
+            }
+            for (int kk = wq; kk < KC; kk += 8)
+                Xs[kk][lane] = (kc + kk < K && g < B.G) ? lx(B, kc + kk, g) : 0.0;
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < KC; ++kk) {
+                const double x = Xs[kk][lane];
+#pragma unroll
+                for (int r = 0; r < RJ; ++r) acc[r] += Es[wq + 8 * r][kk] * x;
+            }
+            __syncthreads();
+        }
+        if (g < B.G) {
+#pragma unroll
+            for (int r = 0; r < RJ; ++r) {
+                const int j = wq + 8 * r;
+                if (j < N) out[B.off + (long long)j * B.G + g] = acc[r];
+            }
+        }
+    }
+}
+
+template <class LX>
+static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, double* out, cudaStream_t s) {
+    const int nmax = max_block_n(c);
+    long long gmax = 0;
+    for (const auto& b : c->blk) gmax = b.G > gmax ? b.G : gmax;
+    const unsigned gx = (unsigned)((gmax + 31) / 32 < 65535 ? (gmax + 31) / 32 : 65535);
+    const dim3 grid(gx, c->nblk);
+    if (nmax <= 16)
+        k_smallmat<2><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    else if (nmax <= 32)
+        k_smallmat<4><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    else if (nmax <= 64)
+        k_smallmat<8><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    else
+        k_smallmat<16><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+}
+
+void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s) {
+    smallmat(c, c->ws.C, 1, LoadPsi{psi}, phi, s);
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode, small part (one CTA per block)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_backward_small(const BlkDesc* __restrict__ blk, Workspace w,
+                                                        double* dE_dfod) {
+    const BlkDesc& B = blk[blockIdx.x];
+    const int N = B.N;
+    const long long mo = B.moff;
+    const double *P = w.P + mo, *T = w.T + mo, *Q = w.Q + mo, *U = w.U + mo, *M = w.M + mo;
+    const double* lam = w.lam + B.orb0;
+    const double* vals = w.vals + mo;
+    const double* rho = w.rho_a + B.orb0;
+    const long long me = w.mat_elems;
+    double* A1 = w.tmp + mo;
+    double* A2 = w.tmp + me + mo;
+    double* A3 = w.tmp + 2 * me + mo;
+    double* Ss = w.tmp + 3 * me + mo;   // Sbar + Sbar^T
+    double* vbar = w.vbar + mo;
+    double* E2 = w.E2 + 2 * mo;         // [N][2N] = [C^T | D]
+    mm(N, P, false, T, true, A1);       // Qbar = P T^T
+    mm(N, U, true, A1, false, A2);      // U^T Qbar
+    mm(N, A2, false, U, false, A3);     // U^T Qbar U
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // o K
+        const double ai = sqrt(lam[e / N]), aj = sqrt(lam[e % N]);
+        A3[e] *= -1.0 / (ai * aj * (ai + aj));
+    }
+    __syncthreads();
+    mm(N, U, false, A3, false, A2);     // U X
+    mm(N, A2, false, U, true, A1);      // Sbar = U X U^T
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) Ss[e] = A1[e] + A1[(e % N) * N + e / N];
+    __syncthreads();
+    mm(N, Q, false, P, false, A1);      // Q P
+    mm(N, Ss, false, T, false, A2);     // Ss T
+    mm(N, A2, false, M, false, A3);     // Ss T M
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) A1[e] += A3[e];   // Tbar
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {          // vbar (product form)
+        double tv = 0.0;
+        for (int a = 0; a < N; ++a) tv += A1[i * N + a] * vals[i * N + a];
+        const double sq = sqrt(rho[i]);
+        for (int a = 0; a < N; ++a)
+            vbar[i * N + a] = A1[i * N + a] / sq - vals[i * N + a] * tv / (rho[i] * sq);
+    }
+    __syncthreads();
+    if (dE_dfod) {
+        for (int e = threadIdx.x; e < 3 * N; e += blockDim.x) {
+            const int i = e / 3, d = e % 3;
+            double s = 0.0;
+            for (int a = 0; a < N; ++a) s += vbar[i * N + a] * w.grads[3 * (mo + i * N + a) + d];
+            dE_dfod[(B.fod_off + i) * 3 + d] = s;
+        }
+    }
+    mm(N, T, true, Ss, false, A2);      // T^T Ss
+    mm(N, A2, false, T, false, A3);     // T^T Ss T
+    for (int e = threadIdx.x; e < 2 * N * N; e += blockDim.x) {
+        const int j = e / (2 * N), k = e % (2 * N);
+        E2[e] = (k < N) ? w.C[mo + k * N + j] : B.dV * A3[j * N + (k - N)];
+    }
+}
+
+void launch_backward_small(const flosic_ctx* c, double* dE_dfod, cudaStream_t s) {
+    k_backward_small<<<c->nblk, 512, 0, s>>>(c->d_blk, c->ws, dE_dfod);
+}
+
+// psibar_a(node) += sum_i vbar_ia L(a_i, node): one warp per orbital a,
+// FODs in sequence (deterministic).
+__global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __restrict__ orb_blk,
+                                 int norb, const double* __restrict__ vbar,
+                                 const double* __restrict__ fods, double* __restrict__ dpsi) {
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (o >= norb) return;
+    const BlkDesc& B = blk[orb_blk[o]];
+    const int a = o - B.orb0;
+    double* u = dpsi + B.off + (long long)a * B.G;
+    for (int i = 0; i < B.N; ++i) {
+        const double coef = vbar[B.moff + i * B.N + a];
+        const double* f = fods + (B.fod_off + i) * 3;
+        const double fa[3] = {f[0], f[1], f[2]};
+        const Cell c = cell_of(B, fa);
+        for (int node = lane; node < 64; node += 32) {
+            const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
+            const int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+            if (qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz) continue;
+            u[((long long)qz * B.ny + qy) * B.nx + qx] += coef * c.L[0][e] * c.L[1][bb] * c.L[2][cc];
+        }
+        __syncwarp();
+    }
+}
+
+void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* Vsrc,
+                   const double* gE, const double* fods, double* dpsi, cudaStream_t s) {
+    LoadPhibarPsi lx{LoadPhibar{phi, Vsrc, gE, c->opt.rho_min}, psi};
+    smallmat(c, c->ws.E2, 2, lx, dpsi, s);
+    k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
+                                                                 c->ws.vbar, fods, dpsi);
+}
+
+}  // namespace flosic
+
+namespace flosic {
+const void* k_lowdin_symbol() { return (const void*)k_lowdin; }
+}  // namespace flosic

@@ -1,0 +1,165 @@
+// Internal declarations of the sm_103a FLO-SIC library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/flosic.h"
+
+namespace flosic {
+
+constexpr int kHalf = 6;          // half-width of the 12th-order stencil
+constexpr int kChunk = 1024;      // grid points per chunk of a chunked kernel
+constexpr int kChunkThreads = 256;
+constexpr int kMaxN = 128;        // orbitals per spin block supported
+constexpr double kPi = 3.14159265358979323846;
+
+// One spin block of one system, as seen by the kernels.
+struct BlkDesc {
+    int nx, ny, nz, N;
+    double h, dV, ox, oy, oz;   // spacing, volume element, origin
+    double cx, cy, cz;          // multipole centre (box centre)
+    long long G;                // grid points
+    long long off;              // offset of orbital 0 in orbital-sized arrays
+    long long moff;             // offset in N x N arrays
+    long long voff;             // offset in V_avg
+    long long fod_off;          // offset (in FODs) of FOD 0
+    int orb0;                   // global index of orbital 0
+    int sys, spin;
+    long long chunk0;           // first global chunk of orbital 0
+    int nchunk;                 // chunks per orbital
+};
+
+// Per-orbital state of the batched conjugate-gradient solver.
+struct CgState {
+    double* rr;        // [norb] r.r (or r.z) of the current iterate
+    double* pq;        // [norb] p.Ap
+    double* bb;        // [norb] ||b||^2 of the current linear system
+    double* thr;       // [norb] stop when rr <= thr
+    double* beta;      // [norb] rr_new / rr_old
+    double* part;      // [nchunk_total] per-chunk partial sums
+    unsigned* count;   // [norb] last-block counters
+    int* active;       // [norb] 1 = CG still iterating
+    int* oactive;      // [norb] 1 = still refining (mixed precision)
+    int* iters;        // [norb] iterations done (all precisions)
+    int* n_active;     // [1] number of orbitals with active = 1
+    int* n_oactive;    // [1] number of orbitals with oactive = 1
+    int* conv;         // [norb] 1 = converged
+};
+
+struct Workspace {
+    // FLO build (N x N per block, packed like S)
+    double *vals, *grads, *rho_a, *T, *M, *S, *Q, *C, *U, *lam, *P;
+    double *vbar;          // [sum N*N] adjoint of psi at the FODs
+    double* tmp;           // [4][sum N*N] scratch of the small kernels
+    double* E2;            // [sum 2 N*N] [C^T | D] of the reverse apply
+    long long mat_elems;   // sum N*N
+    double* mat_part;      // partial N x N sums [kparts][sum N*N]
+    double* mom;           // [norb][10]
+    double* mom_part;      // [nchunk_total][10]
+    double* e_part;        // [nchunk_total][2] energies partials
+    double* e_orb;         // [norb][2] U_i, E_xc,i
+    int* status;           // [4] device status words
+    // Poisson
+    double *b64, *r64, *p64, *q64;   // FP64 CG vectors / refinement
+    float *d32, *r32, *p32, *q32;    // FP32 inner CG vectors
+    double* veff;                    // exact-adjoint effective potential
+    CgState cg;
+};
+
+}  // namespace flosic
+
+struct flosic_ctx {
+    flosic_options opt;
+    std::vector<flosic_system> sys;
+    std::vector<flosic::BlkDesc> blk;       // host copy
+    flosic::BlkDesc* d_blk = nullptr;       // device copy
+    int nblk = 0, norb = 0;
+    long long orb_elems = 0, vavg_elems = 0, mat_elems = 0, nchunk_total = 0;
+    int kparts = 0;                         // K-splits of the grid contractions
+    std::vector<int> h_orb_blk;
+    int* d_orb_blk = nullptr;               // [norb] block of each orbital
+    int* d_chunk_orb = nullptr;             // [nchunk_total] orbital of each chunk
+    int* d_sys_orb0 = nullptr;              // [nsys+1] first orbital of each system
+    flosic::Workspace ws{};
+    bool have_forward = false;
+    std::string err;
+    int* h_pinned = nullptr;                // small pinned host buffer
+    std::vector<void*> allocations;
+};
+
+namespace flosic {
+
+// ---- launchers implemented in the .cu files ----------------------------
+// FLO build (flo_build.cu)
+void launch_interp_fod(const flosic_ctx* c, const double* psi, const double* fods, cudaStream_t s);
+void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s);
+void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s);
+void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s);
+void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,
+                              const double* Vsrc, const double* gE, cudaStream_t s);
+void launch_backward_small(const flosic_ctx* c, double* dE_dfod, cudaStream_t s);
+void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* Vsrc,
+                   const double* gE, const double* fods, double* dpsi, cudaStream_t s);
+// Poisson (poisson.cu)
+void launch_moments(const flosic_ctx* c, const double* rho_src, bool square, cudaStream_t s);
+void launch_rhs(const flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s);
+int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream_t s);
+void finish_poisson(flosic_ctx* c, int* iters, int* conv, cudaStream_t s);
+cudaError_t upload_stencil_constants();
+void launch_bc_adjoint(const flosic_ctx* c, const double* W, const double* V, double* veff,
+                       cudaStream_t s);
+// xc / energies (xc.cu)
+void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi, const double* V,
+                      double scale, double* Vavg, cudaStream_t s);
+void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
+                          cudaStream_t s);
+
+void stencil_weights(double* w);   // 12th-order weights w_0..w_6
+const void* k_lowdin_symbol();
+int check_cuda(flosic_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace flosic
+
+// ---- device helpers ------------------------------------------------------
+namespace flosic {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of one double (fixed order: warps then lanes).  All threads
+// get the result.  scratch must hold 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) scratch[0] = t;
+    __syncthreads();
+    double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int find_block(const BlkDesc* blk, int nblk, int orb) {
+    int b = 0;
+    while (b + 1 < nblk && blk[b + 1].orb0 <= orb) ++b;
+    return b;
+}
+
+}  // namespace flosic

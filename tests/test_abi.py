@@ -1,0 +1,92 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+header declares, and rejects bad descriptors before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "flosic.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_01186_gb300 import build
+    build.build()
+    from paper_2108_01186_gb300 import flosic as F
+    return F.load_library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(flosic_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_step_calls():
+    names = _declared()
+    for n in ("flosic_build_flos", "flosic_orbital_poisson", "flosic_sic_energy_potential",
+              "flosic_sic_backward", "flosic_create", "flosic_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_default_options(lib):
+    from paper_2108_01186_gb300 import flosic as F
+    o = F.FlosicOptions()
+    assert lib.flosic_default_options(ctypes.byref(o)) == 0
+    assert o.precision == F.MIXED and o.cg_tol == 1e-10 and o.preconditioner == F.PC_MG
+    assert lib.flosic_default_options(None) == F.FLOSIC_ERR_ARG
+
+
+def _sys(**kw):
+    from paper_2108_01186_gb300 import flosic as F
+    s = F.FlosicSystem()
+    s.nx = s.ny = s.nz = 8
+    s.h = 0.5
+    s.nspin = 1
+    s.norb[0] = 2
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(h=-1.0), dict(nspin=3)])
+def test_create_rejects_bad_systems(lib, bad):
+    from paper_2108_01186_gb300 import flosic as F
+    h = ctypes.c_void_p()
+    s = _sys(**bad)
+    rc = lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, None)
+    assert rc == F.FLOSIC_ERR_ARG
+    assert not h.value
+    assert len(lib.flosic_last_error(None)) > 0
+
+
+def test_create_rejects_bad_options(lib):
+    from paper_2108_01186_gb300 import flosic as F
+    o = F.default_options(cg_tol=0.0)
+    h = ctypes.c_void_p()
+    s = _sys()
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+    o = F.default_options(precision=7)
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+
+
+def test_too_many_orbitals_rejected(lib):
+    from paper_2108_01186_gb300 import flosic as F
+    h = ctypes.c_void_p()
+    s = _sys()
+    s.norb[0] = 129
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, None) == F.FLOSIC_ERR_ARG
+
+
+def test_null_context_calls_are_rejected(lib):
+    from paper_2108_01186_gb300 import flosic as F
+    assert lib.flosic_build_flos(None, None, None, None, None, None, None) == F.FLOSIC_ERR_ARG
+    assert lib.flosic_destroy(None) == F.FLOSIC_OK
+    out = (ctypes.c_int64 * 6)()
+    assert lib.flosic_layout(None, out) == F.FLOSIC_ERR_ARG
