@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the FLO-SIC step: orbital SIC solves per second at 128^3.
+
+One step is the whole hot path on one batch: Fermi-Loewdin orbitals, one
+Poisson solve per orbital, LSDA energies and the averaged SIC potential,
+then the adjoint (dE_SIC/dpsi and FOD gradients).  Workload: 128^3 grid,
+h = 0.2 bohr, 32 + 32 orbitals on 16 seeded atoms (synthetic Gaussian
+s/p orbitals, seeded FODs), forward + adjoint.  value = orbitals / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--precision mixed|fp64] [--no-cpu-baseline] [--no-e2e]
+
+Under torchrun (N > 1) every rank runs its own independent system (weak
+scaling, no collective on the data path); value = all orbitals / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "orbital SIC solves/s at 128^3, mixed vs FP64 at 1e-6 Ha; HBM % of peak"
+WORKLOAD = "128^3 grid h=0.2 bohr, 32+32 orbitals on 16 atoms, FLO build + 64 Poisson solves + LSDA/E_SIC/V_avg + adjoint"
+CG_TOL = 1e-10
+# Plain-CG iterations the oracle needs per orbital of this workload to reach
+# ||r|| <= 1e-10 ||b|| (measured once on orbital 0 of spin 0); used to scale the
+# oracle's timed sample of iterations up to whole solves.
+ORACLE_CG_ITERS_128 = 687
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--preconditioner", default="mg", choices=["mg", "none"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = max(smax, float(f[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on the host cores on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(system, it_sample=20):
+    """Times the FP64 oracle on a bounded sample of one step and scales it to
+    solves/s: both spins' FLO build, energies and adjoint in full; Poisson
+    for `cores` orbitals at once (OpenMP over orbitals) for it_sample CG
+    iterations, scaled to all orbitals and ORACLE_CG_ITERS_128 iterations."""
+    import oracle
+    oracle.build_library()
+    cores = oracle.max_threads()
+    s = system
+    nsp = len(s.norb)
+    norb = sum(s.norb)
+    t0 = time.perf_counter()
+    blocks = [oracle.build_flos(s.psi[k], s.fods[k], s.grid) for k in range(nsp)]
+    t_build = time.perf_counter() - t0
+    rho = np.concatenate([b["phi"] ** 2 for b in blocks])[:cores]
+    t0 = time.perf_counter()
+    V, _ = oracle.poisson(rho, s.grid, tol=1e-300, max_iter=it_sample)
+    t_pois = time.perf_counter() - t0
+    # energies and adjoint on the (partly solved) potentials: same work as a full step
+    t0 = time.perf_counter()
+    fwd = dict(blocks=[], E_sic=0.0)
+    for k, b in enumerate(blocks):
+        Vk = np.resize(V, b["phi"].shape)
+        eps, vxc = oracle.lsda_pol(b["phi"] ** 2)
+        b.update(rho=b["phi"] ** 2, V=Vk, eps=eps, vxc=vxc, psi=s.psi[k], fods=s.fods[k])
+        fwd["blocks"].append(b)
+    t_en = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sic_backward(fwd, s.grid)
+    t_bw = time.perf_counter() - t0
+    waves = -(-norb // cores)
+    t_full = t_build + t_pois * waves * (ORACLE_CG_ITERS_128 / it_sample) + t_en + t_bw
+    elapsed = t_build + t_pois + t_en + t_bw
+    desc = ("FLO build of both spins, LSDA/energies and adjoint in full; Poisson: %d orbitals x %d CG "
+            "iterations timed, scaled to %d orbitals x %d iterations" % (cores, it_sample, norb, ORACLE_CG_ITERS_128))
+    return dict(value=norb / t_full, unit="solves/s", cores=cores, kind="oracle", sample=desc,
+                sample_seconds=round(elapsed, 2), extrapolated_step_s=round(t_full, 1))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2108_01186_gb300 import synth
+    s = synth.make_config(3)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(s, it_sample=5)
+        if k >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    cb = dict(r)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 64 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "system": "FP64 CPU oracle, host cores"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU path
+# ---------------------------------------------------------------------------
+def traffic_for(kernel_src):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha") != sha:
+        return None
+    return d.get("traffic_bytes_per_launch_scaled")
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2108_01186_gb300 import build, synth
+    from paper_2108_01186_gb300.flosic import Context
+
+    build.build()
+    s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)
+    norb = sum(s.norb)
+    prec = 1 if args.precision == "mixed" else 0
+    pc = 1 if args.preconditioner == "mg" else 0
+    ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc)
+    dev = torch.device("cuda", local)
+    psi_h = torch.from_numpy(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
+    fods_h = torch.from_numpy(np.concatenate([f.ravel() for f in s.fods])).pin_memory()
+    psi = psi_h.to(dev)
+    fods = fods_h.to(dev)
+    gE = torch.ones(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(psi, fods):
+        phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
+        V, iters, conv = ctx.orbital_poisson(phi)
+        E, Vavg, U, Exc = ctx.sic_energy_potential(psi, phi, V, 1.0)
+        dpsi, dfod = ctx.sic_backward(psi, fods, phi, V, gE)
+        return E, Vavg, dpsi, dfod, iters
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(psi, fods)
+    barrier()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    clk = ClockSampler(local)
+    clk.start()
+    iters_sum = np.zeros(norb)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        E, Vavg, dpsi, dfod, iters = step(psi, fods)
+        iters_sum += iters.cpu().numpy()
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * norb / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (CG stencil apply): algorithmic bytes =
+    # read p + write q per point per active orbital per iteration
+    bpp = 8 if prec == 1 else 16
+    alg_bytes = float(np.sum(iters_sum)) * s.G * bpp
+    launches = max(prof["kernel_launches"], 1)
+    achieved = alg_bytes / (prof["kernel_ms"] / 1e3) / 1e9 if prof["kernel_ms"] > 0 else 0.0
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        peak, peak_src = 6800.0, "fallback"
+    roof = {"bound": "hbm", "kernel": "k_cg_apply<float>" if prec == 1 else "k_cg_apply<double>",
+            "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": traffic_for(os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "poisson.cu")),
+            "alg_bytes_per_launch": alg_bytes / launches,
+            "avg_launch_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
+            "share_of_step": round(prof["kernel_ms"] / ms, 4)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        out_E = torch.empty(1, dtype=torch.float64).pin_memory()
+        out_V = torch.empty(ctx.vavg_elems, dtype=torch.float64).pin_memory()
+        out_df = torch.empty(3 * norb, dtype=torch.float64).pin_memory()
+        out_dp = torch.empty(ctx.orb_elems, dtype=torch.float64).pin_memory()
+        ke = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            pd = psi_h.to(dev, non_blocking=True)
+            fd = fods_h.to(dev, non_blocking=True)
+            E, Vavg, dpsi, dfod, _ = step(pd, fd)
+            out_E.copy_(E, non_blocking=True)
+            out_V.copy_(Vavg, non_blocking=True)
+            out_df.copy_(dfod, non_blocking=True)
+            out_dp.copy_(dpsi, non_blocking=True)
+            torch.cuda.synchronize()
+        barrier()
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * norb / te, "unit": "solves/s",
+               "h2d_bytes_per_step": int(psi_h.numel() * 8 + fods_h.numel() * 8),
+               "d2h_bytes_per_step": int((out_E.numel() + out_V.numel() + out_df.numel() + out_dp.numel()) * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(s)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32-cg+f64" if prec == 1 else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.precision, "preconditioner": args.preconditioner,
+                           "cg_tol": CG_TOL, "l2": "inputs larger than L2 (psi 1.07 GB per rank)",
+                           "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": prof["launches"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,16 @@ int flosic_sic_backward(flosic_ctx* ctx, const double* psi, const double* fods,
                         const double* phi, const double* V, const double* gE,
                         double* dE_dpsi, double* dE_dfod, void* stream);
 
+/* Instrumentation (no counterpart in the paper): enable != 0 records a CUDA
+ * event pair around every launch of the dominant kernel (the Poisson CG
+ * stencil apply) on the stream it runs on.  Errors: ARG, CUDA. */
+int flosic_profile(flosic_ctx* ctx, int enable);
+
+/* Host array out[3]: [0] summed duration (ms) of the timed launches,
+ * [1] number of timed launches, [2] kernels launched by ctx (all kinds).
+ * Waits for the last timed launch.  reset != 0 zeroes the counters. */
+int flosic_profile_read(flosic_ctx* ctx, double* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,8 @@ cudaError_t alloc(flosic_ctx* c, T** p, long long n) {
 }
 
 void release(flosic_ctx* c) {
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
     for (void* p : c->allocations) cudaFree(p);
     c->allocations.clear();
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -59,11 +61,38 @@ int read_status(flosic_ctx* c, cudaStream_t s, int* st4) {
     rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (rc) return rc;
     for (int k = 0; k < 4; ++k) st4[k] = c->h_pinned[k];
+    prof_collect(c);
     return FLOSIC_OK;
 }
 }  // namespace
 
 namespace flosic {
+void prof_collect(flosic_ctx* c) {
+    for (int k = 0; k < c->prof_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]) == cudaSuccess) {
+            c->prof_ms += ms;
+            ++c->prof_launches;
+        }
+    }
+    c->prof_used = 0;
+}
+
+void prof_begin(flosic_ctx* c, cudaStream_t s) {
+    if (!c->profiling) return;
+    if (2 * (c->prof_used + 1) > (int)c->prof_ev.size()) {   // pool full: wait and sum
+        cudaEventSynchronize(c->prof_ev[2 * c->prof_used - 1]);
+        prof_collect(c);
+    }
+    cudaEventRecord(c->prof_ev[2 * c->prof_used], s);
+}
+
+void prof_end(flosic_ctx* c, cudaStream_t s) {
+    if (!c->profiling) return;
+    cudaEventRecord(c->prof_ev[2 * c->prof_used + 1], s);
+    ++c->prof_used;
+}
+
 int check_cuda(flosic_ctx* c, cudaError_t e, const char* what) {
     if (e == cudaSuccess) return FLOSIC_OK;
     if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -312,6 +341,37 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
         return FLOSIC_OK;
     }
     return check_cuda(c, cudaGetLastError(), "backward kernels");
+}
+
+int flosic_profile(flosic_ctx* c, int enable) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (enable && c->prof_ev.empty()) {
+        c->prof_ev.resize(2 * 1024);
+        for (auto& e : c->prof_ev) {
+            int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
+            if (rc) return rc;
+        }
+    }
+    c->profiling = enable != 0;
+    return FLOSIC_OK;
+}
+
+int flosic_profile_read(flosic_ctx* c, double* out, int reset) {
+    if (!c || !out) return FLOSIC_ERR_ARG;
+    if (c->prof_used > 0) {
+        int rc = check_cuda(c, cudaEventSynchronize(c->prof_ev[2 * c->prof_used - 1]), "cudaEventSynchronize");
+        if (rc) return rc;
+        prof_collect(c);
+    }
+    out[0] = c->prof_ms;
+    out[1] = (double)c->prof_launches;
+    out[2] = (double)c->launches;
+    if (reset) {
+        c->prof_ms = 0.0;
+        c->prof_launches = 0;
+        c->launches = 0;
+    }
+    return FLOSIC_OK;
 }
 
 }  // extern "C"

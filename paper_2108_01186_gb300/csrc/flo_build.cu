@@ -123,7 +123,7 @@ void launch_interp_fod(const flosic_ctx* c, const double* psi, const double* fod
     const long long total = c->mat_elems;
     const unsigned blocks = (unsigned)((total * 32 + 255) / 256);
     k_interp_fod<<<blocks, 256, 0, s>>>(c->d_blk, c->nblk, total, psi, fods, c->opt.fod_grad_mode,
-                                        c->ws.vals, c->ws.grads, c->ws.status);
+                                        c->ws.vals, c->ws.grads, c->ws.status); note_launch(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,7 +230,8 @@ static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_
         k_contract<4><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
     else
         k_contract<8><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-    k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out);
+    note_launch(c);
+    k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out); note_launch(c);
 }
 
 void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s) {
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
 void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s) {
     const int nmax = max_block_n(c);
     const size_t shm = sizeof(double) * nmax * nmax;
-    k_lowdin<<<c->nblk, 512, shm, s>>>(c->d_blk, c->ws, c->opt.illcond_tol, S_out, Q_out);
+    k_lowdin<<<c->nblk, 512, shm, s>>>(c->d_blk, c->ws, c->opt.illcond_tol, S_out, Q_out); note_launch(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,6 +493,7 @@ static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, doub
         k_smallmat<8><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
     else
         k_smallmat<16><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    note_launch(c);
 }
 
 void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s) {
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(512) k_backward_small(const BlkDesc* __restric
 }
 
 void launch_backward_small(const flosic_ctx* c, double* dE_dfod, cudaStream_t s) {
-    k_backward_small<<<c->nblk, 512, 0, s>>>(c->d_blk, c->ws, dE_dfod);
+    k_backward_small<<<c->nblk, 512, 0, s>>>(c->d_blk, c->ws, dE_dfod); note_launch(c);
 }
 
 // psibar_a(node) += sum_i vbar_ia L(a_i, node): one warp per orbital a,
@@ -593,7 +595,7 @@ void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, co
     LoadPhibarPsi lx{LoadPhibar{phi, Vsrc, gE, c->opt.rho_min}, psi};
     smallmat(c, c->ws.E2, 2, lx, dpsi, s);
     k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                                 c->ws.vbar, fods, dpsi);
+                                                                 c->ws.vbar, fods, dpsi); note_launch(c);
 }
 
 }  // namespace flosic

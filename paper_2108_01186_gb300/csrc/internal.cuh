@@ -88,6 +88,13 @@ struct flosic_ctx {
     bool have_forward = false;
     std::string err;
     int* h_pinned = nullptr;                // small pinned host buffer
+    mutable long long launches = 0;         // kernels launched by this context
+    // optional CUDA-event timing of the dominant kernel (the CG stencil apply)
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;       // start/stop pairs, recorded in order
+    int prof_used = 0;                      // pairs recorded and not yet summed
+    double prof_ms = 0.0;                   // summed duration of timed launches
+    long long prof_launches = 0;
     std::vector<void*> allocations;
 };
 
@@ -121,6 +128,11 @@ void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
 const void* k_lowdin_symbol();
 int check_cuda(flosic_ctx* c, cudaError_t e, const char* what);
+inline void note_launch(const flosic_ctx* c) { ++c->launches; }
+// Event pair around one launch of the dominant kernel (no-op unless profiling).
+void prof_begin(flosic_ctx* c, cudaStream_t s);
+void prof_end(flosic_ctx* c, cudaStream_t s);
+void prof_collect(flosic_ctx* c);   // after a stream sync: sum recorded pairs
 
 }  // namespace flosic
 

@@ -202,9 +202,9 @@ __global__ void k_sum_chunks10(const BlkDesc* __restrict__ blk, const int* __res
 void launch_moments(const flosic_ctx* c, const double* src, bool square, cudaStream_t s) {
     k_moments<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb,
                                                                   c->d_orb_blk, src, square ? 1 : 0,
-                                                                  c->ws.mom_part);
+                                                                  c->ws.mom_part); note_launch(c);
     k_sum_chunks10<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                              c->ws.mom_part, c->ws.mom, 1);
+                                                              c->ws.mom_part, c->ws.mom, 1); note_launch(c);
 }
 
 // Multipole potential at offset R from the centre (moments mom[10]).
@@ -278,7 +278,7 @@ __global__ void k_rhs(const BlkDesc* __restrict__ blk, const int* __restrict__ c
 void launch_rhs(const flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s) {
     k_rhs<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk,
                                                               phi, c->ws.mom, with_bc ? 0 : 1, b,
-                                                              c->ws.cg);
+                                                              c->ws.cg); note_launch(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,6 +492,7 @@ static int read_count(flosic_ctx* c, const int* dptr, cudaStream_t s) {
                    "cudaMemcpyAsync") != FLOSIC_OK)
         return -1;
     if (check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize") != FLOSIC_OK) return -1;
+    prof_collect(c);
     return c->h_pinned[0];
 }
 
@@ -508,52 +509,56 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
     const int check_every = 8;
     if (!warm && check_cuda(c, cudaMemsetAsync(V, 0, sizeof(double) * c->orb_elems, s), "memset V"))
         return FLOSIC_ERR_CUDA;
-    k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st);
+    k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st); note_launch(c);
     if (c->opt.precision == FLOSIC_FP64) {
         k_residual64<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, b, V, w.r64, w.p64, 1,
-                                      tol2, max_iter, st.active, st.n_active, st);
+                                      tol2, max_iter, st.active, st.n_active, st); note_launch(c);
         for (int it = 0; it < max_iter; ++it) {
             if (it % check_every == 0) {
                 const int na = read_count(c, st.n_active, s);
                 if (na < 0) return FLOSIC_ERR_CUDA;
                 if (na == 0) break;
             }
-            k_cg_apply<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p64, w.q64, st);
+            prof_begin(c, s);
+            k_cg_apply<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p64, w.q64, st); note_launch(c);
+            prof_end(c, s);
             k_cg_update<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, V, w.r64, w.p64,
-                                                 w.q64, max_iter, 1, st);
-            k_cg_pupdate<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.p64, st);
+                                                 w.q64, max_iter, 1, st); note_launch(c);
+            k_cg_pupdate<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.p64, st); note_launch(c);
         }
     } else {
         const double inner_tol2 = 1e-10;   // each float32 solve gains ~5 digits
         for (int outer = 0; outer < 40; ++outer) {
             k_residual64<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, b, V, w.r64, nullptr,
-                                          0, tol2, max_iter, st.oactive, st.n_oactive, st);
+                                          0, tol2, max_iter, st.oactive, st.n_oactive, st); note_launch(c);
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
             if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
                 return FLOSIC_ERR_CUDA;
             k_inner_init<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.r32, w.p32,
-                                          w.d32, inner_tol2, tol2, st);
+                                          w.d32, inner_tol2, tol2, st); note_launch(c);
             for (int it = 0; it < max_iter; ++it) {
                 if (it % check_every == 0) {
                     const int ni = read_count(c, st.n_active, s);
                     if (ni < 0) return FLOSIC_ERR_CUDA;
                     if (ni == 0) break;
                 }
-                k_cg_apply<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p32, w.q32, st);
+                prof_begin(c, s);
+                k_cg_apply<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p32, w.q32, st); note_launch(c);
+                prof_end(c, s);
                 k_cg_update<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, w.r32,
-                                                    w.p32, w.q32, max_iter, 0, st);
-                k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st);
+                                                    w.p32, w.q32, max_iter, 0, st); note_launch(c);
+                k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
             }
-            k_correct<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, V, st);
+            k_correct<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, V, st); note_launch(c);
         }
     }
     return check_cuda(c, cudaGetLastError(), "poisson kernels");
 }
 
 void finish_poisson(flosic_ctx* c, int* iters, int* conv, cudaStream_t s) {
-    k_cg_finish<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->ws.cg, iters, conv, c->ws.status);
+    k_cg_finish<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->ws.cg, iters, conv, c->ws.status); note_launch(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -643,11 +648,11 @@ __global__ void k_veff(const BlkDesc* __restrict__ blk, const int* __restrict__ 
 void launch_bc_adjoint(const flosic_ctx* c, const double* W, const double* V, double* veff,
                        cudaStream_t s) {
     k_bcadj_coef<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb,
-                                                                     c->d_orb_blk, W, c->ws.mom_part);
+                                                                     c->d_orb_blk, W, c->ws.mom_part); note_launch(c);
     k_sum_chunks10<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                              c->ws.mom_part, c->ws.mom, 0);
+                                                              c->ws.mom_part, c->ws.mom, 0); note_launch(c);
     k_veff<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk,
-                                                               W, V, c->ws.mom, veff);
+                                                               W, V, c->ws.mom, veff); note_launch(c);
 }
 
 }  // namespace flosic

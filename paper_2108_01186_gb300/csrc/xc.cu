@@ -70,7 +70,7 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
     for (const auto& b : c->blk) cmax = b.nchunk > cmax ? b.nchunk : cmax;
     const dim3 grid(cmax, c->nblk);
     k_xc_energy<<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                               c->ws.e_part);
+                                               c->ws.e_part); note_launch(c);
 }
 
 // One warp per orbital: U_i = (dV/2) sum rho V, E_xc,i = dV sum rho eps.
@@ -109,10 +109,10 @@ __global__ void k_energy_sys(int nsys, const int* __restrict__ sys_orb0, const d
 
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic, cudaStream_t s) {
     k_energy_orb<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb, c->ws.e_part,
-                                                            c->ws.e_orb, U, Exc);
+                                                            c->ws.e_orb, U, Exc); note_launch(c);
     if (E_sic) {
         const int nsys = (int)c->sys.size();
-        k_energy_sys<<<(nsys + 127) / 128, 128, 0, s>>>(nsys, c->d_sys_orb0, c->ws.e_orb, E_sic);
+        k_energy_sys<<<(nsys + 127) / 128, 128, 0, s>>>(nsys, c->d_sys_orb0, c->ws.e_orb, E_sic); note_launch(c);
     }
 }
 

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "OK", 1: "ARG", 2: "CUDA", 3: "ILLCOND", 4: "NOCONV", 5: "NON
 
 ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "flosic_last_error",
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
-                 "flosic_sic_energy_potential", "flosic_sic_backward")
+                 "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
+                 "flosic_profile_read")
 
 
 class FlosicError(RuntimeError):
@@ -67,6 +68,8 @@ def load_library(path=LIB_PATH):
     L.flosic_orbital_poisson.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.flosic_sic_energy_potential.argtypes = [vp, vp, vp, vp, d, vp, vp, vp, vp, vp]
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.flosic_profile.argtypes = [vp, i]
+    L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
     for f in ABI_FUNCTIONS:
         if f != "flosic_last_error":
             getattr(L, f).restype = i
@@ -193,6 +196,14 @@ class Context:
         self._check(self._L.flosic_sic_backward(self._h, _ptr(psi), _ptr(fods), _ptr(phi), _ptr(V), _ptr(gE),
                                                 _ptr(dpsi), _ptr(dfod), _stream()))
         return dpsi, dfod
+
+    def profile(self, enable=True):
+        self._check(self._L.flosic_profile(self._h, int(enable)))
+
+    def profile_read(self, reset=True):
+        out = (ctypes.c_double * 3)()
+        self._check(self._L.flosic_profile_read(self._h, out, int(reset)))
+        return dict(kernel_ms=out[0], kernel_launches=int(out[1]), launches=int(out[2]))
 
     def forward(self, psi, fods, scale=1.0, V0=None):
         phi, S, Q = self.build_flos(psi, fods)
