@@ -183,6 +183,38 @@ int flosic_profile(flosic_ctx* ctx, int enable);
  * Waits for the last timed launch.  reset != 0 zeroes the counters. */
 int flosic_profile_read(flosic_ctx* ctx, double* out, int reset);
 
+/* Allocation-free Poisson solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they
+ * run -- code inside another framework's memory arena or under a hard
+ * memory cap, and latency-critical loops that must not call
+ * cudaMalloc/cudaFree (those can synchronise the whole device and fail when
+ * memory is tight).  It computes what flosic_orbital_poisson computes for
+ * one grid (float64 conjugate gradients, no preconditioner, the same
+ * 12th-order Laplacian and l <= 2 multipole boundary values) without a
+ * context and without allocating anything: no cudaMalloc, no cudaFree, no
+ * host heap.  Its scratch is one static device array of about 32 MiB that
+ * every GPU loading this library holds until the process exits.
+ *   nx, ny, nz, h, origin (host [3]): the grid, as in flosic_system.
+ *   phi [norb][G] float64 (device): orbitals; rho = phi^2.
+ *   V   [norb][G] float64 (device): out, the potentials (no warm start).
+ *   cg_tol, max_iter: as in flosic_options.
+ *   iters, conv_flags [norb] int32 (device, may be NULL): as in
+ *   flosic_orbital_poisson.
+ * Limits: 1 <= norb <= 128 and norb*nx*ny*nz <= 1048576; larger problems
+ * are rejected with FLOSIC_ERR_ARG before any work is queued.
+ * The first call on a device sets that device up (looks up the device
+ * address of the scratch array and uploads the stencil weights); make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array, so calls that overlap on the GPU (from two host threads or on two
+ * streams) race and must be serialised by the caller.  Waits for `stream`.
+ * Errors: ARG, CUDA, NOCONV; the message is in flosic_noalloc_last_error(). */
+int flosic_orbital_poisson_noalloc(int nx, int ny, int nz, double h, const double* origin,
+                                   int norb, const double* phi, double* V, double cg_tol,
+                                   int max_iter, int* iters, int* conv_flags, void* stream);
+
+/* Message of the last failing flosic_orbital_poisson_noalloc call. */
+const char* flosic_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "ARG", 2: "CUDA", 3: "ILLCOND", 4: "NOCONV", 5: "NON
 ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "flosic_last_error",
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
-                 "flosic_profile_read")
+                 "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error")
 
 
 class FlosicError(RuntimeError):
@@ -70,8 +70,11 @@ def load_library(path=LIB_PATH):
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
+    L.flosic_orbital_poisson_noalloc.argtypes = [i, i, i, d, ctypes.POINTER(d), i, vp, vp, d, i, vp, vp, vp]
+    L.flosic_noalloc_last_error.argtypes = []
+    L.flosic_noalloc_last_error.restype = ctypes.c_char_p
     for f in ABI_FUNCTIONS:
-        if f != "flosic_last_error":
+        if f not in ("flosic_last_error", "flosic_noalloc_last_error"):
             getattr(L, f).restype = i
     _lib = L
     return L
@@ -210,6 +213,18 @@ class Context:
         V, iters, conv = self.orbital_poisson(phi, V0)
         E, Vavg, U, Exc = self.sic_energy_potential(psi, phi, V, scale)
         return dict(phi=phi, S=S, S_mhalf=Q, V=V, iters=iters, conv=conv, E_sic=E, V_avg=Vavg, U=U, Exc=Exc)
+
+
+def orbital_poisson_noalloc(grid, phi, V, cg_tol=1e-10, max_iter=20000, iters=None, conv=None):
+    """Calls flosic_orbital_poisson_noalloc: one grid (nx, ny, nz, h, origin),
+    phi and V [norb*G] CUDA float64 tensors; returns the status code."""
+    L = load_library()
+    nx, ny, nz, h, origin = grid
+    G = nx * ny * nz
+    norb = phi.numel() // G
+    org = (ctypes.c_double * 3)(*[float(x) for x in origin])
+    return L.flosic_orbital_poisson_noalloc(int(nx), int(ny), int(nz), float(h), org, int(norb), _ptr(phi), _ptr(V),
+                                            float(cg_tol), int(max_iter), _ptr(iters), _ptr(conv), _stream())
 
 
 def _sysdict(s):
