@@ -185,6 +185,18 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     c->vavg_elems = voff;
     c->mat_elems = moff;
     c->nchunk_total = chunk;
+    // points within 6 of a face, per block (they carry the multipole ghost taps)
+    std::vector<int> bidx;
+    for (BlkDesc& b : c->blk) {
+        b.bnd0 = (long long)bidx.size();
+        for (int z = 0; z < b.nz; ++z)
+            for (int y = 0; y < b.ny; ++y)
+                for (int x = 0; x < b.nx; ++x)
+                    if (x < kHalf || x >= b.nx - kHalf || y < kHalf || y >= b.ny - kHalf || z < kHalf ||
+                        z >= b.nz - kHalf)
+                        bidx.push_back((z * b.ny + y) * b.nx + x);
+        b.nbnd = (int)((long long)bidx.size() - b.bnd0);
+    }
     int kp = (608 + c->nblk - 1) / c->nblk;
     c->kparts = kp < 1 ? 1 : (kp > 1024 ? 1024 : kp);
     std::vector<int> chunk_orb((size_t)chunk);
@@ -205,7 +217,8 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.S, me); A(&w.Q, me); A(&w.C, me); A(&w.U, me); A(&w.lam, orb); A(&w.P, me);
     A(&w.vbar, me); A(&w.tmp, 4 * me); A(&w.E2, 2 * me);
     A(&w.mat_part, (long long)c->kparts * me);
-    A(&w.mom, 10LL * orb); A(&w.mom_part, 10 * chunk);
+    A(&w.mom, 10LL * orb);
+    A(&c->d_bidx, (long long)bidx.size()); A(&c->d_bcoef, 10LL * (long long)bidx.size());
     A(&w.e_part, 2 * chunk); A(&w.e_orb, 2LL * orb);
     A(&w.status, 4);
     A(&w.b64, off); A(&w.r64, off);
@@ -215,9 +228,95 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         A(&w.d32, off); A(&w.r32, off); A(&w.p32, off); A(&w.q32, off);
     }
     if (o.adjoint_mode == FLOSIC_ADJ_EXACT) A(&w.veff, off);
+    A(&w.vsic, off);
+    // level 0 (the fine grid) always, coarser multigrid levels when asked for:
+    // coarsen each block while every side is >= 6
+    Multigrid& M = c->mg;
+    {
+        const bool want_mg = (o.preconditioner == FLOSIC_PC_MG);
+        std::vector<int> nl(c->nblk);
+        std::vector<int> coarsest(c->nblk);
+        M.nlev = 0;
+        M.coarsest_max = 0;
+        for (int b = 0; b < c->nblk; ++b) {
+            int d[3] = {c->blk[b].nx, c->blk[b].ny, c->blk[b].nz};
+            int L = 1;
+            while (want_mg && L < kMaxLevels && d[0] >= 6 && d[1] >= 6 && d[2] >= 6) {
+                for (int k = 0; k < 3; ++k) d[k] /= 2;
+                ++L;
+            }
+            nl[b] = L;
+            coarsest[b] = L - 1;
+            M.nlev = L > M.nlev ? L : M.nlev;
+            const long long Gc = (long long)d[0] * d[1] * d[2];
+            M.coarsest_max = Gc > M.coarsest_max ? Gc : M.coarsest_max;
+        }
+        M.enabled = want_mg && M.coarsest_max <= kCoarseMax;
+        if (!M.enabled) {
+            M.nlev = 1;
+            for (int b = 0; b < c->nblk; ++b) { nl[b] = 1; coarsest[b] = 0; }
+        }
+        const size_t tsz = (o.precision == FLOSIC_FP64) ? sizeof(double) : sizeof(float);
+        for (int l = 0; l < M.nlev; ++l) {
+            long long offl = 0, chl = 0, tl = 0;
+            std::vector<int4> tiles;
+            for (int b = 0; b < c->nblk; ++b) {
+                const BlkDesc& B = c->blk[b];
+                LvlDesc D{};
+                D.off = offl;
+                D.chunk0 = chl;
+                D.tile0 = tl;
+                if (l < nl[b]) {
+                    D.nx = B.nx >> l; D.ny = B.ny >> l; D.nz = B.nz >> l;
+                    D.h = B.h * (double)(1 << l);
+                    D.G = (long long)D.nx * D.ny * D.nz;
+                    D.nchunk = (int)((D.G + kChunk - 1) / kChunk);
+                    D.coarsest = (l == nl[b] - 1) ? 1 : 0;
+                    const int tx = (D.nx + kTileX - 1) / kTileX, ty = (D.ny + kTileY - 1) / kTileY,
+                              tz = (D.nz + kTileZ - 1) / kTileZ;
+                    D.ntile = tx * ty * tz;
+                    for (int i = 0; i < B.N; ++i)
+                        for (int kz = 0; kz < tz; ++kz)
+                            for (int ky = 0; ky < ty; ++ky)
+                                for (int kx = 0; kx < tx; ++kx)
+                                    tiles.push_back(make_int4(B.orb0 + i, kx * kTileX, ky * kTileY, kz * kTileZ));
+                    offl += (long long)B.N * D.G;
+                    chl += (long long)B.N * D.nchunk;
+                    tl += (long long)B.N * D.ntile;
+                }
+                M.h_lvl[l].push_back(D);
+            }
+            M.elems[l] = offl;
+            M.nchunk[l] = chl;
+            M.ntiles[l] = tl;
+            A(&M.d_lvl[l], c->nblk);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(M.d_lvl[l], M.h_lvl[l].data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice);
+            A(&M.d_tiles[l], tl);
+            if (e == cudaSuccess && tl > 0)
+                e = cudaMemcpy(M.d_tiles[l], tiles.data(), sizeof(int4) * tl, cudaMemcpyHostToDevice);
+            if (l > 0) {
+                unsigned char *pr = nullptr, *pe = nullptr, *pt = nullptr;
+                A(&pr, (long long)tsz * offl); A(&pe, (long long)tsz * offl); A(&pt, (long long)tsz * offl);
+                M.r[l] = pr; M.e[l] = pe; M.t[l] = pt;
+            }
+        }
+        A(&M.d_coarsest_level, c->nblk);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(M.d_coarsest_level, coarsest.data(), sizeof(int) * c->nblk, cudaMemcpyHostToDevice);
+        if (M.enabled) {
+            if (o.precision == FLOSIC_FP64) {
+                A(&w.z64, off); A(&w.p64b, off);
+            } else {
+                A(&w.z32, off); A(&w.p32b, off);
+            }
+        }
+    }
     CgState& g = w.cg;
-    A(&g.rr, orb); A(&g.pq, orb); A(&g.bb, orb); A(&g.thr, orb); A(&g.beta, orb);
-    A(&g.part, chunk); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
+    A(&g.rr, orb); A(&g.pq, orb); A(&g.bb, orb); A(&g.thr, orb); A(&g.beta, orb); A(&g.rz, orb);
+    const long long nparts = chunk > M.ntiles[0] ? chunk : M.ntiles[0];
+    A(&w.mom_part, 10 * nparts);
+    A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
@@ -226,6 +325,10 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
     if (e == cudaSuccess) e = upload_stencil_constants();
+    if (e == cudaSuccess) e = upload_boundary_constants();
+    if (e == cudaSuccess && !bidx.empty())
+        e = cudaMemcpy(c->d_bidx, bidx.data(), sizeof(int) * bidx.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !bidx.empty()) e = setup_boundary(c);
     if (e == cudaSuccess) {
         int nmax = 0;
         for (const auto& b : c->blk) nmax = b.N > nmax ? b.N : nmax;
@@ -266,6 +369,7 @@ int flosic_build_flos(flosic_ctx* c, const double* psi, const double* fods, doub
     if (!psi || !fods || !phi) return fail(c, FLOSIC_ERR_ARG, "psi, fods and phi are required");
     cudaStream_t s = (cudaStream_t)stream;
     c->have_forward = false;
+    c->have_energy = false;
     int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
     if (rc) return rc;
     launch_interp_fod(c, psi, fods, s);
@@ -288,7 +392,6 @@ int flosic_orbital_poisson(flosic_ctx* c, const double* phi, double* V, int warm
     cudaStream_t s = (cudaStream_t)stream;
     int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
     if (rc) return rc;
-    launch_moments(c, phi, true, s);
     launch_rhs(c, phi, true, c->ws.b64, s);
     rc = run_poisson(c, c->ws.b64, V, warm_start != 0, s);
     if (rc) return rc;
@@ -309,6 +412,7 @@ int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* 
     cudaStream_t s = (cudaStream_t)stream;
     launch_xc_energy(c, psi, phi, V, scale, V_avg, s);
     launch_energy_reduce(c, U, Exc, E_sic, s);
+    c->have_energy = true;
     return check_cuda(c, cudaGetLastError(), "energy kernels");
 }
 
@@ -319,7 +423,8 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
     if (!psi || !fods || !phi || !V || !gE) return fail(c, FLOSIC_ERR_ARG, "psi, fods, phi, V, gE are required");
     if (!c->have_forward) return fail(c, FLOSIC_ERR_ARG, "no forward step recorded on this context");
     cudaStream_t s = (cudaStream_t)stream;
-    const double* Vsrc = V;
+    if (!c->have_energy) launch_xc_energy(c, psi, phi, V, 1.0, nullptr, s);   // V^SIC only
+    const double* Vsrc = c->ws.vsic;
     if (c->opt.adjoint_mode == FLOSIC_ADJ_EXACT) {
         int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
         if (rc) return rc;
@@ -327,7 +432,7 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
         rc = run_poisson(c, c->ws.b64, c->ws.veff, false, s);
         if (rc) return rc;
         finish_poisson(c, nullptr, nullptr, s);
-        launch_bc_adjoint(c, c->ws.veff, V, c->ws.veff, s);    // veff = (V + G^T rho)/2
+        launch_bc_adjoint(c, c->ws.veff, V, c->ws.veff, s);    // V^SIC of veff = (V + G^T rho)/2
         Vsrc = c->ws.veff;
     }
     launch_backward_contract(c, psi, phi, Vsrc, gE, s);

@@ -1,0 +1,247 @@
+// Right-hand side of the per-orbital Poisson problems (Sec. II.A: Dirichlet
+// values of the potential from a multipole expansion, isolated systems).
+//
+// With the ghost values known, -Delta_h V = 4 pi rho becomes
+//   A V = 4 pi rho + bc,  bc(g) = (1/h^2) sum_{taps of g outside} w_m V_b(R_tap),
+//   V_b(R) = sum_k mom_k beta_k(R),
+//   beta = {1/R, R_x/R^3, R_y/R^3, R_z/R^3, R_x^2/2R^5, R_y^2/2R^5, R_z^2/2R^5,
+//           R_x R_y/R^5, R_x R_z/R^5, R_y R_z/R^5}
+// for the moments mom = {Q, p, Theta_xx, Theta_yy, Theta_zz, Theta_xy,
+// Theta_xz, Theta_yz} of rho about the box centre.  bc is linear in the
+// moments with coefficients that depend only on the grid:
+//   bc(g) = sum_k mom_k B_k(g),  B_k(g) = (1/h^2) sum_taps w_m beta_k(R_tap).
+// B is computed once per context for the points within 6 of a face (the only
+// points with ghost taps); a step then needs one pass for 4 pi rho and the
+// moments, and 10 multiply-adds per boundary point and orbital.  The exact
+// Poisson adjoint uses the same B: its transpose gives sum_g W_g B_k(g).
+#include "internal.cuh"
+
+namespace flosic {
+
+__constant__ double c_wb[kHalf + 1];
+
+cudaError_t upload_boundary_constants() {
+    double w[kHalf + 1];
+    stencil_weights(w);
+    return cudaMemcpyToSymbol(c_wb, w, sizeof(w));
+}
+
+// One thread per boundary point of one block: B[j][0..9].
+__global__ void k_bnd_coef(const BlkDesc* __restrict__ blk, int b, const int* __restrict__ bidx,
+                           double* __restrict__ bcoef) {
+    const BlkDesc& B = blk[b];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B.nbnd) return;
+    const int g = bidx[B.bnd0 + j];
+    const int pl = B.nx * B.ny;
+    const int z = g / pl, rem = g - z * pl, y = rem / B.nx, x = rem - y * B.nx;
+    const int p[3] = {x, y, z};
+    const int n[3] = {B.nx, B.ny, B.nz};
+    const double ih2 = 1.0 / (B.h * B.h);
+    double cf[10];
+    for (int k = 0; k < 10; ++k) cf[k] = 0.0;
+    for (int d = 0; d < 3; ++d)
+        for (int m = 1; m <= kHalf; ++m)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const int qd = p[d] + sg * m;
+                if (qd >= 0 && qd < n[d]) continue;
+                int q[3] = {x, y, z};
+                q[d] = qd;
+                const double Rx = B.ox + B.h * q[0] - B.cx, Ry = B.oy + B.h * q[1] - B.cy,
+                             Rz = B.oz + B.h * q[2] - B.cz;
+                const double ir = rsqrt(Rx * Rx + Ry * Ry + Rz * Rz);
+                const double ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+                const double f = c_wb[m] * ih2;
+                cf[0] += f * ir;
+                cf[1] += f * Rx * ir3;
+                cf[2] += f * Ry * ir3;
+                cf[3] += f * Rz * ir3;
+                cf[4] += f * 0.5 * Rx * Rx * ir5;
+                cf[5] += f * 0.5 * Ry * Ry * ir5;
+                cf[6] += f * 0.5 * Rz * Rz * ir5;
+                cf[7] += f * Rx * Ry * ir5;
+                cf[8] += f * Rx * Rz * ir5;
+                cf[9] += f * Ry * Rz * ir5;
+            }
+    double* out = bcoef + (B.bnd0 + (long long)j) * 10;
+    for (int k = 0; k < 10; ++k) out[k] = cf[k];
+}
+
+cudaError_t setup_boundary(flosic_ctx* c) {
+    for (int b = 0; b < c->nblk; ++b) {
+        const int nb = c->blk[b].nbnd;
+        if (nb == 0) continue;
+        k_bnd_coef<<<(nb + 255) / 256, 256>>>(c->d_blk, b, c->d_bidx, c->d_bcoef);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
+// Pass 1 over the tiles: b = scale * phi^2 and (for the multipole boundary)
+// the l <= 2 moments of phi^2 per orbital.  Per column (x, y) the z-sums
+// S0 = sum rho, S1 = sum rho Z, S2 = sum rho Z^2 give all ten moments.
+__global__ void __launch_bounds__(256) k_rhs_bulk(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                  const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                  const double* __restrict__ phi, double scale, int want_mom,
+                                                  double* __restrict__ b, double* __restrict__ mom_part,
+                                                  double* __restrict__ mom, unsigned* __restrict__ count) {
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    const LvlDesc& D = L[P.b];
+    const BlkDesc& B = blk[P.b];
+    double m[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k] = 0.0;
+    const int x = P.x0 + threadIdx.x;
+    for (int k = 0; k < 2; ++k) {
+        const int y = P.y0 + threadIdx.y + k * (kTileY / 2);
+        if (x >= D.nx || y >= D.ny) continue;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int z = P.z0; z < P.z1; ++z) {
+            const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
+            const double v = phi[g];
+            const double rho = v * v;
+            b[g] = scale * rho;
+            const double Z = B.oz + B.h * z - B.cz;
+            s0 += rho;
+            s1 += rho * Z;
+            s2 += rho * Z * Z;
+        }
+        const double X = B.ox + B.h * x - B.cx, Y = B.oy + B.h * y - B.cy;
+        const double sxx = X * X * s0, syy = Y * Y * s0, r2 = sxx + syy + s2;
+        m[0] += s0;
+        m[1] += X * s0;
+        m[2] += Y * s0;
+        m[3] += s1;
+        m[4] += 3.0 * sxx - r2;
+        m[5] += 3.0 * syy - r2;
+        m[6] += 3.0 * s2 - r2;
+        m[7] += 3.0 * X * Y * s0;
+        m[8] += 3.0 * X * s1;
+        m[9] += 3.0 * Y * s1;
+    }
+    if (!want_mom) return;
+    __shared__ bool last;
+    for (int k = 0; k < 10; ++k) {
+        const double s = block_sum(m[k], scratch);
+        if (linear_tid() == 0) mom_part[(long long)blockIdx.x * 10 + k] = s;
+    }
+    if (linear_tid() == 0) {
+        __threadfence();
+        last = (atomicAdd(count + P.o, 1u) == (unsigned)(D.ntile - 1));
+    }
+    __syncthreads();
+    if (last) {
+        for (int k = 0; k < 10; ++k) {
+            double v = 0.0;
+            for (int t = linear_tid(); t < D.ntile; t += blockDim.x * blockDim.y)
+                v += __ldcg(mom_part + (P.first + t) * 10 + k);
+            v = block_sum(v, scratch);
+            if (linear_tid() == 0) mom[P.o * 10 + k] = v * B.dV;
+        }
+        if (linear_tid() == 0) count[P.o] = 0;
+    }
+}
+
+// Pass 2: b[g_j] += sum_k mom_k B_k(g_j) for every boundary point of every
+// orbital (thread per boundary point, looping over the block's orbitals).
+__global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __restrict__ bidx,
+                         const double* __restrict__ bcoef, const double* __restrict__ mom,
+                         double* __restrict__ rhs) {
+    const BlkDesc& B = blk[b];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B.nbnd) return;
+    const int g = bidx[B.bnd0 + j];
+    double cf[10];
+    const double* src = bcoef + (B.bnd0 + (long long)j) * 10;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) cf[k] = src[k];
+    for (int i = 0; i < B.N; ++i) {
+        const double* mo = mom + (B.orb0 + i) * 10;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc += mo[k] * cf[k];
+        rhs[B.off + (long long)i * B.G + g] += acc;
+    }
+}
+
+void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_rhs_bulk<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi, with_bc ? 4.0 * kPi : 1.0, with_bc ? 1 : 0, b,
+        c->ws.mom_part, c->ws.mom, c->ws.cg.count); note_launch(c);
+    if (!with_bc) return;
+    for (int k = 0; k < c->nblk; ++k) {
+        const int nb = c->blk[k].nbnd;
+        if (nb == 0) continue;
+        k_rhs_bc<<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b); note_launch(c);
+    }
+}
+
+// Exact Poisson adjoint: c_k = sum_g W_g B_k(g) per orbital (K^T of the
+// boundary map, before spreading with the moment weights).
+__global__ void k_bcadj_coef(const BlkDesc* __restrict__ blk, int b, const int* __restrict__ bidx,
+                             const double* __restrict__ bcoef, const double* __restrict__ W,
+                             double* __restrict__ coef) {
+    __shared__ double scratch[32];
+    const BlkDesc& B = blk[b];
+    const int i = blockIdx.x;   // orbital within the block
+    double acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    const double* w = W + B.off + (long long)i * B.G;
+    for (int j = threadIdx.x; j < B.nbnd; j += blockDim.x) {
+        const double wv = w[bidx[B.bnd0 + j]];
+        const double* cf = bcoef + (B.bnd0 + (long long)j) * 10;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] += wv * cf[k];
+    }
+    for (int k = 0; k < 10; ++k) {
+        const double v = block_sum(acc[k], scratch);
+        if (threadIdx.x == 0) coef[(B.orb0 + i) * 10 + k] = v;
+    }
+}
+
+// veff = (V + G^T rho)/2, G^T rho = 4 pi W + dV sum_k c_k mbasis_k(R), with the
+// moment weights mbasis = {1, R, 3RR - R^2 I (xx, yy, zz), 3 R_x R_y, ...};
+// writes V^SIC of the exact adjoint, -(veff + v_xc) = vsic + V - veff.
+__global__ void __launch_bounds__(256) k_veff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                              const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                              const double* __restrict__ W, const double* __restrict__ V,
+                                              const double* __restrict__ coef, const double* __restrict__ vsic,
+                                              double* __restrict__ out) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    const LvlDesc& D = L[P.b];
+    const BlkDesc& B = blk[P.b];
+    double c[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) c[k] = coef[P.o * 10 + k];
+    const int x = P.x0 + threadIdx.x;
+    for (int k = 0; k < 2; ++k) {
+        const int y = P.y0 + threadIdx.y + k * (kTileY / 2);
+        if (x >= D.nx || y >= D.ny) continue;
+        const double Rx = B.ox + B.h * x - B.cx, Ry = B.oy + B.h * y - B.cy;
+        for (int z = P.z0; z < P.z1; ++z) {
+            const double Rz = B.oz + B.h * z - B.cz;
+            const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+            const double kt = c[0] + c[1] * Rx + c[2] * Ry + c[3] * Rz + c[4] * (3 * Rx * Rx - r2) +
+                              c[5] * (3 * Ry * Ry - r2) + c[6] * (3 * Rz * Rz - r2) + c[7] * 3 * Rx * Ry +
+                              c[8] * 3 * Rx * Rz + c[9] * 3 * Ry * Rz;
+            const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
+            const double veff = 0.5 * (V[g] + 4.0 * kPi * W[g] + B.dV * kt);
+            out[g] = vsic[g] + V[g] - veff;
+        }
+    }
+}
+
+void launch_bc_adjoint(flosic_ctx* c, const double* W, const double* V, double* out, cudaStream_t s) {
+    for (int k = 0; k < c->nblk; ++k) {
+        k_bcadj_coef<<<c->blk[k].N, 256, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, W, c->ws.mom); note_launch(c);
+    }
+    const Multigrid& M = c->mg;
+    k_veff<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
+                                                                       W, V, c->ws.mom, c->ws.vsic, out); note_launch(c);
+}
+
+}  // namespace flosic

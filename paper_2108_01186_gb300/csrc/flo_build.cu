@@ -10,7 +10,8 @@
 //   apply:         phi = C psi                 (N x N times N x G)
 // F itself is never stored: phi = Q F = (Q T) psi.
 //
-// Reverse, with Phibar_i = dE/dphi_i = 2 dV V_i^SIC phi_i (times gE):
+// Reverse, with Phibar_i = dE/dphi_i = 2 dV V_i^SIC phi_i (times gE; V^SIC
+// as stored by the energy pass):
 //   P = Phibar psi^T (grid contraction), Qbar = P T^T, Daleckii-Krein
 //   Sbar = U[(U^T Qbar U) o K]U^T with K_ij = -1/(a_i a_j (a_i + a_j)),
 //   a = sqrt(lambda); Tbar = Q P + (Sbar + Sbar^T) T M;
@@ -136,18 +137,15 @@ struct LoadPsi {
     }
 };
 
-// Phibar_i(g) = gE * 2 dV * V_i^SIC(g) * phi_i(g), V^SIC = -(V + v_xc(phi^2)).
+// Phibar_i(g) = gE * 2 dV * V_i^SIC(g) * phi_i(g) with V^SIC = -(V + v_xc)
+// as stored by the energy pass (or its exact-adjoint variant).
 struct LoadPhibar {
     const double* phi;
-    const double* V;
+    const double* vsic;
     const double* gE;
-    double rho_min;
     __device__ __forceinline__ double operator()(const BlkDesc& B, int i, long long g) const {
         const long long k = B.off + (long long)i * B.G + g;
-        const double f = phi[k];
-        double eps, vxc;
-        lsda_pol(f * f, rho_min, eps, vxc);
-        return gE[B.sys] * 2.0 * B.dV * (-(V[k] + vxc)) * f;
+        return gE[B.sys] * 2.0 * B.dV * vsic[k] * phi[k];
     }
 };
 
@@ -239,8 +237,8 @@ void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s) {
 }
 
 void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,
-                              const double* Vsrc, const double* gE, cudaStream_t s) {
-    contract(c, LoadPhibar{phi, Vsrc, gE, c->opt.rho_min}, LoadPsi{psi}, c->ws.P, s);
+                              const double* vsic, const double* gE, cudaStream_t s) {
+    contract(c, LoadPhibar{phi, vsic, gE}, LoadPsi{psi}, c->ws.P, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -590,9 +588,9 @@ __global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __r
     }
 }
 
-void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* Vsrc,
+void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* vsic,
                    const double* gE, const double* fods, double* dpsi, cudaStream_t s) {
-    LoadPhibarPsi lx{LoadPhibar{phi, Vsrc, gE, c->opt.rho_min}, psi};
+    LoadPhibarPsi lx{LoadPhibar{phi, vsic, gE}, psi};
     smallmat(c, c->ws.E2, 2, lx, dpsi, s);
     k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
                                                                  c->ws.vbar, fods, dpsi); note_launch(c);

@@ -31,6 +31,35 @@ struct BlkDesc {
     int sys, spin;
     long long chunk0;           // first global chunk of orbital 0
     int nchunk;                 // chunks per orbital
+    long long bnd0;             // first entry in the boundary-point list
+    int nbnd;                   // points within 6 of a face (they have ghost taps)
+};
+
+// One multigrid level of one spin block (level 0 = the fine grid).
+constexpr int kMaxLevels = 10;
+constexpr int kTileX = 32, kTileY = 16, kTileZ = 32;   // 3-D tiles of the sweeps (threads 32 x 8)
+constexpr int kCoarseSweeps = 40;      // damped-Jacobi sweeps on the coarsest level
+constexpr int kCoarseMax = 2000;       // largest coarsest level (points) kept in shared memory
+struct LvlDesc {
+    int nx, ny, nz;
+    int coarsest;          // 1 if this is the block's last level
+    double h;              // 2^l h
+    long long G;           // points (0: the block has no such level)
+    long long off;         // offset of orbital 0 in this level's arrays
+    long long chunk0;      // first chunk of orbital 0 in this level's chunk table
+    int nchunk;            // chunks per orbital
+    long long tile0;       // first tile of orbital 0 in this level's tile table
+    int ntile;             // tiles per orbital
+};
+
+// Per-level buffers as the kernels see them (passed by value).
+template <class T>
+struct MgPtrs {
+    T* r[kMaxLevels];      // level right-hand side (level 0: the CG residual)
+    T* e[kMaxLevels];      // level correction (level 0: z = M r)
+    T* t[kMaxLevels];      // scratch (level 0: the CG q buffer, idle during the V-cycle)
+    const LvlDesc* lvl[kMaxLevels];
+    const int* coarsest_level;   // [nblk]
 };
 
 // Per-orbital state of the batched conjugate-gradient solver.
@@ -39,8 +68,10 @@ struct CgState {
     double* pq;        // [norb] p.Ap
     double* bb;        // [norb] ||b||^2 of the current linear system
     double* thr;       // [norb] stop when rr <= thr
-    double* beta;      // [norb] rr_new / rr_old
-    double* part;      // [nchunk_total] per-chunk partial sums
+    double* beta;      // [norb] rr_new / rr_old (or rz_new / rz_old)
+    double* rz;        // [norb] r.z of the preconditioned solver
+    double* part;      // [max(chunks, tiles)] per-CTA partial sums
+    double* part2;     // [max(chunks, tiles)] a second set of partial sums
     unsigned* count;   // [norb] last-block counters
     int* active;       // [norb] 1 = CG still iterating
     int* oactive;      // [norb] 1 = still refining (mixed precision)
@@ -66,8 +97,27 @@ struct Workspace {
     // Poisson
     double *b64, *r64, *p64, *q64;   // FP64 CG vectors / refinement
     float *d32, *r32, *p32, *q32;    // FP32 inner CG vectors
-    double* veff;                    // exact-adjoint effective potential
+    double* veff;                    // exact adjoint: zero-boundary solve, then its V^SIC
+    double* vsic;                    // V_i^SIC = -(V_i + v_xc,i) of the last energy pass
+    double *z64, *p64b;              // multigrid PCG (FP64)
+    float *z32, *p32b;               // multigrid PCG (FP32)
     CgState cg;
+};
+
+struct Multigrid {
+    bool enabled = false;
+    int nlev = 0;                              // levels of the deepest block
+    LvlDesc* d_lvl[kMaxLevels] = {};           // [nblk] per level (device)
+    std::vector<LvlDesc> h_lvl[kMaxLevels];
+    long long nchunk[kMaxLevels] = {};         // chunks per level (all orbitals)
+    long long elems[kMaxLevels] = {};          // elements per level (all orbitals)
+    int* d_coarsest_level = nullptr;           // [nblk]
+    int4* d_tiles[kMaxLevels] = {};            // tile -> (orbital, x0, y0, z0) per level
+    long long ntiles[kMaxLevels] = {};
+    long long coarsest_max = 0;
+    void* r[kMaxLevels] = {};                  // levels >= 1 (T = float or double)
+    void* e[kMaxLevels] = {};
+    void* t[kMaxLevels] = {};
 };
 
 }  // namespace flosic
@@ -84,8 +134,12 @@ struct flosic_ctx {
     int* d_orb_blk = nullptr;               // [norb] block of each orbital
     int* d_chunk_orb = nullptr;             // [nchunk_total] orbital of each chunk
     int* d_sys_orb0 = nullptr;              // [nsys+1] first orbital of each system
+    int* d_bidx = nullptr;                  // boundary points (flat index) of every block
+    double* d_bcoef = nullptr;              // [sum nbnd][10] boundary-map coefficients
     flosic::Workspace ws{};
+    flosic::Multigrid mg;
     bool have_forward = false;
+    bool have_energy = false;
     std::string err;
     int* h_pinned = nullptr;                // small pinned host buffer
     mutable long long launches = 0;         // kernels launched by this context
@@ -112,19 +166,25 @@ void launch_backward_small(const flosic_ctx* c, double* dE_dfod, cudaStream_t s)
 void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* Vsrc,
                    const double* gE, const double* fods, double* dpsi, cudaStream_t s);
 // Poisson (poisson.cu)
-void launch_moments(const flosic_ctx* c, const double* rho_src, bool square, cudaStream_t s);
-void launch_rhs(const flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s);
+void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s);
+cudaError_t upload_boundary_constants();
+cudaError_t setup_boundary(flosic_ctx* c);
 int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream_t s);
 void finish_poisson(flosic_ctx* c, int* iters, int* conv, cudaStream_t s);
 cudaError_t upload_stencil_constants();
-void launch_bc_adjoint(const flosic_ctx* c, const double* W, const double* V, double* veff,
-                       cudaStream_t s);
+void launch_bc_adjoint(flosic_ctx* c, const double* W, const double* V, double* out, cudaStream_t s);
 // xc / energies (xc.cu)
 void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi, const double* V,
                       double scale, double* Vavg, cudaStream_t s);
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
                           cudaStream_t s);
 
+template <class T>
+void launch_vcycle(const flosic_ctx* c, const MgPtrs<T>& mp, const int* active, cudaStream_t s);
+template <class T>
+void launch_apply12_pcg(flosic_ctx* c, const T* z, const T* pold, T* pnew, T* q, cudaStream_t s);
+void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
+                       int* flag, int* counter, int want_bb, cudaStream_t s);
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
 const void* k_lowdin_symbol();
 int check_cuda(flosic_ctx* c, cudaError_t e, const char* what);
@@ -150,18 +210,23 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+__device__ __forceinline__ int linear_tid() {
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+
 // Block-wide sum of one double (fixed order: warps then lanes).  All threads
-// get the result.  scratch must hold 32 doubles.
+// get the result.  scratch must hold 32 doubles.  Any block shape.
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
+    const int tid = linear_tid();
+    const int lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) scratch[wid] = v;
     __syncthreads();
-    double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+    double t = (tid < nw) ? scratch[tid] : 0.0;
     if (wid == 0) t = warp_sum(t);
-    if (threadIdx.x == 0) scratch[0] = t;
+    if (tid == 0) scratch[0] = t;
     __syncthreads();
     double r = scratch[0];
     __syncthreads();
@@ -172,6 +237,53 @@ __device__ __forceinline__ int find_block(const BlkDesc* blk, int nblk, int orb)
     int b = 0;
     while (b + 1 < nblk && blk[b + 1].orb0 <= orb) ++b;
     return b;
+}
+
+// ---- 3-D tiles of one orbital (x0, y0, z0; kTileX x kTileY x kTileZ) ----
+struct TilePos {
+    int o, b, x0, y0, z0, z1;
+    long long base;    // offset of the orbital in the level's arrays
+    long long first;   // global tile index of the orbital's first tile
+};
+
+__device__ __forceinline__ TilePos tile_pos(const BlkDesc* blk, const LvlDesc* L, const int4* tiles,
+                                            const int* orb_blk, int t) {
+    const int4 tl = tiles[t];
+    TilePos p;
+    p.o = tl.x;
+    p.b = orb_blk[p.o];
+    const LvlDesc& D = L[p.b];
+    const int i = p.o - blk[p.b].orb0;
+    p.x0 = tl.y;
+    p.y0 = tl.z;
+    p.z0 = tl.w;
+    p.z1 = min(p.z0 + kTileZ, D.nz);
+    p.base = D.off + (long long)i * D.G;
+    p.first = D.tile0 + (long long)i * D.ntile;
+    return p;
+}
+
+// Stores this CTA's partial and returns true in the CTA that arrives last
+// among the ntile CTAs of one orbital.
+__device__ __forceinline__ bool tile_arrive(double partial, double* part, int t, unsigned* counter, int ntile,
+                                            double* scratch) {
+    __shared__ bool last;
+    const double s = block_sum(partial, scratch);
+    if (linear_tid() == 0) {
+        part[t] = s;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == (unsigned)(ntile - 1));
+    }
+    __syncthreads();
+    return last;
+}
+
+// Fixed-order sum of part[first .. first + n) read through L2.
+__device__ __forceinline__ double tile_gather(const double* part, long long first, int n, double* scratch) {
+    double v = 0.0;
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int k = linear_tid(); k < n; k += nt) v += __ldcg(part + first + k);
+    return block_sum(v, scratch);
 }
 
 }  // namespace flosic

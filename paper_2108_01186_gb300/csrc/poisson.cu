@@ -19,6 +19,10 @@ namespace flosic {
 __constant__ double c_w[kHalf + 1];
 __constant__ float c_wf[kHalf + 1];
 
+template <class T> __device__ __forceinline__ T c_wf_or_w(int m);
+template <> __device__ __forceinline__ float c_wf_or_w<float>(int m) { return c_wf[m]; }
+template <> __device__ __forceinline__ double c_wf_or_w<double>(int m) { return c_w[m]; }
+
 // Centred second-derivative weights of order 12 on a unit grid:
 //   w_k = 2 (-1)^{k+1} (6!)^2 / (k^2 (6-k)! (6+k)!), w_0 = -2 sum_k 1/k^2.
 void stencil_weights(double* w) {
@@ -31,7 +35,13 @@ void stencil_weights(double* w) {
     }
 }
 
+cudaError_t upload_stencil12_constants();
+
 cudaError_t upload_stencil_constants() {
+    {
+        cudaError_t e = upload_stencil12_constants();
+        if (e != cudaSuccess) return e;
+    }
     double w[kHalf + 1];
     float wf[kHalf + 1];
     stencil_weights(w);
@@ -144,144 +154,6 @@ __device__ __forceinline__ void xyz_of(long long g, int nx, int ny, int& x, int&
 }
 
 // ---------------------------------------------------------------------------
-// multipole moments (l <= 2) of rho_i about the box centre
-// ---------------------------------------------------------------------------
-__global__ void k_moments(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                          const int* __restrict__ orb_blk, const double* __restrict__ src,
-                          int square, double* __restrict__ mom_part) {
-    __shared__ double scratch[32];
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
-    const BlkDesc& B = blk[P.b];
-    double m[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) m[q] = 0.0;
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.g0 + k;
-        int x, y, z;
-        xyz_of(g, B.nx, B.ny, x, y, z);
-        const double v = src[P.base + g];
-        const double rho = square ? v * v : v;
-        const double Rx = B.ox + B.h * x - B.cx, Ry = B.oy + B.h * y - B.cy, Rz = B.oz + B.h * z - B.cz;
-        const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-        m[0] += rho;
-        m[1] += rho * Rx;
-        m[2] += rho * Ry;
-        m[3] += rho * Rz;
-        m[4] += rho * (3.0 * Rx * Rx - r2);
-        m[5] += rho * (3.0 * Ry * Ry - r2);
-        m[6] += rho * (3.0 * Rz * Rz - r2);
-        m[7] += rho * 3.0 * Rx * Ry;
-        m[8] += rho * 3.0 * Rx * Rz;
-        m[9] += rho * 3.0 * Ry * Rz;
-    }
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-        const double s = block_sum(m[q], scratch);
-        if (threadIdx.x == 0) mom_part[t * 10 + q] = s;
-    }
-}
-
-// One warp per orbital: mom[o][q] = dV * sum over its chunks (fixed order).
-__global__ void k_sum_chunks10(const BlkDesc* __restrict__ blk, const int* __restrict__ orb_blk,
-                               int norb, const double* __restrict__ part, double* __restrict__ out,
-                               int scale_dV) {
-    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (o >= norb) return;
-    const BlkDesc& B = blk[orb_blk[o]];
-    const long long first = B.chunk0 + (long long)(o - B.orb0) * B.nchunk;
-    for (int q = 0; q < 10; ++q) {
-        double v = 0.0;
-        for (int c = lane; c < B.nchunk; c += 32) v += part[(first + c) * 10 + q];
-        v = warp_sum(v);
-        if (lane == 0) out[o * 10 + q] = scale_dV ? v * B.dV : v;
-    }
-}
-
-void launch_moments(const flosic_ctx* c, const double* src, bool square, cudaStream_t s) {
-    k_moments<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb,
-                                                                  c->d_orb_blk, src, square ? 1 : 0,
-                                                                  c->ws.mom_part); note_launch(c);
-    k_sum_chunks10<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                              c->ws.mom_part, c->ws.mom, 1); note_launch(c);
-}
-
-// Multipole potential at offset R from the centre (moments mom[10]).
-__device__ __forceinline__ double multipole_value(const double* mom, double Rx, double Ry, double Rz) {
-    const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-    const double ir = rsqrt(r2);
-    const double ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
-    double v = mom[0] * ir + (mom[1] * Rx + mom[2] * Ry + mom[3] * Rz) * ir3;
-    const double quad = mom[4] * Rx * Rx + mom[5] * Ry * Ry + mom[6] * Rz * Rz +
-                        2.0 * (mom[7] * Rx * Ry + mom[8] * Rx * Rz + mom[9] * Ry * Rz);
-    return v + 0.5 * quad * ir5;
-}
-
-// ---------------------------------------------------------------------------
-// right-hand side: b = 4 pi phi^2 + bc (mode 0) or b = phi^2 (mode 1, zero
-// boundary, for the exact adjoint); also ||b||^2 per orbital.
-// ---------------------------------------------------------------------------
-__global__ void k_rhs(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                      const int* __restrict__ orb_blk, const double* __restrict__ phi,
-                      const double* __restrict__ mom_all, int mode, double* __restrict__ b,
-                      CgState st) {
-    __shared__ double scratch[32];
-    __shared__ double mom[10];
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
-    const BlkDesc& B = blk[P.b];
-    if (threadIdx.x < 10) mom[threadIdx.x] = mom_all[P.o * 10 + threadIdx.x];
-    __syncthreads();
-    const double ih2 = 1.0 / (B.h * B.h);
-    double bb = 0.0;
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.g0 + k;
-        const double v = phi[P.base + g];
-        double val = (mode == 0 ? 4.0 * kPi : 1.0) * v * v;
-        if (mode == 0) {
-            int x, y, z;
-            xyz_of(g, B.nx, B.ny, x, y, z);
-            const int p[3] = {x, y, z};
-            const int n[3] = {B.nx, B.ny, B.nz};
-            double acc = 0.0;
-            for (int d = 0; d < 3; ++d) {
-                if (p[d] >= kHalf && p[d] < n[d] - kHalf) continue;
-                for (int m = 1; m <= kHalf; ++m) {
-                    for (int sg = -1; sg <= 1; sg += 2) {
-                        const int qd = p[d] + sg * m;
-                        if (qd >= 0 && qd < n[d]) continue;
-                        int q[3] = {x, y, z};
-                        q[d] = qd;
-                        const double Rx = B.ox + B.h * q[0] - B.cx;
-                        const double Ry = B.oy + B.h * q[1] - B.cy;
-                        const double Rz = B.oz + B.h * q[2] - B.cz;
-                        acc += c_w[m] * multipole_value(mom, Rx, Ry, Rz);
-                    }
-                }
-            }
-            val += acc * ih2;
-        }
-        b[P.base + g] = val;
-        bb += val * val;
-    }
-    const BlkDesc& Bb = B;
-    if (arrive(bb, st.part, t, st.count + P.o, Bb.nchunk, scratch)) {
-        const double s = gather_sum(st.part, P.first, Bb.nchunk, scratch);
-        if (threadIdx.x == 0) {
-            st.bb[P.o] = s;
-            st.count[P.o] = 0;
-        }
-    }
-}
-
-void launch_rhs(const flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s) {
-    k_rhs<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk,
-                                                              phi, c->ws.mom, with_bc ? 0 : 1, b,
-                                                              c->ws.cg); note_launch(c);
-}
-
-// ---------------------------------------------------------------------------
 // conjugate gradients, batched over orbitals (one CTA per chunk of points)
 // ---------------------------------------------------------------------------
 __global__ void k_cg_reset(int norb, CgState st) {
@@ -296,6 +168,8 @@ __global__ void k_cg_reset(int norb, CgState st) {
     st.iters[o] = 0;
     st.conv[o] = 0;
     st.count[o] = 0;
+    st.rz[o] = 0.0;
+    st.beta[o] = 0.0;
 }
 
 // r = b - A x (float64), rr = r.r; if the orbital already meets the target
@@ -427,6 +301,97 @@ __global__ void k_cg_pupdate(const BlkDesc* __restrict__ blk, const int* __restr
     }
 }
 
+// Preconditioned CG, fused: p = z + beta p_old (p = z on the first
+// iteration, beta = 0), q = A p, pq = p.q.  The taps read z and p_old.
+template <class T>
+__global__ void k_pcg_apply(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
+                            const int* __restrict__ orb_blk, const T* __restrict__ z,
+                            const T* __restrict__ pold, T* __restrict__ pnew, T* __restrict__ q, CgState st) {
+    __shared__ double scratch[32];
+    const long long t = blockIdx.x;
+    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
+    if (!st.active[P.o]) return;
+    const BlkDesc& B = blk[P.b];
+    const double bd = st.beta[P.o];
+    const bool first = (bd == 0.0);
+    const T beta = (T)bd;
+    const T ih2 = (T)(1.0 / (B.h * B.h));
+    const T* zb = z + P.base;
+    const T* pb = pold + P.base;
+    const long long sy = B.nx, sz = (long long)B.nx * B.ny;
+    double pq = 0.0;
+    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
+        const long long g = P.g0 + k;
+        int x, y, zz;
+        xyz_of(g, B.nx, B.ny, x, y, zz);
+        auto pv = [&](long long h) -> T { return first ? zb[h] : zb[h] + beta * pb[h]; };
+        const T pc = pv(g);
+        T acc = T(3) * c_wf_or_w<T>(0) * pc;
+#pragma unroll
+        for (int m = 1; m <= kHalf; ++m) {
+            T sm = 0;
+            if (x - m >= 0) sm += pv(g - m);
+            if (x + m < B.nx) sm += pv(g + m);
+            if (y - m >= 0) sm += pv(g - m * sy);
+            if (y + m < B.ny) sm += pv(g + m * sy);
+            if (zz - m >= 0) sm += pv(g - m * sz);
+            if (zz + m < B.nz) sm += pv(g + m * sz);
+            acc += (T)c_wf_or_w<T>(m) * sm;
+        }
+        const T qv = -acc * ih2;
+        pnew[P.base + g] = pc;
+        q[P.base + g] = qv;
+        pq += (double)pc * (double)qv;
+    }
+    if (arrive(pq, st.part, t, st.count + P.o, B.nchunk, scratch)) {
+        const double sum = gather_sum(st.part, P.first, B.nchunk, scratch);
+        if (threadIdx.x == 0) {
+            st.count[P.o] = 0;
+            st.pq[P.o] = sum;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q with alpha = rz/pq; rr = r.r decides convergence.
+template <class T>
+__global__ void k_pcg_update(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
+                             const int* __restrict__ orb_blk, T* __restrict__ x, T* __restrict__ r,
+                             const T* __restrict__ p, const T* __restrict__ q, int max_iter, int set_conv,
+                             CgState st) {
+    __shared__ double scratch[32];
+    const long long t = blockIdx.x;
+    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
+    if (!st.active[P.o]) return;
+    const BlkDesc& B = blk[P.b];
+    const double pqv = st.pq[P.o];
+    const T alpha = (pqv > 0.0) ? (T)(st.rz[P.o] / pqv) : (T)0;
+    double rr = 0.0;
+    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
+        const long long g = P.base + P.g0 + k;
+        x[g] += alpha * p[g];
+        const T rv = r[g] - alpha * q[g];
+        r[g] = rv;
+        rr += (double)rv * (double)rv;
+    }
+    if (arrive(rr, st.part, t, st.count + P.o, B.nchunk, scratch)) {
+        const double sum = gather_sum(st.part, P.first, B.nchunk, scratch);
+        if (threadIdx.x == 0) {
+            const int o = P.o;
+            st.count[o] = 0;
+            st.rr[o] = sum;
+            const int it = ++st.iters[o];
+            if (!(sum > st.thr[o])) {
+                st.active[o] = 0;
+                if (set_conv) st.conv[o] = 1;
+                atomicSub(st.n_active, 1);
+            } else if (it >= max_iter || !isfinite(sum) || !(pqv > 0.0)) {
+                st.active[o] = 0;
+                atomicSub(st.n_active, 1);
+            }
+        }
+    }
+}
+
 // Start of an inner float32 solve of A d = r64 for orbitals still refining:
 // r32 = p32 = float(r64), d32 = 0, rr = r32.r32; inner target
 // thr = max(inner_tol^2 rr, (tol^2/4) bb).
@@ -454,6 +419,8 @@ __global__ void k_inner_init(const BlkDesc* __restrict__ blk, const int* __restr
             const int o = P.o;
             st.count[o] = 0;
             st.rr[o] = s;
+            st.rz[o] = 0.0;
+            st.beta[o] = 0.0;
             const double a = inner_tol2 * s, c = 0.25 * tol2 * st.bb[o];
             st.thr[o] = a > c ? a : c;
             if (s > st.thr[o]) {
@@ -499,6 +466,49 @@ static int read_count(flosic_ctx* c, const int* dptr, cudaStream_t s) {
 // Solves A V = b for every orbital (b from launch_rhs, ||b||^2 in cg.bb).
 // Returns a flosic status; iteration counts and convergence flags stay in the
 // CG state (copied out by finish_poisson).
+template <class T>
+static MgPtrs<T> mg_ptrs(const flosic_ctx* c, T* r, T* z, T* q) {
+    MgPtrs<T> mp{};
+    for (int l = 0; l < kMaxLevels; ++l) {
+        mp.r[l] = (T*)c->mg.r[l];
+        mp.e[l] = (T*)c->mg.e[l];
+        mp.t[l] = (T*)c->mg.t[l];
+        mp.lvl[l] = c->mg.d_lvl[l];
+    }
+    mp.r[0] = r;
+    mp.e[0] = z;
+    mp.t[0] = q;
+    mp.coarsest_level = c->mg.d_coarsest_level;
+    return mp;
+}
+
+// Multigrid-preconditioned CG on A x = r0 for the active orbitals (r holds
+// the starting residual, rr/thr/active/n_active are set, rz = beta = 0).
+template <class T>
+static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* pa, T* pb, T* q, int set_conv, cudaStream_t s) {
+    CgState& st = c->ws.cg;
+    const unsigned nb = (unsigned)c->nchunk_total;
+    const int TH = kChunkThreads;
+    const int max_iter = c->opt.max_iter;
+    const MgPtrs<T> mp = mg_ptrs<T>(c, r, z, q);
+    for (int it = 0; it < max_iter; ++it) {
+        if (it % 4 == 0) {
+            const int na = read_count(c, st.n_active, s);
+            if (na < 0) return FLOSIC_ERR_CUDA;
+            if (na == 0) break;
+        }
+        launch_vcycle<T>(c, mp, st.active, s);
+        launch_apply12_pcg<T>(c, z, pa, pb, q, s);
+        k_pcg_update<T><<<nb, TH, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, x, r, pb, q, max_iter, set_conv,
+                                          st); note_launch(c);
+        T* tmp = pa; pa = pb; pb = tmp;
+    }
+    return FLOSIC_OK;
+}
+
+// Solves A V = b for every orbital (b from launch_rhs, ||b||^2 in cg.bb).
+// Returns a flosic status; iteration counts and convergence flags stay in the
+// CG state (copied out by finish_poisson).
 int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream_t s) {
     Workspace& w = c->ws;
     CgState& st = w.cg;
@@ -507,30 +517,37 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
     const double tol2 = c->opt.cg_tol * c->opt.cg_tol;
     const int max_iter = c->opt.max_iter;
     const int check_every = 8;
+    const bool mg = c->mg.enabled;
     if (!warm && check_cuda(c, cudaMemsetAsync(V, 0, sizeof(double) * c->orb_elems, s), "memset V"))
         return FLOSIC_ERR_CUDA;
     k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st); note_launch(c);
     if (c->opt.precision == FLOSIC_FP64) {
-        k_residual64<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, b, V, w.r64, w.p64, 1,
-                                      tol2, max_iter, st.active, st.n_active, st); note_launch(c);
-        for (int it = 0; it < max_iter; ++it) {
-            if (it % check_every == 0) {
-                const int na = read_count(c, st.n_active, s);
-                if (na < 0) return FLOSIC_ERR_CUDA;
-                if (na == 0) break;
+        launch_residual12(c, b, V, w.r64, tol2, max_iter, st.active, st.n_active, 1, s);
+        if (!mg && check_cuda(c, cudaMemcpyAsync(w.p64, w.r64, sizeof(double) * c->orb_elems,
+                                                 cudaMemcpyDeviceToDevice, s), "copy p"))
+            return FLOSIC_ERR_CUDA;
+        if (mg) {
+            int rc = pcg_mg<double>(c, V, w.r64, w.z64, w.p64, w.p64b, w.q64, 1, s);
+            if (rc) return rc;
+        } else {
+            for (int it = 0; it < max_iter; ++it) {
+                if (it % check_every == 0) {
+                    const int na = read_count(c, st.n_active, s);
+                    if (na < 0) return FLOSIC_ERR_CUDA;
+                    if (na == 0) break;
+                }
+                prof_begin(c, s);
+                k_cg_apply<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p64, w.q64, st); note_launch(c);
+                prof_end(c, s);
+                k_cg_update<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, V, w.r64, w.p64,
+                                                     w.q64, max_iter, 1, st); note_launch(c);
+                k_cg_pupdate<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.p64, st); note_launch(c);
             }
-            prof_begin(c, s);
-            k_cg_apply<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p64, w.q64, st); note_launch(c);
-            prof_end(c, s);
-            k_cg_update<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, V, w.r64, w.p64,
-                                                 w.q64, max_iter, 1, st); note_launch(c);
-            k_cg_pupdate<double><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.p64, st); note_launch(c);
         }
     } else {
         const double inner_tol2 = 1e-10;   // each float32 solve gains ~5 digits
         for (int outer = 0; outer < 40; ++outer) {
-            k_residual64<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, b, V, w.r64, nullptr,
-                                          0, tol2, max_iter, st.oactive, st.n_oactive, st); note_launch(c);
+            launch_residual12(c, b, V, w.r64, tol2, max_iter, st.oactive, st.n_oactive, outer == 0 ? 1 : 0, s);
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
@@ -538,18 +555,23 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
                 return FLOSIC_ERR_CUDA;
             k_inner_init<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.r32, w.p32,
                                           w.d32, inner_tol2, tol2, st); note_launch(c);
-            for (int it = 0; it < max_iter; ++it) {
-                if (it % check_every == 0) {
-                    const int ni = read_count(c, st.n_active, s);
-                    if (ni < 0) return FLOSIC_ERR_CUDA;
-                    if (ni == 0) break;
+            if (mg) {
+                int rc = pcg_mg<float>(c, w.d32, w.r32, w.z32, w.p32, w.p32b, w.q32, 0, s);
+                if (rc) return rc;
+            } else {
+                for (int it = 0; it < max_iter; ++it) {
+                    if (it % check_every == 0) {
+                        const int ni = read_count(c, st.n_active, s);
+                        if (ni < 0) return FLOSIC_ERR_CUDA;
+                        if (ni == 0) break;
+                    }
+                    prof_begin(c, s);
+                    k_cg_apply<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p32, w.q32, st); note_launch(c);
+                    prof_end(c, s);
+                    k_cg_update<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, w.r32,
+                                                        w.p32, w.q32, max_iter, 0, st); note_launch(c);
+                    k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
                 }
-                prof_begin(c, s);
-                k_cg_apply<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.p32, w.q32, st); note_launch(c);
-                prof_end(c, s);
-                k_cg_update<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, w.r32,
-                                                    w.p32, w.q32, max_iter, 0, st); note_launch(c);
-                k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
             }
             k_correct<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, V, st); note_launch(c);
         }
@@ -559,100 +581,6 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
 
 void finish_poisson(flosic_ctx* c, int* iters, int* conv, cudaStream_t s) {
     k_cg_finish<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->ws.cg, iters, conv, c->ws.status); note_launch(c);
-}
-
-// ---------------------------------------------------------------------------
-// exact Poisson adjoint: transpose of the boundary map
-// ---------------------------------------------------------------------------
-// Coefficients c_m = sum_g W_g (1/h^2) sum_{ghost taps} w_m dV_b/dmom_m(R_tap).
-__global__ void k_bcadj_coef(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                             const int* __restrict__ orb_blk, const double* __restrict__ W,
-                             double* __restrict__ part) {
-    __shared__ double scratch[32];
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
-    const BlkDesc& B = blk[P.b];
-    const double ih2 = 1.0 / (B.h * B.h);
-    double cf[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) cf[q] = 0.0;
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.g0 + k;
-        int x, y, z;
-        xyz_of(g, B.nx, B.ny, x, y, z);
-        const int p[3] = {x, y, z};
-        const int n[3] = {B.nx, B.ny, B.nz};
-        bool near = false;
-        for (int d = 0; d < 3; ++d) near |= (p[d] < kHalf || p[d] >= n[d] - kHalf);
-        if (!near) continue;
-        const double wg = W[P.base + g] * ih2;
-        for (int d = 0; d < 3; ++d) {
-            for (int m = 1; m <= kHalf; ++m) {
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    const int qd = p[d] + sg * m;
-                    if (qd >= 0 && qd < n[d]) continue;
-                    int q[3] = {x, y, z};
-                    q[d] = qd;
-                    const double Rx = B.ox + B.h * q[0] - B.cx;
-                    const double Ry = B.oy + B.h * q[1] - B.cy;
-                    const double Rz = B.oz + B.h * q[2] - B.cz;
-                    const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-                    const double ir = rsqrt(r2), ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
-                    const double f = wg * c_w[m];
-                    cf[0] += f * ir;
-                    cf[1] += f * Rx * ir3;
-                    cf[2] += f * Ry * ir3;
-                    cf[3] += f * Rz * ir3;
-                    cf[4] += f * 0.5 * Rx * Rx * ir5;
-                    cf[5] += f * 0.5 * Ry * Ry * ir5;
-                    cf[6] += f * 0.5 * Rz * Rz * ir5;
-                    cf[7] += f * Rx * Ry * ir5;
-                    cf[8] += f * Rx * Rz * ir5;
-                    cf[9] += f * Ry * Rz * ir5;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-        const double s = block_sum(cf[q], scratch);
-        if (threadIdx.x == 0) part[t * 10 + q] = s;
-    }
-}
-
-// veff = (V + G^T rho)/2 with G^T rho = 4 pi W + dV sum_m c_m basis_m(R).
-__global__ void k_veff(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                       const int* __restrict__ orb_blk, const double* __restrict__ W,
-                       const double* __restrict__ V, const double* __restrict__ coef,
-                       double* __restrict__ veff) {
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
-    const BlkDesc& B = blk[P.b];
-    double c[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) c[q] = coef[P.o * 10 + q];
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.g0 + k;
-        int x, y, z;
-        xyz_of(g, B.nx, B.ny, x, y, z);
-        const double Rx = B.ox + B.h * x - B.cx, Ry = B.oy + B.h * y - B.cy, Rz = B.oz + B.h * z - B.cz;
-        const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-        const double kt = c[0] + c[1] * Rx + c[2] * Ry + c[3] * Rz + c[4] * (3 * Rx * Rx - r2) +
-                          c[5] * (3 * Ry * Ry - r2) + c[6] * (3 * Rz * Rz - r2) + c[7] * 3 * Rx * Ry +
-                          c[8] * 3 * Rx * Rz + c[9] * 3 * Ry * Rz;
-        const long long gi = P.base + g;
-        veff[gi] = 0.5 * (V[gi] + 4.0 * kPi * W[gi] + B.dV * kt);
-    }
-}
-
-void launch_bc_adjoint(const flosic_ctx* c, const double* W, const double* V, double* veff,
-                       cudaStream_t s) {
-    k_bcadj_coef<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb,
-                                                                     c->d_orb_blk, W, c->ws.mom_part); note_launch(c);
-    k_sum_chunks10<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                              c->ws.mom_part, c->ws.mom, 0); note_launch(c);
-    k_veff<<<(unsigned)c->nchunk_total, kChunkThreads, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk,
-                                                               W, V, c->ws.mom, veff); note_launch(c);
 }
 
 }  // namespace flosic

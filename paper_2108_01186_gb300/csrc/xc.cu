@@ -12,10 +12,14 @@ namespace flosic {
 
 constexpr int kXcPts = kChunk / kChunkThreads;   // points per thread
 
+// kF32: pointwise functional in float32 (mixed precision); sums in float64.
+// Also stores V_i^SIC = -(V_i + v_xc,i) for the reverse mode.
+template <bool kF32>
 __global__ void __launch_bounds__(kChunkThreads)
 k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double* __restrict__ phi, const double* __restrict__ V, double scale,
-            double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part) {
+            double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part,
+            double* __restrict__ vsic) {
     __shared__ double red[kChunkThreads / 32][kMaxN][2];
     const BlkDesc& B = blk[blockIdx.y];
     const int c = blockIdx.x;
@@ -35,10 +39,19 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double f = phi[base + g], v = V[base + g], p = psi[base + g];
             const double rho = f * f;
             double eps, vxc;
-            lsda_pol(rho, rho_min, eps, vxc);
+            if (kF32) {
+                float ef, vf;
+                lsda_pol_f((float)rho, (float)rho_min, ef, vf);
+                eps = ef;
+                vxc = vf;
+            } else {
+                lsda_pol(rho, rho_min, eps, vxc);
+            }
             u += rho * v;
             ex += rho * eps;
-            num[k] -= rho * (v + vxc);
+            const double vs = -(v + vxc);
+            vsic[base + g] = vs;
+            num[k] += rho * vs;
             rs[k] += p * p;
         }
         u = warp_sum(u);
@@ -69,8 +82,13 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
     int cmax = 0;
     for (const auto& b : c->blk) cmax = b.nchunk > cmax ? b.nchunk : cmax;
     const dim3 grid(cmax, c->nblk);
-    k_xc_energy<<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                               c->ws.e_part); note_launch(c);
+    if (c->opt.precision == FLOSIC_MIXED)
+        k_xc_energy<true><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
+                                                         c->ws.e_part, c->ws.vsic);
+    else
+        k_xc_energy<false><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
+                                                          c->ws.e_part, c->ws.vsic);
+    note_launch(c);
 }
 
 // One warp per orbital: U_i = (dV/2) sum rho V, E_xc,i = dV sum rho eps.

@@ -43,4 +43,27 @@ __device__ __forceinline__ void lsda_pol(double n, double rho_min, double& eps, 
     v = -k + ec - rs * (1.0 / 3.0) * dec;
 }
 
+// The same functional in float32 arithmetic (mixed-precision path; the
+// energies are still summed in float64).
+__device__ __forceinline__ void lsda_pol_f(float n, float rho_min, float& eps, float& v) {
+    if (!(n > rho_min)) {
+        eps = 0.0f;
+        v = 0.0f;
+        return;
+    }
+    const float k = cbrtf(n * (float)(6.0 / 3.14159265358979323846));
+    const float rs = cbrtf((float)(3.0 / (4.0 * 3.14159265358979323846)) / n);
+    const float srs = sqrtf(rs);
+    using P = Pw92Ferro;
+    const float A = (float)P::A;
+    const float den = 2.0f * A * ((float)P::b1 * srs + (float)P::b2 * rs + (float)P::b3 * rs * srs + (float)P::b4 * rs * rs);
+    const float dden = A * ((float)P::b1 / srs + 2.0f * (float)P::b2 + 3.0f * (float)P::b3 * srs + 4.0f * (float)P::b4 * rs);
+    const float lg = log1pf(1.0f / den);
+    const float pre = -2.0f * A * (1.0f + (float)P::a1 * rs);
+    const float ec = pre * lg;
+    const float dec = -2.0f * A * (float)P::a1 * lg - pre * dden / (den * den + den);
+    eps = -0.75f * k + ec;
+    v = -k + ec - rs * (1.0f / 3.0f) * dec;
+}
+
 }  // namespace flosic
