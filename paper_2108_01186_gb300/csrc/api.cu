@@ -4,6 +4,9 @@
 #include <cstring>
 #include <new>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 using namespace flosic;
@@ -49,6 +52,43 @@ int validate_options(const flosic_options& o, std::string& why) {
     else if (o.preconditioner != FLOSIC_PC_NONE && o.preconditioner != FLOSIC_PC_MG) why = "bad preconditioner";
     else return 0;
     return 1;
+}
+
+// Tensor maps of the level-0 z buffer, one per block: a 4-D view (x, y, z,
+// orbital) with 48 x 28 x 1 x 1 boxes (tile plus halo).  Returns false (and
+// the caller keeps the plain-load stencil) when a block's rows or offset are
+// not 16-byte aligned or the driver entry point is missing.
+bool setup_tensor_maps(flosic_ctx* c, const void* zbuf, size_t elem) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    std::vector<CUtensorMap> maps(c->nblk);
+    for (int b = 0; b < c->nblk; ++b) {
+        const BlkDesc& B = c->blk[b];
+        if ((B.nx * elem) % 16 != 0 || (B.off * (long long)elem) % 16 != 0) return false;
+        const cuuint64_t dims[4] = {(cuuint64_t)B.nx, (cuuint64_t)B.ny, (cuuint64_t)B.nz, (cuuint64_t)B.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)B.nx * elem, (cuuint64_t)B.nx * B.ny * elem,
+                                       (cuuint64_t)B.G * elem};
+        const cuuint32_t box[4] = {48, (cuuint32_t)(kTileY + 2 * kHalf), 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        void* base = (unsigned char*)zbuf + B.off * (long long)elem;
+        CUresult r = encode(&maps[b], elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                            base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(CUtensorMap) * c->nblk) != cudaSuccess) return false;
+    c->allocations.push_back(d);
+    if (cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * c->nblk, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(apply12_tma_symbol(elem == 4), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)apply12_tma_smem(elem)) != cudaSuccess)
+        return false;
+    c->d_tmaps = d;
+    return true;
 }
 
 // Waits for the stream and returns the device status words.
@@ -335,6 +375,11 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(double) * nmax * nmax));
     }
+    if (e == cudaSuccess && M.enabled) {
+        const bool f32 = (o.precision == FLOSIC_MIXED);
+        c->tma_ok = setup_tensor_maps(c, f32 ? (const void*)w.z32 : (const void*)w.z64, f32 ? 4 : 8);
+        cudaGetLastError();   // a refused attribute or entry point only disables the copy-engine path
+    }
     if (e != cudaSuccess) {
         g_create_error = std::string("workspace set-up: ") + cudaGetErrorString(e);
         release(c);
@@ -399,6 +444,7 @@ int flosic_orbital_poisson(flosic_ctx* c, const double* phi, double* V, int warm
     int st[4];
     rc = read_status(c, s, st);
     if (rc) return rc;
+    if (st[3]) return fail(c, FLOSIC_ERR_CUDA, "a stencil copy did not complete (bounded wait expired)");
     if (st[1]) return fail(c, FLOSIC_ERR_NOCONV, "a Poisson solve reached max_iter");
     return FLOSIC_OK;
 }

@@ -149,13 +149,15 @@ struct LoadPhibar {
     }
 };
 
-template <int RM, class LA, class LB>
+// TC: arithmetic of the products and of the sum within one 16-point k tile
+// (float in mixed precision); tile sums accumulate in float64.
+template <int RM, class TC, class LA, class LB>
 __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ blk, int kparts, LA la,
                                                   LB lb, double* __restrict__ part, long long mat_elems) {
     constexpr int KT = 16;
     constexpr int NP = 16 * RM;
-    __shared__ double As[KT][NP + 1];
-    __shared__ double Bs[KT][NP + 1];
+    __shared__ TC As[KT][NP + 1];
+    __shared__ TC Bs[KT][NP + 1];
     const BlkDesc& B = blk[blockIdx.y];
     const int N = B.N;
     const long long G = B.G;
@@ -172,13 +174,18 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
             const int i = idx / KT, kk = idx % KT;
             const long long g = k0 + kk;
             const bool ok = (i < N) && (g < ke);
-            As[kk][i] = ok ? la(B, i, g) : 0.0;
-            Bs[kk][i] = ok ? lb(B, i, g) : 0.0;
+            As[kk][i] = ok ? (TC)la(B, i, g) : TC(0);
+            Bs[kk][i] = ok ? (TC)lb(B, i, g) : TC(0);
         }
         __syncthreads();
+        TC tacc[RM][RM];
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+            for (int q = 0; q < RM; ++q) tacc[r][q] = TC(0);
 #pragma unroll 4
         for (int kk = 0; kk < KT; ++kk) {
-            double a[RM], bv[RM];
+            TC a[RM], bv[RM];
 #pragma unroll
             for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + 16 * r];
 #pragma unroll
@@ -186,8 +193,12 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
-                for (int q = 0; q < RM; ++q) acc[r][q] += a[r] * bv[q];
+                for (int q = 0; q < RM; ++q) tacc[r][q] += a[r] * bv[q];
         }
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+#pragma unroll
+            for (int q = 0; q < RM; ++q) acc[r][q] += (double)tacc[r][q];
         __syncthreads();
     }
 #pragma unroll
@@ -220,14 +231,18 @@ static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_
     const int nmax = max_block_n(c);
     const dim3 grid(c->kparts, c->nblk);
     double* part = c->ws.mat_part;
-    if (nmax <= 16)
-        k_contract<1><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-    else if (nmax <= 32)
-        k_contract<2><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-    else if (nmax <= 64)
-        k_contract<4><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-    else
-        k_contract<8><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    const bool f32 = (c->opt.precision == FLOSIC_MIXED);
+    if (f32) {
+        if (nmax <= 16) k_contract<1, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 32) k_contract<2, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 64) k_contract<4, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else k_contract<8, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    } else {
+        if (nmax <= 16) k_contract<1, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 32) k_contract<2, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 64) k_contract<4, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else k_contract<8, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+    }
     note_launch(c);
     k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out); note_launch(c);
 }
@@ -434,33 +449,34 @@ struct LoadPhibarPsi {   // rows 0..N-1: Phibar; rows N..2N-1: psi
     }
 };
 
-template <int RJ, class LX>
+// TC: arithmetic of the products and sums (float in mixed precision).
+template <int RJ, class TC, class LX>
 __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ blk,
                                                   const double* __restrict__ E, int mult, LX lx,
                                                   double* __restrict__ out) {
     constexpr int TG = 32, KC = 32;
-    __shared__ double Es[8 * RJ][KC + 1];
-    __shared__ double Xs[KC][TG];
+    __shared__ TC Es[8 * RJ][KC + 1];
+    __shared__ TC Xs[KC][TG];
     const BlkDesc& B = blk[blockIdx.y];
     const int N = B.N, K = mult * N;
     const double* Eb = E + mult * B.moff;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     for (long long tile = blockIdx.x; tile * TG < B.G; tile += gridDim.x) {
         const long long g = tile * TG + lane;
-        double acc[RJ];
+        TC acc[RJ];
 #pragma unroll
-        for (int r = 0; r < RJ; ++r) acc[r] = 0.0;
+        for (int r = 0; r < RJ; ++r) acc[r] = TC(0);
         for (int kc = 0; kc < K; kc += KC) {
             for (int e = threadIdx.x; e < 8 * RJ * KC; e += 256) {
                 const int j = e / KC, kk = e % KC;
-                Es[j][kk] = (j < N && kc + kk < K) ? Eb[(long long)j * K + kc + kk] : 0.0;
+                Es[j][kk] = (j < N && kc + kk < K) ? (TC)Eb[(long long)j * K + kc + kk] : TC(0);
             }
             for (int kk = wq; kk < KC; kk += 8)
-                Xs[kk][lane] = (kc + kk < K && g < B.G) ? lx(B, kc + kk, g) : 0.0;
+                Xs[kk][lane] = (kc + kk < K && g < B.G) ? (TC)lx(B, kc + kk, g) : TC(0);
             __syncthreads();
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                const double x = Xs[kk][lane];
+                const TC x = Xs[kk][lane];
 #pragma unroll
                 for (int r = 0; r < RJ; ++r) acc[r] += Es[wq + 8 * r][kk] * x;
             }
@@ -470,7 +486,7 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
 #pragma unroll
             for (int r = 0; r < RJ; ++r) {
                 const int j = wq + 8 * r;
-                if (j < N) out[B.off + (long long)j * B.G + g] = acc[r];
+                if (j < N) out[B.off + (long long)j * B.G + g] = (double)acc[r];
             }
         }
     }
@@ -483,14 +499,17 @@ static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, doub
     for (const auto& b : c->blk) gmax = b.G > gmax ? b.G : gmax;
     const unsigned gx = (unsigned)((gmax + 31) / 32 < 65535 ? (gmax + 31) / 32 : 65535);
     const dim3 grid(gx, c->nblk);
-    if (nmax <= 16)
-        k_smallmat<2><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-    else if (nmax <= 32)
-        k_smallmat<4><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-    else if (nmax <= 64)
-        k_smallmat<8><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-    else
-        k_smallmat<16><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    if (c->opt.precision == FLOSIC_MIXED) {
+        if (nmax <= 16) k_smallmat<2, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 32) k_smallmat<4, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 64) k_smallmat<8, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else k_smallmat<16, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    } else {
+        if (nmax <= 16) k_smallmat<2, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 32) k_smallmat<4, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 64) k_smallmat<8, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else k_smallmat<16, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    }
     note_launch(c);
 }
 

@@ -99,7 +99,7 @@ struct Workspace {
     float *d32, *r32, *p32, *q32;    // FP32 inner CG vectors
     double* veff;                    // exact adjoint: zero-boundary solve, then its V^SIC
     double* vsic;                    // V_i^SIC = -(V_i + v_xc,i) of the last energy pass
-    double *z64, *p64b;              // multigrid PCG (FP64)
+    double *z64, *p64b;              // multigrid PCG (FP64): z = M r, V-cycle scratch
     float *z32, *p32b;               // multigrid PCG (FP32)
     CgState cg;
 };
@@ -143,6 +143,8 @@ struct flosic_ctx {
     std::string err;
     int* h_pinned = nullptr;                // small pinned host buffer
     mutable long long launches = 0;         // kernels launched by this context
+    bool tma_ok = false;                    // stencil planes staged by the copy engine
+    void* d_tmaps = nullptr;                // per-block tensor maps of the z buffer (CUtensorMap)
     // optional CUDA-event timing of the dominant kernel (the CG stencil apply)
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;       // start/stop pairs, recorded in order
@@ -182,7 +184,9 @@ void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E
 template <class T>
 void launch_vcycle(const flosic_ctx* c, const MgPtrs<T>& mp, const int* active, cudaStream_t s);
 template <class T>
-void launch_apply12_pcg(flosic_ctx* c, const T* z, const T* pold, T* pnew, T* q, cudaStream_t s);
+void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s);
+size_t apply12_tma_smem(size_t elem);
+const void* apply12_tma_symbol(bool f32);
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s);
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
@@ -193,6 +197,7 @@ inline void note_launch(const flosic_ctx* c) { ++c->launches; }
 void prof_begin(flosic_ctx* c, cudaStream_t s);
 void prof_end(flosic_ctx* c, cudaStream_t s);
 void prof_collect(flosic_ctx* c);   // after a stream sync: sum recorded pairs
+
 
 }  // namespace flosic
 
@@ -284,6 +289,64 @@ __device__ __forceinline__ double tile_gather(const double* part, long long firs
     const int nt = blockDim.x * blockDim.y * blockDim.z;
     for (int k = linear_tid(); k < n; k += nt) v += __ldcg(part + first + k);
     return block_sum(v, scratch);
+}
+
+template <class T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+
+// Elementwise sweep over one tile, vectorised along x when the rows are
+// aligned (nx a multiple of the vector width); body(g, n) handles n
+// consecutive points starting at flat index g (n = vector width, or 1).
+template <class T, class Body>
+__device__ __forceinline__ void tile_elementwise(const LvlDesc& D, const TilePos& P, Body body) {
+    constexpr int V = Vec<T>::n;
+    constexpr int XG = kTileX / V;               // vector groups per row
+    constexpr int RPI = 256 / XG;                // rows per pass
+    const int tid = linear_tid();
+    const int xg = tid % XG, r0 = tid / XG;
+    const int nz = P.z1 - P.z0;
+    const int nrows = kTileY * nz;
+    const bool vec = (D.nx % V == 0) && (P.base % V == 0);
+    const int x = P.x0 + xg * V;
+#pragma unroll 4
+    for (int row = r0; row < nrows; row += RPI) {
+        const int y = P.y0 + row % kTileY, z = P.z0 + row / kTileY;
+        if (y >= D.ny || x >= D.nx) continue;
+        const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
+        if (vec) {
+            body(g, V);
+        } else {
+            for (int k = 0; k < V && x + k < D.nx; ++k) body(g + k, 1);
+        }
+    }
+}
+
+
+
+// Same sweep, passing the coordinates of the first point: body(x, y, z, g, n).
+template <class T, class Body>
+__device__ __forceinline__ void tile_rows(const LvlDesc& D, const TilePos& P, Body body) {
+    constexpr int V = Vec<T>::n;
+    constexpr int XG = kTileX / V;
+    constexpr int RPI = 256 / XG;
+    const int tid = linear_tid();
+    const int xg = tid % XG, r0 = tid / XG;
+    const int nz = P.z1 - P.z0;
+    const int nrows = kTileY * nz;
+    const bool vec = (D.nx % V == 0) && (P.base % V == 0);
+    const int x = P.x0 + xg * V;
+#pragma unroll 2
+    for (int row = r0; row < nrows; row += RPI) {
+        const int y = P.y0 + row % kTileY, z = P.z0 + row / kTileY;
+        if (y >= D.ny || x >= D.nx) continue;
+        const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
+        if (vec) {
+            body(x, y, z, g, V);
+        } else {
+            for (int k = 0; k < V && x + k < D.nx; ++k) body(x + k, y, z, g + k, 1);
+        }
+    }
 }
 
 }  // namespace flosic

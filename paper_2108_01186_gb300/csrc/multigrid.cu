@@ -51,19 +51,73 @@ __device__ __forceinline__ T nbr6(const T* __restrict__ u, long long g, int x, i
     return s;
 }
 
+// Gathers, for n consecutive points starting at (x, y, z) (n = vector width
+// or 1), the centre values and the sum of the six neighbours (zero outside).
+template <class T, int V>
+__device__ __forceinline__ void centre_nbr(const T* __restrict__ u, const LvlDesc& D, int x, int y, int z,
+                                           long long g, int n, T* c, T* nb) {
+    using VT = typename Vec<T>::type;
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    if (n == V) {
+        const VT cv = *reinterpret_cast<const VT*>(u + g);
+        VT ym, yp, zm, zp;
+        const T* cs = reinterpret_cast<const T*>(&cv);
+        T zero[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) zero[k] = T(0);
+        ym = (y > 0) ? *reinterpret_cast<const VT*>(u + g - sy) : *reinterpret_cast<const VT*>(zero);
+        yp = (y < D.ny - 1) ? *reinterpret_cast<const VT*>(u + g + sy) : *reinterpret_cast<const VT*>(zero);
+        zm = (z > 0) ? *reinterpret_cast<const VT*>(u + g - sz) : *reinterpret_cast<const VT*>(zero);
+        zp = (z < D.nz - 1) ? *reinterpret_cast<const VT*>(u + g + sz) : *reinterpret_cast<const VT*>(zero);
+        const T xl = (x > 0) ? u[g - 1] : T(0);
+        const T xr = (x + V < D.nx) ? u[g + V] : T(0);
+        const T* a = reinterpret_cast<const T*>(&ym);
+        const T* b = reinterpret_cast<const T*>(&yp);
+        const T* cz = reinterpret_cast<const T*>(&zm);
+        const T* d = reinterpret_cast<const T*>(&zp);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            c[k] = cs[k];
+            const T left = (k == 0) ? xl : cs[k - 1];
+            const T right = (k == V - 1) ? xr : cs[k + 1];
+            nb[k] = left + right + a[k] + b[k] + cz[k] + d[k];
+        }
+    } else {
+        c[0] = u[g];
+        T sum = 0;
+        if (x > 0) sum += u[g - 1];
+        if (x < D.nx - 1) sum += u[g + 1];
+        if (y > 0) sum += u[g - sy];
+        if (y < D.ny - 1) sum += u[g + sy];
+        if (z > 0) sum += u[g - sz];
+        if (z < D.nz - 1) sum += u[g + sz];
+        nb[0] = sum;
+    }
+}
+
+template <class T, int V>
+__device__ __forceinline__ void store_n(T* dst, const T* v, int n) {
+    using VT = typename Vec<T>::type;
+    if (n == V) *reinterpret_cast<VT*>(dst) = *reinterpret_cast<const VT*>(v);
+    else dst[0] = v[0];
+}
+
 // s = r - A2 (omega D^-1 r) = (1 - omega) r + (omega/6) sum_nbr r
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_resid_smooth(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                          const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                          const int* __restrict__ active, const T* __restrict__ r,
                                                          T* __restrict__ s, T omega) {
+    constexpr int V = Vec<T>::n;
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
     if (!active[P.o] || D.coarsest) return;
-    const T* rb = r + P.base;
-    T* sb = s + P.base;
-    for_tile_points(D, P, [&](int x, int y, int z, long long g) {
-        sb[g] = (T(1) - omega) * rb[g] + omega * T(1.0 / 6.0) * nbr6(rb, g, x, y, z, D);
+    tile_rows<T>(D, P, [&](int x, int y, int z, long long g, int n) {
+        T c[V], nb[V], out[V];
+        centre_nbr<T, V>(r, D, x, y, z, g, n, c, nb);
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = (T(1) - omega) * c[k] + omega * T(1.0 / 6.0) * nb[k];
+        store_n<T, V>(s + g, out, n);
     });
 }
 
@@ -73,73 +127,51 @@ __global__ void __launch_bounds__(256) k_mg_restrict(const BlkDesc* __restrict__
                                                      const LvlDesc* __restrict__ Lf, const int4* __restrict__ tiles_c,
                                                      const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                      const T* __restrict__ sf, T* __restrict__ rc) {
+    constexpr int V = Vec<T>::n;
     const TilePos P = tile_pos(blk, Lc, tiles_c, orb_blk, blockIdx.x);
     if (!active[P.o]) return;
     const LvlDesc& C = Lc[P.b];
     const LvlDesc& F = Lf[P.b];
     const T* fb = sf + F.off + (long long)(P.o - blk[P.b].orb0) * F.G;
-    T* cb = rc + P.base;
     const long long fy = F.nx, fz = (long long)F.nx * F.ny;
-    for_tile_points(C, P, [&](int X, int Y, int Z, long long g) {
-        T acc = 0;
+    tile_rows<T>(C, P, [&](int X, int Y, int Z, long long g, int n) {
+        T acc[V];
 #pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = T(0);
+        const int xf0 = 2 * X;
         for (int c = 0; c < 3; ++c) {
             const int zf = 2 * Z + c;
             if (zf >= F.nz) continue;
             const T wc = (c == 1) ? T(0.5) : T(0.25);
-#pragma unroll
             for (int b = 0; b < 3; ++b) {
                 const int yf = 2 * Y + b;
                 if (yf >= F.ny) continue;
-                const T wb = (b == 1) ? T(0.5) : T(0.25);
-                const T* row = fb + zf * fz + yf * fy + 2 * X;
-                T rsum = T(0.25) * row[0] + T(0.5) * row[1];
-                if (2 * X + 2 < F.nx) rsum += T(0.25) * row[2];
-                acc += wc * wb * rsum;
+                const T w = wc * ((b == 1) ? T(0.5) : T(0.25));
+                const T* row = fb + zf * fz + yf * fy;
+                T f[2 * V + 1];
+#pragma unroll
+                for (int k = 0; k < 2 * V + 1; ++k) f[k] = (xf0 + k < F.nx) ? row[xf0 + k] : T(0);
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    acc[k] += w * (T(0.25) * f[2 * k] + T(0.5) * f[2 * k + 1] + T(0.25) * f[2 * k + 2]);
             }
         }
-        cb[g] = acc;
+        store_n<T, V>(rc + g, acc, n);
     });
 }
 
-// trilinear prolongation of the coarse correction at fine point (x, y, z)
+// trilinear prolongation at fine x from one coarse row (OOB zero)
 template <class T>
-__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, const LvlDesc& C, int x, int y, int z) {
-    int I0[3], I1[3];
-    T w0[3], w1[3];
-    const int p[3] = {x, y, z};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (p[d] & 1) {              // on a coarse point
-            I0[d] = (p[d] - 1) >> 1; w0[d] = T(1);
-            I1[d] = -1;              w1[d] = T(0);
-        } else {                     // halfway between two coarse points
-            I0[d] = (p[d] >> 1) - 1; w0[d] = T(0.5);
-            I1[d] = p[d] >> 1;       w1[d] = T(0.5);
-        }
+__device__ __forceinline__ T prolong_x(const T* __restrict__ row, int ncx, int x) {
+    if (x & 1) {
+        const int I = (x - 1) >> 1;
+        return (I < ncx) ? row[I] : T(0);
     }
-    const int n[3] = {C.nx, C.ny, C.nz};
-    T acc = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int Z = c ? I1[2] : I0[2];
-        const T wz = c ? w1[2] : w0[2];
-        if (Z < 0 || Z >= n[2] || wz == T(0)) continue;
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const int Y = b ? I1[1] : I0[1];
-            const T wy = b ? w1[1] : w0[1];
-            if (Y < 0 || Y >= n[1] || wy == T(0)) continue;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int X = a ? I1[0] : I0[0];
-                const T wx = a ? w1[0] : w0[0];
-                if (X < 0 || X >= n[0] || wx == T(0)) continue;
-                acc += wz * wy * wx * ec[((long long)Z * n[1] + Y) * n[0] + X];
-            }
-        }
-    }
-    return acc;
+    const int I0 = (x >> 1) - 1, I1 = x >> 1;
+    T v = 0;
+    if (I0 >= 0) v += row[I0];
+    if (I1 < ncx) v += row[I1];
+    return T(0.5) * v;
 }
 
 // t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction)
@@ -149,15 +181,47 @@ __global__ void __launch_bounds__(256) k_mg_prolong(const BlkDesc* __restrict__ 
                                                     const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                     const T* __restrict__ r, const T* __restrict__ ec,
                                                     T* __restrict__ t, T omega) {
+    constexpr int V = Vec<T>::n;
+    using VT = typename Vec<T>::type;
     const TilePos P = tile_pos(blk, Lf, tiles_f, orb_blk, blockIdx.x);
     const LvlDesc& F = Lf[P.b];
     if (!active[P.o] || F.coarsest) return;
     const LvlDesc& C = Lc[P.b];
     const T* eb = ec + C.off + (long long)(P.o - blk[P.b].orb0) * C.G;
-    const T* rb = r + P.base;
-    T* tb = t + P.base;
     const T dinv = omega * T(F.h * F.h / 6.0);
-    for_tile_points(F, P, [&](int x, int y, int z, long long g) { tb[g] = dinv * rb[g] + prolong_at(eb, C, x, y, z); });
+    tile_rows<T>(F, P, [&](int x, int y, int z, long long g, int n) {
+        // coarse rows and weights along y and z
+        int Ys[2], Zs[2];
+        T wy[2], wz[2];
+        int ny_ = 0, nz_ = 0;
+        if (y & 1) { Ys[0] = (y - 1) >> 1; wy[0] = T(1); ny_ = 1; }
+        else { Ys[0] = (y >> 1) - 1; Ys[1] = y >> 1; wy[0] = wy[1] = T(0.5); ny_ = 2; }
+        if (z & 1) { Zs[0] = (z - 1) >> 1; wz[0] = T(1); nz_ = 1; }
+        else { Zs[0] = (z >> 1) - 1; Zs[1] = z >> 1; wz[0] = wz[1] = T(0.5); nz_ = 2; }
+        T out[V];
+        T rv[V];
+        if (n == V) {
+            const VT v = *reinterpret_cast<const VT*>(r + g);
+#pragma unroll
+            for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
+        } else {
+            rv[0] = r[g];
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = (k < n) ? dinv * rv[k] : T(0);
+        for (int a = 0; a < nz_; ++a) {
+            if (Zs[a] < 0 || Zs[a] >= C.nz) continue;
+            for (int b = 0; b < ny_; ++b) {
+                if (Ys[b] < 0 || Ys[b] >= C.ny) continue;
+                const T w = wz[a] * wy[b];
+                const T* row = eb + ((long long)Zs[a] * C.ny + Ys[b]) * C.nx;
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    if (k < n) out[k] += w * prolong_x(row, C.nx, x + k);
+            }
+        }
+        store_n<T, V>(t + g, out, n);
+    });
 }
 
 // e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/6)(h^2 r + sum_nbr t);
@@ -168,20 +232,30 @@ __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict
                                                        const int* __restrict__ active, const T* __restrict__ r,
                                                        const T* __restrict__ t, T* __restrict__ e, T omega,
                                                        CgState st) {
+    constexpr int V = Vec<T>::n;
+    using VT = typename Vec<T>::type;
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
     if (!active[P.o] || D.coarsest) return;
-    const T* tb = t + P.base;
-    const T* rb = r + P.base;
-    T* eb = e + P.base;
     const T h2 = T(D.h * D.h);
     double rz = 0.0;
-    for_tile_points(D, P, [&](int x, int y, int z, long long g) {
-        const T rv = rb[g];
-        const T ev = (T(1) - omega) * tb[g] + omega * T(1.0 / 6.0) * (h2 * rv + nbr6(tb, g, x, y, z, D));
-        eb[g] = ev;
-        if (kLevel0) rz += (double)rv * (double)ev;
+    tile_rows<T>(D, P, [&](int x, int y, int z, long long g, int n) {
+        T c[V], nb[V], rv[V], out[V];
+        centre_nbr<T, V>(t, D, x, y, z, g, n, c, nb);
+        if (n == V) {
+            const VT v = *reinterpret_cast<const VT*>(r + g);
+#pragma unroll
+            for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
+        } else {
+            rv[0] = r[g];
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            out[k] = (T(1) - omega) * c[k] + omega * T(1.0 / 6.0) * (h2 * rv[k] + nb[k]);
+            if (kLevel0 && k < n) rz += (double)rv[k] * (double)out[k];
+        }
+        store_n<T, V>(e + g, out, n);
     });
     if (kLevel0) {
         if (tile_arrive(rz, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {

@@ -392,38 +392,142 @@ __global__ void k_pcg_update(const BlkDesc* __restrict__ blk, const int* __restr
     }
 }
 
-// Start of an inner float32 solve of A d = r64 for orbitals still refining:
-// r32 = p32 = float(r64), d32 = 0, rr = r32.r32; inner target
-// thr = max(inner_tol^2 rr, (tol^2/4) bb).
-__global__ void k_inner_init(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                             const int* __restrict__ orb_blk, const double* __restrict__ r64,
-                             float* __restrict__ r32, float* __restrict__ p32, float* __restrict__ d32,
-                             double inner_tol2, double tol2, CgState st) {
+// x += alpha p, r -= alpha q with alpha = rz/pq; rr = r.r decides
+// convergence (tile version, vectorised).
+template <class T>
+__global__ void __launch_bounds__(256) k_pcg_update_t(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                      T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                      const T* __restrict__ q, int max_iter, int set_conv, CgState st) {
+    using VT = typename Vec<T>::type;
     __shared__ double scratch[32];
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
-    if (!st.oactive[P.o]) return;
-    const BlkDesc& B = blk[P.b];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.active[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    const double pqv = st.pq[P.o];
+    const T alpha = (pqv > 0.0) ? (T)(st.rz[P.o] / pqv) : (T)0;
     double rr = 0.0;
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.base + P.g0 + k;
-        const float v = (float)r64[g];
-        r32[g] = v;
-        p32[g] = v;
-        d32[g] = 0.0f;
-        rr += (double)v * (double)v;
-    }
-    if (arrive(rr, st.part, t, st.count + P.o, B.nchunk, scratch)) {
-        const double s = gather_sum(st.part, P.first, B.nchunk, scratch);
-        if (threadIdx.x == 0) {
+    tile_elementwise<T>(D, P, [&](long long g, int n) {
+        if (n > 1) {
+            VT xv = *reinterpret_cast<VT*>(x + g);
+            VT rv = *reinterpret_cast<VT*>(r + g);
+            const VT pv = *reinterpret_cast<const VT*>(p + g);
+            const VT qv = *reinterpret_cast<const VT*>(q + g);
+            T* xs = reinterpret_cast<T*>(&xv);
+            T* rs = reinterpret_cast<T*>(&rv);
+            const T* ps = reinterpret_cast<const T*>(&pv);
+            const T* qs = reinterpret_cast<const T*>(&qv);
+#pragma unroll
+            for (int k = 0; k < Vec<T>::n; ++k) {
+                xs[k] += alpha * ps[k];
+                rs[k] -= alpha * qs[k];
+                rr += (double)rs[k] * (double)rs[k];
+            }
+            *reinterpret_cast<VT*>(x + g) = xv;
+            *reinterpret_cast<VT*>(r + g) = rv;
+        } else {
+            x[g] += alpha * p[g];
+            const T rv = r[g] - alpha * q[g];
+            r[g] = rv;
+            rr += (double)rv * (double)rv;
+        }
+    });
+    if (tile_arrive(rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
             const int o = P.o;
             st.count[o] = 0;
-            st.rr[o] = s;
+            st.rr[o] = sum;
+            const int it = ++st.iters[o];
+            if (!(sum > st.thr[o])) {
+                st.active[o] = 0;
+                if (set_conv) st.conv[o] = 1;
+                atomicSub(st.n_active, 1);
+            } else if (it >= max_iter || !isfinite(sum) || !(pqv > 0.0)) {
+                st.active[o] = 0;
+                atomicSub(st.n_active, 1);
+            }
+        }
+    }
+}
+
+// Residual of a zero start vector: r = b, rr = bb = b.b; same stopping
+// logic as the stencil residual kernel.
+__global__ void __launch_bounds__(256) k_residual_zero(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                       const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                       const double* __restrict__ b, double* __restrict__ r,
+                                                       double tol2, int* __restrict__ flag, int* __restrict__ counter,
+                                                       CgState st) {
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!flag[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    double bb = 0.0;
+    tile_elementwise<double>(D, P, [&](long long g, int n) {
+        for (int k = 0; k < n; ++k) {
+            const double v = b[g + k];
+            r[g + k] = v;
+            bb += v * v;
+        }
+    });
+    if (tile_arrive(bb, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            const int o = P.o;
+            st.count[o] = 0;
+            st.rr[o] = sum;
+            st.bb[o] = sum;
+            st.thr[o] = tol2 * sum;
+            if (!(sum > st.thr[o])) {
+                flag[o] = 0;
+                st.conv[o] = 1;
+                atomicSub(counter, 1);
+            }
+        }
+    }
+}
+
+// Start of an inner float32 solve (tile version): r32 = float(r64),
+// d32 = 0 (p32 = r32 when given, for the unpreconditioned solver);
+// rr = r32.r32; inner target thr = max(inner_tol^2 rr, (tol^2/4) bb).
+__global__ void __launch_bounds__(256) k_inner_init_t(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                      const double* __restrict__ r64, float* __restrict__ r32,
+                                                      float* __restrict__ p32, float* __restrict__ d32,
+                                                      double inner_tol2, double tol2, CgState st) {
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    double rr = 0.0;
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {
+            const double2 a = *reinterpret_cast<const double2*>(r64 + g);
+            const double2 b = *reinterpret_cast<const double2*>(r64 + g + 2);
+            const float4 v = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+            *reinterpret_cast<float4*>(r32 + g) = v;
+            if (p32) *reinterpret_cast<float4*>(p32 + g) = v;
+            *reinterpret_cast<float4*>(d32 + g) = make_float4(0.f, 0.f, 0.f, 0.f);
+            rr += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        } else {
+            const float v = (float)r64[g];
+            r32[g] = v;
+            if (p32) p32[g] = v;
+            d32[g] = 0.0f;
+            rr += (double)v * (double)v;
+        }
+    });
+    if (tile_arrive(rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            const int o = P.o;
+            st.count[o] = 0;
+            st.rr[o] = sum;
             st.rz[o] = 0.0;
             st.beta[o] = 0.0;
-            const double a = inner_tol2 * s, c = 0.25 * tol2 * st.bb[o];
+            const double a = inner_tol2 * sum, c = 0.25 * tol2 * st.bb[o];
             st.thr[o] = a > c ? a : c;
-            if (s > st.thr[o]) {
+            if (sum > st.thr[o]) {
                 st.active[o] = 1;
                 atomicAdd(st.n_active, 1);
             } else {
@@ -433,17 +537,25 @@ __global__ void k_inner_init(const BlkDesc* __restrict__ blk, const int* __restr
     }
 }
 
-// x64 += d32 for orbitals still refining.
-__global__ void k_correct(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
-                          const int* __restrict__ orb_blk, const float* __restrict__ d32,
-                          double* __restrict__ x, CgState st) {
-    const long long t = blockIdx.x;
-    const ChunkPos P = decode_chunk(blk, chunk_orb, orb_blk, t);
+// x64 += d32 for orbitals still refining (tile version).
+__global__ void __launch_bounds__(256) k_correct_t(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                   const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                   const float* __restrict__ d32, double* __restrict__ x, CgState st) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
-    for (int k = threadIdx.x; k < P.npts; k += blockDim.x) {
-        const long long g = P.base + P.g0 + k;
-        x[g] += (double)d32[g];
-    }
+    const LvlDesc& D = L[P.b];
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {
+            const float4 d = *reinterpret_cast<const float4*>(d32 + g);
+            double2 a = *reinterpret_cast<double2*>(x + g);
+            double2 b = *reinterpret_cast<double2*>(x + g + 2);
+            a.x += d.x; a.y += d.y; b.x += d.z; b.y += d.w;
+            *reinterpret_cast<double2*>(x + g) = a;
+            *reinterpret_cast<double2*>(x + g + 2) = b;
+        } else {
+            x[g] += (double)d32[g];
+        }
+    });
 }
 
 __global__ void k_cg_finish(int norb, CgState st, int* out_iters, int* out_conv, int* status) {
@@ -463,9 +575,12 @@ static int read_count(flosic_ctx* c, const int* dptr, cudaStream_t s) {
     return c->h_pinned[0];
 }
 
-// Solves A V = b for every orbital (b from launch_rhs, ||b||^2 in cg.bb).
-// Returns a flosic status; iteration counts and convergence flags stay in the
-// CG state (copied out by finish_poisson).
+static void launch_residual_zero(flosic_ctx* c, const double* b, double* r, double tol2, int* flag, int* counter,
+                                 cudaStream_t s) {
+    k_residual_zero<<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+        c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, b, r, tol2, flag, counter, c->ws.cg); note_launch(c);
+}
+
 template <class T>
 static MgPtrs<T> mg_ptrs(const flosic_ctx* c, T* r, T* z, T* q) {
     MgPtrs<T> mp{};
@@ -484,13 +599,13 @@ static MgPtrs<T> mg_ptrs(const flosic_ctx* c, T* r, T* z, T* q) {
 
 // Multigrid-preconditioned CG on A x = r0 for the active orbitals (r holds
 // the starting residual, rr/thr/active/n_active are set, rz = beta = 0).
+// The direction image uses the recurrence q = A z + beta q, so the stencil
+// reads one array (z); tbuf is the level-0 scratch of the V-cycle.
 template <class T>
-static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* pa, T* pb, T* q, int set_conv, cudaStream_t s) {
+static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* p, T* tbuf, T* q, int set_conv, cudaStream_t s) {
     CgState& st = c->ws.cg;
-    const unsigned nb = (unsigned)c->nchunk_total;
-    const int TH = kChunkThreads;
     const int max_iter = c->opt.max_iter;
-    const MgPtrs<T> mp = mg_ptrs<T>(c, r, z, q);
+    const MgPtrs<T> mp = mg_ptrs<T>(c, r, z, tbuf);
     for (int it = 0; it < max_iter; ++it) {
         if (it % 4 == 0) {
             const int na = read_count(c, st.n_active, s);
@@ -498,10 +613,9 @@ static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* pa, T* pb, T* q, int set_c
             if (na == 0) break;
         }
         launch_vcycle<T>(c, mp, st.active, s);
-        launch_apply12_pcg<T>(c, z, pa, pb, q, s);
-        k_pcg_update<T><<<nb, TH, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, x, r, pb, q, max_iter, set_conv,
-                                          st); note_launch(c);
-        T* tmp = pa; pa = pb; pb = tmp;
+        launch_apply12_pcg<T>(c, z, p, q, s);
+        k_pcg_update_t<T><<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+            c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, x, r, p, q, max_iter, set_conv, st); note_launch(c);
     }
     return FLOSIC_OK;
 }
@@ -522,7 +636,10 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
         return FLOSIC_ERR_CUDA;
     k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st); note_launch(c);
     if (c->opt.precision == FLOSIC_FP64) {
-        launch_residual12(c, b, V, w.r64, tol2, max_iter, st.active, st.n_active, 1, s);
+        if (warm)
+            launch_residual12(c, b, V, w.r64, tol2, max_iter, st.active, st.n_active, 1, s);
+        else
+            launch_residual_zero(c, b, w.r64, tol2, st.active, st.n_active, s);
         if (!mg && check_cuda(c, cudaMemcpyAsync(w.p64, w.r64, sizeof(double) * c->orb_elems,
                                                  cudaMemcpyDeviceToDevice, s), "copy p"))
             return FLOSIC_ERR_CUDA;
@@ -545,16 +662,20 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
             }
         }
     } else {
-        const double inner_tol2 = 1e-10;   // each float32 solve gains ~5 digits
+        const double inner_tol2 = 1e-12;   // each float32 solve gains ~6 digits
         for (int outer = 0; outer < 40; ++outer) {
-            launch_residual12(c, b, V, w.r64, tol2, max_iter, st.oactive, st.n_oactive, outer == 0 ? 1 : 0, s);
+            if (outer == 0 && !warm)
+                launch_residual_zero(c, b, w.r64, tol2, st.oactive, st.n_oactive, s);
+            else
+                launch_residual12(c, b, V, w.r64, tol2, max_iter, st.oactive, st.n_oactive, outer == 0 ? 1 : 0, s);
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
             if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
                 return FLOSIC_ERR_CUDA;
-            k_inner_init<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r64, w.r32, w.p32,
-                                          w.d32, inner_tol2, tol2, st); note_launch(c);
+            k_inner_init_t<<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+                c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, w.r64, w.r32, mg ? nullptr : w.p32, w.d32,
+                inner_tol2, tol2, st); note_launch(c);
             if (mg) {
                 int rc = pcg_mg<float>(c, w.d32, w.r32, w.z32, w.p32, w.p32b, w.q32, 0, s);
                 if (rc) return rc;
@@ -573,7 +694,8 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
                     k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
                 }
             }
-            k_correct<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.d32, V, st); note_launch(c);
+            k_correct_t<<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+                c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, w.d32, V, st); note_launch(c);
         }
     }
     return check_cuda(c, cudaGetLastError(), "poisson kernels");

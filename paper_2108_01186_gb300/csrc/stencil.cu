@@ -8,6 +8,8 @@
 // value therefore comes from DRAM about once; halos come from L2.  Points
 // outside the interior read as zero (zero ghost values of the correction
 // equation).  Threads: 32 x 8, two y rows each.
+#include <cuda.h>
+
 #include "internal.cuh"
 
 namespace flosic {
@@ -132,34 +134,227 @@ __device__ __forceinline__ void sweep12(const LvlDesc& D, const TilePos& P, cons
     }
 }
 
-// p = z + beta p_old, q = A p, pq = p.q (per orbital, deterministic).
+// PCG direction and its image with one stencil sweep of z (the
+// preconditioned residual): p = z + beta p, q = A z + beta q (first
+// iteration, beta = 0: p = z, q = A z); pq = p.q per orbital.  Plain-load
+// variant for grids whose rows are not 16-byte aligned.
 template <class T>
 __global__ void __launch_bounds__(256) k_apply12_pcg(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                     const T* __restrict__ z, const T* __restrict__ pold,
-                                                     T* __restrict__ pnew, T* __restrict__ q, CgState st) {
+                                                     const T* __restrict__ z, T* __restrict__ p, T* __restrict__ q,
+                                                     CgState st) {
     __shared__ T plane[kPY][kPX];
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.active[P.o]) return;
     const LvlDesc& D = L[P.b];
     const double bd = st.beta[P.o];
-    SrcPcg<T> src{z, pold, (T)bd, bd == 0.0};
+    const bool first = (bd == 0.0);
+    const T beta = (T)bd;
+    SrcPlain<T> src{z};
     const T ih2 = (T)(1.0 / (D.h * D.h));
     double pq = 0.0;
-    sweep12<T>(D, P, src, ih2, [&](long long g, int, T pc, T qv) {
-        pnew[g] = pc;
-        q[g] = qv;
-        pq += (double)pc * (double)qv;
+    sweep12<T>(D, P, src, ih2, [&](long long g, int, T zc, T az) {
+        const T pn = first ? zc : zc + beta * p[g];
+        const T qn = first ? az : az + beta * q[g];
+        p[g] = pn;
+        q[g] = qn;
+        pq += (double)pn * (double)qn;
     }, plane);
     const int o = P.o;
     if (tile_arrive(pq, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
-        const double s = tile_gather(st.part, P.first, D.ntile, scratch);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
             st.count[o] = 0;
-            st.pq[o] = s;
+            st.pq[o] = sum;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// TMA variant: the staged planes (tile plus halo, 48 x 28) arrive by
+// cp.async.bulk.tensor into a ring of kRing shared-memory stages, completed
+// on mbarriers; out-of-range rows, columns and planes are zero-filled by the
+// copy engine, which is exactly the zero ghost value of the correction
+// equation.  Ring: the plane of the output step (x/y taps), the six above it
+// (the head of the register z-queue comes from the plane six steps ahead),
+// and three more planes in flight.
+// ---------------------------------------------------------------------------
+constexpr int kSX = 48;        // staged width: x0 - 8 .. x0 + 39 (x0 - 8 keeps the copy 16-byte aligned)
+constexpr int kSY = kTileY + 2 * kHalf;   // 28: y0 - 6 .. y0 + 21
+constexpr int kRing = 10;
+constexpr long long kWaitLimit = 1LL << 22;   // bounded mbarrier wait (far beyond any real copy latency)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Waits for the phase with the given parity; gives up after kWaitLimit
+// polls and reports it through *err (never hangs the GPU).
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+    const unsigned a = smem_addr(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    atomicOr(err, 1);
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_addr(dst)), "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_apply12_tma(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                     const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                     const CUtensorMap* __restrict__ maps, T* __restrict__ p,
+                                                     T* __restrict__ q, CgState st, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the copy engine wants 128-byte aligned stages: align the base explicitly
+    unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+    T* ring = reinterpret_cast<T*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(T) * kRing * kSY * kSX);
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.active[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    const CUtensorMap* map = maps + P.b;
+    const int oi = P.o - blk[P.b].orb0;
+    const int tid = linear_tid();
+    const int nzt = P.z1 - P.z0;
+    const int np = nzt + 2 * kHalf;           // planes z0-6 .. z1+5
+    const unsigned bytes = sizeof(T) * kSY * kSX;
+    auto slot = [&](int k) { return ring + (size_t)(k % kRing) * kSY * kSX; };
+    auto issue = [&](int k) {
+        uint64_t* b = bar + (k % kRing);
+        mbar_expect_tx(b, bytes);
+        tma_load_4d(slot(k), map, P.x0 - 8, P.y0 - kHalf, P.z0 - kHalf + k, oi, b);
+    };
+    if (tid == 0) {
+        for (int r = 0; r < kRing; ++r) mbar_init(bar + r, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < kRing && k < np; ++k) issue(k);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int lx = tx + 8, ly0 = ty + kHalf, ly1 = ty + kTileY / 2 + kHalf;
+    const int gx = P.x0 + tx, gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
+    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
+    T q0[2 * kHalf + 1], q1[2 * kHalf + 1];
+    // prologue: queue entries from planes 0..11; planes 0..5 are then done
+    // with and their stages are refilled (planes kRing .. kRing + 5)
+#pragma unroll
+    for (int k = 0; k < 2 * kHalf; ++k) {
+        mbar_wait(bar + (k % kRing), (k / kRing) & 1, err);
+        const T* sl = slot(k);
+        q0[k] = sl[ly0 * kSX + lx];
+        q1[k] = sl[ly1 * kSX + lx];
+        if (k < kHalf) {
+            __syncthreads();
+            if (tid == 0 && k + kRing < np) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k + kRing);
+            }
+        }
+    }
+    const double bd = st.beta[P.o];
+    const bool first = (bd == 0.0);
+    const T beta = (T)bd;
+    const T ih2 = (T)(1.0 / (D.h * D.h));
+    const T w0 = T(3) * wgt<T>(0);
+    double pq = 0.0;
+    // p_old and q_old of the thread's two points, loaded one plane ahead
+    T pp0 = 0, pp1 = 0, qq0 = 0, qq1 = 0;
+    if (!first) {
+        const long long zo = P.base + P.z0 * sz;
+        if (in0) { pp0 = p[zo + c0]; qq0 = q[zo + c0]; }
+        if (in1) { pp1 = p[zo + c1]; qq1 = q[zo + c1]; }
+    }
+    for (int s = 0; s < nzt; ++s) {
+        T np0 = 0, np1 = 0, nq0 = 0, nq1 = 0;
+        if (!first && s + 1 < nzt) {
+            const long long zn = P.base + (P.z0 + s + 1) * sz;
+            if (in0) { np0 = p[zn + c0]; nq0 = q[zn + c0]; }
+            if (in1) { np1 = p[zn + c1]; nq1 = q[zn + c1]; }
+        }
+        const int kh = s + 2 * kHalf;      // head plane z + 6
+        mbar_wait(bar + (kh % kRing), (kh / kRing) & 1, err);
+        const T* hs = slot(kh);
+        q0[2 * kHalf] = hs[ly0 * kSX + lx];
+        q1[2 * kHalf] = hs[ly1 * kSX + lx];
+        const T* pl = slot(s + kHalf);     // plane z
+        T a0 = w0 * q0[kHalf], a1 = w0 * q1[kHalf];
+#pragma unroll
+        for (int m = 1; m <= kHalf; ++m) {
+            const T wm = wgt<T>(m);
+            a0 += wm * (pl[ly0 * kSX + lx - m] + pl[ly0 * kSX + lx + m] + pl[(ly0 - m) * kSX + lx] +
+                        pl[(ly0 + m) * kSX + lx] + q0[kHalf - m] + q0[kHalf + m]);
+            a1 += wm * (pl[ly1 * kSX + lx - m] + pl[ly1 * kSX + lx + m] + pl[(ly1 - m) * kSX + lx] +
+                        pl[(ly1 + m) * kSX + lx] + q1[kHalf - m] + q1[kHalf + m]);
+        }
+        const long long zo = P.base + (P.z0 + s) * sz;
+        if (in0) {
+            const long long g = zo + c0;
+            const T pn = q0[kHalf] + beta * pp0;
+            const T qn = -a0 * ih2 + beta * qq0;
+            p[g] = pn;
+            q[g] = qn;
+            pq += (double)pn * (double)qn;
+        }
+        if (in1) {
+            const long long g = zo + c1;
+            const T pn = q1[kHalf] + beta * pp1;
+            const T qn = -a1 * ih2 + beta * qq1;
+            p[g] = pn;
+            q[g] = qn;
+            pq += (double)pn * (double)qn;
+        }
+        pp0 = np0; pp1 = np1; qq0 = nq0; qq1 = nq1;
+        __syncthreads();                   // stage of plane z is free
+        if (tid == 0 && s + kHalf + kRing < np) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(s + kHalf + kRing);
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * kHalf; ++j) {
+            q0[j] = q0[j + 1];
+            q1[j] = q1[j + 1];
+        }
+    }
+    const int o = P.o;
+    if (tile_arrive(pq, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[o] = 0;
+            st.pq[o] = sum;
+        }
+    }
+}
+
+size_t apply12_tma_smem(size_t elem) { return elem * kRing * kSY * kSX + sizeof(uint64_t) * kRing + 128; }
+
+const void* apply12_tma_symbol(bool f32) {
+    return f32 ? (const void*)k_apply12_tma<float> : (const void*)k_apply12_tma<double>;
 }
 
 // r = b - A x in float64, rr = r.r; orbitals whose rr <= tol2 * bb stop
@@ -214,15 +409,22 @@ __global__ void __launch_bounds__(256) k_residual12(const BlkDesc* __restrict__ 
 }
 
 template <class T>
-void launch_apply12_pcg(flosic_ctx* c, const T* z, const T* pold, T* pnew, T* q, cudaStream_t s) {
+void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s) {
     const Multigrid& M = c->mg;
     prof_begin(c, s);
-    k_apply12_pcg<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
-        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, z, pold, pnew, q, c->ws.cg); note_launch(c);
+    if (c->tma_ok) {
+        k_apply12_tma<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), apply12_tma_smem(sizeof(T)), s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_tmaps, p, q, c->ws.cg,
+            c->ws.status + 3);
+    } else {
+        k_apply12_pcg<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, z, p, q, c->ws.cg);
+    }
+    note_launch(c);
     prof_end(c, s);
 }
-template void launch_apply12_pcg<float>(flosic_ctx*, const float*, const float*, float*, float*, cudaStream_t);
-template void launch_apply12_pcg<double>(flosic_ctx*, const double*, const double*, double*, double*, cudaStream_t);
+template void launch_apply12_pcg<float>(flosic_ctx*, const float*, float*, float*, cudaStream_t);
+template void launch_apply12_pcg<double>(flosic_ctx*, const double*, double*, double*, cudaStream_t);
 
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s) {

@@ -69,13 +69,16 @@ def test_build_flos_parity(F, orc, ragged, prec):
     ctx = F.Context([s], precision=prec)
     phi, S, Q = ctx.build_flos(_flat(s.psi), _flat(s.fods))
     phi_b = _blocks(_np(phi), [s])[0]
+    # FP64: float64 throughout; MIXED: grid products in float32 with float64
+    # sums over 16-point tiles (relative error ~1e-7)
+    tphi, tS = (1e-11, 1e-12) if prec == 0 else (2e-6, 1e-6)
     off = 0
     for sp in range(2):
         fl = orc.build_flos(s.psi[sp], s.fods[sp], s.grid)
         N = s.norb[sp]
-        assert np.max(np.abs(phi_b[sp] - fl["phi"])) < 1e-11 * np.max(np.abs(fl["phi"]))
-        assert np.max(np.abs(_np(S)[off:off + N * N].reshape(N, N) - fl["S"])) < 1e-12
-        assert np.max(np.abs(_np(Q)[off:off + N * N].reshape(N, N) - fl["Q"])) < 1e-11
+        assert np.max(np.abs(phi_b[sp] - fl["phi"])) < tphi * np.max(np.abs(fl["phi"]))
+        assert np.max(np.abs(_np(S)[off:off + N * N].reshape(N, N) - fl["S"])) < tS
+        assert np.max(np.abs(_np(Q)[off:off + N * N].reshape(N, N) - fl["Q"])) < 10 * tS
         off += N * N
 
 
