@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict
     const LvlDesc& D = L[P.b];
     if (!active[P.o] || D.coarsest) return;
     const T h2 = T(D.h * D.h);
-    double rz = 0.0;
+    T rz = T(0);   // per-thread partial in the working precision; tile sums in float64
     tile_rows<T>(D, P, [&](int x, int y, int z, long long g, int n) {
         T c[V], nb[V], rv[V], out[V];
         centre_nbr<T, V>(t, D, x, y, z, g, n, c, nb);
@@ -253,12 +253,12 @@ __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             out[k] = (T(1) - omega) * c[k] + omega * T(1.0 / 6.0) * (h2 * rv[k] + nb[k]);
-            if (kLevel0 && k < n) rz += (double)rv[k] * (double)out[k];
+            if (kLevel0 && k < n) rz += rv[k] * out[k];
         }
         store_n<T, V>(e + g, out, n);
     });
     if (kLevel0) {
-        if (tile_arrive(rz, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        if (tile_arrive((double)rz, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
             const double v = tile_gather(st.part, P.first, D.ntile, scratch);
             if (linear_tid() == 0) {
                 st.count[P.o] = 0;

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) k_pcg_update_t(const BlkDesc* __restrict_
     const LvlDesc& D = L[P.b];
     const double pqv = st.pq[P.o];
     const T alpha = (pqv > 0.0) ? (T)(st.rz[P.o] / pqv) : (T)0;
-    double rr = 0.0;
+    T rr = T(0);   // per-thread partial in the working precision; tile sums in float64
     tile_elementwise<T>(D, P, [&](long long g, int n) {
         if (n > 1) {
             VT xv = *reinterpret_cast<VT*>(x + g);
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256) k_pcg_update_t(const BlkDesc* __restrict_
             for (int k = 0; k < Vec<T>::n; ++k) {
                 xs[k] += alpha * ps[k];
                 rs[k] -= alpha * qs[k];
-                rr += (double)rs[k] * (double)rs[k];
+                rr += rs[k] * rs[k];
             }
             *reinterpret_cast<VT*>(x + g) = xv;
             *reinterpret_cast<VT*>(r + g) = rv;
@@ -429,10 +429,10 @@ __global__ void __launch_bounds__(256) k_pcg_update_t(const BlkDesc* __restrict_
             x[g] += alpha * p[g];
             const T rv = r[g] - alpha * q[g];
             r[g] = rv;
-            rr += (double)rv * (double)rv;
+            rr += rv * rv;
         }
     });
-    if (tile_arrive(rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+    if (tile_arrive((double)rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             const int o = P.o;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(256) k_inner_init_t(const BlkDesc* __restrict_
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
     const LvlDesc& D = L[P.b];
-    double rr = 0.0;
+    float rr = 0.0f;
     tile_elementwise<float>(D, P, [&](long long g, int n) {
         if (n == 4) {
             const double2 a = *reinterpret_cast<const double2*>(r64 + g);
@@ -508,16 +508,16 @@ __global__ void __launch_bounds__(256) k_inner_init_t(const BlkDesc* __restrict_
             *reinterpret_cast<float4*>(r32 + g) = v;
             if (p32) *reinterpret_cast<float4*>(p32 + g) = v;
             *reinterpret_cast<float4*>(d32 + g) = make_float4(0.f, 0.f, 0.f, 0.f);
-            rr += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+            rr += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
         } else {
             const float v = (float)r64[g];
             r32[g] = v;
             if (p32) p32[g] = v;
             d32[g] = 0.0f;
-            rr += (double)v * (double)v;
+            rr += v * v;
         }
     });
-    if (tile_arrive(rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+    if (tile_arrive((double)rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             const int o = P.o;

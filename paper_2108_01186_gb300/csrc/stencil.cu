@@ -18,7 +18,13 @@ namespace flosic {
 __constant__ double c_w12[kHalf + 1];
 __constant__ float c_w12f[kHalf + 1];
 
+cudaError_t upload_ff_weights();
+
 cudaError_t upload_stencil12_constants() {
+    {
+        cudaError_t e = upload_ff_weights();
+        if (e != cudaSuccess) return e;
+    }
     double w[kHalf + 1];
     float wf[kHalf + 1];
     stencil_weights(w);
@@ -222,127 +228,167 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Ring stage: the staged plane z with halo (48 x 28), and three 32 x 16
+// centre tiles: z at plane z+6 (head of the register z-queue), p_old and
+// q_old at plane z.  Threads 16 x 8; each owns the 2 x 2 points
+// (x0 + 2tx + a, y0 + 2ty + b).
+constexpr int kStagePlane = kSX * kSY;
+constexpr int kStageCtr = kTileX * kTileY;
+constexpr int kStageElems = kStagePlane + 3 * kStageCtr;
+constexpr int kRing2 = 4;
+
 template <class T>
-__global__ void __launch_bounds__(256) k_apply12_tma(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+__global__ void __launch_bounds__(128) k_apply12_tma(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                     const CUtensorMap* __restrict__ maps, T* __restrict__ p,
-                                                     T* __restrict__ q, CgState st, int* __restrict__ err) {
+                                                     const CUtensorMap* __restrict__ maps, const T* __restrict__ z,
+                                                     T* __restrict__ p, T* __restrict__ q, CgState st,
+                                                     int* __restrict__ err) {
+    using V2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // the copy engine wants 128-byte aligned stages: align the base explicitly
     unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
     T* ring = reinterpret_cast<T*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(T) * kRing * kSY * kSX);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(T) * kRing2 * kStageElems);
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.active[P.o]) return;
     const LvlDesc& D = L[P.b];
-    const CUtensorMap* map = maps + P.b;
+    const CUtensorMap* mp = maps + 4 * P.b;    // z with halo, z centre, p centre, q centre
     const int oi = P.o - blk[P.b].orb0;
-    const int tid = linear_tid();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nzt = P.z1 - P.z0;
-    const int np = nzt + 2 * kHalf;           // planes z0-6 .. z1+5
-    const unsigned bytes = sizeof(T) * kSY * kSX;
-    auto slot = [&](int k) { return ring + (size_t)(k % kRing) * kSY * kSX; };
-    auto issue = [&](int k) {
-        uint64_t* b = bar + (k % kRing);
+    const double bd = st.beta[P.o];
+    const bool first = (bd == 0.0);
+    const unsigned bytes = sizeof(T) * (first ? kStagePlane + kStageCtr : kStageElems);
+    auto stage = [&](int s) { return ring + (size_t)(s % kRing2) * kStageElems; };
+    auto issue = [&](int s) {
+        uint64_t* b = bar + (s % kRing2);
+        T* st_ = stage(s);
+        const int zz = P.z0 + s;
         mbar_expect_tx(b, bytes);
-        tma_load_4d(slot(k), map, P.x0 - 8, P.y0 - kHalf, P.z0 - kHalf + k, oi, b);
+        tma_load_4d(st_, mp + 0, P.x0 - 8, P.y0 - kHalf, zz, oi, b);
+        tma_load_4d(st_ + kStagePlane, mp + 1, P.x0, P.y0, zz + kHalf, oi, b);
+        if (!first) {
+            tma_load_4d(st_ + kStagePlane + kStageCtr, mp + 2, P.x0, P.y0, zz, oi, b);
+            tma_load_4d(st_ + kStagePlane + 2 * kStageCtr, mp + 3, P.x0, P.y0, zz, oi, b);
+        }
     };
     if (tid == 0) {
-        for (int r = 0; r < kRing; ++r) mbar_init(bar + r, 1);
+        for (int r = 0; r < kRing2; ++r) mbar_init(bar + r, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int k = 0; k < kRing && k < np; ++k) issue(k);
+        for (int k = 0; k < kRing2 && k < nzt; ++k) issue(k);
     }
     __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int lx = tx + 8, ly0 = ty + kHalf, ly1 = ty + kTileY / 2 + kHalf;
-    const int gx = P.x0 + tx, gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
-    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
+    const int gx = P.x0 + 2 * tx;
+    const int gy0 = P.y0 + 2 * ty;
+    const bool inx = gx < D.nx;
+    const bool iny[2] = {gy0 < D.ny, gy0 + 1 < D.ny};
     const long long sy = D.nx, sz = (long long)D.nx * D.ny;
-    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
-    T q0[2 * kHalf + 1], q1[2 * kHalf + 1];
-    // prologue: queue entries from planes 0..11; planes 0..5 are then done
-    // with and their stages are refilled (planes kRing .. kRing + 5)
+    // register z-queues of the four points: qz[b][a][j], planes z-6 .. z+6
+    T qz[2][2][2 * kHalf + 1];
 #pragma unroll
-    for (int k = 0; k < 2 * kHalf; ++k) {
-        mbar_wait(bar + (k % kRing), (k / kRing) & 1, err);
-        const T* sl = slot(k);
-        q0[k] = sl[ly0 * kSX + lx];
-        q1[k] = sl[ly1 * kSX + lx];
-        if (k < kHalf) {
-            __syncthreads();
-            if (tid == 0 && k + kRing < np) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(k + kRing);
-            }
+    for (int j = 0; j < 2 * kHalf; ++j) {
+        const int zz = P.z0 - kHalf + j;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            V2 v;
+            v.x = T(0);
+            v.y = T(0);
+            if (inx && iny[b] && zz >= 0 && zz < D.nz)
+                v = *reinterpret_cast<const V2*>(z + P.base + zz * sz + (gy0 + b) * sy + gx);
+            qz[b][0][j] = v.x;
+            qz[b][1][j] = v.y;
         }
     }
-    const double bd = st.beta[P.o];
-    const bool first = (bd == 0.0);
     const T beta = (T)bd;
     const T ih2 = (T)(1.0 / (D.h * D.h));
-    const T w0 = T(3) * wgt<T>(0);
-    double pq = 0.0;
-    // p_old and q_old of the thread's two points, loaded one plane ahead
-    T pp0 = 0, pp1 = 0, qq0 = 0, qq1 = 0;
-    if (!first) {
-        const long long zo = P.base + P.z0 * sz;
-        if (in0) { pp0 = p[zo + c0]; qq0 = q[zo + c0]; }
-        if (in1) { pp1 = p[zo + c1]; qq1 = q[zo + c1]; }
-    }
-    for (int s = 0; s < nzt; ++s) {
-        T np0 = 0, np1 = 0, nq0 = 0, nq1 = 0;
-        if (!first && s + 1 < nzt) {
-            const long long zn = P.base + (P.z0 + s + 1) * sz;
-            if (in0) { np0 = p[zn + c0]; nq0 = q[zn + c0]; }
-            if (in1) { np1 = p[zn + c1]; nq1 = q[zn + c1]; }
-        }
-        const int kh = s + 2 * kHalf;      // head plane z + 6
-        mbar_wait(bar + (kh % kRing), (kh / kRing) & 1, err);
-        const T* hs = slot(kh);
-        q0[2 * kHalf] = hs[ly0 * kSX + lx];
-        q1[2 * kHalf] = hs[ly1 * kSX + lx];
-        const T* pl = slot(s + kHalf);     // plane z
-        T a0 = w0 * q0[kHalf], a1 = w0 * q1[kHalf];
+    T wm[kHalf + 1];
 #pragma unroll
-        for (int m = 1; m <= kHalf; ++m) {
-            const T wm = wgt<T>(m);
-            a0 += wm * (pl[ly0 * kSX + lx - m] + pl[ly0 * kSX + lx + m] + pl[(ly0 - m) * kSX + lx] +
-                        pl[(ly0 + m) * kSX + lx] + q0[kHalf - m] + q0[kHalf + m]);
-            a1 += wm * (pl[ly1 * kSX + lx - m] + pl[ly1 * kSX + lx + m] + pl[(ly1 - m) * kSX + lx] +
-                        pl[(ly1 + m) * kSX + lx] + q1[kHalf - m] + q1[kHalf + m]);
+    for (int m = 0; m <= kHalf; ++m) wm[m] = wgt<T>(m);
+    const T w0 = T(3) * wm[0];
+    T pqf = T(0);
+    const int lx = 2 * tx + 8, ly0 = 2 * ty + kHalf;
+    for (int s = 0; s < nzt; ++s) {
+        mbar_wait(bar + (s % kRing2), (s / kRing2) & 1, err);
+        const T* pl = stage(s);
+        const T* hd = pl + kStagePlane;
+        const T* po = pl + kStagePlane + kStageCtr;
+        const T* qo = pl + kStagePlane + 2 * kStageCtr;
+        // queue heads (plane z + 6) and the y-window of the column pair
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const V2 h = *reinterpret_cast<const V2*>(hd + (2 * ty + b) * kTileX + 2 * tx);
+            qz[b][0][2 * kHalf] = h.x;
+            qz[b][1][2 * kHalf] = h.y;
+        }
+        T yw[2][2 * kHalf + 2];     // [a][k], rows 2ty .. 2ty+13
+#pragma unroll
+        for (int k = 0; k < 2 * kHalf + 2; ++k) {
+            const V2 v = *reinterpret_cast<const V2*>(pl + (2 * ty + k) * kSX + lx);
+            yw[0][k] = v.x;
+            yw[1][k] = v.y;
+        }
+        T out[2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            T xw[2 * kHalf + 2];    // cols lx-6 .. lx+7 of row ly0+b
+#pragma unroll
+            for (int k = 0; k < kHalf + 1; ++k) {
+                const V2 v = *reinterpret_cast<const V2*>(pl + (ly0 + b) * kSX + lx - kHalf + 2 * k);
+                xw[2 * k] = v.x;
+                xw[2 * k + 1] = v.y;
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                T acc = w0 * yw[a][kHalf + b];
+#pragma unroll
+                for (int m = 1; m <= kHalf; ++m)
+                    acc += wm[m] * (xw[kHalf + a - m] + xw[kHalf + a + m] + yw[a][kHalf + b - m] +
+                                    yw[a][kHalf + b + m] + qz[b][a][kHalf - m] + qz[b][a][kHalf + m]);
+                out[b][a] = -acc * ih2;
+            }
         }
         const long long zo = P.base + (P.z0 + s) * sz;
-        if (in0) {
-            const long long g = zo + c0;
-            const T pn = q0[kHalf] + beta * pp0;
-            const T qn = -a0 * ih2 + beta * qq0;
-            p[g] = pn;
-            q[g] = qn;
-            pq += (double)pn * (double)qn;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (!(inx && iny[b])) continue;
+            V2 pn, qn;
+            pn.x = yw[0][kHalf + b];
+            pn.y = yw[1][kHalf + b];
+            qn.x = out[b][0];
+            qn.y = out[b][1];
+            if (!first) {
+                const V2 pv = *reinterpret_cast<const V2*>(po + (2 * ty + b) * kTileX + 2 * tx);
+                const V2 qv = *reinterpret_cast<const V2*>(qo + (2 * ty + b) * kTileX + 2 * tx);
+                pn.x += beta * pv.x;
+                pn.y += beta * pv.y;
+                qn.x += beta * qv.x;
+                qn.y += beta * qv.y;
+            }
+            const long long g = zo + (gy0 + b) * sy + gx;
+            *reinterpret_cast<V2*>(p + g) = pn;
+            *reinterpret_cast<V2*>(q + g) = qn;
+            pqf += pn.x * qn.x + pn.y * qn.y;
         }
-        if (in1) {
-            const long long g = zo + c1;
-            const T pn = q1[kHalf] + beta * pp1;
-            const T qn = -a1 * ih2 + beta * qq1;
-            p[g] = pn;
-            q[g] = qn;
-            pq += (double)pn * (double)qn;
-        }
-        pp0 = np0; pp1 = np1; qq0 = nq0; qq1 = nq1;
-        __syncthreads();                   // stage of plane z is free
-        if (tid == 0 && s + kHalf + kRing < np) {
+        __syncthreads();                   // stage s is free
+        if (tid == 0 && s + kRing2 < nzt) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(s + kHalf + kRing);
+            issue(s + kRing2);
         }
 #pragma unroll
         for (int j = 0; j < 2 * kHalf; ++j) {
-            q0[j] = q0[j + 1];
-            q1[j] = q1[j + 1];
+            qz[0][0][j] = qz[0][0][j + 1];
+            qz[0][1][j] = qz[0][1][j + 1];
+            qz[1][0][j] = qz[1][0][j + 1];
+            qz[1][1][j] = qz[1][1][j + 1];
         }
     }
     const int o = P.o;
-    if (tile_arrive(pq, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
+    if (tile_arrive((double)pqf, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[o] = 0;
@@ -351,7 +397,7 @@ __global__ void __launch_bounds__(256) k_apply12_tma(const BlkDesc* __restrict__
     }
 }
 
-size_t apply12_tma_smem(size_t elem) { return elem * kRing * kSY * kSX + sizeof(uint64_t) * kRing + 128; }
+size_t apply12_tma_smem(size_t elem) { return elem * kRing2 * kStageElems + sizeof(uint64_t) * kRing2 + 128; }
 
 const void* apply12_tma_symbol(bool f32) {
     return f32 ? (const void*)k_apply12_tma<float> : (const void*)k_apply12_tma<double>;
@@ -408,13 +454,194 @@ __global__ void __launch_bounds__(256) k_residual12(const BlkDesc* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float64-accurate residual in float-float arithmetic.  GB300's float64 rate
+// is a small fraction of its float32 rate, so r = b - A x is evaluated with
+// unevaluated pairs (hi, lo) of float32 numbers: Knuth's error-free two-sum
+// for additions and an FMA-based exact two-product, which carry ~48
+// significant bits -- enough for residuals down to 1e-12 of ||b||.
+// ---------------------------------------------------------------------------
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = ff_two_sum(x.h, y.h);
+    const ff t = ff_two_sum(x.l, y.l);
+    s.l += t.h;
+    s = ff_quick(s.h, s.l);
+    s.l += t.l;
+    return ff_quick(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, e);
+    e = fmaf(x.l, y.h, e);
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_split(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+__constant__ float c_wff[2 * (kHalf + 1)];   // w_m as (hi, lo) pairs
+
+cudaError_t upload_ff_weights() {
+    double w[kHalf + 1];
+    stencil_weights(w);
+    float f[2 * (kHalf + 1)];
+    for (int m = 0; m <= kHalf; ++m) {
+        const double ww = (m == 0) ? 3.0 * w[0] : w[m];
+        f[2 * m] = (float)ww;
+        f[2 * m + 1] = (float)(ww - (double)f[2 * m]);
+    }
+    return cudaMemcpyToSymbol(c_wff, f, sizeof(f));
+}
+
+__global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                       const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                       const double* __restrict__ b, const double* __restrict__ x,
+                                                       double* __restrict__ r, double tol2, int max_iter,
+                                                       int* __restrict__ flag, int* __restrict__ counter, int want_bb,
+                                                       CgState st) {
+    __shared__ ff plane[kPY][kPX];
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!flag[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTileX + tx;
+    const int nthr = kTileX * (kTileY / 2);
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    const int gx = P.x0 + tx;
+    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
+    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
+    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
+    long long soff[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) {
+        const int e = tid + j * nthr;
+        soff[j] = -1;
+        if (e < kPX * kPY) {
+            const int yy = e / kPX, xx = e - yy * kPX;
+            const int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
+            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
+        }
+    }
+    const ff zero = {0.f, 0.f};
+    ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * kHalf; ++j) {
+        const int zz = P.z0 - kHalf + j;
+        const bool okz = zz >= 0 && zz < D.nz;
+        q0[j] = (in0 && okz) ? ff_split(x[P.base + zz * sz + c0]) : zero;
+        q1[j] = (in1 && okz) ? ff_split(x[P.base + zz * sz + c1]) : zero;
+    }
+    double pre[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[P.base + P.z0 * sz + soff[j]] : 0.0;
+    ff w[kHalf + 1];
+#pragma unroll
+    for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
+    const double ih2 = 1.0 / (D.h * D.h);
+    float rrf = 0.f, bbf = 0.f;
+    ff* flat = &plane[0][0];
+    for (int z = P.z0; z < P.z1; ++z) {
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int e = tid + j * nthr;
+            if (e < kPX * kPY) flat[e] = ff_split(pre[j]);
+        }
+        {
+            const int zz = z + kHalf;
+            q0[2 * kHalf] = (in0 && zz < D.nz) ? ff_split(x[P.base + zz * sz + c0]) : zero;
+            q1[2 * kHalf] = (in1 && zz < D.nz) ? ff_split(x[P.base + zz * sz + c1]) : zero;
+        }
+        __syncthreads();
+        if (z + 1 < P.z1) {
+            const long long pz = P.base + (z + 1) * sz;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[pz + soff[j]] : 0.0;
+        }
+        const int lx = tx + kHalf;
+        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
+        const bool in[2] = {in0, in1};
+        const long long cc[2] = {c0, c1};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const ff* qk = (k == 0) ? q0 : q1;
+            ff acc = ff_mul(w[0], qk[kHalf]);
+#pragma unroll
+            for (int m = 1; m <= kHalf; ++m) {
+                ff sm = ff_add(plane[ly[k]][lx - m], plane[ly[k]][lx + m]);
+                sm = ff_add(sm, plane[ly[k] - m][lx]);
+                sm = ff_add(sm, plane[ly[k] + m][lx]);
+                sm = ff_add(sm, qk[kHalf - m]);
+                sm = ff_add(sm, qk[kHalf + m]);
+                acc = ff_add(acc, ff_mul(w[m], sm));
+            }
+            if (in[k]) {
+                const long long g = P.base + z * sz + cc[k];
+                const double ax = -((double)acc.h + (double)acc.l) * ih2;
+                const double bv = b[g];
+                const double rv = bv - ax;
+                r[g] = rv;
+                rrf += (float)rv * (float)rv;
+                bbf += (float)bv * (float)bv;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 2 * kHalf; ++j) {
+            q0[j] = q0[j + 1];
+            q1[j] = q1[j + 1];
+        }
+    }
+    const int o = P.o;
+    if (want_bb) {
+        const double bbs = block_sum((double)bbf, scratch);
+        if (linear_tid() == 0) st.part2[blockIdx.x] = bbs;
+    }
+    if (tile_arrive((double)rrf, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (want_bb) {
+            const double sb = tile_gather(st.part2, P.first, D.ntile, scratch);
+            if (linear_tid() == 0) st.bb[o] = sb;
+        }
+        if (linear_tid() == 0) {
+            st.count[o] = 0;
+            st.rr[o] = sum;
+            st.thr[o] = tol2 * st.bb[o];
+            if (!(sum > st.thr[o])) {
+                flag[o] = 0;
+                st.conv[o] = 1;
+                atomicSub(counter, 1);
+            } else if (st.iters[o] >= max_iter || !isfinite(sum)) {
+                flag[o] = 0;
+                atomicSub(counter, 1);
+            }
+        }
+    }
+}
+
 template <class T>
 void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s) {
     const Multigrid& M = c->mg;
     prof_begin(c, s);
     if (c->tma_ok) {
-        k_apply12_tma<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), apply12_tma_smem(sizeof(T)), s>>>(
-            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_tmaps, p, q, c->ws.cg,
+        k_apply12_tma<T><<<(unsigned)M.ntiles[0], dim3(kTileX / 2, kTileY / 2), apply12_tma_smem(sizeof(T)), s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_tmaps, z, p, q, c->ws.cg,
             c->ws.status + 3);
     } else {
         k_apply12_pcg<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
@@ -429,6 +656,12 @@ template void launch_apply12_pcg<double>(flosic_ctx*, const double*, double*, do
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s) {
     const Multigrid& M = c->mg;
+    if (c->opt.precision == FLOSIC_MIXED) {
+        k_residual12_ff<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b, x, r, tol2, max_iter, flag, counter, want_bb,
+            c->ws.cg); note_launch(c);
+        return;
+    }
     k_residual12<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
         c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b, x, r, tol2, max_iter, flag, counter, want_bb,
         c->ws.cg); note_launch(c);
