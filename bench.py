@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--preconditioner", default="mg", choices=["mg", "none"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
     return p.parse_args()
 
 
@@ -197,6 +198,21 @@ def traffic_for(kernel_src):
     return d.get("traffic_bytes_per_launch_scaled")
 
 
+def step_with(ctx, psi, fods, gE):
+    """One forward + adjoint step through the public API."""
+    phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
+    V, iters, conv = ctx.orbital_poisson(phi)
+    E, Vavg, U, Exc = ctx.sic_energy_potential(psi, phi, V, 1.0)
+    dpsi, dfod = ctx.sic_backward(psi, fods, phi, V, gE)
+    return E, Vavg, dpsi, dfod, iters
+
+
+def step_outputs(ctx, psi, fods):
+    phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
+    V, _, _ = ctx.orbital_poisson(phi)
+    return phi, V
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -222,11 +238,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step(psi, fods):
-        phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
-        V, iters, conv = ctx.orbital_poisson(phi)
-        E, Vavg, U, Exc = ctx.sic_energy_potential(psi, phi, V, 1.0)
-        dpsi, dfod = ctx.sic_backward(psi, fods, phi, V, gE)
-        return E, Vavg, dpsi, dfod, iters
+        return step_with(ctx, psi, fods, gE)
 
     def barrier():
         if world > 1:
@@ -261,10 +273,11 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = world * norb / (ms_step / 1e3)
 
-    # roofline of the dominant kernel (CG stencil apply): algorithmic bytes =
-    # read p + write q per point per active orbital per iteration
-    bpp = 8 if prec == 1 else 16
-    alg_bytes = float(np.sum(iters_sum)) * s.G * bpp
+    # roofline of the dominant kernel (the PCG stencil apply): algorithmic
+    # bytes counted on the device per active orbital and launch (read z,
+    # p_old, q_old; write p, q -- 20 B/point in float32, 12 B on a solve's
+    # first iteration)
+    alg_bytes = prof["kernel_bytes"]
     launches = max(prof["kernel_launches"], 1)
     achieved = alg_bytes / (prof["kernel_ms"] / 1e3) / 1e9 if prof["kernel_ms"] > 0 else 0.0
     try:
@@ -272,10 +285,10 @@ def run_gpu(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
         peak, peak_src = 6800.0, "fallback"
-    roof = {"bound": "hbm", "kernel": "k_cg_apply<float>" if prec == 1 else "k_cg_apply<double>",
+    roof = {"bound": "hbm", "kernel": "k_apply12_tma<float>" if prec == 1 else "k_apply12_tma<double>",
             "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": traffic_for(os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "poisson.cu")),
+            "traffic": traffic_for(os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "stencil.cu")),
             "alg_bytes_per_launch": alg_bytes / launches,
             "avg_launch_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
             "share_of_step": round(prof["kernel_ms"] / ms, 4)}
@@ -309,6 +322,39 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(psi_h.numel() * 8 + fods_h.numel() * 8),
                "d2h_bytes_per_step": int((out_E.numel() + out_V.numel() + out_df.numel() + out_dp.numel()) * 8)}
 
+    # the plain float64 path on the same system (the comparison the metric
+    # names), and the mixed path's deviation from it
+    fp64 = None
+    if prec == 1 and not args.no_fp64:
+        E_m, Va_m, U_m, X_m = ctx.sic_energy_potential(psi, *step_outputs(ctx, psi, fods)[:2], 1.0)
+        ctx64 = Context([s], precision=0, cg_tol=CG_TOL, preconditioner=pc)
+        step64 = lambda: step_with(ctx64, psi, fods, gE)
+        step64()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k64 = 2
+        e0.record(stream)
+        for _ in range(k64):
+            o64 = step64()
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1) / k64
+        phi64, V64 = step_outputs(ctx64, psi, fods)
+        E_d, Va_d, U_d, X_d = ctx64.sic_energy_potential(psi, phi64, V64, 1.0)
+        _, df_m = ctx.sic_backward(psi, fods, *step_outputs(ctx, psi, fods), gE, want_dpsi=False)
+        _, df_d = ctx64.sic_backward(psi, fods, phi64, V64, gE, want_dpsi=False)
+        rho_s = (psi.reshape(sum(s.norb), -1) ** 2)
+        mask = torch.cat([rho_s[:s.norb[0]].sum(0), rho_s[s.norb[0]:].sum(0)]) > 1e-12
+        fp64 = {"value": world * norb / (ms64 / 1e3), "unit": "solves/s", "ms_per_step": ms64, "steps": k64,
+                "speedup_mixed_over_fp64": (world * norb / (ms_step / 1e3)) / (world * norb / (ms64 / 1e3)),
+                "mixed_minus_fp64": {
+                    "max_orbital_energy_Ha": float((U_m + X_m - U_d - X_d).abs().max().item()),
+                    "E_sic_Ha": float((E_m - E_d).abs().max().item()),
+                    "V_avg_maxabs_Ha": float((Va_m - Va_d).abs()[mask].max().item()),
+                    "fod_gradient_max_Ha_per_bohr": float((df_m - df_d).abs().max().item())}}
+        del ctx64
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(s)
@@ -320,7 +366,7 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "precision": args.precision, "preconditioner": args.preconditioner,
                            "cg_tol": CG_TOL, "l2": "inputs larger than L2 (psi 1.07 GB per rank)",
                            "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
                 "gpu_launches": prof["launches"]}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -178,9 +178,12 @@ int flosic_sic_backward(flosic_ctx* ctx, const double* psi, const double* fods,
  * stencil apply) on the stream it runs on.  Errors: ARG, CUDA. */
 int flosic_profile(flosic_ctx* ctx, int enable);
 
-/* Host array out[3]: [0] summed duration (ms) of the timed launches,
- * [1] number of timed launches, [2] kernels launched by ctx (all kinds).
- * Waits for the last timed launch.  reset != 0 zeroes the counters. */
+/* Host array out[4]: [0] summed duration (ms) of the timed launches,
+ * [1] number of timed launches, [2] kernels launched by ctx (all kinds),
+ * [3] algorithmic bytes of the stencil-apply launches (per active orbital
+ * and launch: read z, p_old, q_old and write p, q; 3 arrays on the first
+ * iteration of a solve), counted on the device.  Waits for the device.
+ * reset != 0 zeroes the counters. */
 int flosic_profile_read(flosic_ctx* ctx, double* out, int reset);
 
 /* Allocation-free Poisson solve.  The paper has no counterpart: this entry

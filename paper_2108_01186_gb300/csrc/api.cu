@@ -363,13 +363,14 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     const long long nparts = chunk > M.ntiles[0] ? chunk : M.ntiles[0];
     A(&w.mom_part, 10 * nparts);
     A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
-    A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb);
+    A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_orb_blk, c->h_orb_blk.data(), sizeof(int) * c->norb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
+    if (e == cudaSuccess) e = cudaMemset(g.prof_bytes, 0, sizeof(double));
     if (e == cudaSuccess) e = upload_stencil_constants();
     if (e == cudaSuccess) e = upload_boundary_constants();
     if (e == cudaSuccess && !bidx.empty())
@@ -520,13 +521,20 @@ int flosic_profile_read(flosic_ctx* c, double* out, int reset) {
         if (rc) return rc;
         prof_collect(c);
     }
+    double bytes = 0.0;
+    int rc = check_cuda(c, cudaMemcpy(&bytes, c->ws.cg.prof_bytes, sizeof(double), cudaMemcpyDeviceToHost),
+                        "cudaMemcpy(prof_bytes)");
+    if (rc) return rc;
     out[0] = c->prof_ms;
     out[1] = (double)c->prof_launches;
     out[2] = (double)c->launches;
+    out[3] = bytes;
     if (reset) {
         c->prof_ms = 0.0;
         c->prof_launches = 0;
         c->launches = 0;
+        rc = check_cuda(c, cudaMemset(c->ws.cg.prof_bytes, 0, sizeof(double)), "cudaMemset(prof_bytes)");
+        if (rc) return rc;
     }
     return FLOSIC_OK;
 }

@@ -79,6 +79,7 @@ struct CgState {
     int* n_active;     // [1] number of orbitals with active = 1
     int* n_oactive;    // [1] number of orbitals with oactive = 1
     int* conv;         // [norb] 1 = converged
+    double* prof_bytes;  // [1] algorithmic bytes moved by the stencil-apply launches
 };
 
 struct Workspace {

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(256) k_apply12_pcg(const BlkDesc* __restrict__
         if (linear_tid() == 0) {
             st.count[o] = 0;
             st.pq[o] = sum;
+            atomicAdd(st.prof_bytes, (double)D.G * sizeof(T) * (first ? 3 : 5));
         }
     }
 }
@@ -393,6 +394,8 @@ __global__ void __launch_bounds__(128) k_apply12_tma(const BlkDesc* __restrict__
         if (linear_tid() == 0) {
             st.count[o] = 0;
             st.pq[o] = sum;
+            // algorithmic bytes of this orbital: read z (+ p_old, q_old), write p, q
+            atomicAdd(st.prof_bytes, (double)D.G * sizeof(T) * (first ? 3 : 5));
         }
     }
 }

@@ -204,9 +204,9 @@ class Context:
         self._check(self._L.flosic_profile(self._h, int(enable)))
 
     def profile_read(self, reset=True):
-        out = (ctypes.c_double * 3)()
+        out = (ctypes.c_double * 4)()
         self._check(self._L.flosic_profile_read(self._h, out, int(reset)))
-        return dict(kernel_ms=out[0], kernel_launches=int(out[1]), launches=int(out[2]))
+        return dict(kernel_ms=out[0], kernel_launches=int(out[1]), launches=int(out[2]), kernel_bytes=out[3])
 
     def forward(self, psi, fods, scale=1.0, V0=None):
         phi, S, Q = self.build_flos(psi, fods)

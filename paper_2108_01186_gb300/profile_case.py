@@ -1,0 +1,38 @@
+"""A small, self-contained Poisson workload for profiling captures.
+
+One system of n^3 points (spacing 0.2 bohr) with `norb` Gaussian orbital
+densities, solved once by the multigrid-preconditioned CG of the library
+(mixed precision by default).  Small enough for an ncu --set full capture of
+one stencil launch (8 x 128^3 float32 vectors: 64 MiB each, above L2) and
+free of the oracle and of any randomness.
+
+  python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64]
+"""
+import argparse
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--norb", type=int, default=8)
+    ap.add_argument("--fp64", action="store_true")
+    args = ap.parse_args()
+    import torch
+    from paper_2108_01186_gb300 import build
+    from paper_2108_01186_gb300.flosic import Context
+
+    build.build()
+    n, N, h = args.n, args.norb, 0.2
+    o = -0.5 * h * (n - 1)
+    ctx = Context([dict(n=n, h=h, origin=[o, o, o], norb=[N])], precision=0 if args.fp64 else 1,
+                  cg_tol=1e-10, preconditioner=1)
+    x = torch.linspace(o, -o, n, dtype=torch.float64, device="cuda")
+    Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+    phi = torch.cat([torch.exp(-(X - 0.3 * k) ** 2 - Y ** 2 - Z ** 2).reshape(-1) for k in range(N)]).contiguous()
+    V, it, conv = ctx.orbital_poisson(phi)
+    torch.cuda.synchronize()
+    print("iterations", it.tolist(), "converged", conv.tolist())
+
+
+if __name__ == "__main__":
+    main()
