@@ -51,6 +51,10 @@ __device__ __forceinline__ T nbr6(const T* __restrict__ u, long long g, int x, i
     return s;
 }
 
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
 // Gathers, for n consecutive points starting at (x, y, z) (n = vector width
 // or 1), the centre values and the sum of the six neighbours (zero outside).
 template <class T, int V>
@@ -121,19 +125,24 @@ __global__ void __launch_bounds__(256) k_mg_resid_smooth(const BlkDesc* __restri
     });
 }
 
-// r_c(I) = sum over the 27 fine neighbours of 2I+1 of (1/4,1/2,1/4)^3 s_f
+// r_c(I) = sum over the 27 fine neighbours of 2I+1 of (1/4,1/2,1/4)^3 s_f;
+// V consecutive coarse points per thread, fine rows read with vector loads
+// when they are aligned.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_restrict(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ Lc,
                                                      const LvlDesc* __restrict__ Lf, const int4* __restrict__ tiles_c,
                                                      const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                      const T* __restrict__ sf, T* __restrict__ rc) {
     constexpr int V = Vec<T>::n;
+    using VT = typename Vec<T>::type;
     const TilePos P = tile_pos(blk, Lc, tiles_c, orb_blk, blockIdx.x);
     if (!active[P.o]) return;
     const LvlDesc& C = Lc[P.b];
     const LvlDesc& F = Lf[P.b];
-    const T* fb = sf + F.off + (long long)(P.o - blk[P.b].orb0) * F.G;
+    const long long fbase = F.off + (long long)(P.o - blk[P.b].orb0) * F.G;
+    const T* fb = sf + fbase;
     const long long fy = F.nx, fz = (long long)F.nx * F.ny;
+    const bool fvec = (F.nx % (2 * V) == 0) && (fbase % (2 * V) == 0);
     tile_rows<T>(C, P, [&](int X, int Y, int Z, long long g, int n) {
         T acc[V];
 #pragma unroll
@@ -149,8 +158,19 @@ __global__ void __launch_bounds__(256) k_mg_restrict(const BlkDesc* __restrict__
                 const T w = wc * ((b == 1) ? T(0.5) : T(0.25));
                 const T* row = fb + zf * fz + yf * fy;
                 T f[2 * V + 1];
+                if (n == V && fvec) {
+                    const VT a0 = *reinterpret_cast<const VT*>(row + xf0);
+                    const VT a1 = *reinterpret_cast<const VT*>(row + xf0 + V);
 #pragma unroll
-                for (int k = 0; k < 2 * V + 1; ++k) f[k] = (xf0 + k < F.nx) ? row[xf0 + k] : T(0);
+                    for (int k = 0; k < V; ++k) {
+                        f[k] = reinterpret_cast<const T*>(&a0)[k];
+                        f[V + k] = reinterpret_cast<const T*>(&a1)[k];
+                    }
+                    f[2 * V] = (xf0 + 2 * V < F.nx) ? row[xf0 + 2 * V] : T(0);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 2 * V + 1; ++k) f[k] = (xf0 + k < F.nx) ? row[xf0 + k] : T(0);
+                }
 #pragma unroll
                 for (int k = 0; k < V; ++k)
                     acc[k] += w * (T(0.25) * f[2 * k] + T(0.5) * f[2 * k + 1] + T(0.25) * f[2 * k + 2]);
@@ -174,54 +194,80 @@ __device__ __forceinline__ T prolong_x(const T* __restrict__ row, int ncx, int x
     return T(0.5) * v;
 }
 
-// t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction)
+// t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction).
+// One thread per coarse cell (I, J, K) writes the fine points
+// (2I + a, 2J + b, 2K + c), a, b, c in {0, 1}: odd fine coordinates sit on
+// coarse points (weight 1), even ones halfway between I-1 and I (1/2 each),
+// so the eight coarse values at I-1..I, J-1..J, K-1..K give all eight.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_prolong(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ Lf,
                                                     const LvlDesc* __restrict__ Lc, const int4* __restrict__ tiles_f,
                                                     const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                     const T* __restrict__ r, const T* __restrict__ ec,
                                                     T* __restrict__ t, T omega) {
-    constexpr int V = Vec<T>::n;
-    using VT = typename Vec<T>::type;
+    using V2 = typename Vec2<T>::type;
     const TilePos P = tile_pos(blk, Lf, tiles_f, orb_blk, blockIdx.x);
     const LvlDesc& F = Lf[P.b];
     if (!active[P.o] || F.coarsest) return;
     const LvlDesc& C = Lc[P.b];
     const T* eb = ec + C.off + (long long)(P.o - blk[P.b].orb0) * C.G;
     const T dinv = omega * T(F.h * F.h / 6.0);
-    tile_rows<T>(F, P, [&](int x, int y, int z, long long g, int n) {
-        // coarse rows and weights along y and z
-        int Ys[2], Zs[2];
-        T wy[2], wz[2];
-        int ny_ = 0, nz_ = 0;
-        if (y & 1) { Ys[0] = (y - 1) >> 1; wy[0] = T(1); ny_ = 1; }
-        else { Ys[0] = (y >> 1) - 1; Ys[1] = y >> 1; wy[0] = wy[1] = T(0.5); ny_ = 2; }
-        if (z & 1) { Zs[0] = (z - 1) >> 1; wz[0] = T(1); nz_ = 1; }
-        else { Zs[0] = (z >> 1) - 1; Zs[1] = z >> 1; wz[0] = wz[1] = T(0.5); nz_ = 2; }
-        T out[V];
-        T rv[V];
-        if (n == V) {
-            const VT v = *reinterpret_cast<const VT*>(r + g);
+    const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+    const bool vec = (F.nx % 2 == 0) && (P.base % 2 == 0);
+    const int tid = linear_tid();
+    const int Il = tid & 15, yz = tid >> 4;               // 16 x 16 threads
+    const int I = (P.x0 >> 1) + Il;
+    const int zc0 = P.z0 >> 1, zc1 = (P.z1 + 1) >> 1;
+    auto cval = [&](int X, int Y, int Z) -> T {
+        return (X >= 0 && X < C.nx && Y >= 0 && Y < C.ny && Z >= 0 && Z < C.nz)
+                   ? eb[((long long)Z * C.ny + Y) * C.nx + X] : T(0);
+    };
+    if (2 * I >= F.nx) return;
+    for (int cell = yz; cell < (kTileY / 2) * (zc1 - zc0); cell += 16) {
+        const int J = (P.y0 >> 1) + cell % (kTileY / 2);
+        const int K = zc0 + cell / (kTileY / 2);
+        if (2 * J >= F.ny || 2 * K >= F.nz) continue;
+        // x-interpolated coarse rows: xr[j][k][a] for rows J-1+j, planes K-1+k
+        T xr[2][2][2];
 #pragma unroll
-            for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
-        } else {
-            rv[0] = r[g];
-        }
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int k = 0; k < V; ++k) out[k] = (k < n) ? dinv * rv[k] : T(0);
-        for (int a = 0; a < nz_; ++a) {
-            if (Zs[a] < 0 || Zs[a] >= C.nz) continue;
-            for (int b = 0; b < ny_; ++b) {
-                if (Ys[b] < 0 || Ys[b] >= C.ny) continue;
-                const T w = wz[a] * wy[b];
-                const T* row = eb + ((long long)Zs[a] * C.ny + Ys[b]) * C.nx;
+            for (int k = 0; k < 2; ++k) {
+                const T c0 = cval(I - 1, J - 1 + j, K - 1 + k), c1 = cval(I, J - 1 + j, K - 1 + k);
+                xr[j][k][0] = T(0.5) * (c0 + c1);
+                xr[j][k][1] = c1;
+            }
 #pragma unroll
-                for (int k = 0; k < V; ++k)
-                    if (k < n) out[k] += w * prolong_x(row, C.nx, x + k);
+        for (int c = 0; c < 2; ++c) {
+            const int z = 2 * K + c;
+            if (z >= F.nz) continue;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int y = 2 * J + b;
+                if (y >= F.ny) continue;
+                T u[2];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    // y then z: even -> average of the two, odd -> the upper one
+                    const T y0 = b ? xr[1][0][a] : T(0.5) * (xr[0][0][a] + xr[1][0][a]);
+                    const T y1 = b ? xr[1][1][a] : T(0.5) * (xr[0][1][a] + xr[1][1][a]);
+                    u[a] = c ? y1 : T(0.5) * (y0 + y1);
+                }
+                const int x = 2 * I;
+                const long long g = P.base + z * sz + y * sy + x;
+                if (vec && x + 1 < F.nx) {
+                    const V2 rv = *reinterpret_cast<const V2*>(r + g);
+                    V2 out;
+                    out.x = dinv * rv.x + u[0];
+                    out.y = dinv * rv.y + u[1];
+                    *reinterpret_cast<V2*>(t + g) = out;
+                } else {
+                    t[g] = dinv * r[g] + u[0];
+                    if (x + 1 < F.nx) t[g + 1] = dinv * r[g + 1] + u[1];
+                }
             }
         }
-        store_n<T, V>(t + g, out, n);
-    });
+    }
 }
 
 // e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/6)(h^2 r + sum_nbr t);

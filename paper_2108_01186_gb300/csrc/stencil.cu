@@ -493,6 +493,18 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
     e = fmaf(x.l, y.h, e);
     return ff_quick(p, e);
 }
+// Sum of six pairs: exact two-sums on the high parts, the low parts and the
+// rounding errors added in float (error ~ 6 eps^2 of the largest term).
+__device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
+    ff s = ff_two_sum(a.h, b.h);
+    float err = s.l;
+    s = ff_two_sum(s.h, c.h); err += s.l;
+    s = ff_two_sum(s.h, d.h); err += s.l;
+    s = ff_two_sum(s.h, e.h); err += s.l;
+    s = ff_two_sum(s.h, f.h); err += s.l;
+    err += ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
+    return ff_quick(s.h, err);
+}
 __device__ __forceinline__ ff ff_split(double v) {
     const float h = (float)v;
     return {h, (float)(v - (double)h)};
@@ -587,11 +599,8 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
             ff acc = ff_mul(w[0], qk[kHalf]);
 #pragma unroll
             for (int m = 1; m <= kHalf; ++m) {
-                ff sm = ff_add(plane[ly[k]][lx - m], plane[ly[k]][lx + m]);
-                sm = ff_add(sm, plane[ly[k] - m][lx]);
-                sm = ff_add(sm, plane[ly[k] + m][lx]);
-                sm = ff_add(sm, qk[kHalf - m]);
-                sm = ff_add(sm, qk[kHalf + m]);
+                const ff sm = ff_sum6(plane[ly[k]][lx - m], plane[ly[k]][lx + m], plane[ly[k] - m][lx],
+                                      plane[ly[k] + m][lx], qk[kHalf - m], qk[kHalf + m]);
                 acc = ff_add(acc, ff_mul(w[m], sm));
             }
             if (in[k]) {
