@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--workload", default="128", choices=["128", "uneven"],
+                   help="128: the 128^3 forward+adjoint step (default); uneven: 64 systems of "
+                        "48^3..128^3 grids and 2..40 orbitals, forward step")
     return p.parse_args()
 
 
@@ -215,16 +218,15 @@ def step_outputs(ctx, psi, fods):
 
 def run_gpu(args):
     import torch
+    from paper_2108_01186_gb300 import dist as D
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    D.init("nccl")
     from paper_2108_01186_gb300 import build, synth
     from paper_2108_01186_gb300.flosic import Context
 
     build.build()
-    s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)
+    s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)   # each rank: its own system
     norb = sum(s.norb)
     prec = 1 if args.precision == "mixed" else 0
     pc = 1 if args.preconditioner == "mg" else 0
@@ -241,9 +243,7 @@ def run_gpu(args):
         return step_with(ctx, psi, fods, gE)
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        D.barrier(torch.cuda.synchronize)
 
     for _ in range(args.warmup):
         step(psi, fods)
@@ -266,10 +266,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = D.max_over_ranks(ms, dev)
     ms_step = ms / args.steps
     value = world * norb / (ms_step / 1e3)
 
@@ -313,11 +310,7 @@ def run_gpu(args):
             out_dp.copy_(dpsi, non_blocking=True)
             torch.cuda.synchronize()
         barrier()
-        te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = D.max_over_ranks((time.perf_counter() - t0) / ke, dev)
         e2e = {"value": world * norb / te, "unit": "solves/s",
                "h2d_bytes_per_step": int(psi_h.numel() * 8 + fods_h.numel() * 8),
                "d2h_bytes_per_step": int((out_E.numel() + out_V.numel() + out_df.numel() + out_dp.numel()) * 8)}
@@ -373,10 +366,64 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_uneven(args):
+    """Forward step of an uneven batch: 64 independent one-spin systems with
+    grids 48^3..128^3 (h 0.15..0.3 bohr) and 2..40 orbitals, all in one
+    context (every kernel launch covers every system)."""
+    import torch
+    from paper_2108_01186_gb300 import build, synth
+    from paper_2108_01186_gb300 import dist as D
+    from paper_2108_01186_gb300.flosic import Context
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D.init("nccl")
+    build.build()
+    systems = synth.make_uneven_batch(nsys=64, seed_base=2000 + 100000 * rank)
+    norb = sum(sum(x.norb) for x in systems)
+    ctx = Context(systems, precision=1, cg_tol=1e-10, preconditioner=1)
+    dev = torch.device("cuda", local)
+    psi = torch.tensor(np.concatenate([p.ravel() for x in systems for p in x.psi]), device=dev)
+    fods = torch.tensor(np.concatenate([f.ravel() for x in systems for f in x.fods]), device=dev)
+    del systems
+    stream = torch.cuda.current_stream()
+
+    def step():
+        phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
+        V, iters, _ = ctx.orbital_poisson(phi)
+        return ctx.sic_energy_potential(psi, phi, V, 1.0), iters
+
+    for _ in range(args.warmup):
+        step()
+    D.barrier(torch.cuda.synchronize)
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, iters = step()
+    e1.record(stream)
+    D.barrier(torch.cuda.synchronize)
+    clocks = clk.stop()
+    ms = D.max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+    if rank == 0:
+        print(json.dumps({"metric": "orbital SIC solves/s, uneven batch (forward)", "value": world * norb / (ms / 1e3),
+                          "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32-cg+f64", "data": "synthetic",
+                          "config": {"workload": "64 systems, 48^3..128^3, 2..40 orbitals (%d orbitals, %d spin blocks)"
+                                     % (norb, ctx.nblk), "tma_blocks": None,
+                                     "cg_iters_per_orbital_mean": float(iters.float().mean().item())},
+                          "clocks": clocks}), flush=True)
+    D.barrier()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_gpu(args)
 

@@ -56,20 +56,23 @@ int validate_options(const flosic_options& o, std::string& why) {
 
 // Tensor maps of the stencil's operands, four per block, each a 4-D view
 // (x, y, z, orbital): z with 48 x 28 boxes (tile plus halo), and z, p, q with
-// 32 x 16 centre boxes.  Returns false (and the caller keeps the plain-load
-// stencil) when a block's rows or offset are not 16-byte aligned or the
-// driver entry point is missing.
-bool setup_tensor_maps(flosic_ctx* c, const void* zbuf, const void* pbuf, const void* qbuf, size_t elem) {
+// 32 x 16 centre boxes.  Blocks whose rows or offset are not 16-byte aligned
+// keep the plain-load stencil (flag tma = 0 in their level-0 descriptor).
+// Returns the number of blocks on the copy-engine path.
+int setup_tensor_maps(flosic_ctx* c, const void* zbuf, const void* pbuf, const void* qbuf, size_t elem) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q{};
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
-        return false;
+        return 0;
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     std::vector<CUtensorMap> maps(4 * (size_t)c->nblk);
+    std::vector<LvlDesc>& L0 = c->mg.h_lvl[0];
+    int n_ok = 0;
     for (int b = 0; b < c->nblk; ++b) {
         const BlkDesc& B = c->blk[b];
-        if ((B.nx * elem) % 16 != 0 || (B.off * (long long)elem) % 16 != 0) return false;
+        L0[b].tma = 0;
+        if ((B.nx * elem) % 16 != 0 || (B.off * (long long)elem) % 16 != 0) continue;
         const cuuint64_t dims[4] = {(cuuint64_t)B.nx, (cuuint64_t)B.ny, (cuuint64_t)B.nz, (cuuint64_t)B.N};
         const cuuint64_t strides[3] = {(cuuint64_t)B.nx * elem, (cuuint64_t)B.nx * B.ny * elem,
                                        (cuuint64_t)B.G * elem};
@@ -77,24 +80,32 @@ bool setup_tensor_maps(flosic_ctx* c, const void* zbuf, const void* pbuf, const 
         const cuuint32_t box_ctr[4] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 1, 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         const void* bufs[4] = {zbuf, zbuf, pbuf, qbuf};
-        for (int k = 0; k < 4; ++k) {
+        bool ok = true;
+        for (int k = 0; k < 4 && ok; ++k) {
             void* base = (unsigned char*)bufs[k] + B.off * (long long)elem;
-            CUresult r = encode(&maps[4 * b + k], elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                                4, base, dims, strides, k == 0 ? box_halo : box_ctr, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return false;
+            ok = encode(&maps[4 * b + k], elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                        base, dims, strides, k == 0 ? box_halo : box_ctr, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         }
+        if (!ok) continue;
+        L0[b].tma = 1;
+        ++n_ok;
     }
+    if (n_ok == 0) return 0;
     void* d = nullptr;
-    if (cudaMalloc(&d, sizeof(CUtensorMap) * maps.size()) != cudaSuccess) return false;
+    if (cudaMalloc(&d, sizeof(CUtensorMap) * maps.size()) != cudaSuccess) return 0;
     c->allocations.push_back(d);
-    if (cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) return false;
-    if (cudaFuncSetAttribute(apply12_tma_symbol(elem == 4), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)apply12_tma_smem(elem)) != cudaSuccess)
-        return false;
+    if (cudaMemcpy(d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaFuncSetAttribute(apply12_tma_symbol(elem == 4), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)apply12_tma_smem(elem)) != cudaSuccess ||
+        cudaMemcpy(c->mg.d_lvl[0], L0.data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice) != cudaSuccess) {
+        for (auto& D : L0) D.tma = 0;
+        cudaMemcpy(c->mg.d_lvl[0], L0.data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice);
+        return 0;
+    }
     c->d_tmaps = d;
-    return true;
+    return n_ok;
 }
 
 // Waits for the stream and returns the device status words.
@@ -384,7 +395,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     }
     if (e == cudaSuccess && M.enabled) {
         const bool f32 = (o.precision == FLOSIC_MIXED);
-        c->tma_ok = f32 ? setup_tensor_maps(c, w.z32, w.p32, w.q32, 4) : setup_tensor_maps(c, w.z64, w.p64, w.q64, 8);
+        c->n_tma_blocks = f32 ? setup_tensor_maps(c, w.z32, w.p32, w.q32, 4) : setup_tensor_maps(c, w.z64, w.p64, w.q64, 8);
         cudaGetLastError();   // a refused attribute or entry point only disables the copy-engine path
     }
     if (e != cudaSuccess) {

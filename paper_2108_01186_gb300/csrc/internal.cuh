@@ -50,6 +50,7 @@ struct LvlDesc {
     int nchunk;            // chunks per orbital
     long long tile0;       // first tile of orbital 0 in this level's tile table
     int ntile;             // tiles per orbital
+    int tma;               // level 0: 1 if the stencil operands of this block are TMA-staged
 };
 
 // Per-level buffers as the kernels see them (passed by value).
@@ -144,7 +145,7 @@ struct flosic_ctx {
     std::string err;
     int* h_pinned = nullptr;                // small pinned host buffer
     mutable long long launches = 0;         // kernels launched by this context
-    bool tma_ok = false;                    // stencil planes staged by the copy engine
+    int n_tma_blocks = 0;                   // blocks whose stencil operands the copy engine stages
     void* d_tmaps = nullptr;                // per-block tensor maps of the z buffer (CUtensorMap)
     // optional CUDA-event timing of the dominant kernel (the CG stencil apply)
     bool profiling = false;

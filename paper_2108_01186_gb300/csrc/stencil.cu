@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_apply12_pcg(const BlkDesc* __restrict__
     __shared__ T plane[kPY][kPX];
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!st.active[P.o]) return;
+    if (!st.active[P.o] || L[P.b].tma) return;
     const LvlDesc& D = L[P.b];
     const double bd = st.beta[P.o];
     const bool first = (bd == 0.0);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128) k_apply12_tma(const BlkDesc* __restrict__
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(T) * kRing2 * kStageElems);
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!st.active[P.o]) return;
+    if (!st.active[P.o] || !L[P.b].tma) return;
     const LvlDesc& D = L[P.b];
     const CUtensorMap* mp = maps + 4 * P.b;    // z with halo, z centre, p centre, q centre
     const int oi = P.o - blk[P.b].orb0;
@@ -651,15 +651,17 @@ template <class T>
 void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s) {
     const Multigrid& M = c->mg;
     prof_begin(c, s);
-    if (c->tma_ok) {
+    if (c->n_tma_blocks > 0) {       // blocks whose operands the copy engine stages
         k_apply12_tma<T><<<(unsigned)M.ntiles[0], dim3(kTileX / 2, kTileY / 2), apply12_tma_smem(sizeof(T)), s>>>(
             c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_tmaps, z, p, q, c->ws.cg,
             c->ws.status + 3);
-    } else {
+        note_launch(c);
+    }
+    if (c->n_tma_blocks < c->nblk) {  // the rest: the same sweep with plain loads
         k_apply12_pcg<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
             c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, z, p, q, c->ws.cg);
+        note_launch(c);
     }
-    note_launch(c);
     prof_end(c, s);
 }
 template void launch_apply12_pcg<float>(flosic_ctx*, const float*, float*, float*, cudaStream_t);

@@ -75,11 +75,12 @@ def _place_atoms(rng, L, natoms, min_sep=2.0, max_tries=200000):
 
 
 def max_atoms(n, h, min_sep=2.0):
-    """Atoms that fit by a simple packing bound (used to cap orbital counts)."""
+    """Atoms that random rejection sampling places reliably (about 30 % of
+    the simple-cubic packing bound); used to cap orbital counts."""
     L = n * h
     half = L / 2.0 - min(6.0, 0.4 * L)
-    per_side = int(math.floor(2.0 * half / min_sep)) + 1
-    return max(1, per_side ** 3)
+    per_side = 2.0 * half / min_sep + 1.0
+    return max(1, int(0.3 * per_side ** 3))
 
 
 def _basis(atoms, rng, x1d):

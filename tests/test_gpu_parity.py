@@ -168,10 +168,14 @@ def test_forward_config0_fp64_and_mixed(F, orc, pc):
 @pytest.mark.parametrize("pc", [0, 1])
 def test_uneven_batch_matches_per_system_oracle(F, orc, pc):
     # different grids give different multigrid depths (5 is a single level)
+    # aligned rows (nx % 4 == 0: copy-engine stencil) and unaligned ones
+    # (plain-load stencil) in the same batch
     systems = [synth.make_system(18, 0.45, 2, [3], seed=41),
                synth.make_system(23, 0.35, 2, [4, 2], seed=42),
                synth.make_system(15, 0.5, 1, [1], seed=43),
-               synth.make_system(5, 0.9, 1, [1], seed=44)]
+               synth.make_system(5, 0.9, 1, [1], seed=44),
+               synth.make_system(20, 0.45, 1, [3, 3], seed=45),
+               synth.make_system(24, 0.5, 2, [5], seed=46)]
     ctx = F.Context(systems, precision=1, cg_tol=1e-11, preconditioner=pc)
     psi = _flat([p for s in systems for p in s.psi])
     fods = _flat([f for s in systems for f in s.fods])
