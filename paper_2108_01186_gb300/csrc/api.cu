@@ -1,4 +1,5 @@
 // C ABI of the FLO-SIC step: context, workspace and the four step calls.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -314,6 +315,8 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
             for (int b = 0; b < c->nblk; ++b) { nl[b] = 1; coarsest[b] = 0; }
         }
         const size_t tsz = (o.precision == FLOSIC_FP64) ? sizeof(double) : sizeof(float);
+        // last-point diagonal weights per block and dimension, level by level
+        std::vector<std::array<double, 3>> cl(c->nblk, std::array<double, 3>{2.0, 2.0, 2.0});
         for (int l = 0; l < M.nlev; ++l) {
             long long offl = 0, chl = 0, tl = 0;
             std::vector<int4> tiles;
@@ -329,6 +332,14 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                     D.G = (long long)D.nx * D.ny * D.nz;
                     D.nchunk = (int)((D.G + kChunk - 1) / kChunk);
                     D.coarsest = (l == nl[b] - 1) ? 1 : 0;
+                    const int sides[3] = {D.nx, D.ny, D.nz};
+                    D.corr = 0;
+                    for (int k = 0; k < 3; ++k) {
+                        D.cl[k] = (float)cl[b][k];
+                        D.corr |= (cl[b][k] != 2.0) ? 1 : 0;
+                        // the coarse level inherits the Galerkin weight
+                        cl[b][k] = (sides[k] % 2 == 0) ? 2.0 * cl[b][k] - 1.0 : 1.0 + 0.5 * cl[b][k];
+                    }
                     const int tx = (D.nx + kTileX - 1) / kTileX, ty = (D.ny + kTileY - 1) / kTileY,
                               tz = (D.nz + kTileZ - 1) / kTileZ;
                     D.ntile = tx * ty * tz;

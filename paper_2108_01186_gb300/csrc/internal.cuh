@@ -51,6 +51,11 @@ struct LvlDesc {
     long long tile0;       // first tile of orbital 0 in this level's tile table
     int ntile;             // tiles per orbital
     int tma;               // level 0: 1 if the stencil operands of this block are TMA-staged
+    // Diagonal weight (units 1/h_l^2) of the 7-point operator at the last
+    // point of each dimension, 2 elsewhere; differs from 2 on levels whose
+    // parent had an even side (see multigrid.cu).  corr = any of them != 2.
+    float cl[3];
+    int corr;
 };
 
 // Per-level buffers as the kernels see them (passed by value).

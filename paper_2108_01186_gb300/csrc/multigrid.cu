@@ -9,7 +9,14 @@
 // size instead of O(n).
 //
 // Vertex-centred coarsening: coarse point I sits on fine point 2I+1,
-// n_c = floor(n/2); coarsen while every side is >= 6.  Restriction is full
+// n_c = floor(n/2); coarsen while every side is >= 6.  On an even side the
+// last coarse point is the last fine point, so the coarse grid's zero
+// boundary would sit one coarse spacing out while the true one is closer:
+// the 7-point operator of such a level keeps the off-diagonal -1/h_l^2 but
+// takes at the last point of that dimension the diagonal weight of the 1-D
+// Galerkin operator P^T A P / 2 (c' = 2c - 1 for an even parent side,
+// 1 + c/2 for an odd one, c = 2 on the fine grid).  Without it the V-cycle
+// loses most of its strength on grids such as 128^3.  Restriction is full
 // weighting (1/4, 1/2, 1/4 per direction) = (1/8) P^T with P trilinear
 // interpolation.  Smoother: one damped-Jacobi sweep before and after
 // (omega = 0.8); coarsest level: 40 damped-Jacobi sweeps from zero in shared
@@ -49,6 +56,17 @@ __device__ __forceinline__ T nbr6(const T* __restrict__ u, long long g, int x, i
     if (z > 0) s += u[g - sz];
     if (z < D.nz - 1) s += u[g + sz];
     return s;
+}
+
+// 1 / (sum of the diagonal weights) at (x, y, z) of a level: 1/6 away from
+// the last point of every dimension.
+template <class T>
+__device__ __forceinline__ T inv_diag(const LvlDesc& D, int x, int y, int z) {
+    T dd = T(6);
+    if (x == D.nx - 1) dd += T(D.cl[0]) - T(2);
+    if (y == D.ny - 1) dd += T(D.cl[1]) - T(2);
+    if (z == D.nz - 1) dd += T(D.cl[2]) - T(2);
+    return T(1) / dd;
 }
 
 template <class T> struct Vec2;
@@ -106,7 +124,8 @@ __device__ __forceinline__ void store_n(T* dst, const T* v, int n) {
     else dst[0] = v[0];
 }
 
-// s = r - A2 (omega D^-1 r) = (1 - omega) r + (omega/6) sum_nbr r
+// s = r - A2 (omega D^-1 r) = (1 - omega) r + omega sum_nbr r / dd(nbr),
+// dd = 6 except on the last points of a level with corrected weights.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_resid_smooth(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                          const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
@@ -116,7 +135,24 @@ __global__ void __launch_bounds__(256) k_mg_resid_smooth(const BlkDesc* __restri
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
     if (!active[P.o] || D.coarsest) return;
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
     tile_rows<T>(D, P, [&](int x, int y, int z, long long g, int n) {
+        if (D.corr && (x + n >= D.nx - 1 || y >= D.ny - 2 || z >= D.nz - 2)) {
+            // a neighbour may lie on a last point: weight each one
+            for (int k = 0; k < n; ++k) {
+                const int xk = x + k;
+                const long long gk = g + k;
+                T sum = T(0);
+                if (xk > 0) sum += r[gk - 1] * inv_diag<T>(D, xk - 1, y, z);
+                if (xk < D.nx - 1) sum += r[gk + 1] * inv_diag<T>(D, xk + 1, y, z);
+                if (y > 0) sum += r[gk - sy] * inv_diag<T>(D, xk, y - 1, z);
+                if (y < D.ny - 1) sum += r[gk + sy] * inv_diag<T>(D, xk, y + 1, z);
+                if (z > 0) sum += r[gk - sz] * inv_diag<T>(D, xk, y, z - 1);
+                if (z < D.nz - 1) sum += r[gk + sz] * inv_diag<T>(D, xk, y, z + 1);
+                s[gk] = (T(1) - omega) * r[gk] + omega * sum;
+            }
+            return;
+        }
         T c[V], nb[V], out[V];
         centre_nbr<T, V>(r, D, x, y, z, g, n, c, nb);
 #pragma unroll
@@ -255,22 +291,28 @@ __global__ void __launch_bounds__(256) k_mg_prolong(const BlkDesc* __restrict__ 
                 }
                 const int x = 2 * I;
                 const long long g = P.base + z * sz + y * sy + x;
+                T d0 = dinv, d1 = dinv;
+                if (F.corr && (x + 2 >= F.nx || y == F.ny - 1 || z == F.nz - 1)) {
+                    const T oh2 = omega * T(F.h * F.h);
+                    d0 = oh2 * inv_diag<T>(F, x, y, z);
+                    d1 = oh2 * inv_diag<T>(F, x + 1, y, z);
+                }
                 if (vec && x + 1 < F.nx) {
                     const V2 rv = *reinterpret_cast<const V2*>(r + g);
                     V2 out;
-                    out.x = dinv * rv.x + u[0];
-                    out.y = dinv * rv.y + u[1];
+                    out.x = d0 * rv.x + u[0];
+                    out.y = d1 * rv.y + u[1];
                     *reinterpret_cast<V2*>(t + g) = out;
                 } else {
-                    t[g] = dinv * r[g] + u[0];
-                    if (x + 1 < F.nx) t[g + 1] = dinv * r[g + 1] + u[1];
+                    t[g] = d0 * r[g] + u[0];
+                    if (x + 1 < F.nx) t[g + 1] = d1 * r[g + 1] + u[1];
                 }
             }
         }
     }
 }
 
-// e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/6)(h^2 r + sum_nbr t);
+// e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/dd)(h^2 r + sum_nbr t);
 // on level 0 also z.r per orbital -> rz, beta = rz / rz_old.
 template <class T, bool kLevel0>
 __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
@@ -296,9 +338,11 @@ __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict
         } else {
             rv[0] = r[g];
         }
+        const bool edge = !kLevel0 && D.corr && (x + n >= D.nx || y == D.ny - 1 || z == D.nz - 1);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            out[k] = (T(1) - omega) * c[k] + omega * T(1.0 / 6.0) * (h2 * rv[k] + nb[k]);
+            const T w = edge ? inv_diag<T>(D, x + k, y, z) : T(1.0 / 6.0);
+            out[k] = (T(1) - omega) * c[k] + omega * w * (h2 * rv[k] + nb[k]);
             if (kLevel0 && k < n) rz += rv[k] * out[k];
         }
         store_n<T, V>(e + g, out, n);
@@ -339,16 +383,18 @@ __global__ void k_mg_coarsest(const BlkDesc* __restrict__ blk, MgPtrs<T> mp, con
     T* ea = sh + G;
     T* eb = sh + 2 * G;
     const T h2 = T(D.h * D.h);
+    const int pl = D.nx * D.ny;
     for (int k = threadIdx.x; k < G; k += blockDim.x) {
+        const int z = k / pl, rem = k - z * pl, y = rem / D.nx, x = rem - y * D.nx;
         rs[k] = r[k];
-        ea[k] = omega * h2 * T(1.0 / 6.0) * rs[k];
+        ea[k] = omega * h2 * inv_diag<T>(D, x, y, z) * rs[k];
     }
     __syncthreads();
-    const int pl = D.nx * D.ny;
     for (int sw = 1; sw < nsweep; ++sw) {
         for (int k = threadIdx.x; k < G; k += blockDim.x) {
             const int z = k / pl, rem = k - z * pl, y = rem / D.nx, x = rem - y * D.nx;
-            eb[k] = (T(1) - omega) * ea[k] + omega * T(1.0 / 6.0) * (h2 * rs[k] + nbr6(ea, k, x, y, z, D));
+            eb[k] = (T(1) - omega) * ea[k] +
+                    omega * inv_diag<T>(D, x, y, z) * (h2 * rs[k] + nbr6(ea, k, x, y, z, D));
         }
         __syncthreads();
         T* tmp = ea; ea = eb; eb = tmp;
