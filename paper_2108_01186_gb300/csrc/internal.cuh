@@ -40,6 +40,10 @@ constexpr int kMaxLevels = 10;
 constexpr int kTileX = 32, kTileY = 16, kTileZ = 32;   // 3-D tiles of the sweeps (threads 32 x 8)
 constexpr int kCoarseSweeps = 40;      // damped-Jacobi sweeps on the coarsest level
 constexpr int kCoarseMax = 2000;       // largest coarsest level (points) kept in shared memory
+// planes of a tile staged with the 6-point x/y halo by the z-marching sweeps
+constexpr int kPX = kTileX + 2 * kHalf;   // staged plane width
+constexpr int kPY = kTileY + 2 * kHalf;   // staged plane height
+constexpr int kSlots = (kPX * kPY + kTileX * (kTileY / 2) - 1) / (kTileX * (kTileY / 2));   // per thread
 struct LvlDesc {
     int nx, ny, nz;
     int coarsest;          // 1 if this is the block's last level
@@ -178,7 +182,7 @@ void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, co
 void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s);
 cudaError_t upload_boundary_constants();
 cudaError_t setup_boundary(flosic_ctx* c);
-int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream_t s);
+int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s);
 void finish_poisson(flosic_ctx* c, int* iters, int* conv, cudaStream_t s);
 cudaError_t upload_stencil_constants();
 void launch_bc_adjoint(flosic_ctx* c, const double* W, const double* V, double* out, cudaStream_t s);
@@ -196,6 +200,15 @@ size_t apply12_tma_smem(size_t elem);
 const void* apply12_tma_symbol(bool f32);
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s);
+cudaError_t upload_ff_weights();
+// mixed precision: float-float refinement around the float32 inner solves
+// (b is overwritten by its float-float pairs; x holds the solution's pairs)
+void launch_ff_init(flosic_ctx* c, double* b, const double* V, bool warm, float2* x, float* p32, double tol2,
+                    double inner_tol2, cudaStream_t s);
+void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
+                        double inner_tol2, cudaStream_t s);
+void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s);
+void launch_join_ff(flosic_ctx* c, const float2* x, double* V, cudaStream_t s);
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
 const void* k_lowdin_symbol();
 int check_cuda(flosic_ctx* c, cudaError_t e, const char* what);

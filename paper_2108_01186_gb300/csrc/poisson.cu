@@ -487,77 +487,6 @@ __global__ void __launch_bounds__(256) k_residual_zero(const BlkDesc* __restrict
     }
 }
 
-// Start of an inner float32 solve (tile version): r32 = float(r64),
-// d32 = 0 (p32 = r32 when given, for the unpreconditioned solver);
-// rr = r32.r32; inner target thr = max(inner_tol^2 rr, (tol^2/4) bb).
-__global__ void __launch_bounds__(256) k_inner_init_t(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
-                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                      const double* __restrict__ r64, float* __restrict__ r32,
-                                                      float* __restrict__ p32, float* __restrict__ d32,
-                                                      double inner_tol2, double tol2, CgState st) {
-    __shared__ double scratch[32];
-    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!st.oactive[P.o]) return;
-    const LvlDesc& D = L[P.b];
-    float rr = 0.0f;
-    tile_elementwise<float>(D, P, [&](long long g, int n) {
-        if (n == 4) {
-            const double2 a = *reinterpret_cast<const double2*>(r64 + g);
-            const double2 b = *reinterpret_cast<const double2*>(r64 + g + 2);
-            const float4 v = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-            *reinterpret_cast<float4*>(r32 + g) = v;
-            if (p32) *reinterpret_cast<float4*>(p32 + g) = v;
-            *reinterpret_cast<float4*>(d32 + g) = make_float4(0.f, 0.f, 0.f, 0.f);
-            rr += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
-        } else {
-            const float v = (float)r64[g];
-            r32[g] = v;
-            if (p32) p32[g] = v;
-            d32[g] = 0.0f;
-            rr += v * v;
-        }
-    });
-    if (tile_arrive((double)rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
-        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
-        if (linear_tid() == 0) {
-            const int o = P.o;
-            st.count[o] = 0;
-            st.rr[o] = sum;
-            st.rz[o] = 0.0;
-            st.beta[o] = 0.0;
-            const double a = inner_tol2 * sum, c = 0.25 * tol2 * st.bb[o];
-            st.thr[o] = a > c ? a : c;
-            if (sum > st.thr[o]) {
-                st.active[o] = 1;
-                atomicAdd(st.n_active, 1);
-            } else {
-                st.active[o] = 0;
-            }
-        }
-    }
-}
-
-// x64 += d32 for orbitals still refining (tile version).
-__global__ void __launch_bounds__(256) k_correct_t(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
-                                                   const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                   const float* __restrict__ d32, double* __restrict__ x, CgState st) {
-    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!st.oactive[P.o]) return;
-    const LvlDesc& D = L[P.b];
-    tile_elementwise<float>(D, P, [&](long long g, int n) {
-        if (n == 4) {
-            const float4 d = *reinterpret_cast<const float4*>(d32 + g);
-            double2 a = *reinterpret_cast<double2*>(x + g);
-            double2 b = *reinterpret_cast<double2*>(x + g + 2);
-            a.x += d.x; a.y += d.y; b.x += d.z; b.y += d.w;
-            *reinterpret_cast<double2*>(x + g) = a;
-            *reinterpret_cast<double2*>(x + g + 2) = b;
-        } else {
-            x[g] += (double)d32[g];
-        }
-    });
-}
-
 __global__ void k_cg_finish(int norb, CgState st, int* out_iters, int* out_conv, int* status) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= norb) return;
@@ -623,7 +552,7 @@ static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* p, T* tbuf, T* q, int set_
 // Solves A V = b for every orbital (b from launch_rhs, ||b||^2 in cg.bb).
 // Returns a flosic status; iteration counts and convergence flags stay in the
 // CG state (copied out by finish_poisson).
-int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream_t s) {
+int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) {
     Workspace& w = c->ws;
     CgState& st = w.cg;
     const unsigned nb = (unsigned)c->nchunk_total;
@@ -632,7 +561,8 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
     const int max_iter = c->opt.max_iter;
     const int check_every = 8;
     const bool mg = c->mg.enabled;
-    if (!warm && check_cuda(c, cudaMemsetAsync(V, 0, sizeof(double) * c->orb_elems, s), "memset V"))
+    if (!warm && c->opt.precision == FLOSIC_FP64 &&
+        check_cuda(c, cudaMemsetAsync(V, 0, sizeof(double) * c->orb_elems, s), "memset V"))
         return FLOSIC_ERR_CUDA;
     k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st); note_launch(c);
     if (c->opt.precision == FLOSIC_FP64) {
@@ -662,20 +592,22 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
             }
         }
     } else {
+        // float32 inner solves inside a float-float refinement (refine.cu);
+        // b becomes its pairs, the idle float64 residual buffer holds x
         const double inner_tol2 = 1e-12;   // each float32 solve gains ~6 digits
-        for (int outer = 0; outer < 40; ++outer) {
-            if (outer == 0 && !warm)
-                launch_residual_zero(c, b, w.r64, tol2, st.oactive, st.n_oactive, s);
-            else
-                launch_residual12(c, b, V, w.r64, tol2, max_iter, st.oactive, st.n_oactive, outer == 0 ? 1 : 0, s);
+        float2* x = reinterpret_cast<float2*>(w.r64);
+        float* p32 = mg ? nullptr : w.p32;
+        if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset")) return FLOSIC_ERR_CUDA;
+        launch_ff_init(c, b, V, warm, x, p32, tol2, inner_tol2, s);
+        for (int round = 0; round < 40; ++round) {
+            if (round > 0 || warm) {
+                if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
+                    return FLOSIC_ERR_CUDA;
+                launch_residual_ff(c, b, x, p32, tol2, inner_tol2, s);
+            }
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
-            if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
-                return FLOSIC_ERR_CUDA;
-            k_inner_init_t<<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
-                c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, w.r64, w.r32, mg ? nullptr : w.p32, w.d32,
-                inner_tol2, tol2, st); note_launch(c);
             if (mg) {
                 int rc = pcg_mg<float>(c, w.d32, w.r32, w.z32, w.p32, w.p32b, w.q32, 0, s);
                 if (rc) return rc;
@@ -694,9 +626,9 @@ int run_poisson(flosic_ctx* c, const double* b, double* V, bool warm, cudaStream
                     k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
                 }
             }
-            k_correct_t<<<(unsigned)c->mg.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
-                c->d_blk, c->mg.d_lvl[0], c->mg.d_tiles[0], c->d_orb_blk, w.d32, V, st); note_launch(c);
+            launch_correct_ff(c, x, s);
         }
+        launch_join_ff(c, x, V, s);
     }
     return check_cuda(c, cudaGetLastError(), "poisson kernels");
 }

@@ -1,0 +1,338 @@
+// Mixed-precision refinement of the per-orbital Poisson solves (Sec. II.A
+// solves them iteratively; splitting the precision is this library's).
+//
+// The float32 multigrid-preconditioned CG computes corrections d of
+// A d = r.  The solution x, the right-hand side b and the residual
+// r = b - A x live in unevaluated float-float pairs (hi, lo), about 48
+// significant bits: Knuth's error-free two-sum for additions and an
+// FMA-based exact two-product.  GB300 runs float64 at a small fraction of
+// its float32 rate, so inside the refinement loop no float64 operation runs
+// per grid point; float64 appears only where b (and a warm start) are split
+// into pairs at the start and where x is joined into the float64 result.
+//
+// Round structure per orbital:  r = b - A x (pairs) -> stop if
+// r.r <= tol^2 b.b, else a float32 solve of A d = float(r) to
+// max(inner_tol^2 r.r, tol^2 b.b / 4) -> x += d (pairs).
+#include "internal.cuh"
+
+namespace flosic {
+
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = ff_two_sum(x.h, y.h);
+    const ff t = ff_two_sum(x.l, y.l);
+    s.l += t.h;
+    s = ff_quick(s.h, s.l);
+    s.l += t.l;
+    return ff_quick(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, e);
+    e = fmaf(x.l, y.h, e);
+    return ff_quick(p, e);
+}
+// Sum of six pairs: exact two-sums on the high parts, the low parts and the
+// rounding errors added in float (error ~ 6 eps^2 of the largest term).
+__device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
+    ff s = ff_two_sum(a.h, b.h);
+    float err = s.l;
+    s = ff_two_sum(s.h, c.h); err += s.l;
+    s = ff_two_sum(s.h, d.h); err += s.l;
+    s = ff_two_sum(s.h, e.h); err += s.l;
+    s = ff_two_sum(s.h, f.h); err += s.l;
+    err += ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
+    return ff_quick(s.h, err);
+}
+// float64 -> pair and back (the only float64 arithmetic of the scheme)
+__device__ __forceinline__ float2 ff_split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ double ff_join(float2 p) { return (double)p.x + (double)p.y; }
+__device__ __forceinline__ ff as_ff(float2 p) { return {p.x, p.y}; }
+
+__constant__ float c_wff[2 * (kHalf + 1)];   // 3 w_0, w_1 .. w_6 as (hi, lo) pairs
+
+cudaError_t upload_ff_weights() {
+    double w[kHalf + 1];
+    stencil_weights(w);
+    float f[2 * (kHalf + 1)];
+    for (int m = 0; m <= kHalf; ++m) {
+        const double ww = (m == 0) ? 3.0 * w[0] : w[m];
+        f[2 * m] = (float)ww;
+        f[2 * m + 1] = (float)(ww - (double)f[2 * m]);
+    }
+    return cudaMemcpyToSymbol(c_wff, f, sizeof(f));
+}
+
+// Last CTA of an orbital, once r.r is known: the outer stop test, else the
+// start of the next float32 solve (its target, active flag and counters).
+__device__ __forceinline__ void start_round(CgState& st, int o, double rr, double tol2, double inner_tol2,
+                                            int max_iter) {
+    st.rr[o] = rr;
+    st.active[o] = 0;
+    if (!(rr > tol2 * st.bb[o])) {
+        st.oactive[o] = 0;
+        st.conv[o] = 1;
+        atomicSub(st.n_oactive, 1);
+        return;
+    }
+    if (st.iters[o] >= max_iter || !isfinite(rr)) {
+        st.oactive[o] = 0;
+        atomicSub(st.n_oactive, 1);
+        return;
+    }
+    const double a = inner_tol2 * rr, c = 0.25 * tol2 * st.bb[o];
+    st.thr[o] = a > c ? a : c;
+    st.rz[o] = 0.0;
+    st.beta[o] = 0.0;
+    st.active[o] = 1;
+    atomicAdd(st.n_active, 1);
+}
+
+// Start of the refinement: b (float64, overwritten in place by its pairs),
+// x = warm start (pairs) or 0; b.b per orbital.  Without a warm start the
+// residual is b itself: r32 = float(b), d32 = 0 (p32 = r32 when given) and
+// the first float32 solve starts here.
+__global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                 const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                 double* b, const double* __restrict__ V, float2* __restrict__ x,
+                                                 float* __restrict__ r32, float* __restrict__ p32,
+                                                 float* __restrict__ d32, int warm, double tol2, double inner_tol2,
+                                                 int max_iter, CgState st) {
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    float2* bp = reinterpret_cast<float2*>(b);   // same 8 bytes per point
+    float bb = 0.f;
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        for (int k = 0; k < n; ++k) {
+            const float2 v = ff_split(b[g + k]);
+            bp[g + k] = v;
+            bb += v.x * v.x;
+            if (warm) {
+                x[g + k] = ff_split(V[g + k]);
+            } else {
+                x[g + k] = make_float2(0.f, 0.f);
+                r32[g + k] = v.x;
+                d32[g + k] = 0.f;
+                if (p32) p32[g + k] = v.x;
+            }
+        }
+    });
+    if (tile_arrive((double)bb, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[P.o] = 0;
+            st.bb[P.o] = sum;
+            if (!warm) start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
+        }
+    }
+}
+
+// r = b - A x in pairs on the tiles of the stencil sweep (a CTA marches a
+// 32 x 16 column tile along z, planes staged with the 6-point x/y halo in
+// shared memory, the 13 z-values of its columns in registers).  Writes
+// r32 = float(r), d32 = 0 (p32 = r32 when given) and starts the next round.
+__global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                       const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                       const float2* __restrict__ b, const float2* __restrict__ x,
+                                                       float* __restrict__ r32, float* __restrict__ p32,
+                                                       float* __restrict__ d32, double tol2, double inner_tol2,
+                                                       int max_iter, CgState st) {
+    __shared__ ff plane[kPY][kPX];
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTileX + tx;
+    const int nthr = kTileX * (kTileY / 2);
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    const int gx = P.x0 + tx;
+    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
+    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
+    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
+    long long soff[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) {
+        const int e = tid + j * nthr;
+        soff[j] = -1;
+        if (e < kPX * kPY) {
+            const int yy = e / kPX, xx = e - yy * kPX;
+            const int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
+            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
+        }
+    }
+    const float2 zero2 = make_float2(0.f, 0.f);
+    ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * kHalf; ++j) {
+        const int zz = P.z0 - kHalf + j;
+        const bool okz = zz >= 0 && zz < D.nz;
+        q0[j] = as_ff((in0 && okz) ? x[P.base + zz * sz + c0] : zero2);
+        q1[j] = as_ff((in1 && okz) ? x[P.base + zz * sz + c1] : zero2);
+    }
+    float2 pre[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[P.base + P.z0 * sz + soff[j]] : zero2;
+    ff w[kHalf + 1];
+#pragma unroll
+    for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
+    ff ih2;   // 1/h^2 as a pair (once per CTA)
+    {
+        const float2 v = ff_split(1.0 / (D.h * D.h));
+        ih2 = as_ff(v);
+    }
+    float rrf = 0.f;
+    ff* flat = &plane[0][0];
+    for (int z = P.z0; z < P.z1; ++z) {
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int e = tid + j * nthr;
+            if (e < kPX * kPY) flat[e] = as_ff(pre[j]);
+        }
+        {
+            const int zz = z + kHalf;
+            q0[2 * kHalf] = as_ff((in0 && zz < D.nz) ? x[P.base + zz * sz + c0] : zero2);
+            q1[2 * kHalf] = as_ff((in1 && zz < D.nz) ? x[P.base + zz * sz + c1] : zero2);
+        }
+        __syncthreads();
+        if (z + 1 < P.z1) {
+            const long long pz = P.base + (z + 1) * sz;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[pz + soff[j]] : zero2;
+        }
+        const int lx = tx + kHalf;
+        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
+        const bool in[2] = {in0, in1};
+        const long long cc[2] = {c0, c1};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const ff* qk = (k == 0) ? q0 : q1;
+            ff acc = ff_mul(w[0], qk[kHalf]);
+#pragma unroll
+            for (int m = 1; m <= kHalf; ++m) {
+                const ff sm = ff_sum6(plane[ly[k]][lx - m], plane[ly[k]][lx + m], plane[ly[k] - m][lx],
+                                      plane[ly[k] + m][lx], qk[kHalf - m], qk[kHalf + m]);
+                acc = ff_add(acc, ff_mul(w[m], sm));
+            }
+            if (in[k]) {
+                // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
+                const long long g = P.base + z * sz + cc[k];
+                const ff r = ff_add(as_ff(b[g]), ff_mul(acc, ih2));
+                const float rv = r.h;
+                r32[g] = rv;
+                d32[g] = 0.f;
+                if (p32) p32[g] = rv;
+                rrf += rv * rv;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 2 * kHalf; ++j) {
+            q0[j] = q0[j + 1];
+            q1[j] = q1[j + 1];
+        }
+    }
+    if (tile_arrive((double)rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[P.o] = 0;
+            start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
+        }
+    }
+}
+
+// x += d32 in pairs for the orbitals still refining.
+__global__ void __launch_bounds__(256) k_correct_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                    const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                    const float* __restrict__ d32, float2* __restrict__ x,
+                                                    CgState st) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {
+            const float4 d = *reinterpret_cast<const float4*>(d32 + g);
+            float4 a = *reinterpret_cast<float4*>(x + g);       // pairs g, g+1
+            float4 c = *reinterpret_cast<float4*>(x + g + 2);   // pairs g+2, g+3
+            ff s;
+            s = ff_two_sum(a.x, d.x); s = ff_quick(s.h, s.l + a.y); a.x = s.h; a.y = s.l;
+            s = ff_two_sum(a.z, d.y); s = ff_quick(s.h, s.l + a.w); a.z = s.h; a.w = s.l;
+            s = ff_two_sum(c.x, d.z); s = ff_quick(s.h, s.l + c.y); c.x = s.h; c.y = s.l;
+            s = ff_two_sum(c.z, d.w); s = ff_quick(s.h, s.l + c.w); c.z = s.h; c.w = s.l;
+            *reinterpret_cast<float4*>(x + g) = a;
+            *reinterpret_cast<float4*>(x + g + 2) = c;
+        } else {
+            const float2 v = x[g];
+            ff s = ff_two_sum(v.x, d32[g]);
+            s = ff_quick(s.h, s.l + v.y);
+            x[g] = make_float2(s.h, s.l);
+        }
+    });
+}
+
+// V = x (pairs joined into float64), every orbital.
+__global__ void __launch_bounds__(256) k_join_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                 const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                 const float2* __restrict__ x, double* __restrict__ V) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    const LvlDesc& D = L[P.b];
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        for (int k = 0; k < n; ++k) V[g + k] = ff_join(x[g + k]);
+    });
+}
+
+static dim3 tile_threads() { return dim3(kTileX, kTileY / 2); }
+
+// x is the solution in pairs (float2 per point), p32 may be null.
+void launch_ff_init(flosic_ctx* c, double* b, const double* V, bool warm, float2* x, float* p32, double tol2,
+                    double inner_tol2, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_ff_init<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b,
+                                                               V, x, c->ws.r32, p32, c->ws.d32, warm ? 1 : 0, tol2,
+                                                               inner_tol2, c->opt.max_iter, c->ws.cg);
+    note_launch(c);
+}
+
+void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
+                        double inner_tol2, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_residual12_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<const float2*>(b), x, c->ws.r32, p32,
+        c->ws.d32, tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
+    note_launch(c);
+}
+
+void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_correct_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
+                                                                  c->ws.d32, x, c->ws.cg);
+    note_launch(c);
+}
+
+void launch_join_ff(flosic_ctx* c, const float2* x, double* V, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_join_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, x,
+                                                               V);
+    note_launch(c);
+}
+
+}  // namespace flosic

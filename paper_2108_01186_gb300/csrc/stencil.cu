@@ -18,8 +18,6 @@ namespace flosic {
 __constant__ double c_w12[kHalf + 1];
 __constant__ float c_w12f[kHalf + 1];
 
-cudaError_t upload_ff_weights();
-
 cudaError_t upload_stencil12_constants() {
     {
         cudaError_t e = upload_ff_weights();
@@ -38,8 +36,6 @@ template <class T> __device__ __forceinline__ T wgt(int m);
 template <> __device__ __forceinline__ float wgt<float>(int m) { return c_w12f[m]; }
 template <> __device__ __forceinline__ double wgt<double>(int m) { return c_w12[m]; }
 
-constexpr int kPX = kTileX + 2 * kHalf;   // staged plane width
-constexpr int kPY = kTileY + 2 * kHalf;   // staged plane height
 
 // Value source of the stencil: the fused PCG direction p = z + beta p_old
 // (first iteration: p = z) or a plain array.
@@ -62,7 +58,6 @@ struct SrcPlain {
 // A_center = (-Delta_h u) at that point.  The staged plane of z+1 is loaded
 // into registers while plane z is computed, so each thread keeps about a
 // dozen loads in flight.
-constexpr int kSlots = (kPX * kPY + kTileX * (kTileY / 2) - 1) / (kTileX * (kTileY / 2));
 
 template <class T, class Src, class Epi>
 __device__ __forceinline__ void sweep12(const LvlDesc& D, const TilePos& P, const Src& src, T ih2, Epi epi,
@@ -457,196 +452,6 @@ __global__ void __launch_bounds__(256) k_residual12(const BlkDesc* __restrict__ 
     }
 }
 
-// ---------------------------------------------------------------------------
-// Float64-accurate residual in float-float arithmetic.  GB300's float64 rate
-// is a small fraction of its float32 rate, so r = b - A x is evaluated with
-// unevaluated pairs (hi, lo) of float32 numbers: Knuth's error-free two-sum
-// for additions and an FMA-based exact two-product, which carry ~48
-// significant bits -- enough for residuals down to 1e-12 of ||b||.
-// ---------------------------------------------------------------------------
-struct ff {
-    float h, l;
-};
-
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
-    return {s, e};
-}
-__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-    ff s = ff_two_sum(x.h, y.h);
-    const ff t = ff_two_sum(x.l, y.l);
-    s.l += t.h;
-    s = ff_quick(s.h, s.l);
-    s.l += t.l;
-    return ff_quick(s.h, s.l);
-}
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-    const float p = x.h * y.h;
-    float e = fmaf(x.h, y.h, -p);
-    e = fmaf(x.h, y.l, e);
-    e = fmaf(x.l, y.h, e);
-    return ff_quick(p, e);
-}
-// Sum of six pairs: exact two-sums on the high parts, the low parts and the
-// rounding errors added in float (error ~ 6 eps^2 of the largest term).
-__device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
-    ff s = ff_two_sum(a.h, b.h);
-    float err = s.l;
-    s = ff_two_sum(s.h, c.h); err += s.l;
-    s = ff_two_sum(s.h, d.h); err += s.l;
-    s = ff_two_sum(s.h, e.h); err += s.l;
-    s = ff_two_sum(s.h, f.h); err += s.l;
-    err += ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
-    return ff_quick(s.h, err);
-}
-__device__ __forceinline__ ff ff_split(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-
-__constant__ float c_wff[2 * (kHalf + 1)];   // w_m as (hi, lo) pairs
-
-cudaError_t upload_ff_weights() {
-    double w[kHalf + 1];
-    stencil_weights(w);
-    float f[2 * (kHalf + 1)];
-    for (int m = 0; m <= kHalf; ++m) {
-        const double ww = (m == 0) ? 3.0 * w[0] : w[m];
-        f[2 * m] = (float)ww;
-        f[2 * m + 1] = (float)(ww - (double)f[2 * m]);
-    }
-    return cudaMemcpyToSymbol(c_wff, f, sizeof(f));
-}
-
-__global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
-                                                       const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                       const double* __restrict__ b, const double* __restrict__ x,
-                                                       double* __restrict__ r, double tol2, int max_iter,
-                                                       int* __restrict__ flag, int* __restrict__ counter, int want_bb,
-                                                       CgState st) {
-    __shared__ ff plane[kPY][kPX];
-    __shared__ double scratch[32];
-    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!flag[P.o]) return;
-    const LvlDesc& D = L[P.b];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTileX + tx;
-    const int nthr = kTileX * (kTileY / 2);
-    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
-    const int gx = P.x0 + tx;
-    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
-    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
-    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
-    long long soff[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) {
-        const int e = tid + j * nthr;
-        soff[j] = -1;
-        if (e < kPX * kPY) {
-            const int yy = e / kPX, xx = e - yy * kPX;
-            const int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
-            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
-        }
-    }
-    const ff zero = {0.f, 0.f};
-    ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
-#pragma unroll
-    for (int j = 0; j < 2 * kHalf; ++j) {
-        const int zz = P.z0 - kHalf + j;
-        const bool okz = zz >= 0 && zz < D.nz;
-        q0[j] = (in0 && okz) ? ff_split(x[P.base + zz * sz + c0]) : zero;
-        q1[j] = (in1 && okz) ? ff_split(x[P.base + zz * sz + c1]) : zero;
-    }
-    double pre[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[P.base + P.z0 * sz + soff[j]] : 0.0;
-    ff w[kHalf + 1];
-#pragma unroll
-    for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
-    const double ih2 = 1.0 / (D.h * D.h);
-    float rrf = 0.f, bbf = 0.f;
-    ff* flat = &plane[0][0];
-    for (int z = P.z0; z < P.z1; ++z) {
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) {
-            const int e = tid + j * nthr;
-            if (e < kPX * kPY) flat[e] = ff_split(pre[j]);
-        }
-        {
-            const int zz = z + kHalf;
-            q0[2 * kHalf] = (in0 && zz < D.nz) ? ff_split(x[P.base + zz * sz + c0]) : zero;
-            q1[2 * kHalf] = (in1 && zz < D.nz) ? ff_split(x[P.base + zz * sz + c1]) : zero;
-        }
-        __syncthreads();
-        if (z + 1 < P.z1) {
-            const long long pz = P.base + (z + 1) * sz;
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[pz + soff[j]] : 0.0;
-        }
-        const int lx = tx + kHalf;
-        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
-        const bool in[2] = {in0, in1};
-        const long long cc[2] = {c0, c1};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const ff* qk = (k == 0) ? q0 : q1;
-            ff acc = ff_mul(w[0], qk[kHalf]);
-#pragma unroll
-            for (int m = 1; m <= kHalf; ++m) {
-                const ff sm = ff_sum6(plane[ly[k]][lx - m], plane[ly[k]][lx + m], plane[ly[k] - m][lx],
-                                      plane[ly[k] + m][lx], qk[kHalf - m], qk[kHalf + m]);
-                acc = ff_add(acc, ff_mul(w[m], sm));
-            }
-            if (in[k]) {
-                const long long g = P.base + z * sz + cc[k];
-                const double ax = -((double)acc.h + (double)acc.l) * ih2;
-                const double bv = b[g];
-                const double rv = bv - ax;
-                r[g] = rv;
-                rrf += (float)rv * (float)rv;
-                bbf += (float)bv * (float)bv;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 2 * kHalf; ++j) {
-            q0[j] = q0[j + 1];
-            q1[j] = q1[j + 1];
-        }
-    }
-    const int o = P.o;
-    if (want_bb) {
-        const double bbs = block_sum((double)bbf, scratch);
-        if (linear_tid() == 0) st.part2[blockIdx.x] = bbs;
-    }
-    if (tile_arrive((double)rrf, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
-        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
-        if (want_bb) {
-            const double sb = tile_gather(st.part2, P.first, D.ntile, scratch);
-            if (linear_tid() == 0) st.bb[o] = sb;
-        }
-        if (linear_tid() == 0) {
-            st.count[o] = 0;
-            st.rr[o] = sum;
-            st.thr[o] = tol2 * st.bb[o];
-            if (!(sum > st.thr[o])) {
-                flag[o] = 0;
-                st.conv[o] = 1;
-                atomicSub(counter, 1);
-            } else if (st.iters[o] >= max_iter || !isfinite(sum)) {
-                flag[o] = 0;
-                atomicSub(counter, 1);
-            }
-        }
-    }
-}
-
 template <class T>
 void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s) {
     const Multigrid& M = c->mg;
@@ -670,12 +475,6 @@ template void launch_apply12_pcg<double>(flosic_ctx*, const double*, double*, do
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s) {
     const Multigrid& M = c->mg;
-    if (c->opt.precision == FLOSIC_MIXED) {
-        k_residual12_ff<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
-            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b, x, r, tol2, max_iter, flag, counter, want_bb,
-            c->ws.cg); note_launch(c);
-        return;
-    }
     k_residual12<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
         c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b, x, r, tol2, max_iter, flag, counter, want_bb,
         c->ws.cg); note_launch(c);
