@@ -340,6 +340,12 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                         // the coarse level inherits the Galerkin weight
                         cl[b][k] = (sides[k] % 2 == 0) ? 2.0 * cl[b][k] - 1.0 : 1.0 + 0.5 * cl[b][k];
                     }
+                    for (int m = 0; m < 8; ++m) {
+                        double dd = 6.0;
+                        for (int k = 0; k < 3; ++k)
+                            if (m & (1 << k)) dd += (double)D.cl[k] - 2.0;
+                        D.idd[m] = (float)(1.0 / dd);
+                    }
                     const int tx = (D.nx + kTileX - 1) / kTileX, ty = (D.ny + kTileY - 1) / kTileY,
                               tz = (D.nz + kTileZ - 1) / kTileZ;
                     D.ntile = tx * ty * tz;

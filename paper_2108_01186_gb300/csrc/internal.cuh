@@ -60,6 +60,9 @@ struct LvlDesc {
     // parent had an even side (see multigrid.cu).  corr = any of them != 2.
     float cl[3];
     int corr;
+    // 1/dd by which dimensions the point is last in (bit 0 x, 1 y, 2 z),
+    // dd = 6 + sum over those dimensions of (cl - 2)
+    float idd[8];
 };
 
 // Per-level buffers as the kernels see them (passed by value).

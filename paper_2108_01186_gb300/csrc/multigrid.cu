@@ -62,11 +62,8 @@ __device__ __forceinline__ T nbr6(const T* __restrict__ u, long long g, int x, i
 // the last point of every dimension.
 template <class T>
 __device__ __forceinline__ T inv_diag(const LvlDesc& D, int x, int y, int z) {
-    T dd = T(6);
-    if (x == D.nx - 1) dd += T(D.cl[0]) - T(2);
-    if (y == D.ny - 1) dd += T(D.cl[1]) - T(2);
-    if (z == D.nz - 1) dd += T(D.cl[2]) - T(2);
-    return T(1) / dd;
+    const int m = (x == D.nx - 1 ? 1 : 0) | (y == D.ny - 1 ? 2 : 0) | (z == D.nz - 1 ? 4 : 0);
+    return T(D.idd[m]);
 }
 
 template <class T> struct Vec2;
@@ -230,86 +227,93 @@ __device__ __forceinline__ T prolong_x(const T* __restrict__ row, int ncx, int x
     return T(0.5) * v;
 }
 
-// t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction).
-// One thread per coarse cell (I, J, K) writes the fine points
-// (2I + a, 2J + b, 2K + c), a, b, c in {0, 1}: odd fine coordinates sit on
-// coarse points (weight 1), even ones halfway between I-1 and I (1/2 each),
-// so the eight coarse values at I-1..I, J-1..J, K-1..K give all eight.
+// Coarse rows of a fine row along y (or z): odd y sits on coarse (y-1)/2,
+// even y halfway between y/2-1 and y/2 (rows outside the coarse grid drop).
+template <class T>
+__device__ __forceinline__ int coarse_rows(int y, int nc, int* J, T* w) {
+    if (y & 1) {
+        J[0] = (y - 1) >> 1;
+        w[0] = T(1);
+        return 1;
+    }
+    const int lo = (y >> 1) - 1, hi = y >> 1;
+    const bool vlo = lo >= 0, vhi = hi < nc;
+    J[0] = vlo ? lo : hi;
+    J[1] = hi;
+    w[0] = w[1] = T(0.5);
+    return (vlo && vhi) ? 2 : 1;
+}
+
+// t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction),
+// V consecutive fine points of a row per thread: their trilinear values come
+// from the 1, 2 or 4 coarse rows around the row, three (float) or two
+// (double) coarse values each.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_prolong(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ Lf,
                                                     const LvlDesc* __restrict__ Lc, const int4* __restrict__ tiles_f,
                                                     const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                     const T* __restrict__ r, const T* __restrict__ ec,
                                                     T* __restrict__ t, T omega) {
-    using V2 = typename Vec2<T>::type;
+    constexpr int V = Vec<T>::n;
+    using VT = typename Vec<T>::type;
     const TilePos P = tile_pos(blk, Lf, tiles_f, orb_blk, blockIdx.x);
     const LvlDesc& F = Lf[P.b];
     if (!active[P.o] || F.coarsest) return;
     const LvlDesc& C = Lc[P.b];
     const T* eb = ec + C.off + (long long)(P.o - blk[P.b].orb0) * C.G;
-    const T dinv = omega * T(F.h * F.h / 6.0);
-    const long long sy = F.nx, sz = (long long)F.nx * F.ny;
-    const bool vec = (F.nx % 2 == 0) && (P.base % 2 == 0);
-    const int tid = linear_tid();
-    const int Il = tid & 15, yz = tid >> 4;               // 16 x 16 threads
-    const int I = (P.x0 >> 1) + Il;
-    const int zc0 = P.z0 >> 1, zc1 = (P.z1 + 1) >> 1;
-    auto cval = [&](int X, int Y, int Z) -> T {
-        return (X >= 0 && X < C.nx && Y >= 0 && Y < C.ny && Z >= 0 && Z < C.nz)
-                   ? eb[((long long)Z * C.ny + Y) * C.nx + X] : T(0);
-    };
-    if (2 * I >= F.nx) return;
-    for (int cell = yz; cell < (kTileY / 2) * (zc1 - zc0); cell += 16) {
-        const int J = (P.y0 >> 1) + cell % (kTileY / 2);
-        const int K = zc0 + cell / (kTileY / 2);
-        if (2 * J >= F.ny || 2 * K >= F.nz) continue;
-        // x-interpolated coarse rows: xr[j][k][a] for rows J-1+j, planes K-1+k
-        T xr[2][2][2];
+    const T oh2 = omega * T(F.h * F.h);
+    tile_rows<T>(F, P, [&](int x, int y, int z, long long g, int n) {
+        int Jr[2], Kr[2];
+        T wy[2], wz[2];
+        const int nj = coarse_rows<T>(y, C.ny, Jr, wy);
+        const int nk = coarse_rows<T>(z, C.nz, Kr, wz);
+        T u[V];
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < V; ++k) u[k] = T(0);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const T c0 = cval(I - 1, J - 1 + j, K - 1 + k), c1 = cval(I, J - 1 + j, K - 1 + k);
-                xr[j][k][0] = T(0.5) * (c0 + c1);
-                xr[j][k][1] = c1;
-            }
+        for (int b = 0; b < 2; ++b) {
+            if (b >= nk) continue;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int z = 2 * K + c;
-            if (z >= F.nz) continue;
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int y = 2 * J + b;
-                if (y >= F.ny) continue;
-                T u[2];
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    // y then z: even -> average of the two, odd -> the upper one
-                    const T y0 = b ? xr[1][0][a] : T(0.5) * (xr[0][0][a] + xr[1][0][a]);
-                    const T y1 = b ? xr[1][1][a] : T(0.5) * (xr[0][1][a] + xr[1][1][a]);
-                    u[a] = c ? y1 : T(0.5) * (y0 + y1);
-                }
-                const int x = 2 * I;
-                const long long g = P.base + z * sz + y * sy + x;
-                T d0 = dinv, d1 = dinv;
-                if (F.corr && (x + 2 >= F.nx || y == F.ny - 1 || z == F.nz - 1)) {
-                    const T oh2 = omega * T(F.h * F.h);
-                    d0 = oh2 * inv_diag<T>(F, x, y, z);
-                    d1 = oh2 * inv_diag<T>(F, x + 1, y, z);
-                }
-                if (vec && x + 1 < F.nx) {
-                    const V2 rv = *reinterpret_cast<const V2*>(r + g);
-                    V2 out;
-                    out.x = d0 * rv.x + u[0];
-                    out.y = d1 * rv.y + u[1];
-                    *reinterpret_cast<V2*>(t + g) = out;
+            for (int a = 0; a < 2; ++a) {
+                if (a >= nj) continue;
+                const T* row = eb + ((long long)Kr[b] * C.ny + Jr[a]) * C.nx;
+                const T w = wy[a] * wz[b];
+                if (n == V) {
+                    // x is a multiple of V and F.nx of V, so C.nx = F.nx / 2
+                    const int I = x >> 1;
+                    const T e0 = (I >= 1) ? row[I - 1] : T(0);
+                    const T e1 = row[I];
+                    if (V == 4) {
+                        const T e2 = row[I + 1];
+                        u[0] += w * T(0.5) * (e0 + e1);
+                        u[1] += w * e1;
+                        u[2] += w * T(0.5) * (e1 + e2);
+                        u[3] += w * e2;
+                    } else {
+                        u[0] += w * T(0.5) * (e0 + e1);
+                        u[1] += w * e1;
+                    }
                 } else {
-                    t[g] = d0 * r[g] + u[0];
-                    if (x + 1 < F.nx) t[g + 1] = d1 * r[g + 1] + u[1];
+                    u[0] += w * prolong_x(row, C.nx, x);
                 }
             }
         }
-    }
+        T rv[V], out[V];
+        if (n == V) {
+            const VT v = *reinterpret_cast<const VT*>(r + g);
+#pragma unroll
+            for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
+        } else {
+            rv[0] = r[g];
+        }
+        const bool edge = F.corr && (x + n >= F.nx || y == F.ny - 1 || z == F.nz - 1);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const T d = oh2 * (edge ? inv_diag<T>(F, x + k, y, z) : T(1.0 / 6.0));
+            out[k] = d * rv[k] + u[k];
+        }
+        store_n<T, V>(t + g, out, n);
+    });
 }
 
 // e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/dd)(h^2 r + sum_nbr t);
