@@ -78,6 +78,29 @@ cudaError_t setup_boundary(flosic_ctx* c) {
     return e;
 }
 
+// Last tile of an orbital: the ten moments from the per-tile partials
+// (fixed order), times dV.
+__device__ __forceinline__ void gather_moments(const TilePos& P, const LvlDesc& D, const BlkDesc& B,
+                                               const double* __restrict__ mom_part, double* __restrict__ mom,
+                                               unsigned* __restrict__ count, double* scratch) {
+    __shared__ bool last;
+    if (linear_tid() == 0) {
+        __threadfence();
+        last = (atomicAdd(count + P.o, 1u) == (unsigned)(D.ntile - 1));
+    }
+    __syncthreads();
+    if (last) {
+        for (int k = 0; k < 10; ++k) {
+            double v = 0.0;
+            for (int t = linear_tid(); t < D.ntile; t += blockDim.x * blockDim.y)
+                v += __ldcg(mom_part + (P.first + t) * 10 + k);
+            v = block_sum(v, scratch);
+            if (linear_tid() == 0) mom[P.o * 10 + k] = v * B.dV;
+        }
+        if (linear_tid() == 0) count[P.o] = 0;
+    }
+}
+
 // Pass 1 over the tiles: b = scale * phi^2 and (for the multipole boundary)
 // the l <= 2 moments of phi^2 per orbital.  Per column (x, y) the z-sums
 // S0 = sum rho, S1 = sum rho Z, S2 = sum rho Z^2 give all ten moments.
@@ -122,30 +145,87 @@ __global__ void __launch_bounds__(256) k_rhs_bulk(const BlkDesc* __restrict__ bl
         m[9] += 3.0 * Y * s1;
     }
     if (!want_mom) return;
-    __shared__ bool last;
     for (int k = 0; k < 10; ++k) {
         const double s = block_sum(m[k], scratch);
         if (linear_tid() == 0) mom_part[(long long)blockIdx.x * 10 + k] = s;
     }
-    if (linear_tid() == 0) {
-        __threadfence();
-        last = (atomicAdd(count + P.o, 1u) == (unsigned)(D.ntile - 1));
+    gather_moments(P, D, B, mom_part, mom, count, scratch);
+}
+
+// The same pass for the mixed-precision path: b is written as float-float
+// pairs (rho = phi^2 to ~48 bits) and the moments are accumulated as pairs,
+// so they match the float64 pass to ~1e-13 while no float64 operation runs
+// per grid point.
+__global__ void __launch_bounds__(256) k_rhs_bulk_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                     const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                     const double* __restrict__ phi, double scale, int want_mom,
+                                                     float2* __restrict__ b, double* __restrict__ mom_part,
+                                                     double* __restrict__ mom, unsigned* __restrict__ count) {
+    __shared__ double scratch[32];
+    __shared__ double wsum[8][10];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    const LvlDesc& D = L[P.b];
+    const BlkDesc& B = blk[P.b];
+    ff m[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) m[k] = {0.f, 0.f};
+    const ff sc = to_ff(d2ff(scale)), hz = to_ff(d2ff(B.h));
+    const int x = P.x0 + threadIdx.x;
+    for (int k = 0; k < 2; ++k) {
+        const int y = P.y0 + threadIdx.y + k * (kTileY / 2);
+        if (x >= D.nx || y >= D.ny) continue;
+        ff s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
+        ff Z = to_ff(d2ff(B.oz + B.h * P.z0 - B.cz));
+        for (int z = P.z0; z < P.z1; ++z) {
+            const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
+            const float2 f = d2ff(phi[g]);
+            const float ph = f.x * f.x;
+            const ff rho = ff_quick(ph, fmaf(f.x, f.x, -ph) + 2.f * f.x * f.y);
+            const ff bv = ff_mul(sc, rho);
+            b[g] = make_float2(bv.h, bv.l);
+            const ff t = ff_mul(rho, Z);
+            s0 = ff_add(s0, rho);
+            s1 = ff_add(s1, t);
+            s2 = ff_add(s2, ff_mul(t, Z));
+            Z = ff_add(Z, hz);
+        }
+        const ff X = to_ff(d2ff(B.ox + B.h * x - B.cx)), Y = to_ff(d2ff(B.oy + B.h * y - B.cy));
+        const ff sxx = ff_mul(ff_mul(X, X), s0), syy = ff_mul(ff_mul(Y, Y), s0);
+        const ff r2 = ff_add(ff_add(sxx, syy), s2);
+        const ff mr2 = {-r2.h, -r2.l};
+        m[0] = ff_add(m[0], s0);
+        m[1] = ff_add(m[1], ff_mul(X, s0));
+        m[2] = ff_add(m[2], ff_mul(Y, s0));
+        m[3] = ff_add(m[3], s1);
+        m[4] = ff_add(m[4], ff_add(ff_mulf(sxx, 3.f), mr2));
+        m[5] = ff_add(m[5], ff_add(ff_mulf(syy, 3.f), mr2));
+        m[6] = ff_add(m[6], ff_add(ff_mulf(s2, 3.f), mr2));
+        m[7] = ff_add(m[7], ff_mulf(ff_mul(ff_mul(X, Y), s0), 3.f));
+        m[8] = ff_add(m[8], ff_mulf(ff_mul(X, s1), 3.f));
+        m[9] = ff_add(m[9], ff_mulf(ff_mul(Y, s1), 3.f));
+    }
+    if (!want_mom) return;
+    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const ff v = warp_sum(m[k]);
+        if (lane == 0) wsum[wid][k] = ff_to_double(v);
     }
     __syncthreads();
-    if (last) {
-        for (int k = 0; k < 10; ++k) {
-            double v = 0.0;
-            for (int t = linear_tid(); t < D.ntile; t += blockDim.x * blockDim.y)
-                v += __ldcg(mom_part + (P.first + t) * 10 + k);
-            v = block_sum(v, scratch);
-            if (linear_tid() == 0) mom[P.o * 10 + k] = v * B.dV;
-        }
-        if (linear_tid() == 0) count[P.o] = 0;
+    if (tid < 10) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += wsum[w][tid];
+        mom_part[(long long)blockIdx.x * 10 + tid] = s;
     }
+    __syncthreads();
+    gather_moments(P, D, B, mom_part, mom, count, scratch);
 }
 
 // Pass 2: b[g_j] += sum_k mom_k B_k(g_j) for every boundary point of every
 // orbital (thread per boundary point, looping over the block's orbitals).
+// kFF: b holds float-float pairs and the boundary term is formed in pairs
+// (it carries most of ||b||, so it needs the full ~48 bits).
+template <bool kFF>
 __global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __restrict__ bidx,
                          const double* __restrict__ bcoef, const double* __restrict__ mom,
                          double* __restrict__ rhs) {
@@ -153,29 +233,57 @@ __global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __re
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= B.nbnd) return;
     const int g = bidx[B.bnd0 + j];
-    double cf[10];
     const double* src = bcoef + (B.bnd0 + (long long)j) * 10;
+    if (kFF) {
+        ff cf[10];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) cf[k] = src[k];
-    for (int i = 0; i < B.N; ++i) {
-        const double* mo = mom + (B.orb0 + i) * 10;
-        double acc = 0.0;
+        for (int k = 0; k < 10; ++k) cf[k] = to_ff(d2ff(src[k]));
+        float2* rp = reinterpret_cast<float2*>(rhs);
+        for (int i = 0; i < B.N; ++i) {
+            const double* mo = mom + (B.orb0 + i) * 10;
+            ff acc = {0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 10; ++k) acc += mo[k] * cf[k];
-        rhs[B.off + (long long)i * B.G + g] += acc;
+            for (int k = 0; k < 10; ++k) acc = ff_add(acc, ff_mul(to_ff(d2ff(mo[k])), cf[k]));
+            const long long idx = B.off + (long long)i * B.G + g;
+            const ff v = ff_add(to_ff(rp[idx]), acc);
+            rp[idx] = make_float2(v.h, v.l);
+        }
+    } else {
+        double cf[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) cf[k] = src[k];
+        for (int i = 0; i < B.N; ++i) {
+            const double* mo = mom + (B.orb0 + i) * 10;
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) acc += mo[k] * cf[k];
+            rhs[B.off + (long long)i * B.G + g] += acc;
+        }
     }
 }
 
 void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s) {
     const Multigrid& M = c->mg;
-    k_rhs_bulk<<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
-        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi, with_bc ? 4.0 * kPi : 1.0, with_bc ? 1 : 0, b,
-        c->ws.mom_part, c->ws.mom, c->ws.cg.count); note_launch(c);
+    const bool ff = (c->opt.precision == FLOSIC_MIXED);
+    const double scale = with_bc ? 4.0 * kPi : 1.0;
+    const dim3 tb(kTileX, kTileY / 2);
+    if (ff)
+        k_rhs_bulk_ff<<<(unsigned)M.ntiles[0], tb, 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi,
+                                                           scale, with_bc ? 1 : 0, reinterpret_cast<float2*>(b),
+                                                           c->ws.mom_part, c->ws.mom, c->ws.cg.count);
+    else
+        k_rhs_bulk<<<(unsigned)M.ntiles[0], tb, 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi, scale,
+                                                        with_bc ? 1 : 0, b, c->ws.mom_part, c->ws.mom, c->ws.cg.count);
+    note_launch(c);
     if (!with_bc) return;
     for (int k = 0; k < c->nblk; ++k) {
         const int nb = c->blk[k].nbnd;
         if (nb == 0) continue;
-        k_rhs_bc<<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b); note_launch(c);
+        if (ff)
+            k_rhs_bc<true><<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b);
+        else
+            k_rhs_bc<false><<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b);
+        note_launch(c);
     }
 }
 

@@ -18,6 +18,8 @@
 //   vbar = Tbar/sqrt(rho) - v (Tbar.v)/rho^{3/2} (product form of Eq. 11);
 //   dE/da_i = sum_a vbar_ia grad psi_a(a_i);
 //   psibar = C^T Phibar + dV T^T (Sbar + Sbar^T) T psi + interpolation adjoint.
+#include <type_traits>
+
 #include "internal.cuh"
 #include "xc_device.cuh"
 
@@ -130,11 +132,20 @@ void launch_interp_fod(const flosic_ctx* c, const double* psi, const double* fod
 // ---------------------------------------------------------------------------
 // grid contractions C_ij = sum_g A_i(g) B_j(g) per block (K-split partials)
 // ---------------------------------------------------------------------------
+// Operand loaders: operator() gives the float64 value; bindf(B) gives a
+// loader bound to one block that forms the value in float32 from the float64
+// data with integer-op conversions (no float64 operation per element).
 struct LoadPsi {
     const double* p;
     __device__ __forceinline__ double operator()(const BlkDesc& B, int i, long long g) const {
         return p[B.off + (long long)i * B.G + g];
     }
+    struct F {
+        const double* p;
+        long long G;
+        __device__ __forceinline__ float operator()(int i, long long g) const { return d2f(p[(long long)i * G + g]); }
+    };
+    __device__ __forceinline__ F bindf(const BlkDesc& B) const { return F{p + B.off, B.G}; }
 };
 
 // Phibar_i(g) = gE * 2 dV * V_i^SIC(g) * phi_i(g) with V^SIC = -(V + v_xc)
@@ -147,10 +158,25 @@ struct LoadPhibar {
         const long long k = B.off + (long long)i * B.G + g;
         return gE[B.sys] * 2.0 * B.dV * vsic[k] * phi[k];
     }
+    struct F {
+        const double* phi;
+        const double* vsic;
+        long long G;
+        float coef;
+        __device__ __forceinline__ float operator()(int i, long long g) const {
+            const long long k = (long long)i * G + g;
+            return coef * d2f(vsic[k]) * d2f(phi[k]);
+        }
+    };
+    __device__ __forceinline__ F bindf(const BlkDesc& B) const {
+        return F{phi + B.off, vsic + B.off, B.G, (float)(gE[B.sys] * 2.0 * B.dV)};
+    }
 };
 
-// TC: arithmetic of the products and of the sum within one 16-point k tile
-// (float in mixed precision); tile sums accumulate in float64.
+// TC: arithmetic of the products and of the sum within one 16-point k tile.
+// float (mixed precision): float32 operands from the bound loaders, tile sums
+// accumulated as float-float pairs, one float64 addition per matrix element
+// at the end; double: float64 throughout.
 template <int RM, class TC, class LA, class LB>
 __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ blk, int kparts, LA la,
                                                   LB lb, double* __restrict__ part, long long mat_elems) {
@@ -164,18 +190,26 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
     const int kp = blockIdx.x;
     const long long kb = G * kp / kparts, ke = G * (kp + 1) / kparts;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[RM][RM];
+    constexpr bool kF = std::is_same<TC, float>::value;
+    const auto fa = la.bindf(B);
+    const auto fb = lb.bindf(B);
+    TC acc[RM][RM], acl[RM][RM];   // (sum, low part) pairs when kF
 #pragma unroll
     for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int q = 0; q < RM; ++q) acc[r][q] = 0.0;
+        for (int q = 0; q < RM; ++q) acc[r][q] = acl[r][q] = TC(0);
     for (long long k0 = kb; k0 < ke; k0 += KT) {
         for (int idx = threadIdx.x; idx < KT * NP; idx += 256) {
             const int i = idx / KT, kk = idx % KT;
             const long long g = k0 + kk;
             const bool ok = (i < N) && (g < ke);
-            As[kk][i] = ok ? (TC)la(B, i, g) : TC(0);
-            Bs[kk][i] = ok ? (TC)lb(B, i, g) : TC(0);
+            if constexpr (kF) {
+                As[kk][i] = ok ? fa(i, g) : 0.f;
+                Bs[kk][i] = ok ? fb(i, g) : 0.f;
+            } else {
+                As[kk][i] = ok ? la(B, i, g) : 0.0;
+                Bs[kk][i] = ok ? lb(B, i, g) : 0.0;
+            }
         }
         __syncthreads();
         TC tacc[RM][RM];
@@ -198,7 +232,16 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
 #pragma unroll
         for (int r = 0; r < RM; ++r)
 #pragma unroll
-            for (int q = 0; q < RM; ++q) acc[r][q] += (double)tacc[r][q];
+            for (int q = 0; q < RM; ++q) {
+                if constexpr (kF) {   // two-sum into the pair
+                    const float a = acc[r][q], b = tacc[r][q];
+                    const float s2 = a + b, bb = s2 - a;
+                    acl[r][q] += (a - (s2 - bb)) + (b - bb);
+                    acc[r][q] = s2;
+                } else {
+                    acc[r][q] += tacc[r][q];
+                }
+            }
         __syncthreads();
     }
 #pragma unroll
@@ -206,7 +249,10 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
 #pragma unroll
         for (int q = 0; q < RM; ++q) {
             const int i = ty + 16 * r, j = tx + 16 * q;
-            if (i < N && j < N) part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = acc[r][q];
+            double v;
+            if constexpr (kF) v = f2d(acc[r][q]) + f2d(acl[r][q]);
+            else v = acc[r][q];
+            if (i < N && j < N) part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = v;
         }
 }
 
@@ -447,9 +493,20 @@ struct LoadPhibarPsi {   // rows 0..N-1: Phibar; rows N..2N-1: psi
         if (k < B.N) return pb(B, k, g);
         return psi[B.off + (long long)(k - B.N) * B.G + g];
     }
+    struct F {
+        LoadPhibar::F pb;
+        const double* psi;
+        long long G;
+        int N;
+        __device__ __forceinline__ float operator()(int k, long long g) const {
+            return (k < N) ? pb(k, g) : d2f(psi[(long long)(k - N) * G + g]);
+        }
+    };
+    __device__ __forceinline__ F bindf(const BlkDesc& B) const { return F{pb.bindf(B), psi + B.off, B.G, B.N}; }
 };
 
-// TC: arithmetic of the products and sums (float in mixed precision).
+// TC: arithmetic of the products and sums (float in mixed precision, with
+// operands and results converted by integer operations).
 template <int RJ, class TC, class LX>
 __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ blk,
                                                   const double* __restrict__ E, int mult, LX lx,
@@ -461,6 +518,8 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
     const int N = B.N, K = mult * N;
     const double* Eb = E + mult * B.moff;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    constexpr bool kF = std::is_same<TC, float>::value;
+    const auto fx = lx.bindf(B);
     for (long long tile = blockIdx.x; tile * TG < B.G; tile += gridDim.x) {
         const long long g = tile * TG + lane;
         TC acc[RJ];
@@ -469,10 +528,15 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
         for (int kc = 0; kc < K; kc += KC) {
             for (int e = threadIdx.x; e < 8 * RJ * KC; e += 256) {
                 const int j = e / KC, kk = e % KC;
-                Es[j][kk] = (j < N && kc + kk < K) ? (TC)Eb[(long long)j * K + kc + kk] : TC(0);
+                const bool ok = j < N && kc + kk < K;
+                if constexpr (kF) Es[j][kk] = ok ? d2f(Eb[(long long)j * K + kc + kk]) : 0.f;
+                else Es[j][kk] = ok ? Eb[(long long)j * K + kc + kk] : 0.0;
             }
-            for (int kk = wq; kk < KC; kk += 8)
-                Xs[kk][lane] = (kc + kk < K && g < B.G) ? (TC)lx(B, kc + kk, g) : TC(0);
+            for (int kk = wq; kk < KC; kk += 8) {
+                const bool ok = kc + kk < K && g < B.G;
+                if constexpr (kF) Xs[kk][lane] = ok ? fx(kc + kk, g) : 0.f;
+                else Xs[kk][lane] = ok ? lx(B, kc + kk, g) : 0.0;
+            }
             __syncthreads();
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
@@ -486,7 +550,10 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
 #pragma unroll
             for (int r = 0; r < RJ; ++r) {
                 const int j = wq + 8 * r;
-                if (j < N) out[B.off + (long long)j * B.G + g] = (double)acc[r];
+                if (j < N) {
+                    if constexpr (kF) out[B.off + (long long)j * B.G + g] = f2d(acc[r]);
+                    else out[B.off + (long long)j * B.G + g] = acc[r];
+                }
             }
         }
     }

@@ -205,9 +205,9 @@ void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* 
                        int* flag, int* counter, int want_bb, cudaStream_t s);
 cudaError_t upload_ff_weights();
 // mixed precision: float-float refinement around the float32 inner solves
-// (b is overwritten by its float-float pairs; x holds the solution's pairs)
-void launch_ff_init(flosic_ctx* c, double* b, const double* V, bool warm, float2* x, float* p32, double tol2,
-                    double inner_tol2, cudaStream_t s);
+// (b holds float-float pairs, written so by launch_rhs; x the solution's)
+void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,
+                    double tol2, double inner_tol2, cudaStream_t s);
 void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
                         double inner_tol2, cudaStream_t s);
 void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s);
@@ -261,6 +261,146 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return r;
 }
 
+// Block-wide sum of float partials: warps reduce in float, the warp sums
+// are combined in float64 (fixed order).  Returns the sum to every thread.
+__device__ __forceinline__ double block_sum(float v, double* scratch) {
+    const int tid = linear_tid();
+    const int lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = (double)v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += scratch[w];
+        scratch[0] = t;
+    }
+    __syncthreads();
+    const double r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// float64 <-> float32 conversions from integer operations.  GB300 issues
+// every float64 operation, conversions included, at about 1/70 of its
+// float32 rate (measured: ~0.5 Top/s against ~35 Top/s), so a kernel that
+// streams float64 data can afford well under one such operation per value it
+// loads.  These keep per-point work on the integer and float32 pipes.
+// Normal float32 range: magnitudes below 2^-126 become 0, magnitudes beyond
+// the float32 range become infinite (non-finite values stay non-finite).
+// ---------------------------------------------------------------------------
+// round to nearest (ties away from zero)
+__device__ __forceinline__ float d2f(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v) + (1ull << 28);
+    const unsigned hi = (unsigned)(u >> 32);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned m = (unsigned)(u >> 29) & 0x7fffffu;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | m);
+}
+// exact (float32 subnormals flushed to 0)
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned e11 = (e == 255u) ? 2047u : e + 896u;
+    return __hiloint2double((int)(sign | (e11 << 20) | (m >> 3)), (int)(m << 29));
+}
+// float(n) for 0 <= n < 2^29 without a conversion instruction: n = a 2^23 + b
+__device__ __forceinline__ float u29_to_float(unsigned n) {
+    const float a = __uint_as_float(0x4B000000u | (n >> 23)) - 8388608.f;
+    const float b = __uint_as_float(0x4B000000u | (n & 0x7fffffu)) - 8388608.f;
+    return fmaf(a, 8388608.f, b);
+}
+// v = hi + lo, hi = d2f(v), lo = v - hi rounded to float (~48 significant bits)
+__device__ __forceinline__ float2 d2ff(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const float h = d2f(v);
+    const int ev = (int)((u >> 52) & 0x7ffu);
+    const unsigned low = (unsigned)u & 0x1fffffffu;             // the 29 dropped bits
+    const bool up = low >= (1u << 28);                          // h was rounded away from zero
+    const unsigned mag = up ? (1u << 29) - low : low;
+    const int pe = ev - 1075 + 127;                             // 2^(ev - 1075) as a float exponent
+    float lo = 0.f;
+    if (pe >= 1 && pe <= 254) lo = u29_to_float(mag) * __uint_as_float((unsigned)pe << 23);
+    if (up) lo = -lo;
+    if (u >> 63) lo = -lo;
+    return make_float2(h, lo);
+}
+// hi + lo in float64 (one float64 addition)
+__device__ __forceinline__ double ff2d(float2 p) { return f2d(p.x) + f2d(p.y); }
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic: unevaluated pairs (h, l) of float32 numbers with
+// |l| <= ulp(h)/2, about 48 significant bits.  Knuth's error-free two-sum
+// for additions, an FMA-based exact two-product for products.
+// ---------------------------------------------------------------------------
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = ff_two_sum(x.h, y.h);
+    const ff t = ff_two_sum(x.l, y.l);
+    s.l += t.h;
+    s = ff_quick(s.h, s.l);
+    s.l += t.l;
+    return ff_quick(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, e);
+    e = fmaf(x.l, y.h, e);
+    return ff_quick(p, e);
+}
+// Sum of six pairs: exact two-sums on the high parts, the low parts and the
+// rounding errors added in float (error ~ 6 eps^2 of the largest term).
+__device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
+    ff s = ff_two_sum(a.h, b.h);
+    float err = s.l;
+    s = ff_two_sum(s.h, c.h); err += s.l;
+    s = ff_two_sum(s.h, d.h); err += s.l;
+    s = ff_two_sum(s.h, e.h); err += s.l;
+    s = ff_two_sum(s.h, f.h); err += s.l;
+    err += ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
+    return ff_quick(s.h, err);
+}
+// a + b with b a plain float (two-sum, then renormalise)
+__device__ __forceinline__ ff ff_addf(ff a, float b) {
+    const ff s = ff_two_sum(a.h, b);
+    return ff_quick(s.h, s.l + a.l);
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {   // pair times float
+    const float p = a.h * b;
+    return ff_quick(p, fmaf(a.h, b, -p) + a.l * b);
+}
+__device__ __forceinline__ ff to_ff(float2 p) { return {p.x, p.y}; }
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d(a.h) + f2d(a.l); }
+// warp-wide pair sum (every lane gets it)
+__device__ __forceinline__ ff warp_sum(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff w = {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+        v = ff_add(v, w);
+    }
+    return v;
+}
+
 __device__ __forceinline__ int find_block(const BlkDesc* blk, int nblk, int orb) {
     int b = 0;
     while (b + 1 < nblk && blk[b + 1].orb0 <= orb) ++b;
@@ -293,7 +433,8 @@ __device__ __forceinline__ TilePos tile_pos(const BlkDesc* blk, const LvlDesc* L
 
 // Stores this CTA's partial and returns true in the CTA that arrives last
 // among the ntile CTAs of one orbital.
-__device__ __forceinline__ bool tile_arrive(double partial, double* part, int t, unsigned* counter, int ntile,
+template <class P>
+__device__ __forceinline__ bool tile_arrive(P partial, double* part, int t, unsigned* counter, int ntile,
                                             double* scratch) {
     __shared__ bool last;
     const double s = block_sum(partial, scratch);

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) k_mg_postsmooth(const BlkDesc* __restrict
         store_n<T, V>(e + g, out, n);
     });
     if (kLevel0) {
-        if (tile_arrive((double)rz, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        if (tile_arrive(rz, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
             const double v = tile_gather(st.part, P.first, D.ntile, scratch);
             if (linear_tid() == 0) {
                 st.count[P.o] = 0;

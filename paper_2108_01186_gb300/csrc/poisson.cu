@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) k_pcg_update_t(const BlkDesc* __restrict_
             rr += rv * rv;
         }
     });
-    if (tile_arrive((double)rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+    if (tile_arrive(rr, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             const int o = P.o;

@@ -7,8 +7,9 @@
 // significant bits: Knuth's error-free two-sum for additions and an
 // FMA-based exact two-product.  GB300 runs float64 at a small fraction of
 // its float32 rate, so inside the refinement loop no float64 operation runs
-// per grid point; float64 appears only where b (and a warm start) are split
-// into pairs at the start and where x is joined into the float64 result.
+// per grid point; float64 appears only where x is joined into the float64
+// result (one addition per point).  b arrives in pairs from the
+// right-hand-side pass; a warm start is split with integer operations.
 //
 // Round structure per orbital:  r = b - A x (pairs) -> stop if
 // r.r <= tol^2 b.b, else a float32 solve of A d = float(r) to
@@ -17,54 +18,6 @@
 
 namespace flosic {
 
-struct ff {
-    float h, l;
-};
-
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
-    return {s, e};
-}
-__device__ __forceinline__ ff ff_quick(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-    ff s = ff_two_sum(x.h, y.h);
-    const ff t = ff_two_sum(x.l, y.l);
-    s.l += t.h;
-    s = ff_quick(s.h, s.l);
-    s.l += t.l;
-    return ff_quick(s.h, s.l);
-}
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-    const float p = x.h * y.h;
-    float e = fmaf(x.h, y.h, -p);
-    e = fmaf(x.h, y.l, e);
-    e = fmaf(x.l, y.h, e);
-    return ff_quick(p, e);
-}
-// Sum of six pairs: exact two-sums on the high parts, the low parts and the
-// rounding errors added in float (error ~ 6 eps^2 of the largest term).
-__device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
-    ff s = ff_two_sum(a.h, b.h);
-    float err = s.l;
-    s = ff_two_sum(s.h, c.h); err += s.l;
-    s = ff_two_sum(s.h, d.h); err += s.l;
-    s = ff_two_sum(s.h, e.h); err += s.l;
-    s = ff_two_sum(s.h, f.h); err += s.l;
-    err += ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
-    return ff_quick(s.h, err);
-}
-// float64 -> pair and back (the only float64 arithmetic of the scheme)
-__device__ __forceinline__ float2 ff_split(double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-}
-__device__ __forceinline__ double ff_join(float2 p) { return (double)p.x + (double)p.y; }
-__device__ __forceinline__ ff as_ff(float2 p) { return {p.x, p.y}; }
 
 __constant__ float c_wff[2 * (kHalf + 1)];   // 3 w_0, w_1 .. w_6 as (hi, lo) pairs
 
@@ -105,38 +58,36 @@ __device__ __forceinline__ void start_round(CgState& st, int o, double rr, doubl
     atomicAdd(st.n_active, 1);
 }
 
-// Start of the refinement: b (float64, overwritten in place by its pairs),
-// x = warm start (pairs) or 0; b.b per orbital.  Without a warm start the
-// residual is b itself: r32 = float(b), d32 = 0 (p32 = r32 when given) and
-// the first float32 solve starts here.
+// Start of the refinement: b arrives in pairs (from the right-hand-side
+// pass), x = warm start (pairs) or 0; b.b per orbital.  Without a warm start
+// the residual is b itself: r32 = float(b), d32 = 0 (p32 = r32 when given)
+// and the first float32 solve starts here.
 __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                  const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                 double* b, const double* __restrict__ V, float2* __restrict__ x,
-                                                 float* __restrict__ r32, float* __restrict__ p32,
-                                                 float* __restrict__ d32, int warm, double tol2, double inner_tol2,
-                                                 int max_iter, CgState st) {
+                                                 const float2* __restrict__ b, const double* __restrict__ V,
+                                                 float2* __restrict__ x, float* __restrict__ r32,
+                                                 float* __restrict__ p32, float* __restrict__ d32, int warm,
+                                                 double tol2, double inner_tol2, int max_iter, CgState st) {
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
     const LvlDesc& D = L[P.b];
-    float2* bp = reinterpret_cast<float2*>(b);   // same 8 bytes per point
     float bb = 0.f;
     tile_elementwise<float>(D, P, [&](long long g, int n) {
         for (int k = 0; k < n; ++k) {
-            const float2 v = ff_split(b[g + k]);
-            bp[g + k] = v;
-            bb += v.x * v.x;
+            const float bh = b[g + k].x;
+            bb += bh * bh;
             if (warm) {
-                x[g + k] = ff_split(V[g + k]);
+                x[g + k] = d2ff(V[g + k]);
             } else {
                 x[g + k] = make_float2(0.f, 0.f);
-                r32[g + k] = v.x;
+                r32[g + k] = bh;
                 d32[g + k] = 0.f;
-                if (p32) p32[g + k] = v.x;
+                if (p32) p32[g + k] = bh;
             }
         }
     });
-    if (tile_arrive((double)bb, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+    if (tile_arrive(bb, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
@@ -186,8 +137,8 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
     for (int j = 0; j < 2 * kHalf; ++j) {
         const int zz = P.z0 - kHalf + j;
         const bool okz = zz >= 0 && zz < D.nz;
-        q0[j] = as_ff((in0 && okz) ? x[P.base + zz * sz + c0] : zero2);
-        q1[j] = as_ff((in1 && okz) ? x[P.base + zz * sz + c1] : zero2);
+        q0[j] = to_ff((in0 && okz) ? x[P.base + zz * sz + c0] : zero2);
+        q1[j] = to_ff((in1 && okz) ? x[P.base + zz * sz + c1] : zero2);
     }
     float2 pre[kSlots];
 #pragma unroll
@@ -197,8 +148,8 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
     for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
     ff ih2;   // 1/h^2 as a pair (once per CTA)
     {
-        const float2 v = ff_split(1.0 / (D.h * D.h));
-        ih2 = as_ff(v);
+        const float2 v = d2ff(1.0 / (D.h * D.h));
+        ih2 = to_ff(v);
     }
     float rrf = 0.f;
     ff* flat = &plane[0][0];
@@ -206,12 +157,12 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
 #pragma unroll
         for (int j = 0; j < kSlots; ++j) {
             const int e = tid + j * nthr;
-            if (e < kPX * kPY) flat[e] = as_ff(pre[j]);
+            if (e < kPX * kPY) flat[e] = to_ff(pre[j]);
         }
         {
             const int zz = z + kHalf;
-            q0[2 * kHalf] = as_ff((in0 && zz < D.nz) ? x[P.base + zz * sz + c0] : zero2);
-            q1[2 * kHalf] = as_ff((in1 && zz < D.nz) ? x[P.base + zz * sz + c1] : zero2);
+            q0[2 * kHalf] = to_ff((in0 && zz < D.nz) ? x[P.base + zz * sz + c0] : zero2);
+            q1[2 * kHalf] = to_ff((in1 && zz < D.nz) ? x[P.base + zz * sz + c1] : zero2);
         }
         __syncthreads();
         if (z + 1 < P.z1) {
@@ -236,7 +187,7 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
             if (in[k]) {
                 // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
                 const long long g = P.base + z * sz + cc[k];
-                const ff r = ff_add(as_ff(b[g]), ff_mul(acc, ih2));
+                const ff r = ff_add(to_ff(b[g]), ff_mul(acc, ih2));
                 const float rv = r.h;
                 r32[g] = rv;
                 d32[g] = 0.f;
@@ -251,7 +202,7 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
             q1[j] = q1[j + 1];
         }
     }
-    if (tile_arrive((double)rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+    if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
@@ -296,18 +247,18 @@ __global__ void __launch_bounds__(256) k_join_ff(const BlkDesc* __restrict__ blk
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
     tile_elementwise<float>(D, P, [&](long long g, int n) {
-        for (int k = 0; k < n; ++k) V[g + k] = ff_join(x[g + k]);
+        for (int k = 0; k < n; ++k) V[g + k] = ff2d(x[g + k]);
     });
 }
 
 static dim3 tile_threads() { return dim3(kTileX, kTileY / 2); }
 
 // x is the solution in pairs (float2 per point), p32 may be null.
-void launch_ff_init(flosic_ctx* c, double* b, const double* V, bool warm, float2* x, float* p32, double tol2,
-                    double inner_tol2, cudaStream_t s) {
+void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,
+                    double tol2, double inner_tol2, cudaStream_t s) {
     const Multigrid& M = c->mg;
-    k_ff_init<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, b,
-                                                               V, x, c->ws.r32, p32, c->ws.d32, warm ? 1 : 0, tol2,
+    k_ff_init<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
+                                                               reinterpret_cast<const float2*>(b), V, x, c->ws.r32, p32, c->ws.d32, warm ? 1 : 0, tol2,
                                                                inner_tol2, c->opt.max_iter, c->ws.cg);
     note_launch(c);
 }

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k_apply12_tma(const BlkDesc* __restrict__
         }
     }
     const int o = P.o;
-    if (tile_arrive((double)pqf, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
+    if (tile_arrive(pqf, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[o] = 0;

@@ -5,6 +5,8 @@
 //   partial sums of rho_i V_i and rho_i eps_i per orbital (-> U_i, E_xc,i),
 //   V_avg = scale * sum_i rho_i V_i^SIC / rho_spin, V_i^SIC = -(V_i + v_xc,i),
 //   rho_spin = sum_a psi_a^2 (V_avg = 0 where rho_spin <= rho_min).
+#include <type_traits>
+
 #include "internal.cuh"
 #include "xc_device.cuh"
 
@@ -12,7 +14,26 @@ namespace flosic {
 
 constexpr int kXcPts = kChunk / kChunkThreads;   // points per thread
 
-// kF32: pointwise functional in float32 (mixed precision); sums in float64.
+// Warp sum of float partials carried as a float-float pair (two-sum per
+// level), returned in float64.
+__device__ __forceinline__ double warp_sum_ff(float v) {
+    float h = v, l = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        const float s = h + oh, bb = s - h;
+        const float e = (h - (s - bb)) + (oh - bb) + (l + ol);
+        h = s + e;
+        l = e - (h - s);
+    }
+    return f2d(h) + f2d(l);
+}
+
+// kF32 (mixed precision): no float64 operation per point.  The float64
+// inputs are converted with integer operations; rho V (for U_i) is formed and
+// summed as float-float pairs, the functional, V^SIC and V_avg in float32;
+// per-orbital sums are float-float within a warp, float64 across warps.
+// Otherwise float64 throughout.
 // Also stores V_i^SIC = -(V_i + v_xc,i) for the reverse mode.
 template <bool kF32>
 __global__ void __launch_bounds__(kChunkThreads)
@@ -20,52 +41,78 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double* __restrict__ phi, const double* __restrict__ V, double scale,
             double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part,
             double* __restrict__ vsic) {
+    using R = typename std::conditional<kF32, float, double>::type;
     __shared__ double red[kChunkThreads / 32][kMaxN][2];
     const BlkDesc& B = blk[blockIdx.y];
     const int c = blockIdx.x;
     if (c >= B.nchunk) return;
     const long long g0 = (long long)c * kChunk;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double num[kXcPts], rs[kXcPts];
+    const R rmin = (R)rho_min;
+    R num[kXcPts], rs[kXcPts];
 #pragma unroll
-    for (int k = 0; k < kXcPts; ++k) num[k] = rs[k] = 0.0;
+    for (int k = 0; k < kXcPts; ++k) num[k] = rs[k] = R(0);
     for (int i = 0; i < B.N; ++i) {
         const long long base = B.off + (long long)i * B.G;
-        double u = 0.0, ex = 0.0;
+        R u = R(0), ex = R(0);
+        ff uff = {0.f, 0.f};   // kF32: rho V as pairs (U to ~1e-13 relative)
 #pragma unroll
         for (int k = 0; k < kXcPts; ++k) {
             const long long g = g0 + threadIdx.x + k * kChunkThreads;
             if (g >= B.G) continue;
-            const double f = phi[base + g], v = V[base + g], p = psi[base + g];
-            const double rho = f * f;
-            double eps, vxc;
+            R f, v, p, eps, vxc;
             if (kF32) {
+                const float2 f2 = d2ff(phi[base + g]), v2 = d2ff(V[base + g]);
+                f = f2.x;
+                v = v2.x;
+                p = d2f(psi[base + g]);
+                const float ph = f2.x * f2.x;
+                const ff rho2 = ff_quick(ph, fmaf(f2.x, f2.x, -ph) + 2.f * f2.x * f2.y);
+                uff = ff_add(uff, ff_mul(rho2, to_ff(v2)));
                 float ef, vf;
-                lsda_pol_f((float)rho, (float)rho_min, ef, vf);
+                lsda_pol_f(f * f, (float)rmin, ef, vf);
                 eps = ef;
                 vxc = vf;
             } else {
-                lsda_pol(rho, rho_min, eps, vxc);
+                f = phi[base + g];
+                v = V[base + g];
+                p = psi[base + g];
+                double ed, vd;
+                lsda_pol(f * f, rho_min, ed, vd);
+                eps = (R)ed;
+                vxc = (R)vd;
             }
+            const R rho = f * f;
             u += rho * v;
             ex += rho * eps;
-            const double vs = -(v + vxc);
-            vsic[base + g] = vs;
+            const R vs = -(v + vxc);
+            if (kF32) vsic[base + g] = f2d((float)vs);
+            else vsic[base + g] = (double)vs;
             num[k] += rho * vs;
             rs[k] += p * p;
         }
-        u = warp_sum(u);
-        ex = warp_sum(ex);
+        double us, es;
+        if (kF32) {
+            us = ff_to_double(warp_sum(uff));
+            es = warp_sum_ff((float)ex);
+        } else {
+            us = warp_sum((double)u);
+            es = warp_sum((double)ex);
+        }
         if (lane == 0) {
-            red[wid][i][0] = u;
-            red[wid][i][1] = ex;
+            red[wid][i][0] = us;
+            red[wid][i][1] = es;
         }
     }
     if (Vavg) {
 #pragma unroll
         for (int k = 0; k < kXcPts; ++k) {
             const long long g = g0 + threadIdx.x + k * kChunkThreads;
-            if (g < B.G) Vavg[B.voff + g] = (rs[k] > rho_min) ? scale * num[k] / rs[k] : 0.0;
+            if (g >= B.G) continue;
+            if (kF32)
+                Vavg[B.voff + g] = (rs[k] > rmin) ? f2d((float)scale * ((float)num[k] / (float)rs[k])) : 0.0;
+            else
+                Vavg[B.voff + g] = (rs[k] > rmin) ? scale * (double)num[k] / (double)rs[k] : 0.0;
         }
     }
     __syncthreads();
