@@ -346,14 +346,15 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                             if (m & (1 << k)) dd += (double)D.cl[k] - 2.0;
                         D.idd[m] = (float)(1.0 / dd);
                     }
+                    D.tz = (l == 0) ? kTileZ : kTileZc;
                     const int tx = (D.nx + kTileX - 1) / kTileX, ty = (D.ny + kTileY - 1) / kTileY,
-                              tz = (D.nz + kTileZ - 1) / kTileZ;
+                              tz = (D.nz + D.tz - 1) / D.tz;
                     D.ntile = tx * ty * tz;
                     for (int i = 0; i < B.N; ++i)
                         for (int kz = 0; kz < tz; ++kz)
                             for (int ky = 0; ky < ty; ++ky)
                                 for (int kx = 0; kx < tx; ++kx)
-                                    tiles.push_back(make_int4(B.orb0 + i, kx * kTileX, ky * kTileY, kz * kTileZ));
+                                    tiles.push_back(make_int4(B.orb0 + i, kx * kTileX, ky * kTileY, kz * D.tz));
                     offl += (long long)B.N * D.G;
                     chl += (long long)B.N * D.nchunk;
                     tl += (long long)B.N * D.ntile;

@@ -38,6 +38,7 @@ struct BlkDesc {
 // One multigrid level of one spin block (level 0 = the fine grid).
 constexpr int kMaxLevels = 10;
 constexpr int kTileX = 32, kTileY = 16, kTileZ = 32;   // 3-D tiles of the sweeps (threads 32 x 8)
+constexpr int kTileZc = 4;   // tile z-depth on the coarse multigrid levels (enough CTAs to fill the GPU)
 constexpr int kCoarseSweeps = 40;      // damped-Jacobi sweeps on the coarsest level
 constexpr int kCoarseMax = 2000;       // largest coarsest level (points) kept in shared memory
 // planes of a tile staged with the 6-point x/y halo by the z-marching sweeps
@@ -55,6 +56,7 @@ struct LvlDesc {
     long long tile0;       // first tile of orbital 0 in this level's tile table
     int ntile;             // tiles per orbital
     int tma;               // level 0: 1 if the stencil operands of this block are TMA-staged
+    int tz;                // z-depth of this level's tiles (kTileZ on level 0, kTileZc below)
     // Diagonal weight (units 1/h_l^2) of the 7-point operator at the last
     // point of each dimension, 2 elsewhere; differs from 2 on levels whose
     // parent had an even side (see multigrid.cu).  corr = any of them != 2.
@@ -425,7 +427,7 @@ __device__ __forceinline__ TilePos tile_pos(const BlkDesc* blk, const LvlDesc* L
     p.x0 = tl.y;
     p.y0 = tl.z;
     p.z0 = tl.w;
-    p.z1 = min(p.z0 + kTileZ, D.nz);
+    p.z1 = min(p.z0 + D.tz, D.nz);
     p.base = D.off + (long long)i * D.G;
     p.first = D.tile0 + (long long)i * D.ntile;
     return p;
