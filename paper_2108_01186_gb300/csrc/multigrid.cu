@@ -244,76 +244,159 @@ __device__ __forceinline__ int coarse_rows(int y, int nc, int* J, T* w) {
     return (vlo && vhi) ? 2 : 1;
 }
 
-// t = omega D^-1 r + P e_c   (pre-smoothed part plus the coarse correction),
-// V consecutive fine points of a row per thread: their trilinear values come
-// from the 1, 2 or 4 coarse rows around the row, three (float) or two
-// (double) coarse values each.
+// t = omega D^-1 r + P e_c (pre-smoothed part plus the coarse correction)
+// for the V consecutive fine points (x .. x+n-1) of one row: their trilinear
+// values come from the 1, 2 or 4 coarse rows around the row.
+template <class T>
+__device__ __forceinline__ void prolong_row(const LvlDesc& F, const LvlDesc& C, const T* __restrict__ eb,
+                                            const T* __restrict__ r, T* __restrict__ t, T oh2, int x, int y, int z,
+                                            long long g, int n) {
+    constexpr int V = Vec<T>::n;
+    using VT = typename Vec<T>::type;
+    int Jr[2], Kr[2];
+    T wy[2], wz[2];
+    const int nj = coarse_rows<T>(y, C.ny, Jr, wy);
+    const int nk = coarse_rows<T>(z, C.nz, Kr, wz);
+    T u[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) u[k] = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if (b >= nk) continue;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a >= nj) continue;
+            const T* row = eb + ((long long)Kr[b] * C.ny + Jr[a]) * C.nx;
+            const T w = wy[a] * wz[b];
+            if (n == V) {
+                // x is a multiple of V and F.nx of V, so C.nx = F.nx / 2
+                const int I = x >> 1;
+                const T e0 = (I >= 1) ? row[I - 1] : T(0);
+                const T e1 = row[I];
+                if (V == 4) {
+                    const T e2 = row[I + 1];
+                    u[0] += w * T(0.5) * (e0 + e1);
+                    u[1] += w * e1;
+                    u[2] += w * T(0.5) * (e1 + e2);
+                    u[3] += w * e2;
+                } else {
+                    u[0] += w * T(0.5) * (e0 + e1);
+                    u[1] += w * e1;
+                }
+            } else {
+                u[0] += w * prolong_x(row, C.nx, x);
+            }
+        }
+    }
+    T rv[V], out[V];
+    if (n == V) {
+        const VT v = *reinterpret_cast<const VT*>(r + g);
+#pragma unroll
+        for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
+    } else {
+        rv[0] = r[g];
+    }
+    const bool edge = F.corr && (x + n >= F.nx || y == F.ny - 1 || z == F.nz - 1);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const T d = oh2 * (edge ? inv_diag<T>(F, x + k, y, z) : T(1.0 / 6.0));
+        out[k] = d * rv[k] + u[k];
+    }
+    store_n<T, V>(t + g, out, n);
+}
+
+// Prolongation kernel.  float32 rows aligned to 4 go four rows at a time: the
+// fine rows (y, y+1) x (z, z+1), y and z even, share the coarse rows J-1, J
+// and K-1, K (J = y/2, K = z/2), so one thread loads those four coarse rows
+// (three values each, zero outside the coarse grid) and all four fine rows
+// at once.  Everything else goes row by row.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_prolong(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ Lf,
                                                     const LvlDesc* __restrict__ Lc, const int4* __restrict__ tiles_f,
                                                     const int* __restrict__ orb_blk, const int* __restrict__ active,
                                                     const T* __restrict__ r, const T* __restrict__ ec,
                                                     T* __restrict__ t, T omega) {
-    constexpr int V = Vec<T>::n;
-    using VT = typename Vec<T>::type;
     const TilePos P = tile_pos(blk, Lf, tiles_f, orb_blk, blockIdx.x);
     const LvlDesc& F = Lf[P.b];
     if (!active[P.o] || F.coarsest) return;
     const LvlDesc& C = Lc[P.b];
     const T* eb = ec + C.off + (long long)(P.o - blk[P.b].orb0) * C.G;
     const T oh2 = omega * T(F.h * F.h);
-    tile_rows<T>(F, P, [&](int x, int y, int z, long long g, int n) {
-        int Jr[2], Kr[2];
-        T wy[2], wz[2];
-        const int nj = coarse_rows<T>(y, C.ny, Jr, wy);
-        const int nk = coarse_rows<T>(z, C.nz, Kr, wz);
-        T u[V];
+    constexpr bool kQuad = sizeof(T) == sizeof(float);
+    if (!kQuad || F.corr || (F.nx % 4) != 0 || (P.base % 4) != 0) {
+        tile_rows<T>(F, P, [&](int x, int y, int z, long long g, int n) {
+            prolong_row<T>(F, C, eb, r, t, oh2, x, y, z, g, n);
+        });
+        return;
+    }
+    const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+    const T d = oh2 * T(1.0 / 6.0);
+    const int nzp = (P.z1 - P.z0 + 1) >> 1;                 // z pairs in the tile
+    for (int w = linear_tid(); w < 8 * (kTileY / 2) * nzp; w += 256) {
+        const int xg = w & 7, rest = w >> 3;
+        const int yp = rest % (kTileY / 2), zp = rest / (kTileY / 2);
+        const int x = P.x0 + 4 * xg, y = P.y0 + 2 * yp, z = P.z0 + 2 * zp;
+        if (x >= F.nx || y >= F.ny) continue;
+        if (y + 1 >= F.ny || z + 1 >= P.z1) {               // ragged edge: row by row
+            for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < 2; ++b)
+                    if (y + b < F.ny && z + c < P.z1)
+                        prolong_row<T>(F, C, eb, r, t, oh2, x, y + b, z + c,
+                                       P.base + (z + c) * sz + (y + b) * sy + x, 4);
+            continue;
+        }
+        const int I = x >> 1, J = y >> 1, K = z >> 1;
+        // coarse rows (J-1+a, K-1+c), a, c in {0, 1}: values I-1, I, I+1
+        T E[2][2][3];
 #pragma unroll
-        for (int k = 0; k < V; ++k) u[k] = T(0);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            if (b >= nk) continue;
+        for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                if (a >= nj) continue;
-                const T* row = eb + ((long long)Kr[b] * C.ny + Jr[a]) * C.nx;
-                const T w = wy[a] * wz[b];
-                if (n == V) {
-                    // x is a multiple of V and F.nx of V, so C.nx = F.nx / 2
-                    const int I = x >> 1;
-                    const T e0 = (I >= 1) ? row[I - 1] : T(0);
-                    const T e1 = row[I];
-                    if (V == 4) {
-                        const T e2 = row[I + 1];
-                        u[0] += w * T(0.5) * (e0 + e1);
-                        u[1] += w * e1;
-                        u[2] += w * T(0.5) * (e1 + e2);
-                        u[3] += w * e2;
-                    } else {
-                        u[0] += w * T(0.5) * (e0 + e1);
-                        u[1] += w * e1;
-                    }
-                } else {
-                    u[0] += w * prolong_x(row, C.nx, x);
-                }
+                const int JJ = J - 1 + a, KK = K - 1 + c;
+                const bool ok = JJ >= 0 && JJ < C.ny && KK >= 0 && KK < C.nz;
+                const T* row = eb + ((long long)(ok ? KK : 0) * C.ny + (ok ? JJ : 0)) * C.nx;
+                E[c][a][0] = (ok && I >= 1) ? row[I - 1] : T(0);
+                E[c][a][1] = ok ? row[I] : T(0);
+                E[c][a][2] = ok ? row[I + 1] : T(0);
             }
-        }
-        T rv[V], out[V];
-        if (n == V) {
-            const VT v = *reinterpret_cast<const VT*>(r + g);
+        float4 rv[2][2];
 #pragma unroll
-            for (int k = 0; k < V; ++k) rv[k] = reinterpret_cast<const T*>(&v)[k];
-        } else {
-            rv[0] = r[g];
-        }
-        const bool edge = F.corr && (x + n >= F.nx || y == F.ny - 1 || z == F.nz - 1);
+        for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const T d = oh2 * (edge ? inv_diag<T>(F, x + k, y, z) : T(1.0 / 6.0));
-            out[k] = d * rv[k] + u[k];
-        }
-        store_n<T, V>(t + g, out, n);
-    });
+            for (int b = 0; b < 2; ++b)
+                rv[c][b] = *reinterpret_cast<const float4*>(r + P.base + (z + c) * sz + (y + b) * sy + x);
+        // x-interpolated coarse rows
+        T X[2][2][4];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                X[c][a][0] = T(0.5) * (E[c][a][0] + E[c][a][1]);
+                X[c][a][1] = E[c][a][1];
+                X[c][a][2] = T(0.5) * (E[c][a][1] + E[c][a][2]);
+                X[c][a][3] = E[c][a][2];
+            }
+        // even fine index: 1/2 of coarse index - 1 and 1/2 of it; odd: the coarse index
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                T u[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const T y0 = b ? X[0][1][k] : T(0.5) * (X[0][0][k] + X[0][1][k]);   // plane K-1
+                    const T y1 = b ? X[1][1][k] : T(0.5) * (X[1][0][k] + X[1][1][k]);   // plane K
+                    u[k] = c ? y1 : T(0.5) * (y0 + y1);
+                }
+                const float4 v = rv[c][b];
+                float4 o;
+                o.x = d * v.x + u[0];
+                o.y = d * v.y + u[1];
+                o.z = d * v.z + u[2];
+                o.w = d * v.w + u[3];
+                *reinterpret_cast<float4*>(t + P.base + (z + c) * sz + (y + b) * sy + x) = o;
+            }
+    }
 }
 
 // e = t + omega D^-1 (r - A2 t) = (1 - omega) t + (omega/dd)(h^2 r + sum_nbr t);
