@@ -49,10 +49,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
-    p.add_argument("--workload", default="128", choices=["128", "uneven", "fodopt"],
+    p.add_argument("--workload", default="128", choices=["128", "uneven", "fodopt", "hamiltonian"],
                    help="128: the 128^3 forward+adjoint step (default); uneven: 64 systems of "
                         "48^3..128^3 grids and 2..40 orbitals, forward step; fodopt: FIRE FOD relaxation "
-                        "steps at 128^3")
+                        "steps at 128^3; hamiltonian: SC_AvgSIC Hamiltonian apply at 128^3")
     return p.parse_args()
 
 
@@ -470,6 +470,68 @@ def run_fodopt(args):
     D.barrier()
 
 
+def measured_peaks():
+    """MEASURED_PEAKS.json (driver-written), or the recipe's fallback figures."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def run_hamiltonian(args):
+    """SC_AvgSIC Hamiltonian apply H psi = -1/2 Delta_h psi + V_avg psi on the
+    128^3 workload's 32+32 orbitals (inputs in HBM, larger than L2)."""
+    import torch
+    from paper_2108_01186_gb300 import build, synth
+    from paper_2108_01186_gb300 import dist as D
+    from paper_2108_01186_gb300.flosic import Context
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    D.init("nccl")
+    build.build()
+    s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)
+    prec = 0 if args.precision == "fp64" else 1
+    ctx = Context([s], precision=prec, cg_tol=1e-10, preconditioner=1)
+    dev = torch.device("cuda", local)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device=dev)
+    vavg = torch.randn(ctx.vavg_elems, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(1)) * 0.1
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.hamiltonian_apply(psi, None, vavg, out)
+    D.barrier(torch.cuda.synchronize)
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.hamiltonian_apply(psi, None, vavg, out)
+    e1.record(stream)
+    D.barrier(torch.cuda.synchronize)
+    clocks = clk.stop()
+    ms = D.max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+    norb = sum(s.norb)
+    alg = norb * s.G * 16 + ctx.nblk * s.G * 8          # psi in, H psi out, V_avg per spin block
+    peaks = measured_peaks()
+    ach = alg / (ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({"metric": "SC_AvgSIC Hamiltonian applies (orbitals/s) at 128^3", "value": world * norb * 1e3 / ms,
+                          "unit": "orbitals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32-ff" if prec else "f64", "data": "synthetic",
+                          "config": {"workload": "128^3 h=0.2, 32+32 orbitals, H = -1/2 Lap + V_avg",
+                                     "precision": args.precision},
+                          "roofline": {"bound": "hbm", "kernel": "k_hamiltonian_ff" if prec else "k_hamiltonian64",
+                                       "achieved": round(ach, 1), "peak": peaks.get("hbm_gbs"),
+                                       "peak_source": peaks["source"],
+                                       "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                                       "alg_bytes_per_launch": alg},
+                          "clocks": clocks}), flush=True)
+    D.barrier()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -478,6 +540,8 @@ def main():
         run_uneven(args)
     elif args.workload == "fodopt":
         run_fodopt(args)
+    elif args.workload == "hamiltonian":
+        run_hamiltonian(args)
     else:
         run_gpu(args)
 

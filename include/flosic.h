@@ -173,6 +173,27 @@ int flosic_sic_backward(flosic_ctx* ctx, const double* psi, const double* fods,
                         const double* phi, const double* V, const double* gE,
                         double* dE_dpsi, double* dE_dfod, void* stream);
 
+/* SC_AvgSIC Hamiltonian apply (Sec. II.C, Eq. 13): the averaged SIC
+ * potential enters one Kohn-Sham Hamiltonian per spin.  For every orbital a
+ * of every spin block:
+ *   Hpsi_a = -1/2 Delta_h psi_a + (vloc + V_avg) psi_a
+ * with the 12th-order Laplacian of the Poisson solves and zero values
+ * outside the box (orbitals vanish there).
+ * In:  psi [sum N*G] float64, the orbitals H is applied to;
+ *      vloc [sum over systems of G] float64 or NULL: the other local terms
+ *      of Eq. 13 (external, Hartree, exchange-correlation), one field per
+ *      system;
+ *      V_avg [sum G over spin blocks] float64 or NULL: the averaged SIC
+ *      potential as written by flosic_sic_energy_potential (scaled by s).
+ * Out: Hpsi [sum N*G] float64 (must not overlap psi).
+ * Precision follows the context: FP64 in float64; MIXED with the Laplacian
+ * and the potential term in float-float pairs (~48 bits), no float64
+ * arithmetic per point but the final sum.
+ * Errors: ARG (NULL ctx, psi or Hpsi, or Hpsi == psi), CUDA.  Asynchronous
+ * on `stream`. */
+int flosic_hamiltonian_apply(flosic_ctx* ctx, const double* psi, const double* vloc,
+                             const double* V_avg, double* Hpsi, void* stream);
+
 /* Instrumentation (no counterpart in the paper): enable != 0 records a CUDA
  * event pair around every launch of the dominant kernel (the Poisson CG
  * stencil apply) on the stream it runs on.  Errors: ARG, CUDA. */

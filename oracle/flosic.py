@@ -33,7 +33,7 @@ __all__ = [
     "fd_weights", "laplacian", "multipole_moments", "multipole_value", "bc_rhs",
     "bc_rhs_adjoint", "cg_zero_bc", "poisson", "interp", "interp_scatter",
     "grad_central", "lsda_pol", "pw92_ferro", "build_flos", "sic_forward",
-    "sic_backward", "pederson_fod_gradient", "max_threads", "eigh_sym",
+    "sic_backward", "pederson_fod_gradient", "max_threads", "eigh_sym", "hamiltonian_apply",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -118,6 +118,20 @@ def laplacian(u, grid):
     out = np.empty_like(u)
     lib().orc_laplacian(nx, ny, nz, h, _p(u), _p(out))
     return out
+
+
+def hamiltonian_apply(psi, grid, vloc=None, vavg=None):
+    """The SC_AvgSIC Kohn-Sham Hamiltonian of one spin (Sec. II.C, Eq. 13) on
+    the orbitals psi [N, G]: H psi_a = -1/2 Delta_h psi_a + (v_loc + V_avg)
+    psi_a, orbitals zero outside the box; v_loc stands for the other local
+    terms of Eq. 13 (external, Hartree, exchange-correlation)."""
+    psi = np.atleast_2d(_f64(psi))
+    v = np.zeros(psi.shape[1])
+    if vloc is not None:
+        v = v + _f64(vloc)
+    if vavg is not None:
+        v = v + _f64(vavg)
+    return np.stack([-0.5 * laplacian(p, grid) + v * p for p in psi])
 
 
 def multipole_moments(rho, grid):

@@ -211,7 +211,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     c->opt = o;
     c->sys.assign(sys, sys + nsys);
     // spin blocks, packed offsets, chunk table
-    long long off = 0, moff = 0, voff = 0, fod = 0, chunk = 0;
+    long long off = 0, moff = 0, voff = 0, fod = 0, chunk = 0, soff = 0;
     int orb = 0;
     std::vector<int> sys_orb0(nsys + 1, 0);
     for (int s = 0; s < nsys; ++s) {
@@ -226,7 +226,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
             b.cy = y.origin[1] + 0.5 * y.h * (y.ny - 1);
             b.cz = y.origin[2] + 0.5 * y.h * (y.nz - 1);
             b.G = (long long)y.nx * y.ny * y.nz;
-            b.off = off; b.moff = moff; b.voff = voff; b.fod_off = fod;
+            b.off = off; b.moff = moff; b.voff = voff; b.fod_off = fod; b.soff = soff;
             b.orb0 = orb; b.sys = s; b.spin = sp;
             b.nchunk = (int)((b.G + kChunk - 1) / kChunk);
             b.chunk0 = chunk;
@@ -235,7 +235,9 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
             off += b.N * b.G; moff += (long long)b.N * b.N; voff += b.G; fod += b.N;
             chunk += (long long)b.N * b.nchunk; orb += b.N;
         }
+        soff += (long long)y.nx * y.ny * y.nz;
     }
+    c->sgrid_elems = soff;
     sys_orb0[nsys] = orb;
     c->nblk = (int)c->blk.size();
     c->norb = orb;
@@ -496,6 +498,15 @@ int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* 
     launch_energy_reduce(c, U, Exc, E_sic, s);
     c->have_energy = true;
     return check_cuda(c, cudaGetLastError(), "energy kernels");
+}
+
+int flosic_hamiltonian_apply(flosic_ctx* c, const double* psi, const double* vloc, const double* V_avg,
+                             double* Hpsi, void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!psi || !Hpsi) return fail(c, FLOSIC_ERR_ARG, "psi and Hpsi are required");
+    if (Hpsi == psi) return fail(c, FLOSIC_ERR_ARG, "Hpsi must not overlap psi");
+    launch_hamiltonian(c, psi, vloc, V_avg, Hpsi, (cudaStream_t)stream);
+    return check_cuda(c, cudaGetLastError(), "hamiltonian kernel");
 }
 
 int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, const double* phi,

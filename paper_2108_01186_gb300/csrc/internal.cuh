@@ -26,6 +26,7 @@ struct BlkDesc {
     long long off;              // offset of orbital 0 in orbital-sized arrays
     long long moff;             // offset in N x N arrays
     long long voff;             // offset in V_avg
+    long long soff;             // offset of this block's system in per-system grid arrays
     long long fod_off;          // offset (in FODs) of FOD 0
     int orb0;                   // global index of orbital 0
     int sys, spin;
@@ -145,6 +146,7 @@ struct flosic_ctx {
     flosic::BlkDesc* d_blk = nullptr;       // device copy
     int nblk = 0, norb = 0;
     long long orb_elems = 0, vavg_elems = 0, mat_elems = 0, nchunk_total = 0;
+    long long sgrid_elems = 0;   // sum over systems of the grid points (per-system fields)
     int kparts = 0;                         // K-splits of the grid contractions
     std::vector<int> h_orb_blk;
     int* d_orb_blk = nullptr;               // [norb] block of each orbital
@@ -197,6 +199,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
                           cudaStream_t s);
 
+// SC_AvgSIC Hamiltonian apply: H psi = -1/2 Delta_h psi + (v_loc + V_avg) psi
+void launch_hamiltonian(const flosic_ctx* c, const double* psi, const double* vloc, const double* vavg,
+                        double* hpsi, cudaStream_t s);
+cudaError_t upload_hamiltonian_constants();
 template <class T>
 void launch_vcycle(const flosic_ctx* c, const MgPtrs<T>& mp, const int* active, cudaStream_t s);
 template <class T>

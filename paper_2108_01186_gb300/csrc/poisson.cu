@@ -40,6 +40,7 @@ cudaError_t upload_stencil12_constants();
 cudaError_t upload_stencil_constants() {
     {
         cudaError_t e = upload_stencil12_constants();
+        if (e == cudaSuccess) e = upload_hamiltonian_constants();
         if (e != cudaSuccess) return e;
     }
     double w[kHalf + 1];

@@ -14,24 +14,12 @@
 // Round structure per orbital:  r = b - A x (pairs) -> stop if
 // r.r <= tol^2 b.b, else a float32 solve of A d = float(r) to
 // max(inner_tol^2 r.r, tol^2 b.b / 4) -> x += d (pairs).
-#include "internal.cuh"
+#include "ffsweep.cuh"
 
 namespace flosic {
 
 
-__constant__ float c_wff[2 * (kHalf + 1)];   // 3 w_0, w_1 .. w_6 as (hi, lo) pairs
-
-cudaError_t upload_ff_weights() {
-    double w[kHalf + 1];
-    stencil_weights(w);
-    float f[2 * (kHalf + 1)];
-    for (int m = 0; m <= kHalf; ++m) {
-        const double ww = (m == 0) ? 3.0 * w[0] : w[m];
-        f[2 * m] = (float)ww;
-        f[2 * m + 1] = (float)(ww - (double)f[2 * m]);
-    }
-    return cudaMemcpyToSymbol(c_wff, f, sizeof(f));
-}
+cudaError_t upload_ff_weights() { return upload_ffsweep_weights(); }
 
 // Last CTA of an orbital, once r.r is known: the outer stop test, else the
 // start of the next float32 solve (its target, active flag and counters).
@@ -97,9 +85,7 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
     }
 }
 
-// r = b - A x in pairs on the tiles of the stencil sweep (a CTA marches a
-// 32 x 16 column tile along z, planes staged with the 6-point x/y halo in
-// shared memory, the 13 z-values of its columns in registers).  Writes
+// r = b - A x in pairs on the tiles of the float-float sweep.  Writes
 // r32 = float(r), d32 = 0 (p32 = r32 when given) and starts the next round.
 __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                        const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
@@ -112,96 +98,20 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
     const LvlDesc& D = L[P.b];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTileX + tx;
-    const int nthr = kTileX * (kTileY / 2);
-    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
-    const int gx = P.x0 + tx;
-    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
-    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
-    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
-    long long soff[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) {
-        const int e = tid + j * nthr;
-        soff[j] = -1;
-        if (e < kPX * kPY) {
-            const int yy = e / kPX, xx = e - yy * kPX;
-            const int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
-            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
-        }
-    }
-    const float2 zero2 = make_float2(0.f, 0.f);
-    ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
-#pragma unroll
-    for (int j = 0; j < 2 * kHalf; ++j) {
-        const int zz = P.z0 - kHalf + j;
-        const bool okz = zz >= 0 && zz < D.nz;
-        q0[j] = to_ff((in0 && okz) ? x[P.base + zz * sz + c0] : zero2);
-        q1[j] = to_ff((in1 && okz) ? x[P.base + zz * sz + c1] : zero2);
-    }
-    float2 pre[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[P.base + P.z0 * sz + soff[j]] : zero2;
-    ff w[kHalf + 1];
-#pragma unroll
-    for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
-    ff ih2;   // 1/h^2 as a pair (once per CTA)
-    {
-        const float2 v = d2ff(1.0 / (D.h * D.h));
-        ih2 = to_ff(v);
-    }
+    const ff ih2 = to_ff(d2ff(1.0 / (D.h * D.h)));   // once per CTA
     float rrf = 0.f;
-    ff* flat = &plane[0][0];
-    for (int z = P.z0; z < P.z1; ++z) {
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) {
-            const int e = tid + j * nthr;
-            if (e < kPX * kPY) flat[e] = to_ff(pre[j]);
-        }
-        {
-            const int zz = z + kHalf;
-            q0[2 * kHalf] = to_ff((in0 && zz < D.nz) ? x[P.base + zz * sz + c0] : zero2);
-            q1[2 * kHalf] = to_ff((in1 && zz < D.nz) ? x[P.base + zz * sz + c1] : zero2);
-        }
-        __syncthreads();
-        if (z + 1 < P.z1) {
-            const long long pz = P.base + (z + 1) * sz;
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? x[pz + soff[j]] : zero2;
-        }
-        const int lx = tx + kHalf;
-        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
-        const bool in[2] = {in0, in1};
-        const long long cc[2] = {c0, c1};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const ff* qk = (k == 0) ? q0 : q1;
-            ff acc = ff_mul(w[0], qk[kHalf]);
-#pragma unroll
-            for (int m = 1; m <= kHalf; ++m) {
-                const ff sm = ff_sum6(plane[ly[k]][lx - m], plane[ly[k]][lx + m], plane[ly[k] - m][lx],
-                                      plane[ly[k] + m][lx], qk[kHalf - m], qk[kHalf + m]);
-                acc = ff_add(acc, ff_mul(w[m], sm));
-            }
-            if (in[k]) {
-                // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
-                const long long g = P.base + z * sz + cc[k];
-                const ff r = ff_add(to_ff(b[g]), ff_mul(acc, ih2));
-                const float rv = r.h;
-                r32[g] = rv;
-                d32[g] = 0.f;
-                if (p32) p32[g] = rv;
-                rrf += rv * rv;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 2 * kHalf; ++j) {
-            q0[j] = q0[j + 1];
-            q1[j] = q1[j + 1];
-        }
-    }
+    ff_sweep12(
+        D, P, [&](long long g) { return x[g]; },
+        [&](long long g, ff, ff acc) {
+            // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
+            const ff r = ff_add(to_ff(b[g]), ff_mul(acc, ih2));
+            const float rv = r.h;
+            r32[g] = rv;
+            d32[g] = 0.f;
+            if (p32) p32[g] = rv;
+            rrf += rv * rv;
+        },
+        plane);
     if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "OK", 1: "ARG", 2: "CUDA", 3: "ILLCOND", 4: "NOCONV", 5: "NON
 ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "flosic_last_error",
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
-                 "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error")
+                 "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error",
+                 "flosic_hamiltonian_apply")
 
 
 class FlosicError(RuntimeError):
@@ -68,6 +69,7 @@ def load_library(path=LIB_PATH):
     L.flosic_orbital_poisson.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.flosic_sic_energy_potential.argtypes = [vp, vp, vp, vp, d, vp, vp, vp, vp, vp]
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.flosic_hamiltonian_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
     L.flosic_orbital_poisson_noalloc.argtypes = [i, i, i, d, ctypes.POINTER(d), i, vp, vp, d, i, vp, vp, vp]
@@ -199,6 +201,21 @@ class Context:
         self._check(self._L.flosic_sic_backward(self._h, _ptr(psi), _ptr(fods), _ptr(phi), _ptr(V), _ptr(gE),
                                                 _ptr(dpsi), _ptr(dfod), _stream()))
         return dpsi, dfod
+
+    def hamiltonian_apply(self, psi, vloc=None, V_avg=None, out=None):
+        """H psi = -1/2 Delta_h psi + (vloc + V_avg) psi per orbital (the
+        SC_AvgSIC Hamiltonian); vloc one field per system, V_avg one per spin
+        block (as returned by sic_energy_potential), either may be None."""
+        self._req(psi, self.orb_elems, "psi")
+        if vloc is not None:
+            total = sum(g["nx"] * g["ny"] * g["nz"] for g in self.systems)
+            self._req(vloc, total, "vloc")
+        if V_avg is not None:
+            self._req(V_avg, self.vavg_elems, "V_avg")
+        hpsi = self._empty(self.orb_elems) if out is None else out
+        self._check(self._L.flosic_hamiltonian_apply(self._h, _ptr(psi), _ptr(vloc), _ptr(V_avg), _ptr(hpsi),
+                                                     _stream()))
+        return hpsi
 
     def profile(self, enable=True):
         self._check(self._L.flosic_profile(self._h, int(enable)))
