@@ -277,6 +277,13 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.S, me); A(&w.Q, me); A(&w.C, me); A(&w.U, me); A(&w.lam, orb); A(&w.P, me);
     A(&w.vbar, me); A(&w.tmp, 4 * me); A(&w.E2, 2 * me);
     A(&w.mat_part, (long long)c->kparts * me);
+    std::vector<long long> goff;
+    if (o.precision == FLOSIC_MIXED) {
+        A(&w.gram_part, gram_tc_part_elems(c, goff));
+        A(&w.gram_off, c->nblk);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(w.gram_off, goff.data(), sizeof(long long) * c->nblk, cudaMemcpyHostToDevice);
+    }
     A(&w.mom, 10LL * orb);
     A(&c->d_bidx, (long long)bidx.size()); A(&c->d_bcoef, 10LL * (long long)bidx.size());
     A(&w.e_part, 2 * chunk); A(&w.e_orb, 2LL * orb);
@@ -413,6 +420,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(double) * nmax * nmax));
     }
+    if (e == cudaSuccess && o.precision == FLOSIC_MIXED) e = setup_gram_tc();
     if (e == cudaSuccess && M.enabled) {
         const bool f32 = (o.precision == FLOSIC_MIXED);
         c->n_tma_blocks = f32 ? setup_tensor_maps(c, w.z32, w.p32, w.q32, 4) : setup_tensor_maps(c, w.z64, w.p64, w.q64, 8);

@@ -293,8 +293,13 @@ static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_
     k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out); note_launch(c);
 }
 
+// Raw Gram psi psi^T per block: tensor cores (split-BF16) in mixed precision,
+// the float64 contraction otherwise.
 void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s) {
-    contract(c, LoadPsi{psi}, LoadPsi{psi}, c->ws.M, s);
+    if (c->opt.precision == FLOSIC_MIXED)
+        launch_gram_tc(c, psi, s);
+    else
+        contract(c, LoadPsi{psi}, LoadPsi{psi}, c->ws.M, s);
 }
 
 void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,

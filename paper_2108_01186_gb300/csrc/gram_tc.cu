@@ -1,0 +1,291 @@
+// Grid-summed overlap Gram M_ab = sum_g psi_a(g) psi_b(g) on the fifth-
+// generation tensor cores (the overlap of the Fermi orbitals, S = dV F F^T =
+// dV T M T^T, Sec. II, Eqs. 6-8), mixed-precision path.
+//
+// Split-BF16: each float64 value is taken to float32 (integer operations) and
+// written as three bfloat16 terms v = v1 + v2 + v3 (~24 significant bits).
+// The products v1w1 + v1w2 + v2w1 + v1w3 + v3w1 + v2w2 keep float32-level
+// accuracy; they are six tcgen05.mma (kind::f16, bf16 inputs, float32
+// accumulation in tensor memory) per 16-point K slice, M = 128 (orbital rows
+// padded), N = the orbital count rounded up to 32.  One CTA sums a chunk of
+// 2048 grid points of one spin block, writes the float32 partial, and a
+// second kernel adds the partials in float64 in a fixed order.
+//
+// Per 64-point stage the CTA's 128 threads load the N x 64 float64 block,
+// split it and store the three bf16 tiles K-major with the 128-byte swizzle
+// (row r, 16-byte chunk c at chunk c ^ (r mod 8)); thread 0 issues the MMAs
+// and commits them to the stage's mbarrier.  Two stages alternate; every
+// mbarrier wait is bounded and a timeout sets the status word.
+//
+// The tensor cores' float32 accumulation drifts with the length of the
+// accumulation chain (measured: S off by ~1e-5 after 2048 points, ~2e-6
+// after 256).  So the hi x hi products, which carry almost all of the sum,
+// go to a TMEM accumulator that restarts every 64-point stage (two of them,
+// alternating); each finished stage is read back (tcgen05.ld) and added in
+// float32 registers with round-to-nearest.  The five cross products
+// (<= 2^-8 of the total) stay in one accumulator for the whole chunk.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace flosic {
+
+constexpr int kGK = 64;                      // grid points per stage (128 bytes of bf16 per row)
+constexpr int kGChunk = 2048;                // grid points per CTA
+constexpr int kGRows = 128;                  // MMA M: orbital rows, padded
+constexpr int kGTile = kGRows * kGK * 2;     // one bf16 tile: 16 KB
+constexpr int kGStages = 2;
+constexpr int kGSmem = kGStages * 3 * kGTile + 1024;   // + 1024-byte alignment slack
+constexpr long long kGWaitLimit = 1LL << 24;
+
+__device__ __forceinline__ uint32_t g_smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void g_mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(g_smem_addr(bar)), "r"(count) : "memory");
+}
+
+// true once the phase with the given parity has completed; false after the limit
+__device__ __forceinline__ bool g_mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < kGWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(g_smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, consecutive
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                  // version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), float32 D.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// the six split pairs (i, j) with i + j <= 2 (0-based), A split i with B split j
+__constant__ int c_pair_a[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int c_pair_b[6] = {0, 1, 0, 2, 0, 1};
+
+// Reads 32 columns of this warp's 32 TMEM lanes and adds them to acc.
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float* acc) {
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(v[j]);
+}
+
+template <int NB>   // NB = MMA N / 32 (1 .. 4)
+__global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
+                                                    float* __restrict__ part, const long long* __restrict__ part_off,
+                                                    int* __restrict__ status) {
+    extern __shared__ unsigned char g_smem_raw[];
+    __shared__ uint64_t mbar[kGStages];
+    __shared__ uint32_t tmem_base;
+    constexpr int NN = 32 * NB;                      // MMA N (columns of one accumulator)
+    constexpr uint32_t kCols = (3 * NN <= 32) ? 32 : (3 * NN <= 64) ? 64 : (3 * NN <= 128) ? 128
+                               : (3 * NN <= 256) ? 256 : 512;
+    const BlkDesc& B = blk[blockIdx.y];
+    const int N = B.N;
+    const long long g_begin = (long long)blockIdx.x * kGChunk;
+    if (g_begin >= B.G) return;                      // whole CTA
+    const long long g_end = min(g_begin + (long long)kGChunk, B.G);
+    const int nst = (int)((g_end - g_begin + kGK - 1) / kGK);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
+    // zero every tile once: rows N..127 and points past the chunk stay zero
+    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 128)
+        reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        g_mbar_init(&mbar[0], 1);
+        g_mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_addr(&tmem_base)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;                 // columns: [0,NN) and [NN,2NN) hi x hi, [2NN,3NN) cross
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t idesc = umma_idesc_bf16(kGRows, NN);
+    uint32_t phase[kGStages] = {0u, 0u};
+    bool ok = true;
+    float acc[NN];                                   // row 32 warp + lane of the sums
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[j] = 0.f;
+    const double* pb = psi + B.off;
+    const int k = tid & 63;                          // this thread's point within a stage
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (st >= kGStages) {                        // stage st-2 done: its tile may be overwritten
+            ok = g_mbar_wait(&mbar[buf], phase[buf]) && ok;
+            phase[buf] ^= 1u;
+        }
+        unsigned char* tile = base + buf * 3 * kGTile;
+        const long long g = g_begin + (long long)st * kGK + k;
+        for (int a = tid >> 6; a < N; a += 2) {
+            const double v = (g < g_end) ? pb[(long long)a * B.G + g] : 0.0;
+            const float f = d2f(v);
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(f);
+            const float r1 = f - __bfloat162float(b1);
+            const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 b3 = __float2bfloat16_rn(r1 - __bfloat162float(b2));
+            const int off = a * 128 + ((((k >> 3) ^ (a & 7))) << 4) + ((k & 7) << 1);
+            *reinterpret_cast<__nv_bfloat16*>(tile + off) = b1;
+            *reinterpret_cast<__nv_bfloat16*>(tile + kGTile + off) = b2;
+            *reinterpret_cast<__nv_bfloat16*>(tile + 2 * kGTile + off) = b3;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t s0 = g_smem_addr(tile);
+            const uint32_t dhi = tmem + (uint32_t)(buf * NN), dx = tmem + (uint32_t)(2 * NN);
+#pragma unroll
+            for (int kk = 0; kk < kGK / 16; ++kk) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint64_t da = umma_desc_sw128(s0 + c_pair_a[p] * kGTile + kk * 32);
+                    const uint64_t db = umma_desc_sw128(s0 + c_pair_b[p] * kGTile + kk * 32);
+                    if (p == 0) umma_bf16(dhi, da, db, idesc, kk != 0);          // restarts every stage
+                    else umma_bf16(dx, da, db, idesc, (st | kk | (p - 1)) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             g_smem_addr(&mbar[buf]))
+                         : "memory");
+        }
+        if (st >= 1) {                               // add the previous stage's hi x hi sums
+            const int pbuf = buf ^ 1;
+            ok = g_mbar_wait(&mbar[pbuf], phase[pbuf]) && ok;
+            ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld is warp-collective
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(pbuf * NN + 32 * c), acc + 32 * c);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+    }
+    // the last stage (its commit covers every MMA of the CTA): its hi x hi
+    // sums, then the cross products
+    const int lb = (nst - 1) & 1;
+    ok = g_mbar_wait(&mbar[lb], phase[lb]) && ok;
+    ok = __all_sync(0xffffffffu, ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(lb * NN + 32 * c), acc + 32 * c);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(2 * NN + 32 * c), acc + 32 * c);
+        const int r = warp * 32 + lane;
+        float* out = part + part_off[blockIdx.y] + (long long)blockIdx.x * N * N;
+        if (r < N) {
+#pragma unroll
+            for (int j = 0; j < NN; ++j)
+                if (j < N) out[(long long)r * N + j] = acc[j];
+        }
+    } else if (tid == 0) {
+        atomicOr(status + 3, 2);                     // an MMA completion did not arrive in time
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+// M[block][e] = sum over the block's chunks of the float32 partials, in
+// float64 and in chunk order.
+__global__ void k_gram_sum(const BlkDesc* __restrict__ blk, const float* __restrict__ part,
+                           const long long* __restrict__ part_off, double* __restrict__ M) {
+    const BlkDesc& B = blk[blockIdx.y];
+    const int NN2 = B.N * B.N;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NN2) return;
+    const long long nch = (B.G + kGChunk - 1) / kGChunk;
+    const float* p = part + part_off[blockIdx.y] + e;
+    double s = 0.0;
+    for (long long q = 0; q < nch; ++q) s += (double)p[q * NN2];
+    M[B.moff + e] = s;
+}
+
+long long gram_tc_part_elems(const flosic_ctx* c, std::vector<long long>& off) {
+    long long total = 0;
+    off.clear();
+    for (const auto& b : c->blk) {
+        off.push_back(total);
+        total += ((b.G + kGChunk - 1) / kGChunk) * (long long)b.N * b.N;
+    }
+    return total;
+}
+
+cudaError_t setup_gram_tc() {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    return e;
+}
+
+void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
+    long long gmax = 0;
+    int nmax = 0;
+    for (const auto& b : c->blk) {
+        gmax = b.G > gmax ? b.G : gmax;
+        nmax = b.N > nmax ? b.N : nmax;
+    }
+    const dim3 grid((unsigned)((gmax + kGChunk - 1) / kGChunk), (unsigned)c->nblk);
+    const int nb = (nmax + 31) / 32;   // accumulator width for the widest block
+    float* part = c->ws.gram_part;
+    const long long* off = c->ws.gram_off;
+    if (nb <= 1) k_gram_tc<1><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else if (nb == 2) k_gram_tc<2><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else if (nb == 3) k_gram_tc<3><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else k_gram_tc<4><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    note_launch((flosic_ctx*)c);
+    const dim3 g2((unsigned)((nmax * nmax + 255) / 256), (unsigned)c->nblk);
+    k_gram_sum<<<g2, 256, 0, s>>>(c->d_blk, part, off, c->ws.M);
+    note_launch((flosic_ctx*)c);
+}
+
+}  // namespace flosic

@@ -106,6 +106,8 @@ struct Workspace {
     double* E2;            // [sum 2 N*N] [C^T | D] of the reverse apply
     long long mat_elems;   // sum N*N
     double* mat_part;      // partial N x N sums [kparts][sum N*N]
+    float* gram_part;      // mixed path: tensor-core Gram partials [per block: chunks][N][N]
+    long long* gram_off;   // [nblk] offsets into gram_part
     double* mom;           // [norb][10]
     double* mom_part;      // [nchunk_total][10]
     double* e_part;        // [nchunk_total][2] energies partials
@@ -199,6 +201,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
                           cudaStream_t s);
 
+// tensor-core overlap Gram (mixed precision)
+long long gram_tc_part_elems(const flosic_ctx* c, std::vector<long long>& off);
+cudaError_t setup_gram_tc();
+void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s);
 // SC_AvgSIC Hamiltonian apply: H psi = -1/2 Delta_h psi + (v_loc + V_avg) psi
 void launch_hamiltonian(const flosic_ctx* c, const double* psi, const double* vloc, const double* vavg,
                         double* hpsi, cudaStream_t s);

@@ -7,6 +7,7 @@ one stencil launch (8 x 128^3 float32 vectors: 64 MiB each, above L2) and
 free of the oracle and of any randomness.
 
   python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64]
+  python -m paper_2108_01186_gb300.profile_case --case flo     (FLO build, 96^3, 16+16 orbitals)
 """
 import argparse
 
@@ -16,7 +17,12 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--norb", type=int, default=8)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--case", default="poisson", choices=["poisson", "flo"],
+                    help="poisson: one multigrid-PCG solve of Gaussian densities; flo: two FLO builds "
+                         "(tensor-core overlap) of the seeded 96^3, 16+16-orbital system")
     args = ap.parse_args()
+    if args.case == "flo":
+        return flo_case(args)
     import torch
     from paper_2108_01186_gb300 import build
     from paper_2108_01186_gb300.flosic import Context
@@ -32,6 +38,23 @@ def main():
     V, it, conv = ctx.orbital_poisson(phi)
     torch.cuda.synchronize()
     print("iterations", it.tolist(), "converged", conv.tolist())
+
+
+def flo_case(args):
+    import numpy as np
+    import torch
+    from paper_2108_01186_gb300 import build, synth
+    from paper_2108_01186_gb300.flosic import Context
+
+    build.build()
+    s = synth.make_config(1)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device="cuda")
+    fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods]), device="cuda")
+    ctx = Context([s], precision=0 if args.fp64 else 1, cg_tol=1e-10)
+    for _ in range(2):
+        phi, S, Q = ctx.build_flos(psi, fods)
+    torch.cuda.synchronize()
+    print("sum of S", float(S.double().sum()))
 
 
 if __name__ == "__main__":
