@@ -31,6 +31,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "orbital SIC solves/s at 128^3, mixed vs FP64 at 1e-6 Ha; HBM % of peak"
 WORKLOAD = "128^3 grid h=0.2 bohr, 32+32 orbitals on 16 atoms, FLO build + 64 Poisson solves + LSDA/E_SIC/V_avg + adjoint"
+METRIC_192 = "orbital SIC solves/s at 192^3 (120+120 orbitals), mixed precision; HBM % of peak"
+WORKLOAD_192 = ("192^3 grid h=0.15 bohr, 120+120 orbitals on 60 atoms, FLO build (tensor-core overlap) + 240 "
+                "Poisson solves + LSDA/E_SIC/V_avg + adjoint")
 CG_TOL = 1e-10
 # Plain-CG iterations the oracle needs per orbital of this workload to reach
 # ||r|| <= 1e-10 ||b|| (measured once on orbital 0 of spin 0); used to scale the
@@ -46,11 +49,14 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--preconditioner", default="mg", choices=["mg", "none"])
+    p.add_argument("--solver", default="pcg", choices=["pcg", "aar"],
+                   help="float32 inner solver of the mixed path: CG or Alternating Anderson-Richardson")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
-    p.add_argument("--workload", default="128", choices=["128", "uneven", "fodopt", "hamiltonian"],
-                   help="128: the 128^3 forward+adjoint step (default); uneven: 64 systems of "
+    p.add_argument("--workload", default="128", choices=["128", "192", "uneven", "fodopt", "hamiltonian"],
+                   help="128: the 128^3 forward+adjoint step (default); 192: the same step at 192^3 with "
+                        "120+120 orbitals; uneven: 64 systems of "
                         "48^3..128^3 grids and 2..40 orbitals, forward step; fodopt: FIRE FOD relaxation "
                         "steps at 128^3; hamiltonian: SC_AvgSIC Hamiltonian apply at 128^3")
     return p.parse_args()
@@ -227,11 +233,17 @@ def run_gpu(args):
     from paper_2108_01186_gb300.flosic import Context
 
     build.build()
-    s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)   # each rank: its own system
+    if args.workload == "192":   # the largest workload: 192^3, h=0.15, 120+120 orbitals on 60 atoms
+        s = synth.make_system(192, 0.15, 60, [120, 120], seed=4000 + rank)
+        workload = WORKLOAD_192
+    else:
+        s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)   # each rank: its own system
+        workload = WORKLOAD
     norb = sum(s.norb)
     prec = 1 if args.precision == "mixed" else 0
     pc = 1 if args.preconditioner == "mg" else 0
-    ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc)
+    solver = 1 if args.solver == "aar" else 0
+    ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc, solver=solver)
     dev = torch.device("cuda", local)
     psi_h = torch.from_numpy(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
     fods_h = torch.from_numpy(np.concatenate([f.ravel() for f in s.fods])).pin_memory()
@@ -251,6 +263,7 @@ def run_gpu(args):
     barrier()
     ctx.profile(True)
     ctx.profile_read(reset=True)
+    ctx.profile_read_overlap(reset=True)
     clk = ClockSampler(local)
     clk.start()
     iters_sum = np.zeros(norb)
@@ -266,6 +279,7 @@ def run_gpu(args):
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
     prof = ctx.profile_read(reset=True)
+    prof_ov = ctx.profile_read_overlap(reset=True)
     ctx.profile(False)
     ms = D.max_over_ranks(ms, dev)
     ms_step = ms / args.steps
@@ -283,13 +297,37 @@ def run_gpu(args):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
         peak, peak_src = 6800.0, "fallback"
-    roof = {"bound": "hbm", "kernel": "k_apply12_tma<float>" if prec == 1 else "k_apply12_tma<double>",
+    kname = "k_apply12_tma<float>" if prec == 1 else "k_apply12_tma<double>"
+    if solver == 1:
+        kname = "k_residual12_aar<float>"
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": traffic_for(os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "stencil.cu")),
+            "traffic": (traffic_for(os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "stencil.cu"))
+                        if args.workload == "128" and solver == 0 else None),
             "alg_bytes_per_launch": alg_bytes / launches,
             "avg_launch_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
             "share_of_step": round(prof["kernel_ms"] / ms, 4)}
+    # the overlap Gram on the tensor cores (mixed path): algorithmic flops
+    # 2 N^2 G per spin block against the measured dense bf16 peak, and its
+    # float64 reads of psi (8 N G bytes per block) against the HBM peak
+    roof_ov = None
+    if prof_ov["kernel_launches"] > 0 and prof_ov["kernel_ms"] > 0:
+        try:
+            pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            tc_peak, tc_src = float(pk["bf16_tflops"]), "measured"
+        except (OSError, ValueError, KeyError):
+            tc_peak, tc_src = 1900.0, "fallback"
+        sec = prof_ov["kernel_ms"] / 1e3
+        tflops = prof_ov["flops"] / sec / 1e12
+        ov_bytes = prof_ov["kernel_launches"] * sum(8.0 * n * s.G for n in s.norb)
+        roof_ov = {"bound": "latency", "kernel": "k_gram_tc (split-BF16 tcgen05)",
+                   "achieved": round(tflops, 3), "peak": tc_peak, "peak_source": tc_src, "unit": "TFLOP/s",
+                   "frac": round(tflops / tc_peak, 5),
+                   "hbm_achieved_gbs": round(ov_bytes / sec / 1e9, 1),
+                   "hbm_frac": round(ov_bytes / sec / 1e9 / peak, 4),
+                   "avg_launch_ms": prof_ov["kernel_ms"] / prof_ov["kernel_launches"],
+                   "launches": prof_ov["kernel_launches"]}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -350,17 +388,20 @@ def run_gpu(args):
         del ctx64
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "128":
         cpu = oracle_sample(s)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC if args.workload == "128" else METRIC_192, "value": value, "unit": "solves/s",
+                "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32-cg+f64" if prec == 1 else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": args.precision, "preconditioner": args.preconditioner,
-                           "cg_tol": CG_TOL, "l2": "inputs larger than L2 (psi 1.07 GB per rank)",
+                "config": {"workload": workload, "precision": args.precision, "preconditioner": args.preconditioner,
+                           "solver": args.solver,
+                           "cg_tol": CG_TOL,
+                           "l2": "inputs larger than L2 (psi %.2f GB per rank)" % (8e-9 * norb * s.G),
                            "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
+                "roofline": roof, "roofline_overlap": roof_ov, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
                 "gpu_launches": prof["launches"]}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -57,6 +57,10 @@ enum { FLOSIC_FP64 = 0, FLOSIC_MIXED = 1 };                 /* precision */
 enum { FLOSIC_GRAD_INTERP = 0, FLOSIC_GRAD_PAPER = 1 };     /* fod_grad_mode */
 enum { FLOSIC_ADJ_REUSE_V = 0, FLOSIC_ADJ_EXACT = 1 };      /* adjoint_mode */
 enum { FLOSIC_PC_NONE = 0, FLOSIC_PC_MG = 1 };              /* preconditioner */
+/* inner solver of the mixed path: conjugate gradients (this library's
+ * default) or Alternating Anderson-Richardson (the iteration Sec. II.A's code
+ * uses for its electrostatics) */
+enum { FLOSIC_SOLVER_PCG = 0, FLOSIC_SOLVER_AAR = 1 };
 
 typedef struct {
     int nx, ny, nz;       /* interior grid points per direction (>= 1) */
@@ -86,12 +90,21 @@ typedef struct {
     double illcond_tol;   /* ILLCOND when lambda_min(S) < tol*lambda_max(S) */
     int preconditioner;   /* FLOSIC_PC_NONE or FLOSIC_PC_MG (multigrid
                              V-cycle on the 7-point Laplacian) */
+    int solver;           /* FLOSIC_SOLVER_PCG (default) or FLOSIC_SOLVER_AAR:
+                             the float32 inner solver of the MIXED path
+                             (AAR requires MIXED) */
+    double aar_omega;     /* AAR Richardson relaxation (default 0.6) */
+    double aar_beta;      /* AAR Anderson mixing (default 0.6) */
+    int aar_m;            /* AAR history length, 1..8 (default 7) */
+    int aar_p;            /* AAR: every p-th step is an Anderson step, >= 2
+                             (default 6) */
 } flosic_options;
 
 typedef struct flosic_ctx flosic_ctx;
 
 /* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
- * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG.
+ * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG,
+ * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6).
  * Returns FLOSIC_ERR_ARG if opt is NULL. */
 int flosic_default_options(flosic_options* opt);
 
@@ -206,6 +219,14 @@ int flosic_profile(flosic_ctx* ctx, int enable);
  * iteration of a solve), counted on the device.  Waits for the device.
  * reset != 0 zeroes the counters. */
 int flosic_profile_read(flosic_ctx* ctx, double* out, int reset);
+
+/* Instrumentation (no counterpart in the paper), the tensor-core overlap of
+ * the mixed path (timed while flosic_profile is enabled): host array out[3]:
+ * [0] summed duration (ms) of the overlap-kernel launches, [1] their number,
+ * [2] their algorithmic flops (2 N^2 G per spin block and launch; the split
+ * products and padding the tensor cores also execute are not counted).
+ * Waits for the device.  reset != 0 zeroes the counters.  Errors: ARG, CUDA. */
+int flosic_profile_read_overlap(flosic_ctx* ctx, double* out, int reset);
 
 /* Allocation-free Poisson solve.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they

@@ -36,6 +36,8 @@ cudaError_t alloc(flosic_ctx* c, T** p, long long n) {
 void release(flosic_ctx* c) {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
+    for (cudaEvent_t e : c->ov_ev) cudaEventDestroy(e);
+    c->ov_ev.clear();
     for (void* p : c->allocations) cudaFree(p);
     c->allocations.clear();
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -51,6 +53,12 @@ int validate_options(const flosic_options& o, std::string& why) {
     else if (!(o.rho_min >= 0.0)) why = "rho_min must be >= 0";
     else if (!(o.illcond_tol >= 0.0) || !(o.illcond_tol < 1.0)) why = "illcond_tol must be in [0, 1)";
     else if (o.preconditioner != FLOSIC_PC_NONE && o.preconditioner != FLOSIC_PC_MG) why = "bad preconditioner";
+    else if (o.solver != FLOSIC_SOLVER_PCG && o.solver != FLOSIC_SOLVER_AAR) why = "bad solver";
+    else if (o.solver == FLOSIC_SOLVER_AAR && o.precision != FLOSIC_MIXED) why = "the AAR solver requires MIXED precision";
+    else if (o.solver == FLOSIC_SOLVER_AAR && (o.aar_m < 1 || o.aar_m > aar_max_m() || o.aar_p < 2 ||
+                                               !(o.aar_omega > 0.0 && o.aar_omega < 2.0) ||
+                                               !(o.aar_beta > 0.0 && o.aar_beta < 2.0)))
+        why = "AAR parameters out of range (1 <= m <= 8, p >= 2, 0 < omega, beta < 2)";
     else return 0;
     return 1;
 }
@@ -136,6 +144,17 @@ void prof_collect(flosic_ctx* c) {
     c->prof_used = 0;
 }
 
+void ov_collect(flosic_ctx* c) {
+    for (int k = 0; k < c->ov_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ov_ev[2 * k], c->ov_ev[2 * k + 1]) == cudaSuccess) {
+            c->ov_ms += ms;
+            ++c->ov_launches;
+        }
+    }
+    c->ov_used = 0;
+}
+
 void prof_begin(flosic_ctx* c, cudaStream_t s) {
     if (!c->profiling) return;
     if (2 * (c->prof_used + 1) > (int)c->prof_ev.size()) {   // pool full: wait and sum
@@ -170,6 +189,11 @@ int flosic_default_options(flosic_options* opt) {
     opt->rho_min = 1e-30;
     opt->illcond_tol = 1e-10;
     opt->preconditioner = FLOSIC_PC_MG;
+    opt->solver = FLOSIC_SOLVER_PCG;
+    opt->aar_omega = 0.6;
+    opt->aar_beta = 0.6;
+    opt->aar_m = 7;
+    opt->aar_p = 6;
     return FLOSIC_OK;
 }
 
@@ -277,6 +301,12 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.S, me); A(&w.Q, me); A(&w.C, me); A(&w.U, me); A(&w.lam, orb); A(&w.P, me);
     A(&w.vbar, me); A(&w.tmp, 4 * me); A(&w.E2, 2 * me);
     A(&w.mat_part, (long long)c->kparts * me);
+    if (o.solver == FLOSIC_SOLVER_AAR) {
+        float *fp = nullptr, *X = nullptr, *F = nullptr;
+        A(&fp, off); A(&X, (long long)o.aar_m * off); A(&F, (long long)o.aar_m * off);
+        w.aar_fprev = fp; w.aar_X = X; w.aar_F = F;
+        A(&w.aar_gamma, (long long)orb * aar_max_m());
+    }
     std::vector<long long> goff;
     if (o.precision == FLOSIC_MIXED) {
         A(&w.gram_part, gram_tc_part_elems(c, goff));
@@ -388,17 +418,16 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         A(&M.d_coarsest_level, c->nblk);
         if (e == cudaSuccess)
             e = cudaMemcpy(M.d_coarsest_level, coarsest.data(), sizeof(int) * c->nblk, cudaMemcpyHostToDevice);
-        if (M.enabled) {
-            if (o.precision == FLOSIC_FP64) {
-                A(&w.z64, off); A(&w.p64b, off);
-            } else {
-                A(&w.z32, off); A(&w.p32b, off);
-            }
+        if (o.precision == FLOSIC_FP64) {
+            if (M.enabled) { A(&w.z64, off); A(&w.p64b, off); }
+        } else if (M.enabled || o.solver == FLOSIC_SOLVER_AAR) {
+            A(&w.z32, off); A(&w.p32b, off);   // z32: the AAR's f = M r as well
         }
     }
     CgState& g = w.cg;
     A(&g.rr, orb); A(&g.pq, orb); A(&g.bb, orb); A(&g.thr, orb); A(&g.beta, orb); A(&g.rz, orb);
     const long long nparts = chunk > M.ntiles[0] ? chunk : M.ntiles[0];
+    if (o.solver == FLOSIC_SOLVER_AAR) A(&w.aar_part, aar_part_elems(M.ntiles[0]));
     A(&w.mom_part, 10 * nparts);
     A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
@@ -557,6 +586,11 @@ int flosic_profile(flosic_ctx* c, int enable) {
             int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
             if (rc) return rc;
         }
+        c->ov_ev.resize(2 * 64);
+        for (auto& e : c->ov_ev) {
+            int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
+            if (rc) return rc;
+        }
     }
     c->profiling = enable != 0;
     return FLOSIC_OK;
@@ -583,6 +617,24 @@ int flosic_profile_read(flosic_ctx* c, double* out, int reset) {
         c->launches = 0;
         rc = check_cuda(c, cudaMemset(c->ws.cg.prof_bytes, 0, sizeof(double)), "cudaMemset(prof_bytes)");
         if (rc) return rc;
+    }
+    return FLOSIC_OK;
+}
+
+int flosic_profile_read_overlap(flosic_ctx* c, double* out, int reset) {
+    if (!c || !out) return FLOSIC_ERR_ARG;
+    if (c->ov_used > 0) {
+        int rc = check_cuda(c, cudaEventSynchronize(c->ov_ev[2 * c->ov_used - 1]), "cudaEventSynchronize");
+        if (rc) return rc;
+        ov_collect(c);
+    }
+    out[0] = c->ov_ms;
+    out[1] = (double)c->ov_launches;
+    out[2] = c->ov_flops;
+    if (reset) {
+        c->ov_ms = 0.0;
+        c->ov_launches = 0;
+        c->ov_flops = 0.0;
     }
     return FLOSIC_OK;
 }

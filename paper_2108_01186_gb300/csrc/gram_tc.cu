@@ -278,11 +278,25 @@ void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
     const int nb = (nmax + 31) / 32;   // accumulator width for the widest block
     float* part = c->ws.gram_part;
     const long long* off = c->ws.gram_off;
+    flosic_ctx* cm = const_cast<flosic_ctx*>(c);
+    const bool timed = cm->profiling && !cm->ov_ev.empty();
+    if (timed) {
+        if (2 * (cm->ov_used + 1) > (int)cm->ov_ev.size()) {   // pool full: wait and sum
+            cudaEventSynchronize(cm->ov_ev[2 * cm->ov_used - 1]);
+            ov_collect(cm);
+        }
+        cudaEventRecord(cm->ov_ev[2 * cm->ov_used], s);
+        for (const auto& b : c->blk) cm->ov_flops += 2.0 * b.N * b.N * (double)b.G;
+    }
     if (nb <= 1) k_gram_tc<1><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
     else if (nb == 2) k_gram_tc<2><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
     else if (nb == 3) k_gram_tc<3><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
     else k_gram_tc<4><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    note_launch((flosic_ctx*)c);
+    note_launch(cm);
+    if (timed) {
+        cudaEventRecord(cm->ov_ev[2 * cm->ov_used + 1], s);
+        ++cm->ov_used;
+    }
     const dim3 g2((unsigned)((nmax * nmax + 255) / 256), (unsigned)c->nblk);
     k_gram_sum<<<g2, 256, 0, s>>>(c->d_blk, part, off, c->ws.M);
     note_launch((flosic_ctx*)c);

@@ -107,6 +107,10 @@ struct Workspace {
     long long mat_elems;   // sum N*N
     double* mat_part;      // partial N x N sums [kparts][sum N*N]
     float* gram_part;      // mixed path: tensor-core Gram partials [per block: chunks][N][N]
+    // AAR inner solver (mixed path): previous f, history rings of m slots
+    // (dx, df), per-tile dot partials, per-orbital weights
+    float *aar_fprev, *aar_X, *aar_F;
+    double *aar_part, *aar_gamma;
     long long* gram_off;   // [nblk] offsets into gram_part
     double* mom;           // [norb][10]
     double* mom_part;      // [nchunk_total][10]
@@ -171,6 +175,11 @@ struct flosic_ctx {
     int prof_used = 0;                      // pairs recorded and not yet summed
     double prof_ms = 0.0;                   // summed duration of timed launches
     long long prof_launches = 0;
+    // the same for the tensor-core overlap launches (mixed path)
+    std::vector<cudaEvent_t> ov_ev;
+    int ov_used = 0;
+    double ov_ms = 0.0, ov_flops = 0.0;   // timed duration, algorithmic flops (2 N^2 G per block)
+    long long ov_launches = 0;
     std::vector<void*> allocations;
 };
 
@@ -201,6 +210,12 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
                           cudaStream_t s);
 
+// Alternating Anderson-Richardson inner solver (mixed precision)
+template <class T>
+void launch_aar_step(flosic_ctx* c, T* x, T* r, T* f, int k, bool anderson, cudaStream_t s,
+                     void (*precondition)(flosic_ctx*, T*, T*, cudaStream_t));
+long long aar_part_elems(long long ntiles0);
+int aar_max_m();
 // tensor-core overlap Gram (mixed precision)
 long long gram_tc_part_elems(const flosic_ctx* c, std::vector<long long>& off);
 cudaError_t setup_gram_tc();
@@ -213,6 +228,8 @@ template <class T>
 void launch_vcycle(const flosic_ctx* c, const MgPtrs<T>& mp, const int* active, cudaStream_t s);
 template <class T>
 void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s);
+template <class T>
+void launch_residual12_aar(flosic_ctx* c, const T* dx, T* r, cudaStream_t s);
 size_t apply12_tma_smem(size_t elem);
 const void* apply12_tma_symbol(bool f32);
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
@@ -234,6 +251,7 @@ inline void note_launch(const flosic_ctx* c) { ++c->launches; }
 void prof_begin(flosic_ctx* c, cudaStream_t s);
 void prof_end(flosic_ctx* c, cudaStream_t s);
 void prof_collect(flosic_ctx* c);   // after a stream sync: sum recorded pairs
+void ov_collect(flosic_ctx* c);     // the same for the overlap timer
 
 
 }  // namespace flosic

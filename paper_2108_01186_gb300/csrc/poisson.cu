@@ -550,6 +550,27 @@ static int pcg_mg(flosic_ctx* c, T* x, T* r, T* z, T* p, T* tbuf, T* q, int set_
     return FLOSIC_OK;
 }
 
+// The multigrid preconditioner of the AAR steps: f = M r.
+static void aar_vcycle(flosic_ctx* c, float* r, float* f, cudaStream_t s) {
+    launch_vcycle<float>(c, mg_ptrs<float>(c, r, f, c->ws.p32b), c->ws.cg.active, s);
+}
+
+// Float32 AAR on A d = r32 for the active orbitals (d32 = 0, r32 = the
+// starting residual, thr/active/n_active set by the refinement round).
+static int aar_inner(flosic_ctx* c, cudaStream_t s) {
+    Workspace& w = c->ws;
+    const int p = c->opt.aar_p;
+    for (int k = 0; k < c->opt.max_iter; ++k) {
+        if (k % 4 == 0) {
+            const int na = read_count(c, w.cg.n_active, s);
+            if (na < 0) return FLOSIC_ERR_CUDA;
+            if (na == 0) break;
+        }
+        launch_aar_step<float>(c, w.d32, w.r32, w.z32, k, k >= 1 && (k + 1) % p == 0, s, aar_vcycle);
+    }
+    return FLOSIC_OK;
+}
+
 // Solves A V = b for every orbital (b from launch_rhs, ||b||^2 in cg.bb).
 // Returns a flosic status; iteration counts and convergence flags stay in the
 // CG state (copied out by finish_poisson).
@@ -609,7 +630,10 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
-            if (mg) {
+            if (c->opt.solver == FLOSIC_SOLVER_AAR) {
+                int rc = aar_inner(c, s);
+                if (rc) return rc;
+            } else if (mg) {
                 int rc = pcg_mg<float>(c, w.d32, w.r32, w.z32, w.p32, w.p32b, w.q32, 0, s);
                 if (rc) return rc;
             } else {

@@ -452,6 +452,59 @@ __global__ void __launch_bounds__(256) k_residual12(const BlkDesc* __restrict__ 
     }
 }
 
+// The residual of an Alternating Anderson-Richardson step, updated with the
+// last step dx: r -= A dx with one staged sweep of dx, rr = r.r per orbital.
+// (Recomputing b - A x in float32 would stall near eps times the condition
+// number of A; the update carries the rounding of dx only, as CG's
+// recursive residual does, and the float-float refinement around the solve
+// recomputes the true residual.)  The last tile of an orbital counts the
+// step and applies the stop tests (target thr, max_iter, non-finite).
+// Reads dx and r, writes r.
+template <class T>
+__global__ void __launch_bounds__(256) k_residual12_aar(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                        const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                        const T* __restrict__ dx, T* __restrict__ r, int max_iter,
+                                                        CgState st) {
+    __shared__ T plane[kPY][kPX];
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.active[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    SrcPlain<T> src{dx};
+    const T ih2 = (T)(1.0 / (D.h * D.h));
+    T rr = T(0);
+    sweep12<T>(D, P, src, ih2, [&](long long g, int, T, T adx) {
+        const T rv = r[g] - adx;
+        r[g] = rv;
+        rr += rv * rv;
+    }, plane);
+    const int o = P.o;
+    if (tile_arrive(rr, st.part, blockIdx.x, st.count + o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[o] = 0;
+            st.rr[o] = sum;
+            const int it = ++st.iters[o];
+            if (!(sum > st.thr[o]) || it >= max_iter || !isfinite(sum)) {
+                st.active[o] = 0;
+                atomicSub(st.n_active, 1);
+            }
+            atomicAdd(st.prof_bytes, (double)D.G * sizeof(T) * 3);
+        }
+    }
+}
+
+template <class T>
+void launch_residual12_aar(flosic_ctx* c, const T* dx, T* r, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    prof_begin(c, s);
+    k_residual12_aar<T><<<(unsigned)M.ntiles[0], dim3(kTileX, kTileY / 2), 0, s>>>(
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, dx, r, c->opt.max_iter, c->ws.cg);
+    note_launch(c);
+    prof_end(c, s);
+}
+template void launch_residual12_aar<float>(flosic_ctx*, const float*, float*, cudaStream_t);
+
 template <class T>
 void launch_apply12_pcg(flosic_ctx* c, const T* z, T* p, T* q, cudaStream_t s) {
     const Multigrid& M = c->mg;

@@ -18,6 +18,7 @@ FP64, MIXED = 0, 1
 GRAD_INTERP, GRAD_PAPER = 0, 1
 ADJ_REUSE_V, ADJ_EXACT = 0, 1
 PC_NONE, PC_MG = 0, 1
+SOLVER_PCG, SOLVER_AAR = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "ARG", 2: "CUDA", 3: "ILLCOND", 4: "NOCONV", 5: "NONFINITE"}
 
@@ -25,7 +26,7 @@ ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "f
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
                  "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error",
-                 "flosic_hamiltonian_apply")
+                 "flosic_hamiltonian_apply", "flosic_profile_read_overlap")
 
 
 class FlosicError(RuntimeError):
@@ -44,7 +45,9 @@ class FlosicOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cg_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("fod_grad_mode", ctypes.c_int), ("adjoint_mode", ctypes.c_int),
                 ("rho_min", ctypes.c_double), ("illcond_tol", ctypes.c_double),
-                ("preconditioner", ctypes.c_int)]
+                ("preconditioner", ctypes.c_int), ("solver", ctypes.c_int),
+                ("aar_omega", ctypes.c_double), ("aar_beta", ctypes.c_double),
+                ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int)]
 
 
 _lib = None
@@ -72,6 +75,7 @@ def load_library(path=LIB_PATH):
     L.flosic_hamiltonian_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
+    L.flosic_profile_read_overlap.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
     L.flosic_orbital_poisson_noalloc.argtypes = [i, i, i, d, ctypes.POINTER(d), i, vp, vp, d, i, vp, vp, vp]
     L.flosic_noalloc_last_error.argtypes = []
     L.flosic_noalloc_last_error.restype = ctypes.c_char_p
@@ -224,6 +228,13 @@ class Context:
         out = (ctypes.c_double * 4)()
         self._check(self._L.flosic_profile_read(self._h, out, int(reset)))
         return dict(kernel_ms=out[0], kernel_launches=int(out[1]), launches=int(out[2]), kernel_bytes=out[3])
+
+    def profile_read_overlap(self, reset=True):
+        """Timed launches of the mixed path's tensor-core overlap kernel:
+        summed ms, launch count and algorithmic flops (2 N^2 G per block)."""
+        out = (ctypes.c_double * 3)()
+        self._check(self._L.flosic_profile_read_overlap(self._h, out, int(reset)))
+        return dict(kernel_ms=out[0], kernel_launches=int(out[1]), flops=out[2])
 
     def forward(self, psi, fods, scale=1.0, V0=None):
         phi, S, Q = self.build_flos(psi, fods)

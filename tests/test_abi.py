@@ -40,6 +40,7 @@ def test_default_options(lib):
     o = F.FlosicOptions()
     assert lib.flosic_default_options(ctypes.byref(o)) == 0
     assert o.precision == F.MIXED and o.cg_tol == 1e-10 and o.preconditioner == F.PC_MG
+    assert o.solver == F.SOLVER_PCG and (o.aar_omega, o.aar_beta, o.aar_m, o.aar_p) == (0.6, 0.6, 7, 6)
     assert lib.flosic_default_options(None) == F.FLOSIC_ERR_ARG
 
 
@@ -74,6 +75,20 @@ def test_create_rejects_bad_options(lib):
     assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
     o = F.default_options(precision=7)
     assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+
+
+@pytest.mark.parametrize("bad", [dict(solver=2), dict(solver=1, precision=0), dict(solver=1, aar_m=0),
+                                 dict(solver=1, aar_m=9), dict(solver=1, aar_p=1), dict(solver=1, aar_omega=0.0),
+                                 dict(solver=1, aar_beta=2.0)])
+def test_create_rejects_bad_aar_options(lib, bad):
+    # validated before any device work: the AAR solver runs only as the
+    # float32 inner solver of the mixed path, history 1..8, p >= 2
+    from paper_2108_01186_gb300 import flosic as F
+    o = F.default_options(**bad)
+    h = ctypes.c_void_p()
+    s = _sys()
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+    assert not h.value
 
 
 def test_too_many_orbitals_rejected(lib):
