@@ -22,6 +22,15 @@ Steps and the passages they follow:
   dE_SIC/dpsi on the grid.
 * ``pederson_fod_gradient``: the same FOD gradient by Eq. 9, with
   d phi/d a from Eqs. 10-11 and a forward derivative of S^{-1/2}.
+
+Extended systems (``bc`` argument; Sec. II.A: periodic conditions along
+extended directions, Dirichlet values from a dipole correction for surfaces):
+``"isolated"`` (default; zero outside, multipole Dirichlet values),
+``"periodic"`` (every direction periodic; the orbital density is neutralised
+by a uniform background and V has zero mean), ``"slab"`` (periodic along x
+and y; along z the dipole-corrected planar potential of ``slab_bc_rhs``).
+Along a periodic direction the stencil, the interpolation nodes and the FOD
+coordinates wrap around the box.
 """
 import ctypes
 import os
@@ -34,7 +43,11 @@ __all__ = [
     "bc_rhs_adjoint", "cg_zero_bc", "poisson", "interp", "interp_scatter",
     "grad_central", "lsda_pol", "pw92_ferro", "build_flos", "sic_forward",
     "sic_backward", "pederson_fod_gradient", "max_threads", "eigh_sym", "hamiltonian_apply",
+    "BC_MASK", "slab_bc_rhs", "slab_moments",
 ]
+
+# bit d set = periodic along direction d (x = bit 0)
+BC_MASK = {"isolated": 0, "periodic": 7, "slab": 3}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "flosic_oracle.c")
@@ -63,6 +76,11 @@ def lib():
         sig = {
             "orc_fd_weights": (None, [i, _D]),
             "orc_laplacian": (None, [i, i, i, d, _D, _D]),
+            "orc_laplacian_bc": (None, [i, i, i, d, i, _D, _D]),
+            "orc_cg_batch_bc": (None, [i, i, i, i, d, i, _D, _D, d, i, _I]),
+            "orc_slab_bc_rhs": (None, [i, i, i, d, _D, d, d, _D]),
+            "orc_interp_bc": (None, [i, i, i, d, _D, i, i, _D, _D, _D, _D]),
+            "orc_interp_scatter_bc": (None, [i, i, i, d, _D, i, _D, d, _D]),
             "orc_multipole_moments": (None, [i, i, i, d, _D, _D, _D]),
             "orc_multipole_value": (d, [_D, _D]),
             "orc_bc_rhs": (None, [i, i, i, d, _D, _D, _D]),
@@ -112,26 +130,27 @@ def fd_weights(M=6):
     return w
 
 
-def laplacian(u, grid):
+def laplacian(u, grid, bc="isolated"):
     nx, ny, nz, h, _ = _grid(grid)
     u = _f64(u)
     out = np.empty_like(u)
-    lib().orc_laplacian(nx, ny, nz, h, _p(u), _p(out))
+    lib().orc_laplacian_bc(nx, ny, nz, h, BC_MASK[bc], _p(u), _p(out))
     return out
 
 
-def hamiltonian_apply(psi, grid, vloc=None, vavg=None):
+def hamiltonian_apply(psi, grid, vloc=None, vavg=None, bc="isolated"):
     """The SC_AvgSIC Kohn-Sham Hamiltonian of one spin (Sec. II.C, Eq. 13) on
     the orbitals psi [N, G]: H psi_a = -1/2 Delta_h psi_a + (v_loc + V_avg)
-    psi_a, orbitals zero outside the box; v_loc stands for the other local
-    terms of Eq. 13 (external, Hartree, exchange-correlation)."""
+    psi_a, orbitals zero outside the box (periodic along the periodic
+    directions of bc); v_loc stands for the other local terms of Eq. 13
+    (external, Hartree, exchange-correlation)."""
     psi = np.atleast_2d(_f64(psi))
     v = np.zeros(psi.shape[1])
     if vloc is not None:
         v = v + _f64(vloc)
     if vavg is not None:
         v = v + _f64(vavg)
-    return np.stack([-0.5 * laplacian(p, grid) + v * p for p in psi])
+    return np.stack([-0.5 * laplacian(p, grid, bc) + v * p for p in psi])
 
 
 def multipole_moments(rho, grid):
@@ -171,37 +190,75 @@ def cg_zero_bc(b, grid, tol=1e-12, max_iter=100000):
     return x, it
 
 
-def poisson(rho, grid, tol=1e-12, max_iter=100000, V0=None):
-    """Per-orbital Poisson solves: -Delta_h V_i = 4 pi rho_i, multipole (l<=2)
-    Dirichlet values on the 6-layer ghost shell (Sec. II.A).  rho is [n, G].
-    Returns (V [n, G], iterations [n]); iterations -1 = not converged."""
+def slab_moments(rho, grid):
+    """Charge Q = dV sum rho and dipole p_z = dV sum rho (z - c_z) of each row
+    of rho about the box centre c_z (the two numbers the slab boundary needs)."""
+    nx, ny, nz, h, origin = _grid(grid)
+    rho = _f64(np.atleast_2d(rho)).reshape(-1, nz, ny, nx)
+    dV = h ** 3
+    Z = origin[2] + h * np.arange(nz) - (origin[2] + 0.5 * h * (nz - 1))
+    planes = rho.sum(axis=(2, 3))
+    return dV * planes.sum(axis=1), dV * planes @ Z
+
+
+def slab_bc_rhs(Q, pz, grid):
+    """Boundary term of the slab problem for charge Q and dipole p_z: the
+    ghost planes along z hold V_b(z) = -(2 pi/A)(Q |z - c_z| - sgn(z - c_z) p_z),
+    A = nx ny h^2 (Sec. II.A: dipole-corrected Dirichlet values)."""
+    nx, ny, nz, h, origin = _grid(grid)
+    out = np.zeros(nx * ny * nz)
+    lib().orc_slab_bc_rhs(nx, ny, nz, h, _p(origin), float(Q), float(pz), _p(out))
+    return out
+
+
+def poisson(rho, grid, tol=1e-12, max_iter=100000, V0=None, bc="isolated"):
+    """Per-orbital Poisson solves -Delta_h V_i = 4 pi rho_i (Sec. II.A); rho
+    is [n, G].  Boundary by bc: "isolated" = multipole (l <= 2) Dirichlet
+    values on the 6-layer ghost shell; "periodic" = -Delta_h V = 4 pi (rho -
+    mean rho) with zero-mean V; "slab" = periodic along x, y and the
+    dipole-corrected ghost planes of slab_bc_rhs along z.  Returns
+    (V [n, G], iterations [n]); iterations -1 = not converged."""
     nx, ny, nz, h, origin = _grid(grid)
     rho = _f64(np.atleast_2d(rho))
     V = np.zeros_like(rho) if V0 is None else _f64(np.array(V0, dtype=np.float64).reshape(rho.shape))
     it = np.zeros(rho.shape[0], dtype=np.int32)
-    lib().orc_poisson_batch(rho.shape[0], nx, ny, nz, h, _p(origin), _p(rho), _p(V),
-                            tol, max_iter, it.ctypes.data_as(_I))
+    if bc == "isolated":
+        lib().orc_poisson_batch(rho.shape[0], nx, ny, nz, h, _p(origin), _p(rho), _p(V),
+                                tol, max_iter, it.ctypes.data_as(_I))
+        return V, it
+    if bc == "periodic":
+        b = 4.0 * np.pi * (rho - rho.mean(axis=1, keepdims=True))
+        if V0 is not None:
+            V -= V.mean(axis=1, keepdims=True)
+    elif bc == "slab":
+        Q, pz = slab_moments(rho, grid)
+        b = 4.0 * np.pi * rho + np.stack([slab_bc_rhs(Q[i], pz[i], grid) for i in range(rho.shape[0])])
+    else:
+        raise ValueError("unknown boundary %r" % (bc,))
+    b = _f64(b)
+    lib().orc_cg_batch_bc(rho.shape[0], nx, ny, nz, h, BC_MASK[bc], _p(b), _p(V), tol, max_iter,
+                          it.ctypes.data_as(_I))
     return V, it
 
 
-def interp(u, grid, a):
+def interp(u, grid, a, bc="isolated"):
     """Tricubic Lagrange interpolation (Sec. II.B, 'cubic interpolation') of
     the rows of u at point a: values [nf] and exact interpolant gradients
-    [nf, 3]."""
+    [nf, 3].  Nodes wrap along the periodic directions of bc."""
     nx, ny, nz, h, origin = _grid(grid)
     u = _f64(np.atleast_2d(u))
     nf = u.shape[0]
     val = np.zeros(nf)
     grad = np.zeros((nf, 3))
-    lib().orc_interp(nx, ny, nz, h, _p(origin), nf, _p(u), _p(_f64(a)), _p(val), _p(grad))
+    lib().orc_interp_bc(nx, ny, nz, h, _p(origin), BC_MASK[bc], nf, _p(u), _p(_f64(a)), _p(val), _p(grad))
     return val, grad
 
 
-def interp_scatter(grid, a, coef, out):
+def interp_scatter(grid, a, coef, out, bc="isolated"):
     """out += coef * (interpolation weights of point a): adjoint of interp."""
     nx, ny, nz, h, origin = _grid(grid)
     assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
-    lib().orc_interp_scatter(nx, ny, nz, h, _p(origin), _p(_f64(a)), float(coef), _p(out))
+    lib().orc_interp_scatter_bc(nx, ny, nz, h, _p(origin), BC_MASK[bc], _p(_f64(a)), float(coef), _p(out))
 
 
 def grad_central(u, grid):
@@ -239,16 +296,16 @@ def eigh_sym(S):
     return lam, U
 
 
-def _interp_all(psi, grid, fods):
+def _interp_all(psi, grid, fods, bc="isolated"):
     N = fods.shape[0]
     vals = np.zeros((N, psi.shape[0]))       # vals[i, a] = psi_a(a_i)
     grads = np.zeros((N, psi.shape[0], 3))   # grads[i, a] = grad psi_a(a_i)
     for i in range(N):
-        vals[i], grads[i] = interp(psi, grid, fods[i])
+        vals[i], grads[i] = interp(psi, grid, fods[i], bc)
     return vals, grads
 
 
-def build_flos(psi, fods, grid, illcond=1e-10):
+def build_flos(psi, fods, grid, illcond=1e-10, bc="isolated"):
     """One spin block: psi [N, G] (KS orbitals), fods [N, 3].
 
     rho(a_i) = sum_a psi_a(a_i)^2 (unit occupations, Sec. II.B);
@@ -259,7 +316,7 @@ def build_flos(psi, fods, grid, illcond=1e-10):
     fods = _f64(fods).reshape(-1, 3)
     h = float(grid[3])
     dV = h ** 3
-    vals, grads = _interp_all(psi, grid, fods)
+    vals, grads = _interp_all(psi, grid, fods, bc)
     rho_a = np.sum(vals ** 2, axis=1)
     T = vals / np.sqrt(rho_a)[:, None]
     F = T @ psi
@@ -277,7 +334,7 @@ def build_flos(psi, fods, grid, illcond=1e-10):
 # ---------------------------------------------------------------------------
 
 def sic_forward(psi_blocks, fod_blocks, grid, scale=1.0, rho_min=1e-30, tol=1e-12,
-                max_iter=100000, illcond=1e-10, V0_blocks=None):
+                max_iter=100000, illcond=1e-10, V0_blocks=None, bc="isolated"):
     """One system.  psi_blocks / fod_blocks: one [N, G] / [N, 3] array per
     spin.  Returns a dict with per-spin lists and the scalar E_sic."""
     h = float(grid[3])
@@ -285,10 +342,10 @@ def sic_forward(psi_blocks, fod_blocks, grid, scale=1.0, rho_min=1e-30, tol=1e-1
     out = dict(blocks=[], E_sic=0.0)
     for s, (psi, fods) in enumerate(zip(psi_blocks, fod_blocks)):
         psi = _f64(psi)
-        fl = build_flos(psi, fods, grid, illcond)
+        fl = build_flos(psi, fods, grid, illcond, bc)
         phi = fl["phi"]
         rho = phi ** 2                                  # orbital densities
-        V, it = poisson(rho, grid, tol, max_iter, None if V0_blocks is None else V0_blocks[s])
+        V, it = poisson(rho, grid, tol, max_iter, None if V0_blocks is None else V0_blocks[s], bc)
         eps, vxc = lsda_pol(rho, rho_min)
         U = 0.5 * dV * np.sum(rho * V, axis=1)         # self-Hartree U[rho_i]
         Exc = dV * np.sum(rho * eps, axis=1)           # E_xc[rho_i, 0]
@@ -323,7 +380,7 @@ def _exact_hartree_gradient(blk, grid, tol, max_iter):
 
 
 def sic_backward(fwd, grid, gE=1.0, adjoint="reuse_v", grad_mode="interp_exact",
-                 tol=1e-12, max_iter=100000):
+                 tol=1e-12, max_iter=100000, bc="isolated"):
     """Reverse mode of sic_forward for E_sic (times the upstream gE).
 
     adjoint='reuse_v': dU_i/drho_i = dV V_i (the potential itself);
@@ -331,7 +388,11 @@ def sic_backward(fwd, grid, gE=1.0, adjoint="reuse_v", grad_mode="interp_exact",
     grad_mode='interp_exact': grad psi(a) is the derivative of the cubic
     interpolant; 'paper_central': central-difference grid gradient then the
     same cubic interpolation (Sec. II.B).
+    Extended systems (bc != "isolated") take adjoint='reuse_v' and
+    grad_mode='interp_exact' only.
     Returns (dE_dpsi per spin [N, G], dE_dfod per spin [N, 3])."""
+    if bc != "isolated" and (adjoint != "reuse_v" or grad_mode != "interp_exact"):
+        raise ValueError("extended systems: adjoint='reuse_v' and grad_mode='interp_exact' only")
     h = float(grid[3])
     dV = h ** 3
     dpsi, dfod = [], []
@@ -356,7 +417,7 @@ def sic_backward(fwd, grid, gE=1.0, adjoint="reuse_v", grad_mode="interp_exact",
             cgrad = np.stack([grad_central(psi[a], grid) for a in range(psi.shape[0])])  # [Na,3,G]
         for i in range(N):
             for a in range(psi.shape[0]):
-                interp_scatter(grid, fods[i], vb[i, a], psib[a])
+                interp_scatter(grid, fods[i], vb[i, a], psib[a], bc)
             if grad_mode == "interp_exact":
                 force[i] = vb[i] @ grads[i]
             else:

@@ -19,7 +19,10 @@
  *     point outside the interior (zero Dirichlet, Sec. II.A, M-SPARC);
  *   - integrals are dV * sum_g with dV = h^3 (trapezoid rule on a uniform
  *     grid whose end values vanish, Sec. II.A);
- *   - the multipole centre c is the box centre origin + h*(n-1)/2.
+ *   - the multipole centre c is the box centre origin + h*(n-1)/2;
+ *   - extended systems (the *_bc variants): a mask per, bit d set = periodic
+ *     along direction d (x = bit 0), replaces the zero outside values along
+ *     those directions.
  */
 #include <math.h>
 #include <stdint.h>
@@ -61,8 +64,11 @@ void orc_fd_weights(int M, double* w) {
 /* 3-D Laplacian Delta_h u at every interior point, with u = 0 outside
  * the interior.  out[g] = (1/h^2) sum_d [w_0 u_g + sum_k w_k (u_{g+k e_d} +
  * u_{g-k e_d})].  Plain loop with a bounds test on every tap. */
-void orc_laplacian(int nx, int ny, int nz, double h, const double* u,
-                   double* out) {
+/* Delta_h u.  per: bit d set = periodic along direction d (taps wrap
+ * around the box, Sec. II.A's conditions for extended directions); clear =
+ * zero outside the interior. */
+void orc_laplacian_bc(int nx, int ny, int nz, double h, int per, const double* u,
+                      double* out) {
     double w[ORC_M + 1];
     orc_fd_weights(ORC_M, w);
     const double ih2 = 1.0 / (h * h);
@@ -78,12 +84,21 @@ void orc_laplacian(int nx, int ny, int nz, double h, const double* u,
                         for (int s = -1; s <= 1; s += 2) {
                             int q[3] = {p[0], p[1], p[2]};
                             q[d] += s * m;
-                            if (q[d] < 0 || q[d] >= n[d]) continue;
+                            if (q[d] < 0 || q[d] >= n[d]) {
+                                if (!((per >> d) & 1)) continue;
+                                q[d] = ((q[d] % n[d]) + n[d]) % n[d];
+                            }
                             int64_t gq = ((int64_t)q[2] * ny + q[1]) * nx + q[0];
                             acc += w[m] * u[gq];
                         }
                 out[g] = acc * ih2;
             }
+}
+
+/* Delta_h u with zero values outside the interior (isolated systems). */
+void orc_laplacian(int nx, int ny, int nz, double h, const double* u,
+                   double* out) {
+    orc_laplacian_bc(nx, ny, nz, h, 0, u, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -236,17 +251,21 @@ static double orc_dot(int64_t n, const double* a, const double* b) {
     return s;
 }
 
-/* Plain (unpreconditioned) conjugate gradients on A x = b, A = -Delta_h with
- * zero ghosts (symmetric positive definite).  x holds the start vector on
- * entry and the solution on exit.  Stops when ||r|| <= tol ||b||.  Returns
- * the iteration count, or -1 if max_iter was reached first. */
-int orc_cg(int nx, int ny, int nz, double h, const double* b, double* x,
-           double tol, int max_iter) {
+/* Plain (unpreconditioned) conjugate gradients on A x = b, A = -Delta_h
+ * with the boundary mask per of orc_laplacian_bc (zero ghosts along the
+ * other directions).  A is symmetric positive definite, or, when every
+ * direction is periodic, semidefinite with the constants as null space; b
+ * must then have zero sum, and from a zero-sum start every iterate keeps a
+ * zero sum (the minimum-norm solution).  x holds the start vector on entry
+ * and the solution on exit.  Stops when ||r|| <= tol ||b||.  Returns the
+ * iteration count, or -1 if max_iter was reached first. */
+int orc_cg_bc(int nx, int ny, int nz, double h, int per, const double* b, double* x,
+              double tol, int max_iter) {
     int64_t G = (int64_t)nx * ny * nz;
     double* r = (double*)malloc(sizeof(double) * G);
     double* p = (double*)malloc(sizeof(double) * G);
     double* q = (double*)malloc(sizeof(double) * G);
-    orc_laplacian(nx, ny, nz, h, x, q);
+    orc_laplacian_bc(nx, ny, nz, h, per, x, q);
     for (int64_t g = 0; g < G; ++g) {
         r[g] = b[g] + q[g];  /* b - A x = b + Delta_h x */
         p[g] = r[g];
@@ -261,7 +280,7 @@ int orc_cg(int nx, int ny, int nz, double h, const double* b, double* x,
     while (result < 0) {
         if (rr <= tol * tol * bb) { result = it; break; }
         if (it >= max_iter) break;
-        orc_laplacian(nx, ny, nz, h, p, q);
+        orc_laplacian_bc(nx, ny, nz, h, per, p, q);
         for (int64_t g = 0; g < G; ++g) q[g] = -q[g];  /* q = A p */
         double alpha = rr / orc_dot(G, p, q);
         for (int64_t g = 0; g < G; ++g) {
@@ -278,6 +297,12 @@ int orc_cg(int nx, int ny, int nz, double h, const double* b, double* x,
     free(p);
     free(q);
     return result;
+}
+
+/* Conjugate gradients with zero ghosts in every direction. */
+int orc_cg(int nx, int ny, int nz, double h, const double* b, double* x,
+           double tol, int max_iter) {
+    return orc_cg_bc(nx, ny, nz, h, 0, b, x, tol, max_iter);
 }
 
 /* One orbital: solve -Delta_h V = 4 pi rho with multipole (l <= 2) Dirichlet
@@ -318,6 +343,48 @@ void orc_cg_batch(int nrhs, int nx, int ny, int nz, double h, const double* b,
                           tol, max_iter);
 }
 
+/* Solves A x = b (A with boundary mask per) for many right-hand sides. */
+void orc_cg_batch_bc(int nrhs, int nx, int ny, int nz, double h, int per,
+                     const double* b, double* x, double tol, int max_iter,
+                     int* iters) {
+    int64_t G = (int64_t)nx * ny * nz;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int o = 0; o < nrhs; ++o)
+        iters[o] = orc_cg_bc(nx, ny, nz, h, per, b + (int64_t)o * G,
+                             x + (int64_t)o * G, tol, max_iter);
+}
+
+/* Slab (periodic along x and y, finite along z; Sec. II.A: Dirichlet values
+ * from a dipole correction for surfaces).  The ghost planes along z carry
+ * the potential of the planar average of rho, which depends on its charge Q
+ * and dipole p_z = sum rho (z - c_z) dV only:
+ *   V_b(z) = -(2 pi / A) (Q |z - c_z| - sgn(z - c_z) p_z),  A = nx ny h^2,
+ * i.e. the 1-D field of charged sheets, -2 pi |z - z'| / A per unit charge.
+ * Adds (1/h^2) sum over the z-taps of g that leave the box of w_m V_b to
+ * out[g] (points within 6 planes of a z face). */
+void orc_slab_bc_rhs(int nx, int ny, int nz, double h, const double* origin,
+                     double Q, double pz, double* out) {
+    double w[ORC_M + 1];
+    orc_fd_weights(ORC_M, w);
+    const double ih2 = 1.0 / (h * h);
+    const double area = (double)nx * ny * h * h;
+    const double cz = origin[2] + 0.5 * h * (nz - 1);
+    for (int k = 0; k < nz; ++k) {
+        double acc = 0.0;
+        for (int m = 1; m <= ORC_M; ++m)
+            for (int s = -1; s <= 1; s += 2) {
+                int q = k + s * m;
+                if (q >= 0 && q < nz) continue;
+                double Z = origin[2] + h * q - cz;
+                double sg = (Z > 0.0) ? 1.0 : -1.0;
+                acc += w[m] * (-2.0 * ORC_PI / area) * (Q * fabs(Z) - sg * pz);
+            }
+        if (acc == 0.0) continue;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) out[((int64_t)k * ny + j) * nx + i] += acc * ih2;
+    }
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -356,36 +423,50 @@ static void orc_lagrange4(double t, double* L, double* dL) {
     }
 }
 
-/* Locate the cell of coordinate u (grid units): i0 = floor(u), t = u - i0. */
-static void orc_cell(double u, int* i0, double* t) {
+/* Locate the cell of coordinate u (grid units): i0 = floor(u), t = u - i0.
+ * Along a periodic direction of n points u is first reduced to [0, n). */
+static void orc_cell(double u, int n, int periodic, int* i0, double* t) {
+    if (periodic) u -= n * floor(u / n);
     double f = floor(u);
     *i0 = (int)f;
     *t = u - f;
 }
 
+/* Node index q along a direction of n points: wrapped when periodic, else
+ * -1 when outside (the node counts as zero). */
+static int orc_node(int q, int n, int periodic) {
+    if (q >= 0 && q < n) return q;
+    if (!periodic) return -1;
+    return ((q % n) + n) % n;
+}
+
 /* Tricubic tensor-product Lagrange interpolant of nfield fields ([nfield][G])
  * at point a: val[f] and grad[f][3] (exact derivative of the interpolant, in
- * 1/bohr).  Nodes outside the interior count as zero. */
-void orc_interp(int nx, int ny, int nz, double h, const double* origin,
-                int nfield, const double* u, const double* a, double* val,
-                double* grad) {
+ * 1/bohr).  Along a direction whose bit of per is set the field is periodic
+ * (nodes wrap); along the others nodes outside the interior count as zero. */
+void orc_interp_bc(int nx, int ny, int nz, double h, const double* origin, int per,
+                   int nfield, const double* u, const double* a, double* val,
+                   double* grad) {
     int64_t G = (int64_t)nx * ny * nz;
     int i0[3];
     double t[3], L[3][4], dL[3][4];
+    const int n[3] = {nx, ny, nz};
     for (int d = 0; d < 3; ++d) {
-        orc_cell((a[d] - origin[d]) / h, &i0[d], &t[d]);
+        orc_cell((a[d] - origin[d]) / h, n[d], (per >> d) & 1, &i0[d], &t[d]);
         orc_lagrange4(t[d], L[d], dL[d]);
     }
-    const int n[3] = {nx, ny, nz};
     for (int f = 0; f < nfield; ++f) {
         double v = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
         for (int c = 0; c < 4; ++c)
             for (int b = 0; b < 4; ++b)
                 for (int e = 0; e < 4; ++e) {
                     int q[3] = {i0[0] - 1 + e, i0[1] - 1 + b, i0[2] - 1 + c};
-                    if (q[0] < 0 || q[0] >= n[0] || q[1] < 0 || q[1] >= n[1] ||
-                        q[2] < 0 || q[2] >= n[2])
-                        continue;
+                    int skip = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        q[d] = orc_node(q[d], n[d], (per >> d) & 1);
+                        if (q[d] < 0) skip = 1;
+                    }
+                    if (skip) continue;
                     double uv = u[(int64_t)f * G + ((int64_t)q[2] * ny + q[1]) * nx + q[0]];
                     v += L[0][e] * L[1][b] * L[2][c] * uv;
                     gx += dL[0][e] * L[1][b] * L[2][c] * uv;
@@ -401,27 +482,42 @@ void orc_interp(int nx, int ny, int nz, double h, const double* origin,
     }
 }
 
-/* Adjoint of orc_interp's value map for one field: out[node] += coef *
- * weight(node) over the 64 nodes of the cell of a (nodes outside skipped). */
-void orc_interp_scatter(int nx, int ny, int nz, double h, const double* origin,
-                        const double* a, double coef, double* out) {
+void orc_interp(int nx, int ny, int nz, double h, const double* origin,
+                int nfield, const double* u, const double* a, double* val,
+                double* grad) {
+    orc_interp_bc(nx, ny, nz, h, origin, 0, nfield, u, a, val, grad);
+}
+
+/* Adjoint of orc_interp_bc's value map for one field: out[node] += coef *
+ * weight(node) over the 64 nodes of the cell of a (wrapped along periodic
+ * directions, skipped outside along the others). */
+void orc_interp_scatter_bc(int nx, int ny, int nz, double h, const double* origin, int per,
+                           const double* a, double coef, double* out) {
     int i0[3];
     double t[3], L[3][4], dL[3][4];
+    const int n[3] = {nx, ny, nz};
     for (int d = 0; d < 3; ++d) {
-        orc_cell((a[d] - origin[d]) / h, &i0[d], &t[d]);
+        orc_cell((a[d] - origin[d]) / h, n[d], (per >> d) & 1, &i0[d], &t[d]);
         orc_lagrange4(t[d], L[d], dL[d]);
     }
-    const int n[3] = {nx, ny, nz};
     for (int c = 0; c < 4; ++c)
         for (int b = 0; b < 4; ++b)
             for (int e = 0; e < 4; ++e) {
                 int q[3] = {i0[0] - 1 + e, i0[1] - 1 + b, i0[2] - 1 + c};
-                if (q[0] < 0 || q[0] >= n[0] || q[1] < 0 || q[1] >= n[1] ||
-                    q[2] < 0 || q[2] >= n[2])
-                    continue;
+                int skip = 0;
+                for (int d = 0; d < 3; ++d) {
+                    q[d] = orc_node(q[d], n[d], (per >> d) & 1);
+                    if (q[d] < 0) skip = 1;
+                }
+                if (skip) continue;
                 out[((int64_t)q[2] * ny + q[1]) * nx + q[0]] +=
                     coef * L[0][e] * L[1][b] * L[2][c];
             }
+}
+
+void orc_interp_scatter(int nx, int ny, int nz, double h, const double* origin,
+                        const double* a, double coef, double* out) {
+    orc_interp_scatter_bc(nx, ny, nz, h, origin, 0, a, coef, out);
 }
 
 /* Grid gradient of the paper's force scheme (Sec. II.B): central difference

@@ -23,6 +23,9 @@ with its grid spacings and sp-shell orbitals):
   within 1e-3 h of a grid plane.
 * seeds: ``seed = 1000 * config + system``; spin s uses seed + 7919 s for its
   coefficients and FODs.
+* extended systems (``make_extended_system``): the same recipe on a periodic
+  cell; along periodic directions atoms lie anywhere in the cell and each
+  basis function is summed over its periodic images.
 """
 import math
 from dataclasses import dataclass, field
@@ -147,6 +150,68 @@ def make_system(n, h, natoms, norb, seed):
         Qm, _ = np.linalg.qr(M)
         psi = np.ascontiguousarray((Qm / math.sqrt(dV)).T)
         sysm.psi.append(psi)
+        sysm.fods.append(_draw_fods(srng, atoms, N, sysm.origin, h))
+    return sysm
+
+
+_PERIODIC_AXES = {"periodic": (0, 1, 2), "slab": (0, 1)}
+
+
+def make_extended_system(n, h, natoms, norb, seed, bc, images=2):
+    """One extended system on an n^3 cell (bc "periodic": all directions
+    periodic; "slab": x and y periodic, z finite).  As make_system, except:
+    along the periodic directions atoms are placed anywhere in the cell (at
+    least 2 bohr apart by the minimum-image distance) and every basis
+    function is summed over its periodic images up to ``images`` cells away,
+    so orbitals and FODs cross the cell faces; along a finite z atoms keep
+    make_system's padding."""
+    axes = _PERIODIC_AXES[bc]
+    rng = np.random.default_rng(seed)
+    L = n * h
+    pad = min(6.0, 0.4 * L)
+    lo = np.array([-L / 2 if d in axes else -L / 2 + pad for d in range(3)])
+    hi = np.array([L / 2 if d in axes else L / 2 - pad for d in range(3)])
+    atoms = []
+    tries = 0
+    while len(atoms) < natoms:
+        tries += 1
+        if tries > 200000:
+            raise ValueError("cannot place %d atoms in the cell" % natoms)
+        x = rng.uniform(lo, hi)
+        ok = True
+        for a in atoms:
+            d = x - a
+            for ax in axes:
+                d[ax] -= L * np.round(d[ax] / L)
+            if np.linalg.norm(d) < 2.0:
+                ok = False
+                break
+        if ok:
+            atoms.append(x)
+    atoms = np.array(atoms)
+    sysm = System(n=n, h=h, norb=list(norb), atoms=atoms)
+    x1d = sysm.origin[0] + h * np.arange(n)
+    dV = h ** 3
+    rng_img = range(-images, images + 1)
+    shifts = [np.array([i if 0 in axes else 0, j if 1 in axes else 0, k if 2 in axes else 0]) * L
+              for i in (rng_img if 0 in axes else (0,))
+              for j in (rng_img if 1 in axes else (0,))
+              for k in (rng_img if 2 in axes else (0,))]
+    for sp, N in enumerate(norb):
+        srng = np.random.default_rng(seed + 7919 * sp)
+        B = None
+        # the same exponents for every image of a function: draw them once
+        state = srng.bit_generator.state
+        for sh in shifts:
+            srng.bit_generator.state = state
+            Bi = _basis(atoms + sh, srng, x1d)
+            B = Bi if B is None else B + Bi
+        if N > B.shape[0]:
+            raise ValueError("more orbitals than basis functions")
+        C = srng.normal(size=(N, B.shape[0]))
+        M = (C @ B).T * math.sqrt(dV)
+        Qm, _ = np.linalg.qr(M)
+        sysm.psi.append(np.ascontiguousarray((Qm / math.sqrt(dV)).T))
         sysm.fods.append(_draw_fods(srng, atoms, N, sysm.origin, h))
     return sysm
 
