@@ -49,8 +49,9 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--preconditioner", default="mg", choices=["mg", "none"])
-    p.add_argument("--solver", default="pcg", choices=["pcg", "aar"],
-                   help="float32 inner solver of the mixed path: CG or Alternating Anderson-Richardson")
+    p.add_argument("--solver", default="pcg", choices=["pcg", "aar", "kron"],
+                   help="float32 inner solver of the mixed path: CG, Alternating Anderson-Richardson, "
+                        "or the Kronecker-product eigen-solver")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
@@ -242,7 +243,7 @@ def run_gpu(args):
     norb = sum(s.norb)
     prec = 1 if args.precision == "mixed" else 0
     pc = 1 if args.preconditioner == "mg" else 0
-    solver = 1 if args.solver == "aar" else 0
+    solver = {"pcg": 0, "aar": 1, "kron": 2}[args.solver]
     ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc, solver=solver)
     dev = torch.device("cuda", local)
     psi_h = torch.from_numpy(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
@@ -308,6 +309,18 @@ def run_gpu(args):
             "alg_bytes_per_launch": alg_bytes / launches,
             "avg_launch_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
             "share_of_step": round(prof["kernel_ms"] / ms, 4)}
+    if solver == 2:
+        # the Kronecker solver's six transform passes: float32 FMA-bound dense
+        # 1-D transforms, 2 n flops per point and pass (counted on the device);
+        # peak = 152 SMs x 128 FP32 lanes x 2 flops x the 2.07 GHz maximum clock
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        tfl = prof["kernel_bytes"] / (prof["kernel_ms"] / 1e3) / 1e12 if prof["kernel_ms"] > 0 else 0.0
+        roof = {"bound": "alu", "kernel": "k_kron_pass (6 passes per solve)", "achieved": round(tfl, 2),
+                "peak": round(fp32_peak, 1), "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "unit": "TFLOP/s", "frac": round(tfl / fp32_peak, 4), "traffic": None,
+                "alg_flops_per_solve": prof["kernel_bytes"] / launches,
+                "avg_solve_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
+                "share_of_step": round(prof["kernel_ms"] / ms, 4)}
     # the overlap Gram on the tensor cores (mixed path): algorithmic flops
     # 2 N^2 G per spin block against the measured dense bf16 peak, and its
     # float64 reads of psi (8 N G bytes per block) against the HBM peak

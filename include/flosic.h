@@ -58,9 +58,27 @@ enum { FLOSIC_GRAD_INTERP = 0, FLOSIC_GRAD_PAPER = 1 };     /* fod_grad_mode */
 enum { FLOSIC_ADJ_REUSE_V = 0, FLOSIC_ADJ_EXACT = 1 };      /* adjoint_mode */
 enum { FLOSIC_PC_NONE = 0, FLOSIC_PC_MG = 1 };              /* preconditioner */
 /* inner solver of the mixed path: conjugate gradients (this library's
- * default) or Alternating Anderson-Richardson (the iteration Sec. II.A's code
- * uses for its electrostatics) */
-enum { FLOSIC_SOLVER_PCG = 0, FLOSIC_SOLVER_AAR = 1 };
+ * default), Alternating Anderson-Richardson (the iteration Sec. II.A's code
+ * uses for its electrostatics), or the Kronecker-product solver: Sec. II.A
+ * writes the Laplacian as a Kronecker sum A = T_x (+) T_y (+) T_z of 1-D
+ * operators; with the eigen-decompositions T_d = Q_d L_d Q_d^T the inverse
+ * is (Q_x x Q_y x Q_z) (L_x (+) L_y (+) L_z)^{-1} (Q_x x Q_y x Q_z)^T,
+ * applied in float32 as six dense 1-D transforms per orbital (one "iteration"
+ * per application; the float-float refinement around it reaches cg_tol) */
+enum { FLOSIC_SOLVER_PCG = 0, FLOSIC_SOLVER_AAR = 1, FLOSIC_SOLVER_KRON = 2 };
+/* boundary conditions of the orbital Poisson problems (Sec. II.A: Dirichlet
+ * values from a multipole expansion for isolated systems, periodic conditions
+ * along extended directions, a dipole correction for surfaces):
+ *   ISOLATED: multipole (l <= 2) values on the ghost shell;
+ *   PERIODIC: every direction periodic; each orbital density is neutralised
+ *             by a uniform background and V_i has zero mean;
+ *   SLAB:     periodic along x and y; along z the ghost planes carry the
+ *             planar-average potential -(2 pi/A)(Q |z - c_z| - sgn(z - c_z) p_z)
+ *             of the orbital's charge Q and dipole p_z (A = nx ny h^2).
+ * Along periodic directions the stencil, the FOD interpolation nodes and the
+ * FOD coordinates wrap around the cell.  PERIODIC and SLAB require the KRON
+ * solver, ADJ_REUSE_V, GRAD_INTERP and periodic sides of at least 13. */
+enum { FLOSIC_BC_ISOLATED = 0, FLOSIC_BC_PERIODIC = 1, FLOSIC_BC_SLAB = 2 };
 
 typedef struct {
     int nx, ny, nz;       /* interior grid points per direction (>= 1) */
@@ -98,13 +116,15 @@ typedef struct {
     int aar_m;            /* AAR history length, 1..8 (default 7) */
     int aar_p;            /* AAR: every p-th step is an Anderson step, >= 2
                              (default 6) */
+    int boundary;         /* FLOSIC_BC_ISOLATED (default), _PERIODIC, _SLAB */
 } flosic_options;
 
 typedef struct flosic_ctx flosic_ctx;
 
 /* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
  * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG,
- * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6).
+ * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6), BC_ISOLATED.  The KRON solver
+ * requires MIXED and every side <= 216.
  * Returns FLOSIC_ERR_ARG if opt is NULL. */
 int flosic_default_options(flosic_options* opt);
 

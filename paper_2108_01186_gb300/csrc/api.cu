@@ -53,8 +53,16 @@ int validate_options(const flosic_options& o, std::string& why) {
     else if (!(o.rho_min >= 0.0)) why = "rho_min must be >= 0";
     else if (!(o.illcond_tol >= 0.0) || !(o.illcond_tol < 1.0)) why = "illcond_tol must be in [0, 1)";
     else if (o.preconditioner != FLOSIC_PC_NONE && o.preconditioner != FLOSIC_PC_MG) why = "bad preconditioner";
-    else if (o.solver != FLOSIC_SOLVER_PCG && o.solver != FLOSIC_SOLVER_AAR) why = "bad solver";
-    else if (o.solver == FLOSIC_SOLVER_AAR && o.precision != FLOSIC_MIXED) why = "the AAR solver requires MIXED precision";
+    else if (o.solver != FLOSIC_SOLVER_PCG && o.solver != FLOSIC_SOLVER_AAR && o.solver != FLOSIC_SOLVER_KRON)
+        why = "bad solver";
+    else if (o.solver != FLOSIC_SOLVER_PCG && o.precision != FLOSIC_MIXED)
+        why = "the AAR and KRON solvers require MIXED precision";
+    else if (o.boundary != FLOSIC_BC_ISOLATED && o.boundary != FLOSIC_BC_PERIODIC && o.boundary != FLOSIC_BC_SLAB)
+        why = "bad boundary";
+    else if (o.boundary != FLOSIC_BC_ISOLATED &&
+             (o.solver != FLOSIC_SOLVER_KRON || o.adjoint_mode != FLOSIC_ADJ_REUSE_V ||
+              o.fod_grad_mode != FLOSIC_GRAD_INTERP))
+        why = "PERIODIC and SLAB boundaries require the KRON solver, ADJ_REUSE_V and GRAD_INTERP";
     else if (o.solver == FLOSIC_SOLVER_AAR && (o.aar_m < 1 || o.aar_m > aar_max_m() || o.aar_p < 2 ||
                                                !(o.aar_omega > 0.0 && o.aar_omega < 2.0) ||
                                                !(o.aar_beta > 0.0 && o.aar_beta < 2.0)))
@@ -194,6 +202,7 @@ int flosic_default_options(flosic_options* opt) {
     opt->aar_beta = 0.6;
     opt->aar_m = 7;
     opt->aar_p = 6;
+    opt->boundary = FLOSIC_BC_ISOLATED;
     return FLOSIC_OK;
 }
 
@@ -229,6 +238,20 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                 g_create_error = buf;
                 return FLOSIC_ERR_ARG;
             }
+        const int per = boundary_mask(o.boundary);
+        const int n3[3] = {y.nx, y.ny, y.nz};
+        for (int d = 0; d < 3; ++d) {
+            if (((per >> d) & 1) && n3[d] < 2 * kHalf + 1) {
+                snprintf(buf, sizeof buf, "system %d: periodic sides need >= %d points", s, 2 * kHalf + 1);
+                g_create_error = buf;
+                return FLOSIC_ERR_ARG;
+            }
+            if (o.solver == FLOSIC_SOLVER_KRON && n3[d] > kron_max_n()) {
+                snprintf(buf, sizeof buf, "system %d: the KRON solver takes sides <= %d", s, kron_max_n());
+                g_create_error = buf;
+                return FLOSIC_ERR_ARG;
+            }
+        }
     }
     flosic_ctx* c = new (std::nothrow) flosic_ctx();
     if (!c) { g_create_error = "out of host memory"; return FLOSIC_ERR_ARG; }
@@ -252,6 +275,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
             b.G = (long long)y.nx * y.ny * y.nz;
             b.off = off; b.moff = moff; b.voff = voff; b.fod_off = fod; b.soff = soff;
             b.orb0 = orb; b.sys = s; b.spin = sp;
+            b.per = boundary_mask(o.boundary);
             b.nchunk = (int)((b.G + kChunk - 1) / kChunk);
             b.chunk0 = chunk;
             c->blk.push_back(b);
@@ -269,15 +293,17 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     c->vavg_elems = voff;
     c->mat_elems = moff;
     c->nchunk_total = chunk;
-    // points within 6 of a face, per block (they carry the multipole ghost taps)
+    // points within 6 of a non-periodic face, per block (they carry the
+    // ghost taps of the Dirichlet values)
     std::vector<int> bidx;
     for (BlkDesc& b : c->blk) {
         b.bnd0 = (long long)bidx.size();
+        const bool fx = !(b.per & 1), fy = !(b.per & 2), fz = !(b.per & 4);
         for (int z = 0; z < b.nz; ++z)
             for (int y = 0; y < b.ny; ++y)
                 for (int x = 0; x < b.nx; ++x)
-                    if (x < kHalf || x >= b.nx - kHalf || y < kHalf || y >= b.ny - kHalf || z < kHalf ||
-                        z >= b.nz - kHalf)
+                    if ((fx && (x < kHalf || x >= b.nx - kHalf)) || (fy && (y < kHalf || y >= b.ny - kHalf)) ||
+                        (fz && (z < kHalf || z >= b.nz - kHalf)))
                         bidx.push_back((z * b.ny + y) * b.nx + x);
         b.nbnd = (int)((long long)bidx.size() - b.bnd0);
     }
@@ -330,7 +356,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     // coarsen each block while every side is >= 6
     Multigrid& M = c->mg;
     {
-        const bool want_mg = (o.preconditioner == FLOSIC_PC_MG);
+        const bool want_mg = (o.preconditioner == FLOSIC_PC_MG && o.solver != FLOSIC_SOLVER_KRON);
         std::vector<int> nl(c->nblk);
         std::vector<int> coarsest(c->nblk);
         M.nlev = 0;
@@ -386,6 +412,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                         D.idd[m] = (float)(1.0 / dd);
                     }
                     D.tz = (l == 0) ? kTileZ : kTileZc;
+                    D.per = (l == 0) ? B.per : 0;
                     const int tx = (D.nx + kTileX - 1) / kTileX, ty = (D.ny + kTileY - 1) / kTileY,
                               tz = (D.nz + D.tz - 1) / D.tz;
                     D.ntile = tx * ty * tz;
@@ -432,6 +459,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
+    if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) e = setup_kron(c);   // sets the blocks' kq, kl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_orb_blk, c->h_orb_blk.data(), sizeof(int) * c->norb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);

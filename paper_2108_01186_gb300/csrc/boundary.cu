@@ -1,5 +1,7 @@
 // Right-hand side of the per-orbital Poisson problems (Sec. II.A: Dirichlet
-// values of the potential from a multipole expansion, isolated systems).
+// values of the potential from a multipole expansion, isolated systems; a
+// dipole correction for slabs; periodic cells take a neutralising
+// background instead of ghost values).
 //
 // With the ghost values known, -Delta_h V = 4 pi rho becomes
 //   A V = 4 pi rho + bc,  bc(g) = (1/h^2) sum_{taps of g outside} w_m V_b(R_tap),
@@ -40,11 +42,23 @@ __global__ void k_bnd_coef(const BlkDesc* __restrict__ blk, int b, const int* __
     const double ih2 = 1.0 / (B.h * B.h);
     double cf[10];
     for (int k = 0; k < 10; ++k) cf[k] = 0.0;
+    // slab: periodic along x and y, ghost planes along z hold
+    // V_b(Z) = -(2 pi/A)(Q |Z| - sgn(Z) p_z), linear in mom[0] = Q and mom[3] = p_z
+    const bool slab = (B.per == 3);
+    const double area = (double)B.nx * B.ny * B.h * B.h;
     for (int d = 0; d < 3; ++d)
         for (int m = 1; m <= kHalf; ++m)
             for (int sg = -1; sg <= 1; sg += 2) {
+                if ((B.per >> d) & 1) continue;   // periodic direction: the tap wraps, no ghost value
                 const int qd = p[d] + sg * m;
                 if (qd >= 0 && qd < n[d]) continue;
+                if (slab) {
+                    const double Z = B.oz + B.h * qd - B.cz;
+                    const double f = c_wb[m] * ih2 * (2.0 * kPi / area);
+                    cf[0] -= f * fabs(Z);
+                    cf[3] += f * (Z > 0.0 ? 1.0 : -1.0);
+                    continue;
+                }
                 int q[3] = {x, y, z};
                 q[d] = qd;
                 const double Rx = B.ox + B.h * q[0] - B.cx, Ry = B.oy + B.h * q[1] - B.cy,
@@ -262,6 +276,25 @@ __global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __re
     }
 }
 
+// Periodic cells: b -= 4 pi Q / (G dV), the uniform background that
+// neutralises each orbital density (b in pairs, Q = mom[0]).
+__global__ void __launch_bounds__(256) k_rhs_neutralise_ff(const BlkDesc* __restrict__ blk,
+                                                           const LvlDesc* __restrict__ L,
+                                                           const int4* __restrict__ tiles,
+                                                           const int* __restrict__ orb_blk,
+                                                           const double* __restrict__ mom, float2* __restrict__ b) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    const LvlDesc& D = L[P.b];
+    const BlkDesc& B = blk[P.b];
+    const ff sh = to_ff(d2ff(-4.0 * kPi * mom[P.o * 10] / ((double)B.G * B.dV)));   // once per CTA
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        for (int k = 0; k < n; ++k) {
+            const ff v = ff_add(to_ff(b[g + k]), sh);
+            b[g + k] = make_float2(v.h, v.l);
+        }
+    });
+}
+
 void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaStream_t s) {
     const Multigrid& M = c->mg;
     const bool ff = (c->opt.precision == FLOSIC_MIXED);
@@ -276,6 +309,12 @@ void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaS
                                                         with_bc ? 1 : 0, b, c->ws.mom_part, c->ws.mom, c->ws.cg.count);
     note_launch(c);
     if (!with_bc) return;
+    if (c->opt.boundary == FLOSIC_BC_PERIODIC) {   // mixed precision only (validated)
+        k_rhs_neutralise_ff<<<(unsigned)M.ntiles[0], tb, 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
+                                                                 c->ws.mom, reinterpret_cast<float2*>(b));
+        note_launch(c);
+        return;
+    }
     for (int k = 0; k < c->nblk; ++k) {
         const int nb = c->blk[k].nbnd;
         if (nb == 0) continue;

@@ -6,7 +6,8 @@
 // marches along z: per plane the tile plus its 6-point x/y halo is staged in
 // shared memory as pairs, each thread keeps the 13 z-values of its two
 // columns in registers, and the next plane's slots are loaded while the
-// current one is computed.  Values outside the interior read as zero.
+// current one is computed.  Values outside the interior read as zero, or,
+// along the periodic directions of the level (D.per), wrap around the box.
 #pragma once
 #include "internal.cuh"
 
@@ -49,15 +50,19 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
         soff[j] = -1;
         if (e < kPX * kPY) {
             const int yy = e / kPX, xx = e - yy * kPX;
-            const int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
+            int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
+            if (D.per & 1) px = wrap_coord(px, D.nx);
+            if (D.per & 2) py = wrap_coord(py, D.ny);
             if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
         }
     }
     const float2 zero2 = make_float2(0.f, 0.f);
     ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
 #pragma unroll
+    const bool pz = (D.per & 4) != 0;
     for (int j = 0; j < 2 * kHalf; ++j) {
-        const int zz = P.z0 - kHalf + j;
+        int zz = P.z0 - kHalf + j;
+        if (pz) zz = wrap_coord(zz, D.nz);
         const bool okz = zz >= 0 && zz < D.nz;
         q0[j] = to_ff((in0 && okz) ? load(P.base + zz * sz + c0) : zero2);
         q1[j] = to_ff((in1 && okz) ? load(P.base + zz * sz + c1) : zero2);
@@ -76,7 +81,8 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
             if (e < kPX * kPY) flat[e] = to_ff(pre[j]);
         }
         {
-            const int zz = z + kHalf;
+            int zz = z + kHalf;
+            if (pz) zz = wrap_coord(zz, D.nz);
             q0[2 * kHalf] = to_ff((in0 && zz < D.nz) ? load(P.base + zz * sz + c0) : zero2);
             q1[2 * kHalf] = to_ff((in1 && zz < D.nz) ? load(P.base + zz * sz + c1) : zero2);
         }

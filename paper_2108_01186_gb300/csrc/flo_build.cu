@@ -46,16 +46,28 @@ struct Cell {
     double L[3][4], dL[3][4];
 };
 
+// Along a periodic direction of n points the coordinate is first reduced
+// to [0, n) grid units (the FOD's image inside the cell).
 __device__ __forceinline__ Cell cell_of(const BlkDesc& B, const double* a) {
     Cell c;
     const double o[3] = {B.ox, B.oy, B.oz};
+    const int n[3] = {B.nx, B.ny, B.nz};
     for (int d = 0; d < 3; ++d) {
-        const double u = (a[d] - o[d]) / B.h;
+        double u = (a[d] - o[d]) / B.h;
+        if ((B.per >> d) & 1) u -= n[d] * floor(u / n[d]);
         const double f = floor(u);
         c.i0[d] = (int)f;
         lagrange4(u - f, c.L[d], c.dL[d]);
     }
     return c;
+}
+
+// interpolation nodes along periodic directions wrap around the cell (the
+// nodes of one cell lie at most 2 points outside it)
+__device__ __forceinline__ void wrap_node(const BlkDesc& B, int& qx, int& qy, int& qz) {
+    if (B.per & 1) qx = wrap_coord(qx, B.nx);
+    if (B.per & 2) qy = wrap_coord(qy, B.ny);
+    if (B.per & 4) qz = wrap_coord(qz, B.nz);
 }
 
 // one of the paper's grid-gradient components at an interior node: central
@@ -93,7 +105,8 @@ __global__ void k_interp_fod(const BlkDesc* __restrict__ blk, int nblk, long lon
     double v = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
     for (int node = lane; node < 64; node += 32) {
         const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
-        const int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+        int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+        if (B.per) wrap_node(B, qx, qy, qz);
         if (qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz) continue;
         const double uv = u[((long long)qz * B.ny + qy) * B.nx + qx];
         const double wgt = c.L[0][e] * c.L[1][bb] * c.L[2][cc];
@@ -671,7 +684,8 @@ __global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __r
         const Cell c = cell_of(B, fa);
         for (int node = lane; node < 64; node += 32) {
             const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
-            const int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+            int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+            if (B.per) wrap_node(B, qx, qy, qz);
             if (qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz) continue;
             u[((long long)qz * B.ny + qy) * B.nx + qx] += coef * c.L[0][e] * c.L[1][bb] * c.L[2][cc];
         }

@@ -33,8 +33,18 @@ struct BlkDesc {
     long long chunk0;           // first global chunk of orbital 0
     int nchunk;                 // chunks per orbital
     long long bnd0;             // first entry in the boundary-point list
-    int nbnd;                   // points within 6 of a face (they have ghost taps)
+    int nbnd;                   // points within 6 of a Dirichlet face (they have ghost taps)
+    int per;                    // periodic directions (bit 0 x, 1 y, 2 z)
+    long long kq[3];            // Kronecker solver: offsets of Q_d (then Q_d^T) in the matrix table
+    long long kl[3];            // and of the eigenvalues of T_d
 };
+
+// periodic-direction mask of a boundary mode
+inline int boundary_mask(int boundary) {
+    return boundary == FLOSIC_BC_PERIODIC ? 7 : (boundary == FLOSIC_BC_SLAB ? 3 : 0);
+}
+// wraps a coordinate of a periodic direction that is at most n outside [0, n)
+__host__ __device__ __forceinline__ int wrap_coord(int q, int n) { return q < 0 ? q + n : (q >= n ? q - n : q); }
 
 // One multigrid level of one spin block (level 0 = the fine grid).
 constexpr int kMaxLevels = 10;
@@ -57,6 +67,7 @@ struct LvlDesc {
     long long tile0;       // first tile of orbital 0 in this level's tile table
     int ntile;             // tiles per orbital
     int tma;               // level 0: 1 if the stencil operands of this block are TMA-staged
+    int per;               // level 0: periodic directions (bit 0 x, 1 y, 2 z); 0 on coarse levels
     int tz;                // z-depth of this level's tiles (kTileZ on level 0, kTileZc below)
     // Diagonal weight (units 1/h_l^2) of the 7-point operator at the last
     // point of each dimension, 2 elsewhere; differs from 2 on levels whose
@@ -145,6 +156,20 @@ struct Multigrid {
 
 }  // namespace flosic
 
+namespace flosic {
+// Kronecker-product solver: transform matrices, eigenvalues and the launch
+// shape of its three passes (x, y, z lines).
+struct KronPlan {
+    float* mat = nullptr;          // per distinct 1-D operator: Q (n x n), then Q^T
+    float* lam = nullptr;          // per distinct 1-D operator: eigenvalues (n)
+    long long* items = nullptr;    // [3][nblk + 1] first tile of each block per pass
+    long long total[3] = {0, 0, 0};
+    int threads[3] = {0, 0, 0};
+    size_t smem[3] = {0, 0, 0};
+    int grid[3] = {0, 0, 0};
+};
+}  // namespace flosic
+
 struct flosic_ctx {
     flosic_options opt;
     std::vector<flosic_system> sys;
@@ -162,6 +187,7 @@ struct flosic_ctx {
     double* d_bcoef = nullptr;              // [sum nbnd][10] boundary-map coefficients
     flosic::Workspace ws{};
     flosic::Multigrid mg;
+    flosic::KronPlan kron;
     bool have_forward = false;
     bool have_energy = false;
     std::string err;
@@ -210,6 +236,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
 void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E_sic,
                           cudaStream_t s);
 
+// Kronecker-product inner solver (mixed precision)
+int kron_max_n();
+cudaError_t setup_kron(flosic_ctx* c);
+void launch_kron_solve(flosic_ctx* c, const float* r, float* d, float* t1, float* t2, cudaStream_t s);
 // Alternating Anderson-Richardson inner solver (mixed precision)
 template <class T>
 void launch_aar_step(flosic_ctx* c, T* x, T* r, T* f, int k, bool anderson, cudaStream_t s,

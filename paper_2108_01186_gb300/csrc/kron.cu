@@ -1,0 +1,397 @@
+// Kronecker-product solver of the per-orbital Poisson problems.
+//
+// Sec. II.A writes the finite-difference Laplacian in Kronecker-product
+// form: with zero ghost values (the Dirichlet data sit in the right-hand
+// side) or periodic wrap-around along each direction,
+//   A = -Delta_h = T_x (+) T_y (+) T_z,   T_d = -(1/h^2) D2_d,
+// where D2_d is the 1-D 12th-order second difference of direction d.  Each
+// T_d is symmetric; with T_d = Q_d L_d Q_d^T (computed once per context in
+// float64 on the host by cyclic Jacobi) the inverse is
+//   A^{-1} = (Q_x x Q_y x Q_z) diag(1 / (l_i + l_j + l_k)) (Q_x x Q_y x Q_z)^T.
+// In a periodic cell the constant mode (l = 0 in every direction) is the
+// null space of A; its coefficient is set to zero (zero-mean potential).
+//
+// On the device the inverse is six dense 1-D transforms per orbital (three
+// forward with Q_d, three back with Q_d^T, the diagonal scaling folded into
+// the forward z pass), each a float32 matrix product over one direction's
+// lines.  A persistent CTA keeps the n x n transform matrix of its block in
+// shared memory and streams 32-line tiles through it: per tile a coalesced
+// load of n x 32 values, a register-tiled product (8 x 4 outputs per thread,
+// n threads), a transpose through shared memory and a coalesced store.  The
+// mixed refinement calls it as its float32 inner solve; the float-float
+// residual around it carries the accuracy to the requested tolerance.
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace flosic {
+namespace {
+
+constexpr int kKronCols = 32;                  // lines per tile
+constexpr int kKronLd = kKronCols + 4;         // shared row stride of a tile (16-byte rows)
+constexpr int kKronMaxN = 216;                 // (216^2 + 216 * 36) floats fit in 227 KB
+
+// Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix A (row
+// major, destroyed): on return A's diagonal holds the eigenvalues and the
+// columns of V the eigenvectors.  Each rotation annihilates a_pq
+// (tau = (a_qq - a_pp) / 2 a_pq, t = sgn(tau) / (|tau| + sqrt(1 + tau^2))).
+void jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    double fro = 0.0;
+    for (double a : A) fro += a * a;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off <= 1e-32 * fro) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+                for (int k = 0; k < n; ++k) {   // columns p, q
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = cs * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+}
+
+// T_d of one direction: n points, spacing h, periodic or zero outside.
+std::vector<double> axis_operator(int n, double h, bool periodic) {
+    double w[kHalf + 1];
+    stencil_weights(w);
+    std::vector<double> T((size_t)n * n, 0.0);
+    const double ih2 = 1.0 / (h * h);
+    for (int j = 0; j < n; ++j)
+        for (int m = -kHalf; m <= kHalf; ++m) {
+            int q = j + m;
+            if (q < 0 || q >= n) {
+                if (!periodic) continue;
+                q = ((q % n) + n) % n;
+            }
+            T[(size_t)j * n + q] -= w[m < 0 ? -m : m] * ih2;
+        }
+    return T;
+}
+
+__host__ __device__ inline int round8(int n) { return (n + 7) & ~7; }
+
+// device array owned by the context (freed with it)
+template <class T>
+cudaError_t ctx_alloc(flosic_ctx* c, T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (n > 0 ? n : 1));
+    if (e == cudaSuccess) {
+        c->allocations.push_back(q);
+        *p = static_cast<T*>(q);
+    }
+    return e;
+}
+
+struct KronArgs {
+    const BlkDesc* blk;
+    int nblk;
+    const long long* item0;   // [nblk + 1] first tile item of each block in this pass
+    const float* mat;         // transform matrices (Q_d and Q_d^T per distinct operator)
+    const float* lam;         // eigenvalues per distinct operator
+    const float* in;
+    float* out;
+    const int* active;
+    double* flops;            // algorithmic flop counter (profiling)
+    int axis;                 // 0 x, 1 y, 2 z
+    int inverse;              // 0: coefficients = Q^T v; 1: values = Q c
+    int scale;                // forward z pass: divide by l_i + l_j + l_k
+};
+
+// Item -> (block, orbital, tile): tiles of 32 lines along the pass direction.
+//   x: lines are grid rows (y, z), tile q = rows 32q .. 32q+31 (a contiguous run of 32 nx values)
+//   y: lines are (x, z) columns at fixed z, tile q = (z, x-group)
+//   z: lines are xy points, tile q = xy points 32q .. 32q+31
+__device__ __forceinline__ int pass_groups(const BlkDesc& B, int axis) {
+    if (axis == 0) return (B.ny * B.nz + kKronCols - 1) / kKronCols;
+    if (axis == 1) return B.nz * ((B.nx + kKronCols - 1) / kKronCols);
+    return (B.nx * B.ny + kKronCols - 1) / kKronCols;
+}
+
+__global__ void __launch_bounds__(kKronMaxN) k_kron_pass(KronArgs a, long long total) {
+    extern __shared__ __align__(16) float kron_smem[];
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * per_cta;
+    const long long it1 = it0 + per_cta < total ? it0 + per_cta : total;
+    if (it0 >= it1) return;
+    int b = 0;
+    while (b + 1 < a.nblk && it0 >= a.item0[b + 1]) ++b;
+    int cur = -1;
+    float* Pm = kron_smem;   // [n8][n8], then the tile [n8][kKronLd]
+    float* S = nullptr;
+    int n = 0, n8 = 0;
+    for (long long item = it0; item < it1; ++item) {
+        while (b + 1 < a.nblk && item >= a.item0[b + 1]) ++b;
+        const BlkDesc& B = a.blk[b];
+        const int groups = pass_groups(B, a.axis);
+        const long long r = item - a.item0[b];
+        const int i_orb = (int)(r / groups), q = (int)(r % groups);
+        if (!a.active[B.orb0 + i_orb]) continue;   // uniform across the CTA
+        __syncthreads();   // the previous tile's store has read S; P may be replaced
+        if (b != cur) {
+            n = (a.axis == 0) ? B.nx : (a.axis == 1 ? B.ny : B.nz);
+            n8 = round8(n);
+            const float* src = a.mat + B.kq[a.axis] + (a.inverse ? (long long)n * n : 0);
+            for (int e = tid; e < n8 * n8; e += nthr) {
+                const int j = e / n8, i = e - j * n8;
+                Pm[e] = (j < n && i < n) ? src[j * n + i] : 0.f;
+            }
+            S = Pm + n8 * n8;
+            cur = b;
+        }
+        const long long base = B.off + (long long)i_orb * B.G;
+        const long long sxy = (long long)B.nx * B.ny;
+        // element (j, c) of the tile: position j along the line of column c
+        long long cbase;   // address of (0, 0); column stride and line stride below
+        long long cstride, jstride;
+        int ncol;          // valid columns
+        if (a.axis == 0) {
+            const int rows = B.ny * B.nz;
+            cbase = base + (long long)q * kKronCols * B.nx;
+            cstride = B.nx;
+            jstride = 1;
+            ncol = min(kKronCols, rows - q * kKronCols);
+        } else if (a.axis == 1) {
+            const int gx = (B.nx + kKronCols - 1) / kKronCols;
+            const int zi = q / gx, xg = q - zi * gx;
+            cbase = base + (long long)zi * sxy + (long long)xg * kKronCols;
+            cstride = 1;
+            jstride = B.nx;
+            ncol = min(kKronCols, B.nx - xg * kKronCols);
+        } else {
+            cbase = base + (long long)q * kKronCols;
+            cstride = 1;
+            jstride = sxy;
+            ncol = (int)min((long long)kKronCols, sxy - (long long)q * kKronCols);
+        }
+        if (a.axis == 0) {   // a run of ncol rows of nx contiguous values
+            for (int e = tid; e < kKronCols * n8; e += nthr) {
+                const int c = e / n8, j = e - c * n8;
+                S[j * kKronLd + c] = (c < ncol && j < n) ? a.in[cbase + (long long)c * cstride + j] : 0.f;
+            }
+        } else {             // n rows of 32 contiguous values
+            for (int e = tid; e < kKronCols * n8; e += nthr) {
+                const int j = e / kKronCols, c = e - j * kKronCols;
+                S[j * kKronLd + c] = (c < ncol && j < n) ? a.in[cbase + (long long)j * jstride + c] : 0.f;
+            }
+        }
+        __syncthreads();
+        // out[i][c] = sum_j P[j][i] S[j][c]; thread: rows r0 .. r0+7, columns c0 .. c0+3
+        const int cq = tid & 7, ib = tid >> 3;
+        const int r0 = ib * 8, c0 = cq * 4;
+        const bool comp = r0 < n8;
+        float acc[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        if (comp) {
+#pragma unroll 4
+            for (int j = 0; j < n; ++j) {
+                const float4 p0 = *reinterpret_cast<const float4*>(Pm + j * n8 + r0);
+                const float4 p1 = *reinterpret_cast<const float4*>(Pm + j * n8 + r0 + 4);
+                const float4 sv = *reinterpret_cast<const float4*>(S + j * kKronLd + c0);
+                const float pr[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+                const float sc[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pr[u], sc[v], acc[u][v]);
+            }
+            if (a.scale) {   // forward z pass: column c is the xy mode (i, j) = (t % nx, t / nx)
+                const float* lx = a.lam + B.kl[0];
+                const float* ly = a.lam + B.kl[1];
+                const float* lz = a.lam + B.kl[2];
+                float lxy[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const long long t = (long long)q * kKronCols + c0 + v;
+                    const int ti = (int)(t < sxy ? t : 0);
+                    const int yi = ti / B.nx, xi = ti - yi * B.nx;
+                    lxy[v] = lx[xi] + ly[yi];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = r0 + u < n ? r0 + u : 0;
+                    const float l3 = lz[k];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float s = lxy[v] + l3;
+                        acc[u][v] = (s > 0.f) ? acc[u][v] / s : 0.f;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (comp) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                *reinterpret_cast<float4*>(S + (r0 + u) * kKronLd + c0) =
+                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+        }
+        __syncthreads();
+        if (a.axis == 0) {
+            for (int e = tid; e < kKronCols * n8; e += nthr) {
+                const int c = e / n8, j = e - c * n8;
+                if (c < ncol && j < n) a.out[cbase + (long long)c * cstride + j] = S[j * kKronLd + c];
+            }
+        } else {
+            for (int e = tid; e < kKronCols * n8; e += nthr) {
+                const int j = e / kKronCols, c = e - j * kKronCols;
+                if (c < ncol && j < n) a.out[cbase + (long long)j * jstride + c] = S[j * kKronLd + c];
+            }
+        }
+        if (a.flops && tid == 0) atomicAdd(a.flops, 2.0 * n * n * ncol);
+    }
+}
+
+// Orbitals solved this round: leave the inner solve, count one application.
+__global__ void k_kron_done(int norb, CgState st) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < norb && st.active[o]) {
+        st.active[o] = 0;
+        ++st.iters[o];
+    }
+}
+
+}  // namespace
+
+int kron_max_n() { return kKronMaxN; }
+
+// Host set-up: the eigen-decomposition of every distinct 1-D operator
+// (n, h, periodic), Q and Q^T in float32, the eigenvalues (the periodic
+// constant mode set to exactly zero), per-block offsets and the tile counts
+// of the three passes.
+cudaError_t setup_kron(flosic_ctx* c) {
+    std::map<std::tuple<int, double, int>, std::pair<long long, long long>> seen;
+    std::vector<float> mat, lam;
+    KronPlan& K = c->kron;
+    for (BlkDesc& B : c->blk) {
+        const int nd[3] = {B.nx, B.ny, B.nz};
+        for (int d = 0; d < 3; ++d) {
+            const int n = nd[d];
+            const int periodic = (B.per >> d) & 1;
+            const auto key = std::make_tuple(n, B.h, periodic);
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                std::vector<double> T = axis_operator(n, B.h, periodic != 0), V;
+                jacobi_eigen(n, T, V);
+                const long long qo = (long long)mat.size(), lo = (long long)lam.size();
+                mat.resize(mat.size() + 2 * (size_t)n * n);
+                for (int j = 0; j < n; ++j)
+                    for (int k = 0; k < n; ++k) {
+                        mat[qo + (size_t)j * n + k] = (float)V[(size_t)j * n + k];              // Q[j][k]
+                        mat[qo + (size_t)n * n + (size_t)k * n + j] = (float)V[(size_t)j * n + k];  // Q^T
+                    }
+                int kmin = 0;
+                for (int k = 0; k < n; ++k) {
+                    lam.push_back((float)T[(size_t)k * n + k]);
+                    if (std::fabs(T[(size_t)k * n + k]) < std::fabs(T[(size_t)kmin * n + kmin])) kmin = k;
+                }
+                if (periodic) lam[lo + kmin] = 0.f;
+                it = seen.emplace(key, std::make_pair(qo, lo)).first;
+            }
+            B.kq[d] = it->second.first;
+            B.kl[d] = it->second.second;
+        }
+    }
+    cudaError_t e = ctx_alloc(c, &K.mat, mat.size());
+    if (e == cudaSuccess) e = ctx_alloc(c, &K.lam, lam.size());
+    if (e == cudaSuccess) e = cudaMemcpy(K.mat, mat.data(), sizeof(float) * mat.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(K.lam, lam.data(), sizeof(float) * lam.size(), cudaMemcpyHostToDevice);
+    // tile items per pass and block
+    std::vector<long long> items(3 * (size_t)(c->nblk + 1));
+    for (int d = 0; d < 3; ++d) {
+        long long acc = 0;
+        int nmax = 8;
+        for (int b = 0; b < c->nblk; ++b) {
+            const BlkDesc& B = c->blk[b];
+            items[(size_t)d * (c->nblk + 1) + b] = acc;
+            long long g;
+            if (d == 0) g = (B.ny * (long long)B.nz + kKronCols - 1) / kKronCols;
+            else if (d == 1) g = (long long)B.nz * ((B.nx + kKronCols - 1) / kKronCols);
+            else g = ((long long)B.nx * B.ny + kKronCols - 1) / kKronCols;
+            acc += g * B.N;
+            const int n = d == 0 ? B.nx : (d == 1 ? B.ny : B.nz);
+            nmax = n > nmax ? n : nmax;
+        }
+        items[(size_t)d * (c->nblk + 1) + c->nblk] = acc;
+        K.total[d] = acc;
+        K.threads[d] = round8(nmax);
+        K.smem[d] = (size_t)(round8(nmax) * round8(nmax) + round8(nmax) * kKronLd) * sizeof(float);
+    }
+    if (e == cudaSuccess) e = ctx_alloc(c, &K.items, items.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(K.items, items.data(), sizeof(long long) * items.size(), cudaMemcpyHostToDevice);
+    size_t smax = 0;
+    for (int d = 0; d < 3; ++d) smax = K.smem[d] > smax ? K.smem[d] : smax;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_kron_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kron_pass, K.threads[d], K.smem[d]);
+        long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        K.grid[d] = (int)(grid < K.total[d] ? grid : (K.total[d] > 0 ? K.total[d] : 1));
+    }
+    return e;
+}
+
+// d = A^{-1} r for the active orbitals (float32); t1, t2 are scratch arrays
+// of the orbital size.  Marks the orbitals done and counts one iteration.
+void launch_kron_solve(flosic_ctx* c, const float* r, float* d, float* t1, float* t2, cudaStream_t s) {
+    const KronPlan& K = c->kron;
+    KronArgs a{};
+    a.blk = c->d_blk;
+    a.nblk = c->nblk;
+    a.mat = K.mat;
+    a.lam = K.lam;
+    a.active = c->ws.cg.active;
+    a.flops = c->profiling ? c->ws.cg.prof_bytes : nullptr;
+    struct Step { int axis, inverse, scale; const float* in; float* out; };
+    const Step steps[6] = {{0, 0, 0, r, t1}, {1, 0, 0, t1, t2}, {2, 0, 1, t2, t1},
+                           {2, 1, 0, t1, t2}, {1, 1, 0, t2, t1}, {0, 1, 0, t1, d}};
+    prof_begin(c, s);
+    for (const Step& st : steps) {
+        a.axis = st.axis;
+        a.inverse = st.inverse;
+        a.scale = st.scale;
+        a.in = st.in;
+        a.out = st.out;
+        a.item0 = K.items + (size_t)st.axis * (c->nblk + 1);
+        k_kron_pass<<<K.grid[st.axis], K.threads[st.axis], K.smem[st.axis], s>>>(a, K.total[st.axis]);
+        note_launch(c);
+    }
+    prof_end(c, s);
+    k_kron_done<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->ws.cg);
+    note_launch(c);
+}
+
+}  // namespace flosic

@@ -618,7 +618,7 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
         // b becomes its pairs, the idle float64 residual buffer holds x
         const double inner_tol2 = 1e-12;   // each float32 solve gains ~6 digits
         float2* x = reinterpret_cast<float2*>(w.r64);
-        float* p32 = mg ? nullptr : w.p32;
+        float* p32 = (mg || c->opt.solver != FLOSIC_SOLVER_PCG) ? nullptr : w.p32;
         if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset")) return FLOSIC_ERR_CUDA;
         launch_ff_init(c, b, V, warm, x, p32, tol2, inner_tol2, s);
         for (int round = 0; round < 40; ++round) {
@@ -630,7 +630,9 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
             if (na == 0) break;
-            if (c->opt.solver == FLOSIC_SOLVER_AAR) {
+            if (c->opt.solver == FLOSIC_SOLVER_KRON) {
+                launch_kron_solve(c, w.r32, w.d32, w.p32, w.q32, s);
+            } else if (c->opt.solver == FLOSIC_SOLVER_AAR) {
                 int rc = aar_inner(c, s);
                 if (rc) return rc;
             } else if (mg) {

@@ -18,7 +18,8 @@ FP64, MIXED = 0, 1
 GRAD_INTERP, GRAD_PAPER = 0, 1
 ADJ_REUSE_V, ADJ_EXACT = 0, 1
 PC_NONE, PC_MG = 0, 1
-SOLVER_PCG, SOLVER_AAR = 0, 1
+SOLVER_PCG, SOLVER_AAR, SOLVER_KRON = 0, 1, 2
+BC_ISOLATED, BC_PERIODIC, BC_SLAB = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ARG", 2: "CUDA", 3: "ILLCOND", 4: "NOCONV", 5: "NONFINITE"}
 
@@ -47,7 +48,7 @@ class FlosicOptions(ctypes.Structure):
                 ("rho_min", ctypes.c_double), ("illcond_tol", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("solver", ctypes.c_int),
                 ("aar_omega", ctypes.c_double), ("aar_beta", ctypes.c_double),
-                ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int)]
+                ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 _lib = None

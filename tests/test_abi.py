@@ -77,7 +77,7 @@ def test_create_rejects_bad_options(lib):
     assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
 
 
-@pytest.mark.parametrize("bad", [dict(solver=2), dict(solver=1, precision=0), dict(solver=1, aar_m=0),
+@pytest.mark.parametrize("bad", [dict(solver=3), dict(solver=1, precision=0), dict(solver=1, aar_m=0),
                                  dict(solver=1, aar_m=9), dict(solver=1, aar_p=1), dict(solver=1, aar_omega=0.0),
                                  dict(solver=1, aar_beta=2.0)])
 def test_create_rejects_bad_aar_options(lib, bad):
@@ -105,3 +105,32 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.flosic_destroy(None) == F.FLOSIC_OK
     out = (ctypes.c_int64 * 6)()
     assert lib.flosic_layout(None, out) == F.FLOSIC_ERR_ARG
+
+
+@pytest.mark.parametrize("bad", [dict(solver=2, precision=0), dict(boundary=3), dict(boundary=1),
+                                 dict(boundary=2, solver=1),
+                                 dict(boundary=1, solver=2, adjoint_mode=1),
+                                 dict(boundary=2, solver=2, fod_grad_mode=1)])
+def test_create_rejects_bad_boundary_options(lib, bad):
+    # extended boundaries run on the Kronecker solver only (mixed precision),
+    # with the V-reusing adjoint and the interpolant's FOD gradient
+    from paper_2108_01186_gb300 import flosic as F
+    o = F.default_options(**bad)
+    h = ctypes.c_void_p()
+    s = _sys(nx=16, ny=16, nz=16)
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+    assert not h.value
+
+
+@pytest.mark.parametrize("dims,opts", [((12, 16, 16), dict(boundary=1, solver=2)),
+                                       ((16, 12, 16), dict(boundary=2, solver=2)),
+                                       ((16, 16, 217), dict(solver=2))])
+def test_create_rejects_bad_extended_grids(lib, dims, opts):
+    # periodic sides need 13 points (the stencil's taps stay distinct); the
+    # Kronecker solver keeps an n x n matrix in shared memory (n <= 216)
+    from paper_2108_01186_gb300 import flosic as F
+    o = F.default_options(**opts)
+    h = ctypes.c_void_p()
+    s = _sys(nx=dims[0], ny=dims[1], nz=dims[2])
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
+    assert b"13" in lib.flosic_last_error(None) or b"216" in lib.flosic_last_error(None)
