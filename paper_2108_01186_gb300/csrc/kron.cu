@@ -15,9 +15,10 @@
 // forward with Q_d, three back with Q_d^T, the diagonal scaling folded into
 // the forward z pass), each a float32 matrix product over one direction's
 // lines.  A persistent CTA keeps the n x n transform matrix of its block in
-// shared memory and streams 32-line tiles through it: per tile a coalesced
-// load of n x 32 values, a register-tiled product (8 x 4 outputs per thread,
-// n threads), a transpose through shared memory and a coalesced store.  The
+// shared memory and streams 64-line tiles through it: the next tile is
+// fetched into registers (coalesced) while the current one is multiplied
+// (8 x 4 outputs per thread, 2n threads), and results are stored from
+// registers.  The
 // mixed refinement calls it as its float32 inner solve; the float-float
 // residual around it carries the accuracy to the requested tolerance.
 #include <cmath>
@@ -30,9 +31,10 @@
 namespace flosic {
 namespace {
 
-constexpr int kKronCols = 32;                  // lines per tile
+constexpr int kKronCols = 64;                  // lines per tile
 constexpr int kKronLd = kKronCols + 4;         // shared row stride of a tile (16-byte rows)
-constexpr int kKronMaxN = 216;                 // (216^2 + 216 * 36) floats fit in 227 KB
+constexpr int kKronMaxN = 208;                 // (208^2 + 208 * 68) floats fit in 227 KB
+constexpr int kKronPre = kKronCols / 2;        // tile values per thread (2 n8 threads, n8 x 64 values)
 
 // Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix A (row
 // major, destroyed): on return A's diagonal holds the eigenvalues and the
@@ -121,17 +123,86 @@ struct KronArgs {
     int scale;                // forward z pass: divide by l_i + l_j + l_k
 };
 
-// Item -> (block, orbital, tile): tiles of 32 lines along the pass direction.
-//   x: lines are grid rows (y, z), tile q = rows 32q .. 32q+31 (a contiguous run of 32 nx values)
+// Item -> (block, orbital, tile): tiles of kKronCols lines along the pass direction.
+//   x: lines are grid rows (y, z), tile q = rows q*C .. q*C+C-1 (a contiguous run of C*nx values)
 //   y: lines are (x, z) columns at fixed z, tile q = (z, x-group)
-//   z: lines are xy points, tile q = xy points 32q .. 32q+31
+//   z: lines are xy points, tile q = xy points q*C .. q*C+C-1
 __device__ __forceinline__ int pass_groups(const BlkDesc& B, int axis) {
     if (axis == 0) return (B.ny * B.nz + kKronCols - 1) / kKronCols;
     if (axis == 1) return B.nz * ((B.nx + kKronCols - 1) / kKronCols);
     return (B.nx * B.ny + kKronCols - 1) / kKronCols;
 }
 
-__global__ void __launch_bounds__(kKronMaxN) k_kron_pass(KronArgs a, long long total) {
+// Addressing of one tile: element (j, c) = position j along line c lies at
+// cbase + c * cstride + j * jstride; ncol lines are valid.
+struct Tile {
+    long long cbase, cstride, jstride;
+    int ncol, q;
+};
+
+__device__ __forceinline__ Tile tile_of(const BlkDesc& B, int axis, int i_orb, int q) {
+    Tile t;
+    const long long base = B.off + (long long)i_orb * B.G;
+    const long long sxy = (long long)B.nx * B.ny;
+    t.q = q;
+    if (axis == 0) {
+        t.cbase = base + (long long)q * kKronCols * B.nx;
+        t.cstride = B.nx;
+        t.jstride = 1;
+        t.ncol = min(kKronCols, B.ny * B.nz - q * kKronCols);
+    } else if (axis == 1) {
+        const int gx = (B.nx + kKronCols - 1) / kKronCols;
+        const int zi = q / gx, xg = q - zi * gx;
+        t.cbase = base + (long long)zi * sxy + (long long)xg * kKronCols;
+        t.cstride = 1;
+        t.jstride = B.nx;
+        t.ncol = min(kKronCols, B.nx - xg * kKronCols);
+    } else {
+        t.cbase = base + (long long)q * kKronCols;
+        t.cstride = 1;
+        t.jstride = sxy;
+        t.ncol = (int)min((long long)kKronCols, sxy - (long long)q * kKronCols);
+    }
+    return t;
+}
+
+// The thread's share of a tile (kKronPre values; the CTA has 2 * n8 threads
+// and a tile n8 * kKronCols values): coalesced along the contiguous
+// direction (j for x lines, c otherwise).
+__device__ __forceinline__ void tile_coords(int axis, int e, int n8, int& j, int& c) {
+    if (axis == 0) { c = e / n8; j = e - c * n8; }
+    else { j = e / kKronCols; c = e - j * kKronCols; }
+}
+
+__device__ __forceinline__ void tile_fetch(const float* __restrict__ in, const Tile& t, int axis, int n, int n8,
+                                           int tid, int nthr, float* pre) {
+#pragma unroll
+    for (int k = 0; k < kKronPre; ++k) {
+        int j, c;
+        tile_coords(axis, tid + k * nthr, n8, j, c);
+        pre[k] = (c < t.ncol && j < n) ? __ldcs(in + t.cbase + (long long)c * t.cstride + (long long)j * t.jstride)
+                                       : 0.f;
+    }
+}
+
+// next item at or after it whose orbital is active (it1 if none)
+__device__ __forceinline__ long long next_active(const KronArgs& a, long long it, long long it1, int& b) {
+    for (; it < it1; ++it) {
+        while (b + 1 < a.nblk && it >= a.item0[b + 1]) ++b;
+        const BlkDesc& B = a.blk[b];
+        const int groups = pass_groups(B, a.axis);
+        const int i_orb = (int)((it - a.item0[b]) / groups);
+        if (a.active[B.orb0 + i_orb]) return it;
+    }
+    return it1;
+}
+
+// One pass: out[i][c] = sum_j P[j][i] in[j][c] over every tile of the
+// CTA's contiguous item range.  Thread (ib, cq) owns rows 8 ib .. 8 ib + 7
+// and columns 4 cq .. 4 cq + 3 of the n8 x kKronCols product; the next
+// tile's values are fetched into registers while the current one is
+// multiplied, and results go from registers straight to global memory.
+__global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long long total) {
     extern __shared__ __align__(16) float kron_smem[];
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -139,78 +210,63 @@ __global__ void __launch_bounds__(kKronMaxN) k_kron_pass(KronArgs a, long long t
     const long long it0 = (long long)blockIdx.x * per_cta;
     const long long it1 = it0 + per_cta < total ? it0 + per_cta : total;
     if (it0 >= it1) return;
-    int b = 0;
-    while (b + 1 < a.nblk && it0 >= a.item0[b + 1]) ++b;
-    int cur = -1;
-    float* Pm = kron_smem;   // [n8][n8], then the tile [n8][kKronLd]
-    float* S = nullptr;
-    int n = 0, n8 = 0;
-    for (long long item = it0; item < it1; ++item) {
-        while (b + 1 < a.nblk && item >= a.item0[b + 1]) ++b;
+    int bs = 0;   // block of the item being fetched
+    long long item = next_active(a, it0, it1, bs);
+    if (item >= it1) return;
+    float pre[kKronPre];
+    int cur = -1, n = 0, n8 = 0;
+    {
+        const BlkDesc& B = a.blk[bs];
+        n = (a.axis == 0) ? B.nx : (a.axis == 1 ? B.ny : B.nz);
+        n8 = round8(n);
+        const int groups = pass_groups(B, a.axis);
+        const long long r = item - a.item0[bs];
+        tile_fetch(a.in, tile_of(B, a.axis, (int)(r / groups), (int)(r % groups)), a.axis, n, n8, tid, nthr, pre);
+    }
+    float* Pm = kron_smem;
+    const int cq = tid % (kKronCols / 4), ib = tid / (kKronCols / 4);
+    while (item < it1) {
+        const int b = bs;
         const BlkDesc& B = a.blk[b];
         const int groups = pass_groups(B, a.axis);
         const long long r = item - a.item0[b];
-        const int i_orb = (int)(r / groups), q = (int)(r % groups);
-        if (!a.active[B.orb0 + i_orb]) continue;   // uniform across the CTA
-        __syncthreads();   // the previous tile's store has read S; P may be replaced
+        const Tile t = tile_of(B, a.axis, (int)(r / groups), (int)(r % groups));
+        __syncthreads();   // the previous tile's product has finished reading S (and P)
         if (b != cur) {
             n = (a.axis == 0) ? B.nx : (a.axis == 1 ? B.ny : B.nz);
             n8 = round8(n);
             const float* src = a.mat + B.kq[a.axis] + (a.inverse ? (long long)n * n : 0);
             for (int e = tid; e < n8 * n8; e += nthr) {
-                const int j = e / n8, i = e - j * n8;
-                Pm[e] = (j < n && i < n) ? src[j * n + i] : 0.f;
+                const int jj = e / n8, ii = e - jj * n8;
+                Pm[e] = (jj < n && ii < n) ? src[jj * n + ii] : 0.f;
             }
-            S = Pm + n8 * n8;
             cur = b;
         }
-        const long long base = B.off + (long long)i_orb * B.G;
-        const long long sxy = (long long)B.nx * B.ny;
-        // element (j, c) of the tile: position j along the line of column c
-        long long cbase;   // address of (0, 0); column stride and line stride below
-        long long cstride, jstride;
-        int ncol;          // valid columns
-        if (a.axis == 0) {
-            const int rows = B.ny * B.nz;
-            cbase = base + (long long)q * kKronCols * B.nx;
-            cstride = B.nx;
-            jstride = 1;
-            ncol = min(kKronCols, rows - q * kKronCols);
-        } else if (a.axis == 1) {
-            const int gx = (B.nx + kKronCols - 1) / kKronCols;
-            const int zi = q / gx, xg = q - zi * gx;
-            cbase = base + (long long)zi * sxy + (long long)xg * kKronCols;
-            cstride = 1;
-            jstride = B.nx;
-            ncol = min(kKronCols, B.nx - xg * kKronCols);
-        } else {
-            cbase = base + (long long)q * kKronCols;
-            cstride = 1;
-            jstride = sxy;
-            ncol = (int)min((long long)kKronCols, sxy - (long long)q * kKronCols);
-        }
-        if (a.axis == 0) {   // a run of ncol rows of nx contiguous values
-            for (int e = tid; e < kKronCols * n8; e += nthr) {
-                const int c = e / n8, j = e - c * n8;
-                S[j * kKronLd + c] = (c < ncol && j < n) ? a.in[cbase + (long long)c * cstride + j] : 0.f;
-            }
-        } else {             // n rows of 32 contiguous values
-            for (int e = tid; e < kKronCols * n8; e += nthr) {
-                const int j = e / kKronCols, c = e - j * kKronCols;
-                S[j * kKronLd + c] = (c < ncol && j < n) ? a.in[cbase + (long long)j * jstride + c] : 0.f;
-            }
+        float* S = Pm + n8 * n8;
+#pragma unroll
+        for (int k = 0; k < kKronPre; ++k) {
+            int j, c;
+            tile_coords(a.axis, tid + k * nthr, n8, j, c);
+            if (c < kKronCols && j < n8) S[j * kKronLd + c] = pre[k];   // (a smaller block's n8 leaves extra slots)
         }
         __syncthreads();
-        // out[i][c] = sum_j P[j][i] S[j][c]; thread: rows r0 .. r0+7, columns c0 .. c0+3
-        const int cq = tid & 7, ib = tid >> 3;
+        // fetch the next active tile while this one is multiplied
+        long long nxt = next_active(a, item + 1, it1, bs);
+        if (nxt < it1) {
+            const BlkDesc& Bn = a.blk[bs];
+            const int nn = (a.axis == 0) ? Bn.nx : (a.axis == 1 ? Bn.ny : Bn.nz);
+            const int gn = pass_groups(Bn, a.axis);
+            const long long rn = nxt - a.item0[bs];
+            tile_fetch(a.in, tile_of(Bn, a.axis, (int)(rn / gn), (int)(rn % gn)), a.axis, nn, round8(nn), tid,
+                       nthr, pre);
+        }
         const int r0 = ib * 8, c0 = cq * 4;
-        const bool comp = r0 < n8;
         float acc[8][4];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        if (comp) {
+        if (r0 < n8) {
 #pragma unroll 4
             for (int j = 0; j < n; ++j) {
                 const float4 p0 = *reinterpret_cast<const float4*>(Pm + j * n8 + r0);
@@ -224,14 +280,15 @@ __global__ void __launch_bounds__(kKronMaxN) k_kron_pass(KronArgs a, long long t
                     for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pr[u], sc[v], acc[u][v]);
             }
             if (a.scale) {   // forward z pass: column c is the xy mode (i, j) = (t % nx, t / nx)
+                const long long sxy = (long long)B.nx * B.ny;
                 const float* lx = a.lam + B.kl[0];
                 const float* ly = a.lam + B.kl[1];
                 const float* lz = a.lam + B.kl[2];
                 float lxy[4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    const long long t = (long long)q * kKronCols + c0 + v;
-                    const int ti = (int)(t < sxy ? t : 0);
+                    const long long tt = (long long)t.q * kKronCols + c0 + v;
+                    const int ti = (int)(tt < sxy ? tt : 0);
                     const int yi = ti / B.nx, xi = ti - yi * B.nx;
                     lxy[v] = lx[xi] + ly[yi];
                 }
@@ -241,32 +298,26 @@ __global__ void __launch_bounds__(kKronMaxN) k_kron_pass(KronArgs a, long long t
                     const float l3 = lz[k];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const float s = lxy[v] + l3;
-                        acc[u][v] = (s > 0.f) ? acc[u][v] / s : 0.f;
+                        const float sm = lxy[v] + l3;
+                        acc[u][v] = (sm > 0.f) ? acc[u][v] / sm : 0.f;
                     }
                 }
             }
-        }
-        __syncthreads();
-        if (comp) {
+            // results straight from registers: rows r0 .. r0+7 of columns c0 .. c0+3
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                *reinterpret_cast<float4*>(S + (r0 + u) * kKronLd + c0) =
-                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
-        }
-        __syncthreads();
-        if (a.axis == 0) {
-            for (int e = tid; e < kKronCols * n8; e += nthr) {
-                const int c = e / n8, j = e - c * n8;
-                if (c < ncol && j < n) a.out[cbase + (long long)c * cstride + j] = S[j * kKronLd + c];
-            }
-        } else {
-            for (int e = tid; e < kKronCols * n8; e += nthr) {
-                const int j = e / kKronCols, c = e - j * kKronCols;
-                if (c < ncol && j < n) a.out[cbase + (long long)j * jstride + c] = S[j * kKronLd + c];
+            for (int u = 0; u < 8; ++u) {
+                const int i = r0 + u;
+                if (i >= n) break;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int c = c0 + v;
+                    if (c < t.ncol) __stcs(a.out + t.cbase + (long long)c * t.cstride + (long long)i * t.jstride,
+                                           acc[u][v]);
+                }
             }
         }
-        if (a.flops && tid == 0) atomicAdd(a.flops, 2.0 * n * n * ncol);
+        if (a.flops && tid == 0) atomicAdd(a.flops, 2.0 * n * n * t.ncol);
+        item = nxt;
     }
 }
 
@@ -342,7 +393,7 @@ cudaError_t setup_kron(flosic_ctx* c) {
         }
         items[(size_t)d * (c->nblk + 1) + c->nblk] = acc;
         K.total[d] = acc;
-        K.threads[d] = round8(nmax);
+        K.threads[d] = 2 * round8(nmax);
         K.smem[d] = (size_t)(round8(nmax) * round8(nmax) + round8(nmax) * kKronLd) * sizeof(float);
     }
     if (e == cudaSuccess) e = ctx_alloc(c, &K.items, items.size());
