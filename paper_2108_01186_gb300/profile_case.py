@@ -6,7 +6,7 @@ densities, solved once by the multigrid-preconditioned CG of the library
 one stencil launch (8 x 128^3 float32 vectors: 64 MiB each, above L2) and
 free of the oracle and of any randomness.
 
-  python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64]
+  python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64] [--solver kron]
   python -m paper_2108_01186_gb300.profile_case --case flo     (FLO build, 96^3, 16+16 orbitals)
 """
 import argparse
@@ -17,6 +17,8 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--norb", type=int, default=8)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--solver", default="pcg", choices=["pcg", "kron"],
+                    help="inner solver of the mixed refinement (kron: the Kronecker-product transforms)")
     ap.add_argument("--case", default="poisson", choices=["poisson", "flo"],
                     help="poisson: one multigrid-PCG solve of Gaussian densities; flo: two FLO builds "
                          "(tensor-core overlap) of the seeded 96^3, 16+16-orbital system")
@@ -31,7 +33,7 @@ def main():
     n, N, h = args.n, args.norb, 0.2
     o = -0.5 * h * (n - 1)
     ctx = Context([dict(n=n, h=h, origin=[o, o, o], norb=[N])], precision=0 if args.fp64 else 1,
-                  cg_tol=1e-10, preconditioner=1)
+                  cg_tol=1e-10, preconditioner=1, solver=2 if args.solver == "kron" else 0)
     x = torch.linspace(o, -o, n, dtype=torch.float64, device="cuda")
     Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
     phi = torch.cat([torch.exp(-(X - 0.3 * k) ** 2 - Y ** 2 - Z ** 2).reshape(-1) for k in range(N)]).contiguous()
