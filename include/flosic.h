@@ -124,7 +124,7 @@ typedef struct flosic_ctx flosic_ctx;
 /* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
  * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG,
  * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6), BC_ISOLATED.  The KRON solver
- * requires MIXED and every side <= 208.
+ * requires MIXED and every side <= 256.
  * Returns FLOSIC_ERR_ARG if opt is NULL. */
 int flosic_default_options(flosic_options* opt);
 

@@ -14,11 +14,13 @@
 // On the device the inverse is six dense 1-D transforms per orbital (three
 // forward with Q_d, three back with Q_d^T, the diagonal scaling folded into
 // the forward z pass), each a float32 matrix product over one direction's
-// lines.  A persistent CTA keeps the n x n transform matrix of its block in
-// shared memory and streams 64-line tiles through it: the next tile is
-// fetched into registers (coalesced) while the current one is multiplied
-// (8 x 4 outputs per thread, 2n threads), and results are stored from
-// registers.  The
+// lines.  T_d commutes with the reflection j -> n-1-j (it is persymmetric),
+// so its eigenvectors are even or odd and each transform is two half-size
+// products on the even and odd parts of the line (half the flops).  A
+// persistent CTA keeps the two half-size matrices of its block in shared
+// memory and streams 64-line tiles through them: the next tile is fetched
+// into registers (coalesced) while the current one is multiplied (8 x 4
+// outputs per thread, about 2n threads).  The
 // mixed refinement calls it as its float32 inner solve; the float-float
 // residual around it carries the accuracy to the requested tolerance.
 #include <cmath>
@@ -33,7 +35,7 @@ namespace {
 
 constexpr int kKronCols = 64;                  // lines per tile
 constexpr int kKronLd = kKronCols + 4;         // shared row stride of a tile (16-byte rows)
-constexpr int kKronMaxN = 208;                 // (208^2 + 208 * 68) floats fit in 227 KB
+constexpr int kKronMaxN = 256;                 // 2 (128^2) + 256 * 68 floats fit in 227 KB
 constexpr int kKronPre = kKronCols / 2;        // tile values per thread (2 n8 threads, n8 x 64 values)
 
 // Cyclic Jacobi eigen-decomposition of the symmetric n x n matrix A (row
@@ -166,24 +168,49 @@ __device__ __forceinline__ Tile tile_of(const BlkDesc& B, int axis, int i_orb, i
     return t;
 }
 
-// The thread's share of a tile (kKronPre values; the CTA has 2 * n8 threads
-// and a tile n8 * kKronCols values): coalesced along the contiguous
-// direction (j for x lines, c otherwise).
-__device__ __forceinline__ void tile_coords(int axis, int e, int n8, int& j, int& c) {
-    if (axis == 0) { c = e / n8; j = e - c * n8; }
-    else { j = e / kKronCols; c = e - j * kKronCols; }
+// The thread's kKronPre elements of a tile of R rows (R a multiple of 32,
+// the CTA's 2 Rmax threads): element k is (j0 + k jstep, c0 + k cstep),
+// coalesced along the contiguous direction.  x lines (j contiguous): lanes
+// take consecutive j, warp g covers line g / (R/32) + 2k, rows
+// 32 (g mod R/32) ..; y, z lines (c contiguous): lanes take consecutive c.
+struct TileMap {
+    int j0, jstep, c0, cstep;
+    bool on;
+};
+
+__device__ __forceinline__ TileMap tile_map(int axis, int tid, int nthr, int R) {
+    TileMap m;
+    if (axis == 0) {
+        const int rb = R >> 5, g0 = tid >> 5;
+        m.on = g0 < 2 * rb;
+        m.c0 = m.on ? g0 / rb : 0;
+        m.cstep = 2;
+        m.j0 = (tid & 31) + 32 * (m.on ? g0 % rb : 0);
+        m.jstep = 0;
+    } else {
+        m.on = true;
+        m.c0 = tid & (kKronCols - 1);
+        m.cstep = 0;
+        m.j0 = tid >> 6;
+        m.jstep = nthr >> 6;
+    }
+    return m;
 }
 
-__device__ __forceinline__ void tile_fetch(const float* __restrict__ in, const Tile& t, int axis, int n, int n8,
-                                           int tid, int nthr, float* pre) {
+__device__ __forceinline__ void tile_fetch(const float* __restrict__ in, const Tile& t, const TileMap& mp, int n,
+                                           float* pre) {
 #pragma unroll
     for (int k = 0; k < kKronPre; ++k) {
-        int j, c;
-        tile_coords(axis, tid + k * nthr, n8, j, c);
-        pre[k] = (c < t.ncol && j < n) ? __ldcs(in + t.cbase + (long long)c * t.cstride + (long long)j * t.jstride)
-                                       : 0.f;
+        const int j = mp.j0 + k * mp.jstep, c = mp.c0 + k * mp.cstep;
+        pre[k] = (mp.on && c < t.ncol && j < n)
+                     ? __ldcs(in + t.cbase + (long long)c * t.cstride + (long long)j * t.jstride)
+                     : 0.f;
     }
 }
+
+// rows of the two halves in shared memory: the even part padded to 8, the
+// whole tile to 32 (the odd part takes the rest)
+__host__ __device__ __forceinline__ int kron_rows(int n) { return ((round8((n + 1) / 2) + round8(n / 2)) + 31) & ~31; }
 
 // next item at or after it whose orbital is active (it1 if none)
 __device__ __forceinline__ long long next_active(const KronArgs& a, long long it, long long it1, int& b) {
@@ -197,11 +224,24 @@ __device__ __forceinline__ long long next_active(const KronArgs& a, long long it
     return it1;
 }
 
-// One pass: out[i][c] = sum_j P[j][i] in[j][c] over every tile of the
-// CTA's contiguous item range.  Thread (ib, cq) owns rows 8 ib .. 8 ib + 7
-// and columns 4 cq .. 4 cq + 3 of the n8 x kKronCols product; the next
-// tile's values are fetched into registers while the current one is
-// multiplied, and results go from registers straight to global memory.
+__device__ __forceinline__ int axis_n(const BlkDesc& B, int axis) {
+    return axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+}
+
+// One pass over every tile of the CTA's contiguous item range.
+//
+// Even/odd split: T_d commutes with the reflection j -> n-1-j, so its
+// eigenvectors are symmetric or antisymmetric and the transform splits into
+// two half-size products.  Forward: s_k = v_k + v_{n-1-k} (k < ns, the middle
+// point doubled), a_k = v_k - v_{n-1-k} (k < na); coefficients
+// c_s = Fs^T s, c_a = Fa^T a, stored as [c_s | c_a] along the line.
+// Inverse: S = Is c_s, A = Ia c_a; v_k = S_k + A_k, v_{n-1-k} = S_k - A_k,
+// v_mid = S_mid.  (Fs, Fa, Is, Ia carry the 1/sqrt 2 of the even/odd basis.)
+//
+// Thread (ib, cq) owns output rows 8 ib .. 8 ib + 7 (the symmetric half in
+// rows [0, ns8), the antisymmetric half in [ns8, ns8 + na8)) and columns
+// 4 cq .. 4 cq + 3; the next tile is fetched into registers while the
+// current one is multiplied.
 __global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long long total) {
     extern __shared__ __align__(16) float kron_smem[];
     const int tid = threadIdx.x;
@@ -214,64 +254,100 @@ __global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long lo
     long long item = next_active(a, it0, it1, bs);
     if (item >= it1) return;
     float pre[kKronPre];
-    int cur = -1, n = 0, n8 = 0;
     {
         const BlkDesc& B = a.blk[bs];
-        n = (a.axis == 0) ? B.nx : (a.axis == 1 ? B.ny : B.nz);
-        n8 = round8(n);
+        const int nn = axis_n(B, a.axis);
         const int groups = pass_groups(B, a.axis);
         const long long r = item - a.item0[bs];
-        tile_fetch(a.in, tile_of(B, a.axis, (int)(r / groups), (int)(r % groups)), a.axis, n, n8, tid, nthr, pre);
+        tile_fetch(a.in, tile_of(B, a.axis, (int)(r / groups), (int)(r % groups)),
+                   tile_map(a.axis, tid, nthr, kron_rows(nn)), nn, pre);
     }
-    float* Pm = kron_smem;
+    float* Ps = kron_smem;
+    float* Pa = nullptr;
+    float* S = nullptr;
+    int cur = -1, n = 0, ns = 0, na = 0, ns8 = 0, na8 = 0, R = 0;
+    TileMap mp{};
     const int cq = tid % (kKronCols / 4), ib = tid / (kKronCols / 4);
+    const int r0 = ib * 8, c0 = cq * 4;
     while (item < it1) {
         const int b = bs;
         const BlkDesc& B = a.blk[b];
         const int groups = pass_groups(B, a.axis);
-        const long long r = item - a.item0[b];
-        const Tile t = tile_of(B, a.axis, (int)(r / groups), (int)(r % groups));
-        __syncthreads();   // the previous tile's product has finished reading S (and P)
+        const long long rr = item - a.item0[b];
+        const Tile t = tile_of(B, a.axis, (int)(rr / groups), (int)(rr % groups));
+        __syncthreads();   // the previous tile is finished with S (and the matrices)
         if (b != cur) {
-            n = (a.axis == 0) ? B.nx : (a.axis == 1 ? B.ny : B.nz);
-            n8 = round8(n);
-            const float* src = a.mat + B.kq[a.axis] + (a.inverse ? (long long)n * n : 0);
-            for (int e = tid; e < n8 * n8; e += nthr) {
-                const int jj = e / n8, ii = e - jj * n8;
-                Pm[e] = (jj < n && ii < n) ? src[jj * n + ii] : 0.f;
+            n = axis_n(B, a.axis);
+            ns = (n + 1) / 2;
+            na = n / 2;
+            ns8 = round8(ns);
+            R = kron_rows(n);
+            na8 = R - ns8;
+            mp = tile_map(a.axis, tid, nthr, R);
+            Pa = Ps + ns8 * ns8;
+            S = Pa + na8 * na8;
+            const float* src = a.mat + B.kq[a.axis] + (a.inverse ? (long long)ns * ns + (long long)na * na : 0);
+            for (int e = tid; e < ns8 * ns8; e += nthr) {
+                const int jj = e / ns8, ii = e - jj * ns8;
+                Ps[e] = (jj < ns && ii < ns) ? src[jj * ns + ii] : 0.f;
+            }
+            const float* srca = src + (long long)ns * ns;
+            for (int e = tid; e < na8 * na8; e += nthr) {
+                const int jj = e / na8, ii = e - jj * na8;
+                Pa[e] = (jj < na && ii < na) ? srca[jj * na + ii] : 0.f;
             }
             cur = b;
         }
-        float* S = Pm + n8 * n8;
 #pragma unroll
         for (int k = 0; k < kKronPre; ++k) {
-            int j, c;
-            tile_coords(a.axis, tid + k * nthr, n8, j, c);
-            if (c < kKronCols && j < n8) S[j * kKronLd + c] = pre[k];   // (a smaller block's n8 leaves extra slots)
+            const int j = mp.j0 + k * mp.jstep, c = mp.c0 + k * mp.cstep;
+            if (mp.on && j < R) S[j * kKronLd + c] = pre[k];   // (a smaller block leaves extra slots)
         }
         __syncthreads();
+        if (!a.inverse) {   // fold each line into its even and odd parts
+            for (int e = tid; e < na * kKronCols; e += nthr) {
+                const int k = e >> 6, c = e & (kKronCols - 1);
+                const float u = S[k * kKronLd + c], w = S[(n - 1 - k) * kKronLd + c];
+                S[k * kKronLd + c] = u + w;
+                S[(n - 1 - k) * kKronLd + c] = u - w;
+            }
+            if (n & 1)
+                for (int c = tid; c < kKronCols; c += nthr) S[na * kKronLd + c] *= 2.f;
+            __syncthreads();
+        }
         // fetch the next active tile while this one is multiplied
         long long nxt = next_active(a, item + 1, it1, bs);
         if (nxt < it1) {
             const BlkDesc& Bn = a.blk[bs];
-            const int nn = (a.axis == 0) ? Bn.nx : (a.axis == 1 ? Bn.ny : Bn.nz);
+            const int nn = axis_n(Bn, a.axis);
             const int gn = pass_groups(Bn, a.axis);
             const long long rn = nxt - a.item0[bs];
-            tile_fetch(a.in, tile_of(Bn, a.axis, (int)(rn / gn), (int)(rn % gn)), a.axis, nn, round8(nn), tid,
-                       nthr, pre);
+            tile_fetch(a.in, tile_of(Bn, a.axis, (int)(rn / gn), (int)(rn % gn)),
+                       tile_map(a.axis, tid, nthr, kron_rows(nn)), nn, pre);
         }
-        const int r0 = ib * 8, c0 = cq * 4;
+        const bool sym = r0 < ns8;
+        const int m0 = sym ? r0 : r0 - ns8;             // first mode (or position) of this thread
+        const int K = sym ? ns : na;
+        const int pld = sym ? ns8 : na8;
+        const float* P = sym ? Ps : Pa;
+        // input row of the k-th term: forward s_k = row k, a_k = row n-1-k;
+        // inverse c_s[k] = row k, c_a[k] = row ns + k
+        const int rbase = sym ? 0 : (a.inverse ? ns : n - 1);
+        const int rstep = (!sym && !a.inverse) ? -1 : 1;
         float acc[8][4];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        if (r0 < n8) {
+        const bool comp = r0 < R;
+        if (comp) {
+            const float* srow = S + rbase * kKronLd + c0;
+            const int sstep = rstep * kKronLd;
 #pragma unroll 4
-            for (int j = 0; j < n; ++j) {
-                const float4 p0 = *reinterpret_cast<const float4*>(Pm + j * n8 + r0);
-                const float4 p1 = *reinterpret_cast<const float4*>(Pm + j * n8 + r0 + 4);
-                const float4 sv = *reinterpret_cast<const float4*>(S + j * kKronLd + c0);
+            for (int k = 0; k < K; ++k) {
+                const float4 p0 = *reinterpret_cast<const float4*>(P + k * pld + m0);
+                const float4 p1 = *reinterpret_cast<const float4*>(P + k * pld + m0 + 4);
+                const float4 sv = *reinterpret_cast<const float4*>(srow + k * sstep);
                 const float pr[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
                 const float sc[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
@@ -279,44 +355,72 @@ __global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long lo
 #pragma unroll
                     for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pr[u], sc[v], acc[u][v]);
             }
-            if (a.scale) {   // forward z pass: column c is the xy mode (i, j) = (t % nx, t / nx)
-                const long long sxy = (long long)B.nx * B.ny;
-                const float* lx = a.lam + B.kl[0];
-                const float* ly = a.lam + B.kl[1];
-                const float* lz = a.lam + B.kl[2];
-                float lxy[4];
+        }
+        const int nmode = sym ? ns : na;                 // valid outputs of this half
+        const int pos0 = sym ? 0 : ns;                   // their place along the line
+        if (!a.inverse) {
+            if (comp) {
+                if (a.scale) {   // forward z pass: column c is the xy mode (t % nx, t / nx)
+                    const long long sxy = (long long)B.nx * B.ny;
+                    const float* lx = a.lam + B.kl[0];
+                    const float* ly = a.lam + B.kl[1];
+                    const float* lz = a.lam + B.kl[2];
+                    float lxy[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const long long tt = (long long)t.q * kKronCols + c0 + v;
-                    const int ti = (int)(tt < sxy ? tt : 0);
-                    const int yi = ti / B.nx, xi = ti - yi * B.nx;
-                    lxy[v] = lx[xi] + ly[yi];
+                    for (int v = 0; v < 4; ++v) {
+                        const long long tt = (long long)t.q * kKronCols + c0 + v;
+                        const int ti = (int)(tt < sxy ? tt : 0);
+                        const int yi = ti / B.nx, xi = ti - yi * B.nx;
+                        lxy[v] = lx[xi] + ly[yi];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int m = m0 + u;
+                        const float l3 = lz[m < nmode ? pos0 + m : 0];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const float sm = lxy[v] + l3;
+                            acc[u][v] = (sm > 0.f) ? acc[u][v] / sm : 0.f;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = r0 + u < n ? r0 + u : 0;
-                    const float l3 = lz[k];
+                    const int m = m0 + u;
+                    if (m >= nmode) break;
+                    const long long off = t.cbase + (long long)(pos0 + m) * t.jstride;
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const float sm = lxy[v] + l3;
-                        acc[u][v] = (sm > 0.f) ? acc[u][v] / sm : 0.f;
+                        const int c = c0 + v;
+                        if (c < t.ncol) __stcs(a.out + off + (long long)c * t.cstride, acc[u][v]);
                     }
                 }
             }
-            // results straight from registers: rows r0 .. r0+7 of columns c0 .. c0+3
+        } else {
+            __syncthreads();   // every product has read its coefficients
+            if (comp) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = r0 + u;
-                if (i >= n) break;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int c = c0 + v;
-                    if (c < t.ncol) __stcs(a.out + t.cbase + (long long)c * t.cstride + (long long)i * t.jstride,
-                                           acc[u][v]);
+                for (int u = 0; u < 8; ++u) {
+                    const int m = m0 + u;
+                    if (m < nmode)
+                        *reinterpret_cast<float4*>(S + (pos0 + m) * kKronLd + c0) =
+                            make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
                 }
             }
+            __syncthreads();
+            // v_k = S_k + A_k, v_{n-1-k} = S_k - A_k, v_mid = S_mid (rows: S at k, A at ns + k)
+#pragma unroll 4
+            for (int k = 0; k < kKronPre; ++k) {
+                const int j = mp.j0 + k * mp.jstep, c = mp.c0 + k * mp.cstep;
+                if (!mp.on || j >= n || c >= t.ncol) continue;
+                float v;
+                if (j < na) v = S[j * kKronLd + c] + S[(ns + j) * kKronLd + c];
+                else if (j >= ns) v = S[(n - 1 - j) * kKronLd + c] - S[(ns + n - 1 - j) * kKronLd + c];
+                else v = S[j * kKronLd + c];
+                __stcs(a.out + t.cbase + (long long)c * t.cstride + (long long)j * t.jstride, v);
+            }
         }
-        if (a.flops && tid == 0) atomicAdd(a.flops, 2.0 * n * n * t.ncol);
+        if (a.flops && tid == 0) atomicAdd(a.flops, 2.0 * ((double)ns * ns + (double)na * na) * t.ncol);
         item = nxt;
     }
 }
@@ -334,10 +438,10 @@ __global__ void k_kron_done(int norb, CgState st) {
 
 int kron_max_n() { return kKronMaxN; }
 
-// Host set-up: the eigen-decomposition of every distinct 1-D operator
-// (n, h, periodic), Q and Q^T in float32, the eigenvalues (the periodic
-// constant mode set to exactly zero), per-block offsets and the tile counts
-// of the three passes.
+// Host set-up: for every distinct 1-D operator (n, h, periodic) the
+// eigen-decompositions of its even and odd blocks, the forward and inverse
+// half-size matrices in float32, the eigenvalues (the periodic constant mode
+// set to exactly zero), per-block offsets and the tile counts of the passes.
 cudaError_t setup_kron(flosic_ctx* c) {
     std::map<std::tuple<int, double, int>, std::pair<long long, long long>> seen;
     std::vector<float> mat, lam;
@@ -350,20 +454,59 @@ cudaError_t setup_kron(flosic_ctx* c) {
             const auto key = std::make_tuple(n, B.h, periodic);
             auto it = seen.find(key);
             if (it == seen.end()) {
-                std::vector<double> T = axis_operator(n, B.h, periodic != 0), V;
-                jacobi_eigen(n, T, V);
+                const std::vector<double> T = axis_operator(n, B.h, periodic != 0);
+                const int ns = (n + 1) / 2, na = n / 2;
+                // even/odd basis: e_k = (d_k + d_{n-1-k}) / sqrt 2 (k < na), e_mid = d_mid;
+                // o_k = (d_k - d_{n-1-k}) / sqrt 2; T is persymmetric, so U^T T U is block diagonal
+                const double r2 = std::sqrt(0.5);
+                std::vector<double> Ts((size_t)ns * ns), Ta((size_t)na * na), Vs, Va;
+                // support of e_k / o_k: points k and n-1-k with weights (w, w) / (w, -w)
+                auto proj = [&](int k, int l, bool odd) {
+                    const int pk[2] = {k, n - 1 - k}, pl[2] = {l, n - 1 - l};
+                    const double wk = (!odd && k == n - 1 - k) ? 1.0 : r2;
+                    const double wl = (!odd && l == n - 1 - l) ? 1.0 : r2;
+                    const int mk = (pk[0] == pk[1]) ? 1 : 2, ml = (pl[0] == pl[1]) ? 1 : 2;
+                    double v = 0.0;
+                    for (int a = 0; a < mk; ++a)
+                        for (int b = 0; b < ml; ++b) {
+                            const double sa = (odd && a == 1) ? -1.0 : 1.0, sb = (odd && b == 1) ? -1.0 : 1.0;
+                            v += sa * wk * T[(size_t)pk[a] * n + pl[b]] * sb * wl;
+                        }
+                    return v;
+                };
+                for (int k = 0; k < ns; ++k)
+                    for (int l = 0; l < ns; ++l) Ts[(size_t)k * ns + l] = proj(k, l, false);
+                for (int k = 0; k < na; ++k)
+                    for (int l = 0; l < na; ++l) Ta[(size_t)k * na + l] = proj(k, l, true);
+                jacobi_eigen(ns, Ts, Vs);
+                if (na > 0) jacobi_eigen(na, Ta, Va);
+                // forward Fs[k][m] = Vs[k][m] fs_k (fs = 1/sqrt 2, 1/2 at the middle: s_mid = 2 v_mid),
+                // Fa = Va / sqrt 2; inverse in the kernel's transposed form Is[m][k] = Vs[k][m] gs_k
+                // (gs = 1/sqrt 2, 1 at the middle), Ia[m][k] = Va[k][m] / sqrt 2
                 const long long qo = (long long)mat.size(), lo = (long long)lam.size();
-                mat.resize(mat.size() + 2 * (size_t)n * n);
-                for (int j = 0; j < n; ++j)
-                    for (int k = 0; k < n; ++k) {
-                        mat[qo + (size_t)j * n + k] = (float)V[(size_t)j * n + k];              // Q[j][k]
-                        mat[qo + (size_t)n * n + (size_t)k * n + j] = (float)V[(size_t)j * n + k];  // Q^T
+                mat.resize(mat.size() + 2 * ((size_t)ns * ns + (size_t)na * na));
+                float* Fs = mat.data() + qo;
+                float* Fa = Fs + (size_t)ns * ns;
+                float* Is = Fa + (size_t)na * na;
+                float* Ia = Is + (size_t)ns * ns;
+                for (int k = 0; k < ns; ++k)
+                    for (int m = 0; m < ns; ++m) {
+                        const double v = Vs[(size_t)k * ns + m];
+                        Fs[(size_t)k * ns + m] = (float)(v * (k < na ? r2 : 0.5));
+                        Is[(size_t)m * ns + k] = (float)(v * (k < na ? r2 : 1.0));
                     }
-                int kmin = 0;
-                for (int k = 0; k < n; ++k) {
-                    lam.push_back((float)T[(size_t)k * n + k]);
-                    if (std::fabs(T[(size_t)k * n + k]) < std::fabs(T[(size_t)kmin * n + kmin])) kmin = k;
+                for (int k = 0; k < na; ++k)
+                    for (int m = 0; m < na; ++m) {
+                        const double v = Va[(size_t)k * na + m] * r2;
+                        Fa[(size_t)k * na + m] = (float)v;
+                        Ia[(size_t)m * na + k] = (float)v;
+                    }
+                int kmin = 0;   // the periodic constant mode is symmetric
+                for (int k = 0; k < ns; ++k) {
+                    lam.push_back((float)Ts[(size_t)k * ns + k]);
+                    if (std::fabs(Ts[(size_t)k * ns + k]) < std::fabs(Ts[(size_t)kmin * ns + kmin])) kmin = k;
                 }
+                for (int k = 0; k < na; ++k) lam.push_back((float)Ta[(size_t)k * na + k]);
                 if (periodic) lam[lo + kmin] = 0.f;
                 it = seen.emplace(key, std::make_pair(qo, lo)).first;
             }
@@ -380,6 +523,7 @@ cudaError_t setup_kron(flosic_ctx* c) {
     for (int d = 0; d < 3; ++d) {
         long long acc = 0;
         int nmax = 8;
+        size_t smem = 0;   // the largest block's need (not monotone in n: the odd half fills the rows up to 32)
         for (int b = 0; b < c->nblk; ++b) {
             const BlkDesc& B = c->blk[b];
             items[(size_t)d * (c->nblk + 1) + b] = acc;
@@ -390,11 +534,14 @@ cudaError_t setup_kron(flosic_ctx* c) {
             acc += g * B.N;
             const int n = d == 0 ? B.nx : (d == 1 ? B.ny : B.nz);
             nmax = n > nmax ? n : nmax;
+            const int Rb = kron_rows(n), s8 = round8((n + 1) / 2), a8 = Rb - s8;
+            const size_t need = (size_t)(s8 * s8 + a8 * a8 + Rb * kKronLd) * sizeof(float);
+            smem = need > smem ? need : smem;
         }
         items[(size_t)d * (c->nblk + 1) + c->nblk] = acc;
         K.total[d] = acc;
-        K.threads[d] = 2 * round8(nmax);
-        K.smem[d] = (size_t)(round8(nmax) * round8(nmax) + round8(nmax) * kKronLd) * sizeof(float);
+        K.threads[d] = 2 * kron_rows(nmax);   // kron_rows is monotone in n
+        K.smem[d] = smem;
     }
     if (e == cudaSuccess) e = ctx_alloc(c, &K.items, items.size());
     if (e == cudaSuccess)
