@@ -269,6 +269,94 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
         }
 }
 
+// Mixed-precision variant of k_contract: 64-point steps whose operand values
+// (float32 from the bound loaders) are fetched into registers while the
+// previous step is multiplied; float sums of 16-point sub-tiles are
+// two-summed into (sum, low) pairs as in k_contract.
+template <int RM, class LA, class LB>
+__global__ void __launch_bounds__(256) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
+                                                    double* __restrict__ part, long long mat_elems) {
+    constexpr int KT = 64;
+    constexpr int NP = 16 * RM;
+    constexpr int PER = KT * NP / 256;   // values per thread and operand per step
+    __shared__ float As[KT][NP + 1];
+    __shared__ float Bs[KT][NP + 1];
+    const BlkDesc& B = blk[blockIdx.y];
+    const int N = B.N;
+    const long long G = B.G;
+    const int kp = blockIdx.x;
+    const long long kb = G * kp / kparts, ke = G * (kp + 1) / kparts;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const auto fa = la.bindf(B);
+    const auto fb = lb.bindf(B);
+    // element t of a step: orbital (tid >> 6) + 4 t, point tid & 63 (coalesced along the points)
+    const int kk0 = tid & (KT - 1), i0 = tid >> 6;
+    float pa[PER], pb[PER];
+    auto fetch = [&](long long k0) {
+        const long long g = k0 + kk0;
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int i = i0 + 4 * t;
+            const bool ok = (i < N) && (g < ke);
+            pa[t] = ok ? fa(i, g) : 0.f;
+            pb[t] = ok ? fb(i, g) : 0.f;
+        }
+    };
+    float acc[RM][RM], acl[RM][RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < RM; ++q) acc[r][q] = acl[r][q] = 0.f;
+    if (kb < ke) fetch(kb);
+    for (long long k0 = kb; k0 < ke; k0 += KT) {
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            As[kk0][i0 + 4 * t] = pa[t];
+            Bs[kk0][i0 + 4 * t] = pb[t];
+        }
+        __syncthreads();
+        if (k0 + KT < ke) fetch(k0 + KT);
+#pragma unroll
+        for (int sub = 0; sub < KT / 16; ++sub) {
+            float tacc[RM][RM];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < RM; ++q) tacc[r][q] = 0.f;
+#pragma unroll 4
+            for (int kk = sub * 16; kk < sub * 16 + 16; ++kk) {
+                float a[RM], bv[RM];
+#pragma unroll
+                for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+                for (int q = 0; q < RM; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+                for (int r = 0; r < RM; ++r)
+#pragma unroll
+                    for (int q = 0; q < RM; ++q) tacc[r][q] = fmaf(a[r], bv[q], tacc[r][q]);
+            }
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < RM; ++q) {   // two-sum into the pair
+                    const float a = acc[r][q], b = tacc[r][q];
+                    const float s2 = a + b, bb = s2 - a;
+                    acl[r][q] += (a - (s2 - bb)) + (b - bb);
+                    acc[r][q] = s2;
+                }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int q = 0; q < RM; ++q) {
+            const int i = ty + 16 * r, j = tx + 16 * q;
+            if (i < N && j < N)
+                part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = f2d(acc[r][q]) + f2d(acl[r][q]);
+        }
+}
+
 // out[e] = sum_kp part[kp][e] in a fixed order
 __global__ void k_sum_parts(const double* __restrict__ part, int kparts, long long n,
                             double* __restrict__ out) {
@@ -292,9 +380,9 @@ static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_
     double* part = c->ws.mat_part;
     const bool f32 = (c->opt.precision == FLOSIC_MIXED);
     if (f32) {
-        if (nmax <= 16) k_contract<1, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 32) k_contract<2, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 64) k_contract<4, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        if (nmax <= 16) k_contract_f<1><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 32) k_contract_f<2><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 64) k_contract_f<4><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
         else k_contract<8, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
     } else {
         if (nmax <= 16) k_contract<1, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);

@@ -378,9 +378,9 @@ __global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long lo
                         const int m = m0 + u;
                         const float l3 = lz[m < nmode ? pos0 + m : 0];
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) {
+                        for (int v = 0; v < 4; ++v) {   // (fast division: 2 ulp, far below the solve's accuracy)
                             const float sm = lxy[v] + l3;
-                            acc[u][v] = (sm > 0.f) ? acc[u][v] / sm : 0.f;
+                            acc[u][v] = (sm > 0.f) ? __fdividef(acc[u][v], sm) : 0.f;
                         }
                     }
                 }
