@@ -384,15 +384,37 @@ __global__ void __launch_bounds__(2 * kKronMaxN) k_kron_pass(KronArgs a, long lo
                         }
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int m = m0 + u;
-                    if (m >= nmode) break;
-                    const long long off = t.cbase + (long long)(pos0 + m) * t.jstride;
+                if (a.axis == 0) {   // per line c: 8 consecutive positions (two 16-byte stores when aligned)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const int c = c0 + v;
-                        if (c < t.ncol) __stcs(a.out + off + (long long)c * t.cstride, acc[u][v]);
+                        if (c >= t.ncol) break;
+                        const long long off = t.cbase + (long long)c * t.cstride + pos0 + m0;
+                        if (m0 + 7 < nmode && (off & 3) == 0) {
+                            __stcs(reinterpret_cast<float4*>(a.out + off),
+                                   make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]));
+                            __stcs(reinterpret_cast<float4*>(a.out + off + 4),
+                                   make_float4(acc[4][v], acc[5][v], acc[6][v], acc[7][v]));
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (m0 + u < nmode) __stcs(a.out + off + u, acc[u][v]);
+                        }
+                    }
+                } else {             // per position: 4 consecutive lines (one 16-byte store when aligned)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int m = m0 + u;
+                        if (m >= nmode) break;
+                        const long long off = t.cbase + (long long)(pos0 + m) * t.jstride + c0;
+                        if (c0 + 3 < t.ncol && (off & 3) == 0) {
+                            __stcs(reinterpret_cast<float4*>(a.out + off),
+                                   make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]));
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                if (c0 + v < t.ncol) __stcs(a.out + off + v, acc[u][v]);
+                        }
                     }
                 }
             }
