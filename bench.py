@@ -479,7 +479,8 @@ def run_uneven(args):
     build.build()
     systems = synth.make_uneven_batch(nsys=64, seed_base=2000 + 100000 * rank)
     norb = sum(sum(x.norb) for x in systems)
-    ctx = Context(systems, precision=1, cg_tol=1e-10, preconditioner=1)
+    solver = {"pcg": 0, "aar": 1, "kron": 2}[args.solver]
+    ctx = Context(systems, precision=1, cg_tol=1e-10, preconditioner=1, solver=solver)
     dev = torch.device("cuda", local)
     psi = torch.tensor(np.concatenate([p.ravel() for x in systems for p in x.psi]), device=dev)
     fods = torch.tensor(np.concatenate([f.ravel() for x in systems for f in x.fods]), device=dev)
@@ -511,7 +512,7 @@ def run_uneven(args):
                           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                           "dtype": "f32-cg+f64", "data": "synthetic",
                           "config": {"workload": "64 systems, 48^3..128^3, 2..40 orbitals (%d orbitals, %d spin blocks)"
-                                     % (norb, ctx.nblk), "tma_blocks": None,
+                                     % (norb, ctx.nblk), "solver": args.solver,
                                      "cg_iters_per_orbital_mean": float(iters.float().mean().item())},
                           "clocks": clocks}), flush=True)
     D.barrier()
@@ -531,7 +532,8 @@ def run_fodopt(args):
     build.build()
     s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)
     norb = sum(s.norb)
-    ctx = Context([s], precision=1, cg_tol=1e-10, preconditioner=1)
+    solver = {"pcg": 0, "aar": 1, "kron": 2}[args.solver]
+    ctx = Context([s], precision=1, cg_tol=1e-10, preconditioner=1, solver=solver)
     dev = torch.device("cuda", local)
     psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device=dev)
     fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods]), device=dev)
@@ -560,6 +562,7 @@ def run_fodopt(args):
                           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f32-cg+f64", "data": "synthetic",
                           "config": {"workload": "128^3 h=0.2, 32+32 orbitals, FIRE over 64 FODs",
+                                     "solver": args.solver,
                                      "orbital_solves_per_s": world * norb * 1e3 / ms,
                                      "cg_iters_cold_first_step": it[0],
                                      "cg_iters_warm_mean": float(np.mean(it[args.warmup + 1:])),

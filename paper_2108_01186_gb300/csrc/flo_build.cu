@@ -612,12 +612,14 @@ struct LoadPhibarPsi {   // rows 0..N-1: Phibar; rows N..2N-1: psi
 };
 
 // TC: arithmetic of the products and sums (float in mixed precision, with
-// operands and results converted by integer operations).
-template <int RJ, class TC, class LX>
+// operands and results converted by integer operations).  A CTA takes tiles
+// of 32 PTS points (lane l: points l + 32 q, q < PTS), so each chunk of E
+// staged in shared memory serves PTS x 32 points.
+template <int RJ, int PTS, class TC, class LX>
 __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ blk,
                                                   const double* __restrict__ E, int mult, LX lx,
                                                   double* __restrict__ out) {
-    constexpr int TG = 32, KC = 32;
+    constexpr int TG = 32 * PTS, KC = 32;
     __shared__ TC Es[8 * RJ][KC + 1];
     __shared__ TC Xs[KC][TG];
     const BlkDesc& B = blk[blockIdx.y];
@@ -627,10 +629,11 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
     constexpr bool kF = std::is_same<TC, float>::value;
     const auto fx = lx.bindf(B);
     for (long long tile = blockIdx.x; tile * TG < B.G; tile += gridDim.x) {
-        const long long g = tile * TG + lane;
-        TC acc[RJ];
+        TC acc[RJ][PTS];
 #pragma unroll
-        for (int r = 0; r < RJ; ++r) acc[r] = TC(0);
+        for (int r = 0; r < RJ; ++r)
+#pragma unroll
+            for (int q = 0; q < PTS; ++q) acc[r][q] = TC(0);
         for (int kc = 0; kc < K; kc += KC) {
             for (int e = threadIdx.x; e < 8 * RJ * KC; e += 256) {
                 const int j = e / KC, kk = e % KC;
@@ -639,26 +642,39 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
                 else Es[j][kk] = ok ? Eb[(long long)j * K + kc + kk] : 0.0;
             }
             for (int kk = wq; kk < KC; kk += 8) {
-                const bool ok = kc + kk < K && g < B.G;
-                if constexpr (kF) Xs[kk][lane] = ok ? fx(kc + kk, g) : 0.f;
-                else Xs[kk][lane] = ok ? lx(B, kc + kk, g) : 0.0;
+#pragma unroll
+                for (int q = 0; q < PTS; ++q) {
+                    const long long g = tile * TG + lane + 32 * q;
+                    const bool ok = kc + kk < K && g < B.G;
+                    if constexpr (kF) Xs[kk][lane + 32 * q] = ok ? fx(kc + kk, g) : 0.f;
+                    else Xs[kk][lane + 32 * q] = ok ? lx(B, kc + kk, g) : 0.0;
+                }
             }
             __syncthreads();
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                const TC x = Xs[kk][lane];
+                TC x[PTS];
 #pragma unroll
-                for (int r = 0; r < RJ; ++r) acc[r] += Es[wq + 8 * r][kk] * x;
+                for (int q = 0; q < PTS; ++q) x[q] = Xs[kk][lane + 32 * q];
+#pragma unroll
+                for (int r = 0; r < RJ; ++r) {
+                    const TC ev = Es[wq + 8 * r][kk];
+#pragma unroll
+                    for (int q = 0; q < PTS; ++q) acc[r][q] += ev * x[q];
+                }
             }
             __syncthreads();
         }
-        if (g < B.G) {
+#pragma unroll
+        for (int q = 0; q < PTS; ++q) {
+            const long long g = tile * TG + lane + 32 * q;
+            if (g >= B.G) continue;
 #pragma unroll
             for (int r = 0; r < RJ; ++r) {
                 const int j = wq + 8 * r;
                 if (j < N) {
-                    if constexpr (kF) out[B.off + (long long)j * B.G + g] = f2d(acc[r]);
-                    else out[B.off + (long long)j * B.G + g] = acc[r];
+                    if constexpr (kF) out[B.off + (long long)j * B.G + g] = f2d(acc[r][q]);
+                    else out[B.off + (long long)j * B.G + g] = acc[r][q];
                 }
             }
         }
@@ -670,18 +686,20 @@ static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, doub
     const int nmax = max_block_n(c);
     long long gmax = 0;
     for (const auto& b : c->blk) gmax = b.G > gmax ? b.G : gmax;
-    const unsigned gx = (unsigned)((gmax + 31) / 32 < 65535 ? (gmax + 31) / 32 : 65535);
-    const dim3 grid(gx, c->nblk);
-    if (c->opt.precision == FLOSIC_MIXED) {
-        if (nmax <= 16) k_smallmat<2, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else if (nmax <= 32) k_smallmat<4, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else if (nmax <= 64) k_smallmat<8, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else k_smallmat<16, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-    } else {
-        if (nmax <= 16) k_smallmat<2, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else if (nmax <= 32) k_smallmat<4, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else if (nmax <= 64) k_smallmat<8, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
-        else k_smallmat<16, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    if (c->opt.precision == FLOSIC_MIXED) {   // 32-point tiles (128-point tiles measured no faster)
+        const unsigned gx = (unsigned)((gmax + 31) / 32 < 65535 ? (gmax + 31) / 32 : 65535);
+        const dim3 grid(gx, c->nblk);
+        if (nmax <= 16) k_smallmat<2, 1, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 32) k_smallmat<4, 1, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 64) k_smallmat<8, 1, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else k_smallmat<16, 1, float><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+    } else {                                   // 32-point tiles
+        const unsigned gx = (unsigned)((gmax + 31) / 32 < 65535 ? (gmax + 31) / 32 : 65535);
+        const dim3 grid(gx, c->nblk);
+        if (nmax <= 16) k_smallmat<2, 1, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 32) k_smallmat<4, 1, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else if (nmax <= 64) k_smallmat<8, 1, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
+        else k_smallmat<16, 1, double><<<grid, 256, 0, s>>>(c->d_blk, E, mult, lx, out);
     }
     note_launch(c);
 }

@@ -8,6 +8,7 @@ free of the oracle and of any randomness.
 
   python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64] [--solver kron]
   python -m paper_2108_01186_gb300.profile_case --case flo     (FLO build, 96^3, 16+16 orbitals)
+  python -m paper_2108_01186_gb300.profile_case --case step --norb 12   (forward + adjoint, 128^3, 12+12)
 """
 import argparse
 
@@ -19,12 +20,16 @@ def main():
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--solver", default="pcg", choices=["pcg", "kron"],
                     help="inner solver of the mixed refinement (kron: the Kronecker-product transforms)")
-    ap.add_argument("--case", default="poisson", choices=["poisson", "flo"],
+    ap.add_argument("--case", default="poisson", choices=["poisson", "flo", "step"],
                     help="poisson: one multigrid-PCG solve of Gaussian densities; flo: two FLO builds "
-                         "(tensor-core overlap) of the seeded 96^3, 16+16-orbital system")
+                         "(tensor-core overlap) of the seeded 96^3, 16+16-orbital system; step: one "
+                         "forward + adjoint step (Kronecker solver) of a seeded 128^3 system with "
+                         "norb + norb orbitals")
     args = ap.parse_args()
     if args.case == "flo":
         return flo_case(args)
+    if args.case == "step":
+        return step_case(args)
     import torch
     from paper_2108_01186_gb300 import build
     from paper_2108_01186_gb300.flosic import Context
@@ -57,6 +62,24 @@ def flo_case(args):
         phi, S, Q = ctx.build_flos(psi, fods)
     torch.cuda.synchronize()
     print("sum of S", float(S.double().sum()))
+
+
+def step_case(args):
+    import numpy as np
+    import torch
+    from paper_2108_01186_gb300 import build, synth
+    from paper_2108_01186_gb300.flosic import Context
+
+    build.build()
+    s = synth.make_system(128, 0.2, 8, [args.norb, args.norb], seed=77)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device="cuda")
+    fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods]), device="cuda")
+    ctx = Context([s], precision=1, cg_tol=1e-10, solver=2)
+    out = ctx.forward(psi, fods)
+    gE = torch.ones(1, dtype=torch.float64, device="cuda")
+    dpsi, dfod = ctx.sic_backward(psi, fods, out["phi"], out["V"], gE)
+    torch.cuda.synchronize()
+    print("E_sic", float(out["E_sic"][0]), "max |dE/da|", float(dfod.abs().max()))
 
 
 if __name__ == "__main__":
