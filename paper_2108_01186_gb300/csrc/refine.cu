@@ -62,6 +62,27 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
     const LvlDesc& D = L[P.b];
     float bb = 0.f;
     tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {   // aligned group of four points: 16-byte accesses
+            const float4 b01 = *reinterpret_cast<const float4*>(b + g);       // pairs g, g+1
+            const float4 b23 = *reinterpret_cast<const float4*>(b + g + 2);   // pairs g+2, g+3
+            const float4 bh = make_float4(b01.x, b01.z, b23.x, b23.z);
+            bb += bh.x * bh.x + bh.y * bh.y + bh.z * bh.z + bh.w * bh.w;
+            if (warm) {
+                const double2 v01 = *reinterpret_cast<const double2*>(V + g);
+                const double2 v23 = *reinterpret_cast<const double2*>(V + g + 2);
+                const float2 a = d2ff(v01.x), c = d2ff(v01.y), e = d2ff(v23.x), f = d2ff(v23.y);
+                *reinterpret_cast<float4*>(x + g) = make_float4(a.x, a.y, c.x, c.y);
+                *reinterpret_cast<float4*>(x + g + 2) = make_float4(e.x, e.y, f.x, f.y);
+            } else {
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4*>(x + g) = z4;
+                *reinterpret_cast<float4*>(x + g + 2) = z4;
+                *reinterpret_cast<float4*>(r32 + g) = bh;
+                *reinterpret_cast<float4*>(d32 + g) = z4;
+                if (p32) *reinterpret_cast<float4*>(p32 + g) = bh;
+            }
+            return;
+        }
         for (int k = 0; k < n; ++k) {
             const float bh = b[g + k].x;
             bb += bh * bh;
@@ -157,6 +178,14 @@ __global__ void __launch_bounds__(256) k_join_ff(const BlkDesc* __restrict__ blk
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
     tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {   // aligned group of four points: 16-byte accesses
+            const float4 a = *reinterpret_cast<const float4*>(x + g);
+            const float4 c = *reinterpret_cast<const float4*>(x + g + 2);
+            *reinterpret_cast<double2*>(V + g) = make_double2(ff2d(make_float2(a.x, a.y)), ff2d(make_float2(a.z, a.w)));
+            *reinterpret_cast<double2*>(V + g + 2) =
+                make_double2(ff2d(make_float2(c.x, c.y)), ff2d(make_float2(c.z, c.w)));
+            return;
+        }
         for (int k = 0; k < n; ++k) V[g + k] = ff2d(x[g + k]);
     });
 }

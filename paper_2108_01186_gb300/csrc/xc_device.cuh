@@ -44,24 +44,31 @@ __device__ __forceinline__ void lsda_pol(double n, double rho_min, double& eps, 
 }
 
 // The same functional in float32 arithmetic (mixed-precision path; the
-// energies are still summed in float64).
+// energies are still summed in float64).  One cube root serves both k and
+// rs (rs = (3/4pi)^{1/3} / n^{1/3}, k = (6/pi)^{1/3} n^{1/3}); reciprocals and
+// the inverse square root use the fast float forms (a few ulp, far below the
+// path's 1e-6 Ha target per orbital energy); log1p keeps its accuracy for the
+// small arguments of low densities.
 __device__ __forceinline__ void lsda_pol_f(float n, float rho_min, float& eps, float& v) {
     if (!(n > rho_min)) {
         eps = 0.0f;
         v = 0.0f;
         return;
     }
-    const float k = cbrtf(n * (float)(6.0 / 3.14159265358979323846));
-    const float rs = cbrtf((float)(3.0 / (4.0 * 3.14159265358979323846)) / n);
-    const float srs = sqrtf(rs);
+    const float cn = cbrtf(n);
+    const float k = (float)1.2407009817988002 * cn;                   // (6/pi)^{1/3} n^{1/3}
+    const float rs = __fdividef((float)0.62035049089940001, cn);      // (3/(4 pi))^{1/3} / n^{1/3}
+    const float irs = rsqrtf(rs);
+    const float srs = rs * irs;
     using P = Pw92Ferro;
     const float A = (float)P::A;
     const float den = 2.0f * A * ((float)P::b1 * srs + (float)P::b2 * rs + (float)P::b3 * rs * srs + (float)P::b4 * rs * rs);
-    const float dden = A * ((float)P::b1 / srs + 2.0f * (float)P::b2 + 3.0f * (float)P::b3 * srs + 4.0f * (float)P::b4 * rs);
-    const float lg = log1pf(1.0f / den);
+    const float dden = A * ((float)P::b1 * irs + 2.0f * (float)P::b2 + 3.0f * (float)P::b3 * srs + 4.0f * (float)P::b4 * rs);
+    const float iden = __fdividef(1.0f, den);
+    const float lg = log1pf(iden);
     const float pre = -2.0f * A * (1.0f + (float)P::a1 * rs);
     const float ec = pre * lg;
-    const float dec = -2.0f * A * (float)P::a1 * lg - pre * dden / (den * den + den);
+    const float dec = -2.0f * A * (float)P::a1 * lg - __fdividef(pre * dden * iden, 1.0f + den);
     eps = -0.75f * k + ec;
     v = -k + ec - rs * (1.0f / 3.0f) * dec;
 }
