@@ -245,24 +245,30 @@ __global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __re
                          double* __restrict__ rhs) {
     const BlkDesc& B = blk[b];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= B.nbnd) return;
-    const int g = bidx[B.bnd0 + j];
-    const double* src = bcoef + (B.bnd0 + (long long)j) * 10;
-    if (kFF) {
+    if (kFF) {   // the block's moments as pairs, converted once per CTA
+        extern __shared__ float2 mom_ff[];
+        for (int e = threadIdx.x; e < 10 * B.N; e += blockDim.x) mom_ff[e] = d2ff(mom[B.orb0 * 10 + e]);
+        __syncthreads();
+        if (j >= B.nbnd) return;
+        const int g = bidx[B.bnd0 + j];
+        const double* src = bcoef + (B.bnd0 + (long long)j) * 10;
         ff cf[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) cf[k] = to_ff(d2ff(src[k]));
         float2* rp = reinterpret_cast<float2*>(rhs);
         for (int i = 0; i < B.N; ++i) {
-            const double* mo = mom + (B.orb0 + i) * 10;
+            const float2* mo = mom_ff + i * 10;
             ff acc = {0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 10; ++k) acc = ff_add(acc, ff_mul(to_ff(d2ff(mo[k])), cf[k]));
+            for (int k = 0; k < 10; ++k) acc = ff_add(acc, ff_mul(to_ff(mo[k]), cf[k]));
             const long long idx = B.off + (long long)i * B.G + g;
             const ff v = ff_add(to_ff(rp[idx]), acc);
             rp[idx] = make_float2(v.h, v.l);
         }
     } else {
+        if (j >= B.nbnd) return;
+        const int g = bidx[B.bnd0 + j];
+        const double* src = bcoef + (B.bnd0 + (long long)j) * 10;
         double cf[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) cf[k] = src[k];
@@ -319,7 +325,8 @@ void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaS
         const int nb = c->blk[k].nbnd;
         if (nb == 0) continue;
         if (ff)
-            k_rhs_bc<true><<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b);
+            k_rhs_bc<true><<<(nb + 127) / 128, 128, sizeof(float2) * 10 * c->blk[k].N, s>>>(c->d_blk, k, c->d_bidx,
+                                                                                       c->d_bcoef, c->ws.mom, b);
         else
             k_rhs_bc<false><<<(nb + 127) / 128, 128, 0, s>>>(c->d_blk, k, c->d_bidx, c->d_bcoef, c->ws.mom, b);
         note_launch(c);
