@@ -324,9 +324,19 @@ def run_gpu(args):
         # peak = 152 SMs x 128 FP32 lanes x 2 flops x the 2.07 GHz maximum clock
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         tfl = prof["kernel_bytes"] / (prof["kernel_ms"] / 1e3) / 1e12 if prof["kernel_ms"] > 0 else 0.0
+        kt = None   # DRAM bytes per solve from the committed capture, while kron.cu is unchanged
+        try:
+            kd = json.load(open(os.path.join(ROOT, "profiles", "kron_traffic.json")))
+            ksrc = os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "kron.cu")
+            if (kd.get("source_sha") == hashlib.sha256(open(ksrc, "rb").read()).hexdigest()[:16]
+                    and args.workload == "128"):
+                kt = kd.get("traffic_bytes_per_solve_scaled")
+        except (OSError, ValueError):
+            kt = None
         roof = {"bound": "alu", "kernel": "k_kron_pass (6 passes per solve)", "achieved": round(tfl, 2),
                 "peak": round(fp32_peak, 1), "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "unit": "TFLOP/s", "frac": round(tfl / fp32_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(tfl / fp32_peak, 4), "traffic": kt,
+                "traffic_per": "solve (6 launches)", "alg_bytes_per_solve": 6 * 8 * norb * s.G,
                 "alg_flops_per_solve": prof["kernel_bytes"] / launches,
                 "avg_solve_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
                 "share_of_step": round(prof["kernel_ms"] / ms, 4)}
