@@ -16,7 +16,9 @@
  *  - A batch holds nsys independent systems.  System s has an nx*ny*nz
  *    interior grid with spacing h (bohr); point (i,j,k) sits at
  *    origin + h*(i,j,k) and has flat index (k*ny + j)*nx + i (x fastest).
- *    G = nx*ny*nz.  Orbitals vanish outside the interior (zero Dirichlet).
+ *    G = nx*ny*nz.  Orbitals vanish outside the interior (zero Dirichlet),
+ *    except along the periodic directions of flosic_options.boundary, where
+ *    they wrap around the cell.
  *  - A "spin block" is one spin of one system with N = norb[spin] orbitals.
  *    Blocks are ordered system-major, then spin.  Orbital-sized arrays
  *    (psi, phi, V, dE_dpsi) are the blocks' [N][G] float64 arrays packed
@@ -164,13 +166,18 @@ int flosic_build_flos(flosic_ctx* ctx, const double* psi, const double* fods,
                       double* phi, double* S, double* S_mhalf, void* stream);
 
 /* Steps a6-a7 (Sec. II.A): per orbital, -Delta_h V_i = 4 pi phi_i^2 with the
- * 12th-order centred Laplacian and Dirichlet values from the l <= 2
- * multipole expansion of phi_i^2 about the box centre on the 6-layer ghost
- * shell; conjugate gradients to ||b - A V|| <= cg_tol ||b||.
+ * 12th-order centred Laplacian and, by flosic_options.boundary, Dirichlet
+ * values from the l <= 2 multipole expansion of phi_i^2 about the box centre
+ * on the 6-layer ghost shell (isolated), a neutralising background with
+ * zero-mean V (periodic), or the dipole-corrected planar potential on the
+ * z ghost planes (slab); solved to ||b - A V|| <= cg_tol ||b|| by the
+ * options' solver (FP64: float64 CG; MIXED: float32 inner solves -- CG, AAR
+ * or the Kronecker-product inverse -- inside a float-float refinement).
  * In:  phi [sum N*G] float64.  In/out: V [sum N*G] float64 (in: warm start
  * if warm_start != 0, ignored otherwise; out: the potentials).
- * Out (may be NULL): iters [orbitals] int32 (CG iterations per orbital, all
- * precisions summed), conv_flags [orbitals] int32 (1 = converged).
+ * Out (may be NULL): iters [orbitals] int32 (inner iterations per orbital,
+ * all refinement rounds summed; one per Kronecker application),
+ * conv_flags [orbitals] int32 (1 = converged).
  * Errors: ARG, CUDA, NOCONV (some orbital hit max_iter; V holds the last
  * iterate).  Waits for `stream` before returning. */
 int flosic_orbital_poisson(flosic_ctx* ctx, const double* phi, double* V,
