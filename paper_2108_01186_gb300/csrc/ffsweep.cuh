@@ -32,7 +32,12 @@ static inline cudaError_t upload_ffsweep_weights() {
 // load(g) -> float2 pair of the operand at flat index g (only called for
 // points inside the grid); epi(g, centre, lap) with lap = h^2 Delta_h u at g
 // as a pair, called for every point of the tile inside the grid.
-template <class Load, class Epi>
+// kSloppy: the seven weighted terms are accumulated with the two-sum of the
+// high parts and a plain sum of the low parts (error ~ eps^2 times the sum
+// of the terms' magnitudes, ~1e-12 of the result for the smooth potentials
+// of the refinement residual) instead of the renormalised pair addition
+// (error ~ eps^2 of the result, kept for the Hamiltonian apply).
+template <bool kSloppy = false, class Load, class Epi>
 __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, Load load, Epi epi,
                                            ff (*plane)[kPX]) {
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -104,7 +109,13 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
             for (int m = 1; m <= kHalf; ++m) {
                 const ff sm = ff_sum6(plane[ly[k]][lx - m], plane[ly[k]][lx + m], plane[ly[k] - m][lx],
                                       plane[ly[k] + m][lx], qk[kHalf - m], qk[kHalf + m]);
-                acc = ff_add(acc, ff_mul(w[m], sm));
+                const ff tm = ff_mul(w[m], sm);
+                if constexpr (kSloppy) {
+                    const ff s2 = ff_two_sum(acc.h, tm.h);
+                    acc = ff_quick(s2.h, s2.l + (acc.l + tm.l));
+                } else {
+                    acc = ff_add(acc, tm);
+                }
             }
             if (in[k]) epi(P.base + z * sz + cc[k], qk[kHalf], acc);
         }

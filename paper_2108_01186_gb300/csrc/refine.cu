@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
     const LvlDesc& D = L[P.b];
     const ff ih2 = to_ff(d2ff(1.0 / (D.h * D.h)));   // once per CTA
     float rrf = 0.f;
-    ff_sweep12(
+    ff_sweep12<true>(
         D, P, [&](long long g) { return x[g]; },
         [&](long long g, ff, ff acc) {
             // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
