@@ -63,11 +63,11 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
     }
     const float2 zero2 = make_float2(0.f, 0.f);
     ff q0[2 * kHalf + 1], q1[2 * kHalf + 1];
+    const bool perz = (D.per & 4) != 0;
 #pragma unroll
-    const bool pz = (D.per & 4) != 0;
     for (int j = 0; j < 2 * kHalf; ++j) {
         int zz = P.z0 - kHalf + j;
-        if (pz) zz = wrap_coord(zz, D.nz);
+        if (perz) zz = wrap_coord(zz, D.nz);
         const bool okz = zz >= 0 && zz < D.nz;
         q0[j] = to_ff((in0 && okz) ? load(P.base + zz * sz + c0) : zero2);
         q1[j] = to_ff((in1 && okz) ? load(P.base + zz * sz + c1) : zero2);
@@ -87,7 +87,7 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
         }
         {
             int zz = z + kHalf;
-            if (pz) zz = wrap_coord(zz, D.nz);
+            if (perz) zz = wrap_coord(zz, D.nz);
             q0[2 * kHalf] = to_ff((in0 && zz < D.nz) ? load(P.base + zz * sz + c0) : zero2);
             q1[2 * kHalf] = to_ff((in1 && zz < D.nz) ? load(P.base + zz * sz + c1) : zero2);
         }
