@@ -83,7 +83,8 @@ enum { FLOSIC_SOLVER_PCG = 0, FLOSIC_SOLVER_AAR = 1, FLOSIC_SOLVER_KRON = 2 };
 enum { FLOSIC_BC_ISOLATED = 0, FLOSIC_BC_PERIODIC = 1, FLOSIC_BC_SLAB = 2 };
 
 typedef struct {
-    int nx, ny, nz;       /* interior grid points per direction (>= 1) */
+    int nx, ny, nz;       /* interior grid points per direction (>= 1;
+                             nx*ny*nz < 2^31) */
     double h;             /* grid spacing, bohr (> 0) */
     double origin[3];     /* position of point (0,0,0), bohr */
     int nspin;            /* 1 or 2 */
@@ -92,8 +93,10 @@ typedef struct {
 
 typedef struct {
     int precision;        /* FLOSIC_FP64: every step in float64.
-                             FLOSIC_MIXED: Poisson CG in float32 with float64
-                             residual refinement; the rest float64. */
+                             FLOSIC_MIXED: float32 inner Poisson solves
+                             inside a float-float residual refinement, the
+                             overlap on the tensor cores (split bf16); the
+                             rest float64. */
     double cg_tol;        /* relative residual ||b - A V|| / ||b|| per solve */
     int max_iter;         /* CG iteration cap per solve (all refinement
                              sweeps together) */
@@ -110,9 +113,10 @@ typedef struct {
     double illcond_tol;   /* ILLCOND when lambda_min(S) < tol*lambda_max(S) */
     int preconditioner;   /* FLOSIC_PC_NONE or FLOSIC_PC_MG (multigrid
                              V-cycle on the 7-point Laplacian) */
-    int solver;           /* FLOSIC_SOLVER_PCG (default) or FLOSIC_SOLVER_AAR:
-                             the float32 inner solver of the MIXED path
-                             (AAR requires MIXED) */
+    int solver;           /* FLOSIC_SOLVER_PCG (default), FLOSIC_SOLVER_AAR
+                             or FLOSIC_SOLVER_KRON: the float32 inner solver
+                             of the MIXED path (AAR and KRON require MIXED;
+                             FP64 runs PCG) */
     double aar_omega;     /* AAR Richardson relaxation (default 0.6) */
     double aar_beta;      /* AAR Anderson mixing (default 0.6) */
     int aar_m;            /* AAR history length, 1..8 (default 7) */
@@ -140,8 +144,8 @@ int flosic_create(flosic_ctx** ctx, const flosic_system* sys, int nsys,
 /* Frees the context and its workspace.  NULL is a no-op. */
 int flosic_destroy(flosic_ctx* ctx);
 
-/* Message of the last failing call on ctx (or of the last failed
- * flosic_create when ctx is NULL).  Owned by the library. */
+/* Message of the last failing call on ctx (or of the calling thread's last
+ * failed flosic_create when ctx is NULL).  Owned by the library. */
 const char* flosic_last_error(const flosic_ctx* ctx);
 
 /* Packed sizes (host array out[6]): [0] orbitals in the batch, [1] elements

@@ -13,7 +13,7 @@
 using namespace flosic;
 
 namespace {
-std::string g_create_error;   // message of the last failed flosic_create
+thread_local std::string g_create_error;   // message of this thread's last failed flosic_create
 
 int fail(flosic_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
@@ -224,6 +224,11 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         if (y.nx < 1 || y.ny < 1 || y.nz < 1 || !(y.h > 0.0) || !std::isfinite(y.h) ||
             !std::isfinite(y.origin[0]) || !std::isfinite(y.origin[1]) || !std::isfinite(y.origin[2])) {
             snprintf(buf, sizeof buf, "system %d: bad grid", s);
+            g_create_error = buf;
+            return FLOSIC_ERR_ARG;
+        }
+        if ((long long)y.nx * y.ny * y.nz > kMaxGridPoints) {   // block-local point indices are 32-bit
+            snprintf(buf, sizeof buf, "system %d: more than %lld grid points", s, kMaxGridPoints);
             g_create_error = buf;
             return FLOSIC_ERR_ARG;
         }
@@ -609,15 +614,24 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
 int flosic_profile(flosic_ctx* c, int enable) {
     if (!c) return FLOSIC_ERR_ARG;
     if (enable && c->prof_ev.empty()) {
-        c->prof_ev.resize(2 * 1024);
-        for (auto& e : c->prof_ev) {
-            int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
-            if (rc) return rc;
-        }
-        c->ov_ev.resize(2 * 64);
-        for (auto& e : c->ov_ev) {
-            int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
-            if (rc) return rc;
+        // both pools or neither: a partial pool is destroyed again
+        auto make = [&](std::vector<cudaEvent_t>& pool, int n) {
+            for (int k = 0; k < n; ++k) {
+                cudaEvent_t e = nullptr;
+                int rc = check_cuda(c, cudaEventCreate(&e), "cudaEventCreate");
+                if (rc) return rc;
+                pool.push_back(e);
+            }
+            return (int)FLOSIC_OK;
+        };
+        int rc = make(c->prof_ev, 2 * 1024);
+        if (!rc) rc = make(c->ov_ev, 2 * 64);
+        if (rc) {
+            for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+            for (cudaEvent_t e : c->ov_ev) cudaEventDestroy(e);
+            c->prof_ev.clear();
+            c->ov_ev.clear();
+            return rc;
         }
     }
     c->profiling = enable != 0;

@@ -15,6 +15,7 @@ constexpr int kHalf = 6;          // half-width of the 12th-order stencil
 constexpr int kChunk = 1024;      // grid points per chunk of a chunked kernel
 constexpr int kChunkThreads = 256;
 constexpr int kMaxN = 128;        // orbitals per spin block supported
+constexpr long long kMaxGridPoints = 2147483647LL;   // nx*ny*nz per system (32-bit point indices)
 constexpr double kPi = 3.14159265358979323846;
 
 // One spin block of one system, as seen by the kernels.

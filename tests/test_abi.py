@@ -134,3 +134,13 @@ def test_create_rejects_bad_extended_grids(lib, dims, opts):
     s = _sys(nx=dims[0], ny=dims[1], nz=dims[2])
     assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, ctypes.byref(o)) == F.FLOSIC_ERR_ARG
     assert b"13" in lib.flosic_last_error(None) or b"256" in lib.flosic_last_error(None)
+
+
+def test_create_rejects_grids_beyond_32bit_point_indices(lib):
+    # block-local point indices are 32-bit: nx*ny*nz must stay below 2^31
+    from paper_2108_01186_gb300 import flosic as F
+    h = ctypes.c_void_p()
+    s = _sys(nx=1291, ny=1291, nz=1291)
+    assert lib.flosic_create(ctypes.byref(h), ctypes.byref(s), 1, None) == F.FLOSIC_ERR_ARG
+    assert not h.value
+    assert b"grid points" in lib.flosic_last_error(None)
