@@ -8,7 +8,7 @@ free of the oracle and of any randomness.
 
   python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64] [--solver kron]
   python -m paper_2108_01186_gb300.profile_case --case flo     (FLO build, 96^3, 16+16 orbitals)
-  python -m paper_2108_01186_gb300.profile_case --case step --norb 12   (forward + adjoint, 128^3, 12+12)
+  python -m paper_2108_01186_gb300.profile_case --case step --norb 12   (forward + adjoint, n^3, 12+12)
 """
 import argparse
 
@@ -23,8 +23,8 @@ def main():
     ap.add_argument("--case", default="poisson", choices=["poisson", "flo", "step"],
                     help="poisson: one multigrid-PCG solve of Gaussian densities; flo: two FLO builds "
                          "(tensor-core overlap) of the seeded 96^3, 16+16-orbital system; step: one "
-                         "forward + adjoint step (Kronecker solver) of a seeded 128^3 system with "
-                         "norb + norb orbitals")
+                         "forward + adjoint step (Kronecker solver) of a seeded n^3 system "
+                         "(spacing 0.2 bohr) with norb + norb orbitals")
     args = ap.parse_args()
     if args.case == "flo":
         return flo_case(args)
@@ -71,7 +71,7 @@ def step_case(args):
     from paper_2108_01186_gb300.flosic import Context
 
     build.build()
-    s = synth.make_system(128, 0.2, 8, [args.norb, args.norb], seed=77)
+    s = synth.make_system(args.n, 0.2, 8, [args.norb, args.norb], seed=77)
     psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device="cuda")
     fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods]), device="cuda")
     ctx = Context([s], precision=1, cg_tol=1e-10, solver=2)
