@@ -681,6 +681,162 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
     }
 }
 
+// Raw operand loaders of the row-tile kernel below: load() issues the
+// float64 loads of X_k(g) and returns them untouched (so the next k group
+// can be in flight while the current one is multiplied); cvt() forms the
+// float32 value with integer-op conversions.
+struct RawPsi {
+    static constexpr int kGroup = 16;   // k values fetched ahead
+    using Raw = double;
+    const double* p;
+    struct Bound {
+        const double* p;
+        long long G;
+        __device__ __forceinline__ Raw load(int k, long long g) const { return __ldcs(p + (long long)k * G + g); }
+        __device__ __forceinline__ float cvt(int, Raw r) const { return d2f(r); }
+    };
+    __device__ __forceinline__ static Raw zero() { return 0.0; }
+    __device__ __forceinline__ Bound bind(const BlkDesc& B) const { return Bound{p + B.off, B.G}; }
+};
+
+// rows k < N: Phibar_k = coef V_k^SIC phi_k (two loads); rows N..2N-1: psi
+struct RawPhibarPsi {
+    static constexpr int kGroup = 8;
+    using Raw = double2;
+    const double* phi;
+    const double* vsic;
+    const double* gE;
+    const double* psi;
+    struct Bound {
+        const double *phi, *vsic, *psi;
+        long long G;
+        int N;
+        float coef;
+        __device__ __forceinline__ Raw load(int k, long long g) const {
+            if (k < N) {
+                const long long e = (long long)k * G + g;
+                return make_double2(__ldcs(phi + e), __ldcs(vsic + e));
+            }
+            return make_double2(__ldcs(psi + (long long)(k - N) * G + g), 0.0);
+        }
+        __device__ __forceinline__ float cvt(int k, Raw r) const {
+            return (k < N) ? coef * d2f(r.y) * d2f(r.x) : d2f(r.x);
+        }
+    };
+    __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
+    __device__ __forceinline__ Bound bind(const BlkDesc& B) const {
+        return Bound{phi + B.off, vsic + B.off, psi + B.off, B.G, B.N, (float)(gE[B.sys] * 2.0 * B.dV)};
+    }
+};
+
+constexpr int kRowTile = 256;     // points per tile of the row-tile kernel (one per thread)
+constexpr int kRowMaxK = 64;      // K = mult N it takes (N <= 32, mult <= 2)
+
+// out_j(g) = sum_k E_jk X_k(g) for blocks with N <= NJ <= 32 (mixed
+// precision): one point per thread with all N outputs in registers, E (as
+// float, transposed) in shared memory for the whole block, so a k step is
+// NJ/4 broadcast 16-byte shared loads and NJ FMAs per point.  Persistent
+// CTAs walk a contiguous range of the (block, 256-point tile) items; the raw
+// loads of the next k group (or of the next tile's first group) are issued
+// before the current group is multiplied.
+template <int NJ, class RX>
+__global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __restrict__ blk, int nblk,
+                                                               long long total, const double* __restrict__ E,
+                                                               int mult, RX rx, double* __restrict__ out) {
+    constexpr int KU = RX::kGroup;
+    __shared__ float4 es4[(kRowMaxK + 16) * (NJ / 4)];   // [k][j] rows, zero for k >= K
+    float* es = reinterpret_cast<float*>(es4);
+    const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * per_cta;
+    const long long it1 = it0 + per_cta < total ? it0 + per_cta : total;
+    if (it0 >= it1) return;   // uniform over the CTA
+    // block of the first item
+    int b = 0;
+    long long base = 0;
+    for (;;) {
+        const long long nt = (blk[b].G + kRowTile - 1) / kRowTile;
+        if (it0 < base + nt || b + 1 >= nblk) break;
+        base += nt;
+        ++b;
+    }
+    const int tid = threadIdx.x;
+    long long item = it0;
+    while (item < it1) {
+        const BlkDesc& B = blk[b];
+        const int N = B.N, K = mult * N;
+        const int ngroup = (K + KU - 1) / KU;
+        const long long ntile = (B.G + kRowTile - 1) / kRowTile;
+        const long long item_end = (base + ntile < it1) ? base + ntile : it1;
+        {   // E of this block, transposed, as float
+            const double* Eb = E + (long long)mult * B.moff;
+            __syncthreads();   // the previous block's products are done with es
+            for (int e = tid; e < ngroup * KU * NJ; e += kRowTile) {
+                const int k = e / NJ, j = e - k * NJ;
+                es[e] = (j < N && k < K) ? d2f(Eb[(long long)j * K + k]) : 0.f;
+            }
+            __syncthreads();
+        }
+        const auto fx = rx.bind(B);
+        typename RX::Raw raw[KU];
+        auto fetch = [&](long long tl, int grp) {
+            const long long g = tl * kRowTile + tid;
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int k = grp * KU + u;
+                raw[u] = (g < B.G && k < K) ? fx.load(k, g) : RX::zero();
+            }
+        };
+        fetch(item - base, 0);
+        for (; item < item_end; ++item) {
+            const long long g = (item - base) * kRowTile + tid;
+            float acc[NJ];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[j] = 0.f;
+            for (int grp = 0; grp < ngroup; ++grp) {
+                float x[KU];
+#pragma unroll
+                for (int u = 0; u < KU; ++u) x[u] = fx.cvt(grp * KU + u, raw[u]);
+                if (grp + 1 < ngroup) fetch(item - base, grp + 1);
+                else if (item + 1 < item_end) fetch(item + 1 - base, 0);
+                const float4* er = es4 + (long long)grp * KU * (NJ / 4);
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+#pragma unroll
+                    for (int q = 0; q < NJ / 4; ++q) {
+                        const float4 ev = er[u * (NJ / 4) + q];
+                        acc[4 * q + 0] = fmaf(ev.x, x[u], acc[4 * q + 0]);
+                        acc[4 * q + 1] = fmaf(ev.y, x[u], acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(ev.z, x[u], acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(ev.w, x[u], acc[4 * q + 3]);
+                    }
+                }
+            }
+            if (g < B.G) {
+                double* o = out + B.off + g;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+                    if (j < N) __stcs(o + (long long)j * B.G, f2d(acc[j]));
+            }
+        }
+        base += ntile;
+        ++b;
+    }
+}
+
+template <class RX>
+static bool smallmat_rows(const flosic_ctx* c, const double* E, int mult, RX rx, double* out, cudaStream_t s) {
+    const int nmax = max_block_n(c);
+    if (c->opt.precision != FLOSIC_MIXED || nmax > 32 || mult * nmax > kRowMaxK) return false;
+    long long total = 0;
+    for (const auto& b : c->blk) total += (b.G + kRowTile - 1) / kRowTile;
+    const unsigned grid = (unsigned)(total < 2 * 152 ? total : 2 * 152);   // one wave of 2 CTAs per SM
+    if (nmax <= 8) k_smallmat_rows<8><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
+    else if (nmax <= 16) k_smallmat_rows<16><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
+    else k_smallmat_rows<32><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
+    note_launch(c);
+    return true;
+}
+
 template <class LX>
 static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, double* out, cudaStream_t s) {
     const int nmax = max_block_n(c);
@@ -705,7 +861,7 @@ static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, doub
 }
 
 void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s) {
-    smallmat(c, c->ws.C, 1, LoadPsi{psi}, phi, s);
+    if (!smallmat_rows(c, c->ws.C, 1, RawPsi{psi}, phi, s)) smallmat(c, c->ws.C, 1, LoadPsi{psi}, phi, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -801,8 +957,10 @@ __global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __r
 
 void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* vsic,
                    const double* gE, const double* fods, double* dpsi, cudaStream_t s) {
-    LoadPhibarPsi lx{LoadPhibar{phi, vsic, gE}, psi};
-    smallmat(c, c->ws.E2, 2, lx, dpsi, s);
+    if (!smallmat_rows(c, c->ws.E2, 2, RawPhibarPsi{phi, vsic, gE, psi}, dpsi, s)) {
+        LoadPhibarPsi lx{LoadPhibar{phi, vsic, gE}, psi};
+        smallmat(c, c->ws.E2, 2, lx, dpsi, s);
+    }
     k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
                                                                  c->ws.vbar, fods, dpsi); note_launch(c);
 }
