@@ -312,7 +312,15 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
                         bidx.push_back((z * b.ny + y) * b.nx + x);
         b.nbnd = (int)((long long)bidx.size() - b.bnd0);
     }
-    int kp = (608 + c->nblk - 1) / c->nblk;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 152;
+        cudaGetLastError();   // a failure here surfaces at the first allocation
+        c->num_sms = sms;
+    }
+    int kp = (4 * c->num_sms + c->nblk - 1) / c->nblk;   // one wave of four 256-thread CTAs per SM
     c->kparts = kp < 1 ? 1 : (kp > 1024 ? 1024 : kp);
     std::vector<int> chunk_orb((size_t)chunk);
     for (const BlkDesc& b : c->blk)

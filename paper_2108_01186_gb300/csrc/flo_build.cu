@@ -157,6 +157,11 @@ struct LoadPsi {
         const double* p;
         long long G;
         __device__ __forceinline__ float operator()(int i, long long g) const { return d2f(p[(long long)i * G + g]); }
+        // split form: the float64 load alone (kept in flight), then the conversion
+        using Raw = double;
+        __device__ __forceinline__ Raw raw(int i, long long g) const { return __ldcs(p + (long long)i * G + g); }
+        __device__ __forceinline__ static Raw zero() { return 0.0; }
+        __device__ __forceinline__ float cvt(Raw r) const { return d2f(r); }
     };
     __device__ __forceinline__ F bindf(const BlkDesc& B) const { return F{p + B.off, B.G}; }
 };
@@ -180,6 +185,13 @@ struct LoadPhibar {
             const long long k = (long long)i * G + g;
             return coef * d2f(vsic[k]) * d2f(phi[k]);
         }
+        using Raw = double2;   // (phi, V^SIC)
+        __device__ __forceinline__ Raw raw(int i, long long g) const {
+            const long long k = (long long)i * G + g;
+            return make_double2(__ldcs(phi + k), __ldcs(vsic + k));
+        }
+        __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
+        __device__ __forceinline__ float cvt(Raw r) const { return coef * d2f(r.y) * d2f(r.x); }
     };
     __device__ __forceinline__ F bindf(const BlkDesc& B) const {
         return F{phi + B.off, vsic + B.off, B.G, (float)(gE[B.sys] * 2.0 * B.dV)};
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
 // previous step is multiplied; float sums of 16-point sub-tiles are
 // two-summed into (sum, low) pairs as in k_contract.
 template <int RM, class LA, class LB>
-__global__ void __launch_bounds__(256) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
+__global__ void __launch_bounds__(256, RM <= 2 ? 3 : 1) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
                                                     double* __restrict__ part, long long mat_elems) {
     constexpr int KT = 64;
     constexpr int NP = 16 * RM;
@@ -289,17 +301,31 @@ __global__ void __launch_bounds__(256) k_contract_f(const BlkDesc* __restrict__ 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const auto fa = la.bindf(B);
     const auto fb = lb.bindf(B);
-    // element t of a step: orbital (tid >> 6) + 4 t, point tid & 63 (coalesced along the points)
+    // element t of a step: orbital (tid >> 6) + 4 t, point tid & 63 (coalesced along the points).
+    // RM <= 2: the next step's float64 loads stay raw in registers while this
+    // step is multiplied and are converted when they are staged; RM = 4 (16
+    // values per operand and thread) converts them as they arrive.
+    constexpr bool kRaw = RM <= 2;
     const int kk0 = tid & (KT - 1), i0 = tid >> 6;
-    float pa[PER], pb[PER];
+    using FA = std::remove_const_t<decltype(fa)>;
+    using FB = std::remove_const_t<decltype(fb)>;
+    using RA = std::conditional_t<kRaw, typename FA::Raw, float>;
+    using RB = std::conditional_t<kRaw, typename FB::Raw, float>;
+    RA pa[PER];
+    RB pb[PER];
     auto fetch = [&](long long k0) {
         const long long g = k0 + kk0;
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
             const int i = i0 + 4 * t;
             const bool ok = (i < N) && (g < ke);
-            pa[t] = ok ? fa(i, g) : 0.f;
-            pb[t] = ok ? fb(i, g) : 0.f;
+            if constexpr (kRaw) {
+                pa[t] = ok ? fa.raw(i, g) : FA::zero();
+                pb[t] = ok ? fb.raw(i, g) : FB::zero();
+            } else {
+                pa[t] = ok ? fa(i, g) : 0.f;
+                pb[t] = ok ? fb(i, g) : 0.f;
+            }
         }
     };
     float acc[RM][RM], acl[RM][RM];
@@ -312,8 +338,13 @@ __global__ void __launch_bounds__(256) k_contract_f(const BlkDesc* __restrict__ 
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
-            As[kk0][i0 + 4 * t] = pa[t];
-            Bs[kk0][i0 + 4 * t] = pb[t];
+            if constexpr (kRaw) {
+                As[kk0][i0 + 4 * t] = fa.cvt(pa[t]);
+                Bs[kk0][i0 + 4 * t] = fb.cvt(pb[t]);
+            } else {
+                As[kk0][i0 + 4 * t] = pa[t];
+                Bs[kk0][i0 + 4 * t] = pb[t];
+            }
         }
         __syncthreads();
         if (k0 + KT < ke) fetch(k0 + KT);
@@ -376,22 +407,27 @@ static int max_block_n(const flosic_ctx* c) {
 template <class LA, class LB>
 static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_t s) {
     const int nmax = max_block_n(c);
-    const dim3 grid(c->kparts, c->nblk);
-    double* part = c->ws.mat_part;
     const bool f32 = (c->opt.precision == FLOSIC_MIXED);
+    int kparts = c->kparts;   // one wave: 4 CTAs per SM, 3 for the raw-prefetch float kernels
+    if (f32 && nmax <= 32) {
+        const int k3 = (3 * c->num_sms + c->nblk - 1) / c->nblk;
+        kparts = k3 < 1 ? 1 : (k3 < kparts ? k3 : kparts);
+    }
+    const dim3 grid(kparts, c->nblk);
+    double* part = c->ws.mat_part;
     if (f32) {
-        if (nmax <= 16) k_contract_f<1><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 32) k_contract_f<2><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 64) k_contract_f<4><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else k_contract<8, float><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        if (nmax <= 16) k_contract_f<1><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 32) k_contract_f<2><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 64) k_contract_f<4><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else k_contract<8, float><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
     } else {
-        if (nmax <= 16) k_contract<1, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 32) k_contract<2, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else if (nmax <= 64) k_contract<4, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
-        else k_contract<8, double><<<grid, 256, 0, s>>>(c->d_blk, c->kparts, la, lb, part, c->mat_elems);
+        if (nmax <= 16) k_contract<1, double><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 32) k_contract<2, double><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else if (nmax <= 64) k_contract<4, double><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
+        else k_contract<8, double><<<grid, 256, 0, s>>>(c->d_blk, kparts, la, lb, part, c->mat_elems);
     }
     note_launch(c);
-    k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, c->kparts, c->mat_elems, out); note_launch(c);
+    k_sum_parts<<<(unsigned)((c->mat_elems + 255) / 256), 256, 0, s>>>(part, kparts, c->mat_elems, out); note_launch(c);
 }
 
 // Raw Gram psi psi^T per block: tensor cores (split-BF16) in mixed precision,
@@ -829,7 +865,8 @@ static bool smallmat_rows(const flosic_ctx* c, const double* E, int mult, RX rx,
     if (c->opt.precision != FLOSIC_MIXED || nmax > 32 || mult * nmax > kRowMaxK) return false;
     long long total = 0;
     for (const auto& b : c->blk) total += (b.G + kRowTile - 1) / kRowTile;
-    const unsigned grid = (unsigned)(total < 2 * 152 ? total : 2 * 152);   // one wave of 2 CTAs per SM
+    const long long wave = 2LL * c->num_sms;   // one wave of 2 CTAs per SM
+    const unsigned grid = (unsigned)(total < wave ? total : wave);
     if (nmax <= 8) k_smallmat_rows<8><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
     else if (nmax <= 16) k_smallmat_rows<16><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
     else k_smallmat_rows<32><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);

@@ -180,6 +180,7 @@ struct flosic_ctx {
     long long orb_elems = 0, vavg_elems = 0, mat_elems = 0, nchunk_total = 0;
     long long sgrid_elems = 0;   // sum over systems of the grid points (per-system fields)
     int kparts = 0;                         // K-splits of the grid contractions
+    int num_sms = 152;                      // multiprocessors of the context's device
     std::vector<int> h_orb_blk;
     int* d_orb_blk = nullptr;               // [norb] block of each orbital
     int* d_chunk_orb = nullptr;             // [nchunk_total] orbital of each chunk
