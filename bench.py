@@ -139,7 +139,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle, timed on the host cores on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(system, it_sample=20):
+def oracle_sample(system, it_sample=50):
     """Times the FP64 oracle on a bounded sample of one step and scales it to
     solves/s: both spins' FLO build, energies and adjoint in full; Poisson
     for `cores` orbitals at once (OpenMP over orbitals) for it_sample CG
