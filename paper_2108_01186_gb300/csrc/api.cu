@@ -484,12 +484,8 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     if (e == cudaSuccess && !bidx.empty())
         e = cudaMemcpy(c->d_bidx, bidx.data(), sizeof(int) * bidx.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !bidx.empty()) e = setup_boundary(c);
-    if (e == cudaSuccess) {
-        int nmax = 0;
-        for (const auto& b : c->blk) nmax = b.N > nmax ? b.N : nmax;
-        e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double) * nmax * nmax));
-    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lowdin_smem(c));
     if (e == cudaSuccess && o.precision == FLOSIC_MIXED) e = setup_gram_tc();
     if (e == cudaSuccess && M.enabled) {
         const bool f32 = (o.precision == FLOSIC_MIXED);

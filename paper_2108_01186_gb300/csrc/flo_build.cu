@@ -463,27 +463,34 @@ __device__ void mm(int N, const double* A, bool ta, const double* Bm, bool tb, d
     __syncthreads();
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric matrix S (shared, N x N,
-// row-major), round-robin ordering so that the N/2 rotations of a round are
-// disjoint and run in parallel.  On exit S is diagonal (the eigenvalues) and
-// U (global) holds the eigenvectors as columns.
-__device__ void jacobi_eig(int N, double* S, double* U) {
+// Cyclic Jacobi eigen-decomposition of the symmetric matrix S (N x N,
+// row-major, shared memory), round-robin ordering so that the N/2 rotations
+// of a round are disjoint and run in parallel.  On exit S is diagonal (the
+// eigenvalues) and U holds the eigenvectors as columns.  Stops when the
+// squared off-diagonal norm is at most tol times the squared diagonal one,
+// or after max_sweeps sweeps.  T = float runs the rounds in float32.
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <class T>
+__device__ void jacobi_eig_t(int N, T* S, T* U, double tol, int max_sweeps) {
     __shared__ int rp[kMaxN / 2], rq[kMaxN / 2];
-    __shared__ double rc[kMaxN / 2], rs[kMaxN / 2];
+    __shared__ T rc[kMaxN / 2], rs[kMaxN / 2];
     __shared__ double scratch[32];
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[e] = (e / N == e % N) ? 1.0 : 0.0;
+    const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[e] = (e / N == e % N) ? T(1) : T(0);
     __syncthreads();
     const int N2 = N + (N & 1);
     const int m = N2 - 1;
-    for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
-        double off = 0.0, dg = 0.0;
+    for (int sweep = 0; sweep < max_sweeps && N > 1; ++sweep) {
+        T off = T(0), dg = T(0);
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-            const double v = S[e];
+            const T v = S[e];
             if (e / N == e % N) dg += v * v; else off += v * v;
         }
-        off = block_sum(off, scratch);
-        dg = block_sum(dg, scratch);
-        if (off <= 1e-30 * dg) break;
+        const double offs = block_sum(off, scratch);
+        const double dgs = block_sum(dg, scratch);
+        if (offs <= tol * dgs) break;
         for (int round = 0; round < m; ++round) {
             if (threadIdx.x < N2 / 2) {
                 const int t = threadIdx.x;
@@ -496,20 +503,20 @@ __device__ void jacobi_eig(int N, double* S, double* U) {
                     q = (round - t + m) % m + 1;
                 }
                 if (p > q) { const int tmp = p; p = q; q = tmp; }
-                double c = 1.0, s = 0.0;
+                T c = T(1), sn = T(0);
                 if (q < N) {
-                    const double apq = S[p * N + q];
-                    if (fabs(apq) > 1e-300) {
-                        const double th = (S[q * N + q] - S[p * N + p]) / (2.0 * apq);
-                        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = rsqrt(tt * tt + 1.0);
-                        s = tt * c;
+                    const T apq = S[p * N + q];
+                    if (fabs(apq) > tiny) {
+                        const T th = (S[q * N + q] - S[p * N + p]) / (T(2) * apq);
+                        const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                        c = rsq(tt * tt + T(1));
+                        sn = tt * c;
                     }
                 }
                 rp[t] = p;
                 rq[t] = q < N ? q : p;   // dummy partner: identity rotation
                 rc[t] = c;
-                rs[t] = (q < N) ? s : 0.0;
+                rs[t] = (q < N) ? sn : T(0);
             }
             __syncthreads();
             const int np = N2 / 2;
@@ -517,35 +524,51 @@ __device__ void jacobi_eig(int N, double* S, double* U) {
                 const int t = e / N, k = e % N;
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
-                const double c = rc[t], s = rs[t];
-                const double a = S[p * N + k], b = S[q * N + k];
-                S[p * N + k] = c * a - s * b;
-                S[q * N + k] = s * a + c * b;
+                const T c = rc[t], sn = rs[t];
+                const T a = S[p * N + k], b = S[q * N + k];
+                S[p * N + k] = c * a - sn * b;
+                S[q * N + k] = sn * a + c * b;
             }
             __syncthreads();
             for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // columns p, q
                 const int t = e / N, k = e % N;
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
-                const double c = rc[t], s = rs[t];
-                double a = S[k * N + p], b = S[k * N + q];
-                S[k * N + p] = c * a - s * b;
-                S[k * N + q] = s * a + c * b;
+                const T c = rc[t], sn = rs[t];
+                T a = S[k * N + p], b = S[k * N + q];
+                S[k * N + p] = c * a - sn * b;
+                S[k * N + q] = sn * a + c * b;
                 a = U[k * N + p];
                 b = U[k * N + q];
-                U[k * N + p] = c * a - s * b;
-                U[k * N + q] = s * a + c * b;
+                U[k * N + p] = c * a - sn * b;
+                U[k * N + q] = sn * a + c * b;
             }
             __syncthreads();
         }
     }
 }
 
+__device__ void jacobi_eig(int N, double* S, double* U) { jacobi_eig_t<double>(N, S, U, 1e-30, 40); }
+
+// Blocks of up to this many orbitals take the two-stage eigen-solver in the
+// mixed path (its four N x N work matrices fit in shared memory).
+constexpr int kLowdinTwoStageMax = 64;
+
 // Per block: T, S, eigen-pairs, Q = S^{-1/2}, C = Q T; ILLCOND / NONFINITE.
+//
+// two_stage (mixed path, every block N <= kLowdinTwoStageMax): float32 Jacobi
+// sweeps to an off-diagonal norm of ~3e-6, two float64 Newton-Schulz steps
+// U <- U (3I - U^T U) / 2 that make U orthogonal to float64 rounding, then
+// float64 Jacobi on the nearly diagonal U^T S U (two sweeps) and U <- U V.
+// The float64 sweeps, each a chain of barrier-separated rounds on one SM's
+// float64 pipe, drop from ~8 to ~2; the eigenpairs are those of the float64
+// decomposition to rounding.  Otherwise float64 Jacobi from the start.
 __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk, Workspace w,
-                                                double illcond, double* S_out, double* Q_out) {
+                                                double illcond, double* S_out, double* Q_out,
+                                                int two_stage) {
     extern __shared__ double Ssh[];
     __shared__ double scratch[32];
+    __shared__ double il[kMaxN];
     const BlkDesc& B = blk[blockIdx.x];
     const int N = B.N;
     const long long mo = B.moff;
@@ -596,9 +619,43 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
         if (S_out) S_out[mo + e] = Ssh[e];
     }
     __syncthreads();
-    jacobi_eig(N, Ssh, U);
+    if (two_stage) {
+        double* U64 = Ssh + N * N;   // shared: U, V (float64), S and U in float32
+        double* V64 = U64 + N * N;
+        float* S32 = reinterpret_cast<float*>(V64 + N * N);
+        float* U32 = S32 + N * N;
+        double* Y = w.tmp + w.mat_elems + mo;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) S32[e] = d2f(Ssh[e]);
+        __syncthreads();
+        jacobi_eig_t<float>(N, S32, U32, 1e-11, 12);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) U64[e] = f2d(U32[e]);
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {   // U <- U (3I - U^T U) / 2
+            mm(N, U64, true, U64, false, X);
+            for (int e = threadIdx.x; e < N * N; e += blockDim.x)
+                X[e] = ((e / N == e % N) ? 1.5 : 0.0) - 0.5 * X[e];
+            __syncthreads();
+            mm(N, U64, false, X, false, Y);
+            for (int e = threadIdx.x; e < N * N; e += blockDim.x) U64[e] = Y[e];
+            __syncthreads();
+        }
+        mm(N, Ssh, false, U64, false, X);   // X = S U
+        mm(N, U64, true, X, false, Y);      // Y = U^T S U
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // exact symmetry
+            const int i = e / N, j = e % N;
+            Ssh[e] = (i == j) ? Y[e] : 0.5 * (Y[e] + Y[j * N + i]);
+        }
+        __syncthreads();
+        jacobi_eig_t<double>(N, Ssh, V64, 1e-30, 40);
+        mm(N, U64, false, V64, false, U);   // U = U V
+    } else {
+        jacobi_eig(N, Ssh, U);
+    }
     double* lam = w.lam + B.orb0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) lam[i] = Ssh[i * N + i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        lam[i] = Ssh[i * N + i];
+        il[i] = rsqrt(fmax(Ssh[i * N + i], 1e-300));
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double lmin = lam[0], lmax = lam[0];
@@ -611,7 +668,7 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // Q = U L^{-1/2} U^T
         const int i = e / N, j = e % N;
         double s = 0.0;
-        for (int k = 0; k < N; ++k) s += U[i * N + k] * U[j * N + k] * rsqrt(fmax(lam[k], 1e-300));
+        for (int k = 0; k < N; ++k) s += U[i * N + k] * U[j * N + k] * il[k];
         Q[e] = s;
         if (Q_out) Q_out[mo + e] = s;
     }
@@ -619,10 +676,19 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
     mm(N, Q, false, T, false, w.C + mo);   // C = Q T
 }
 
+static bool lowdin_two_stage(const flosic_ctx* c) {
+    return c->opt.precision == FLOSIC_MIXED && max_block_n(c) <= kLowdinTwoStageMax;
+}
+
+size_t lowdin_smem(const flosic_ctx* c) {
+    const size_t n2 = (size_t)max_block_n(c) * max_block_n(c);
+    return lowdin_two_stage(c) ? n2 * (3 * sizeof(double) + 2 * sizeof(float)) : n2 * sizeof(double);
+}
+
 void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s) {
-    const int nmax = max_block_n(c);
-    const size_t shm = sizeof(double) * nmax * nmax;
-    k_lowdin<<<c->nblk, 512, shm, s>>>(c->d_blk, c->ws, c->opt.illcond_tol, S_out, Q_out); note_launch(c);
+    k_lowdin<<<c->nblk, 512, lowdin_smem(c), s>>>(c->d_blk, c->ws, c->opt.illcond_tol, S_out, Q_out,
+                                                   lowdin_two_stage(c) ? 1 : 0);
+    note_launch(c);
 }
 
 // ---------------------------------------------------------------------------
