@@ -1,10 +1,11 @@
-"""A small, self-contained Poisson workload for profiling captures.
+"""Small, self-contained workloads for profiling captures (none uses the oracle).
 
-One system of n^3 points (spacing 0.2 bohr) with `norb` Gaussian orbital
-densities, solved once by the multigrid-preconditioned CG of the library
-(mixed precision by default).  Small enough for an ncu --set full capture of
-one stencil launch (8 x 128^3 float32 vectors: 64 MiB each, above L2) and
-free of the oracle and of any randomness.
+Default case: one system of n^3 points (spacing 0.2 bohr) with `norb` Gaussian
+orbital densities (no randomness), solved once by the library's multigrid-
+preconditioned CG or Kronecker solver (mixed precision by default).  Small
+enough for an ncu --set full capture of one stencil launch (8 x 128^3 float32
+vectors: 64 MiB each, above L2).  The flo and step cases use the seeded
+synthetic systems of the benchmark's recipe.
 
   python -m paper_2108_01186_gb300.profile_case --n 128 --norb 8 [--fp64] [--solver kron]
   python -m paper_2108_01186_gb300.profile_case --case flo     (FLO build, 96^3, 16+16 orbitals)
