@@ -6,6 +6,7 @@ the header describes (per spin block [N][G] arrays packed back to back).
 There is no CPU fallback: if the library or a GPU is missing, calls raise.
 """
 import ctypes
+import functools
 import os
 
 import torch
@@ -106,6 +107,16 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _on_device(fn):
+    """Runs a Context method with the context's device current (the library
+    launches on the current device, on its current stream)."""
+    @functools.wraps(fn)
+    def wrapper(self, *args, **kwargs):
+        with torch.cuda.device(self.device):
+            return fn(self, *args, **kwargs)
+    return wrapper
+
+
 class Context:
     """A batch of systems on the current CUDA device (owns the workspace).
 
@@ -157,11 +168,17 @@ class Context:
     def _empty(self, n, dtype=torch.float64):
         return torch.empty(n, dtype=dtype, device=self.device)
 
-    def _req(self, t, n, name):
-        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
-            raise FlosicError(FLOSIC_ERR_ARG, "%s must be a contiguous CUDA float64 tensor of %d elements" % (name, n))
+    def _req(self, t, n, name, dtype=torch.float64):
+        """Every array handed to the library: a contiguous tensor of the
+        expected type and size on the context's device (the C ABI takes bare
+        pointers and cannot check them)."""
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == self.device and t.dtype == dtype
+                and t.is_contiguous() and t.numel() == n):
+            raise FlosicError(FLOSIC_ERR_ARG, "%s must be a contiguous %s tensor of %d elements on %s"
+                              % (name, dtype, n, self.device))
 
     # ---- the four calls of the step --------------------------------------
+    @_on_device
     def build_flos(self, psi, fods, want_matrices=True):
         self._req(psi, self.orb_elems, "psi")
         self._req(fods, 3 * self.norb, "fods")
@@ -171,6 +188,7 @@ class Context:
         self._check(self._L.flosic_build_flos(self._h, _ptr(psi), _ptr(fods), _ptr(phi), _ptr(S), _ptr(Q), _stream()))
         return phi, S, Q
 
+    @_on_device
     def orbital_poisson(self, phi, V=None, check=True):
         self._req(phi, self.orb_elems, "phi")
         warm = V is not None
@@ -185,6 +203,7 @@ class Context:
             self._check(rc)
         return V, iters, conv
 
+    @_on_device
     def sic_energy_potential(self, psi, phi, V, scale=1.0):
         for t, nm in ((psi, "psi"), (phi, "phi"), (V, "V")):
             self._req(t, self.orb_elems, nm)
@@ -196,6 +215,7 @@ class Context:
                                                         _ptr(U), _ptr(Exc), _ptr(E), _ptr(Vavg), _stream()))
         return E, Vavg, U, Exc
 
+    @_on_device
     def sic_backward(self, psi, fods, phi, V, gE, want_dpsi=True):
         for t, nm in ((psi, "psi"), (phi, "phi"), (V, "V")):
             self._req(t, self.orb_elems, nm)
@@ -207,6 +227,7 @@ class Context:
                                                 _ptr(dpsi), _ptr(dfod), _stream()))
         return dpsi, dfod
 
+    @_on_device
     def hamiltonian_apply(self, psi, vloc=None, V_avg=None, out=None):
         """H psi = -1/2 Delta_h psi + (vloc + V_avg) psi per orbital (the
         SC_AvgSIC Hamiltonian); vloc one field per system, V_avg one per spin
@@ -217,19 +238,24 @@ class Context:
             self._req(vloc, total, "vloc")
         if V_avg is not None:
             self._req(V_avg, self.vavg_elems, "V_avg")
+        if out is not None:
+            self._req(out, self.orb_elems, "out")
         hpsi = self._empty(self.orb_elems) if out is None else out
         self._check(self._L.flosic_hamiltonian_apply(self._h, _ptr(psi), _ptr(vloc), _ptr(V_avg), _ptr(hpsi),
                                                      _stream()))
         return hpsi
 
+    @_on_device
     def profile(self, enable=True):
         self._check(self._L.flosic_profile(self._h, int(enable)))
 
+    @_on_device
     def profile_read(self, reset=True):
         out = (ctypes.c_double * 4)()
         self._check(self._L.flosic_profile_read(self._h, out, int(reset)))
         return dict(kernel_ms=out[0], kernel_launches=int(out[1]), launches=int(out[2]), kernel_bytes=out[3])
 
+    @_on_device
     def profile_read_overlap(self, reset=True):
         """Timed launches of the mixed path's tensor-core overlap kernel:
         summed ms, launch count and algorithmic flops (2 N^2 G per block)."""
@@ -237,6 +263,7 @@ class Context:
         self._check(self._L.flosic_profile_read_overlap(self._h, out, int(reset)))
         return dict(kernel_ms=out[0], kernel_launches=int(out[1]), flops=out[2])
 
+    @_on_device
     def forward(self, psi, fods, scale=1.0, V0=None):
         phi, S, Q = self.build_flos(psi, fods)
         V, iters, conv = self.orbital_poisson(phi, V0)
@@ -246,13 +273,24 @@ class Context:
 
 def orbital_poisson_noalloc(grid, phi, V, cg_tol=1e-10, max_iter=20000, iters=None, conv=None):
     """Calls flosic_orbital_poisson_noalloc: one grid (nx, ny, nz, h, origin),
-    phi and V [norb*G] CUDA float64 tensors; returns the status code."""
+    phi and V [norb*G] CUDA float64 tensors on one device (iters, conv:
+    optional [norb] int32 tensors there); returns the status code."""
     L = load_library()
     nx, ny, nz, h, origin = grid
     G = nx * ny * nz
-    norb = phi.numel() // G
+    norb = phi.numel() // G if isinstance(phi, torch.Tensor) and G > 0 else 0
+
+    def ok(t, n, dtype):
+        return (isinstance(t, torch.Tensor) and t.is_cuda and t.device == phi.device and t.dtype == dtype
+                and t.is_contiguous() and t.numel() == n)
+
+    if not (norb > 0 and ok(phi, norb * G, torch.float64) and ok(V, norb * G, torch.float64)
+            and all(t is None or ok(t, norb, torch.int32) for t in (iters, conv))):
+        raise FlosicError(FLOSIC_ERR_ARG, "phi and V: contiguous CUDA float64 tensors of norb*G elements on one "
+                                          "device; iters, conv: None or int32 tensors of norb elements there")
     org = (ctypes.c_double * 3)(*[float(x) for x in origin])
-    return L.flosic_orbital_poisson_noalloc(int(nx), int(ny), int(nz), float(h), org, int(norb), _ptr(phi), _ptr(V),
+    with torch.cuda.device(phi.device):
+        return L.flosic_orbital_poisson_noalloc(int(nx), int(ny), int(nz), float(h), org, int(norb), _ptr(phi), _ptr(V),
                                             float(cg_tol), int(max_iter), _ptr(iters), _ptr(conv), _stream())
 
 
