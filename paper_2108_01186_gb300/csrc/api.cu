@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include <cuda.h>
@@ -176,6 +178,24 @@ void prof_end(flosic_ctx* c, cudaStream_t s) {
     if (!c->profiling) return;
     cudaEventRecord(c->prof_ev[2 * c->prof_used + 1], s);
     ++c->prof_used;
+}
+
+// The dynamic shared-memory limit is a property of the kernel on a device,
+// not of a context: raise it to the largest size any context has needed, and
+// never lower it (a later context with smaller blocks must not break the
+// launches of an earlier one).
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> granted;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = granted[std::make_pair(fn, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 int check_cuda(flosic_ctx* c, cudaError_t e, const char* what) {
@@ -485,7 +505,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         e = cudaMemcpy(c->d_bidx, bidx.data(), sizeof(int) * bidx.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !bidx.empty()) e = setup_boundary(c);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_lowdin_symbol(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lowdin_smem(c));
+        e = ensure_dyn_smem(k_lowdin_symbol(), lowdin_smem(c));
     if (e == cudaSuccess && o.precision == FLOSIC_MIXED) e = setup_gram_tc();
     if (e == cudaSuccess && M.enabled) {
         const bool f32 = (o.precision == FLOSIC_MIXED);

@@ -219,6 +219,9 @@ void launch_interp_fod(const flosic_ctx* c, const double* psi, const double* fod
 void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s);
 void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s);
 size_t lowdin_smem(const flosic_ctx* c);   // dynamic shared memory of the Loewdin kernel
+// raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (never lowers it; thread-safe)
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
 void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s);
 void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,
                               const double* Vsrc, const double* gE, cudaStream_t s);

@@ -571,7 +571,7 @@ cudaError_t setup_kron(flosic_ctx* c) {
     size_t smax = 0;
     for (int d = 0; d < 3; ++d) smax = K.smem[d] > smax ? K.smem[d] : smax;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_kron_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+        e = ensure_dyn_smem((const void*)k_kron_pass, smax);
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
