@@ -470,3 +470,74 @@ def test_paper_central_gradient_converges_to_exact(orc):
         _, gc = orc.sic_backward(f, s.grid, grad_mode="paper_central")
         gaps.append(np.max(np.abs(g[0] - gc[0])))
     assert gaps[1] < gaps[0] / 3.0
+
+
+# --------------------------------------------------------------------------
+# c-6: the PW92 constants (Sec. III names PW92 correlation; the paper prints
+# no constants, so they are pinned to the PW92 publication's table)
+# --------------------------------------------------------------------------
+
+def _pw92_golden():
+    vals = {}
+    for line in open(os.path.join(GOLD, "pw92_ferro.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split()
+            vals[k] = v
+    return vals
+
+
+def _pw92_decimal(rs, c):
+    """The ferromagnetic PW92 fit at rs from the table row c, in 40-digit
+    decimal arithmetic (independent of the oracle's float64 evaluation)."""
+    from decimal import Decimal, localcontext
+    with localcontext() as ctx:
+        ctx.prec = 40
+        r = Decimal(rs)
+        s = r.sqrt()
+        A, a1 = Decimal(c["A"]), Decimal(c["alpha1"])
+        b1, b2, b3, b4 = (Decimal(c[k]) for k in ("beta1", "beta2", "beta3", "beta4"))
+        den = 2 * A * (b1 * s + b2 * r + b3 * r * s + b4 * r ** (int(c["p"]) + 1))
+        return float(-2 * A * (1 + a1 * r) * (1 + 1 / den).ln())
+
+
+PW92_RS = (1e-4, 1e-3, 1e-2, 0.1, 0.3, 0.5, 1.0, 2.0, 3.0, 5.0, 8.0, 12.0, 20.0, 35.0, 60.0, 100.0)
+
+
+def test_pw92_table_row_is_self_consistent():
+    c = _pw92_golden()
+    A, b1, b2, c1 = (float(c[k]) for k in ("A", "beta1", "beta2", "c1"))
+    # A is the RPA high-density coefficient (1 - ln 2)/(2 pi^2) of the
+    # polarised gas, rounded to the printed digits
+    assert abs(A - (1 - math.log(2)) / (2 * math.pi ** 2)) < 5e-7
+    # beta1 and beta2 follow from c0 = A and c1 (within the printed rounding)
+    assert abs(math.exp(-c1 / (2 * A)) / (2 * A) - b1) < 5e-4
+    assert abs(2 * A * b1 ** 2 - b2) < 5e-4
+
+
+def test_pw92_oracle_matches_table_row(orc):
+    c = _pw92_golden()
+    for rs in PW92_RS:
+        ec, dec = orc.pw92_ferro(rs)
+        ref = _pw92_decimal(rs, c)
+        assert abs(ec - ref) <= 1e-12 * abs(ref), rs
+        # the derivative against a central difference of the decimal fit
+        d = 1e-5 * rs
+        fd = (_pw92_decimal(rs + d, c) - _pw92_decimal(rs - d, c)) / (2 * d)
+        assert abs(dec - fd) <= 1e-7 * abs(fd) + 1e-12, rs
+
+
+def test_pw92_pin_catches_a_one_digit_change():
+    """Changing any table constant by one unit in its last printed digit
+    moves the fit by far more than the 1e-12 bar of the previous test at
+    some tested rs, so a mistyped constant in the oracle cannot pass."""
+    c = _pw92_golden()
+    base = [_pw92_decimal(rs, c) for rs in PW92_RS]
+    for k in ("A", "alpha1", "beta1", "beta2", "beta3", "beta4"):
+        digits = c[k].split(".")[1]
+        step = 10.0 ** -len(digits)
+        for sgn in (1, -1):
+            bumped = dict(c)
+            bumped[k] = repr(float(c[k]) + sgn * step)
+            worst = max(abs(_pw92_decimal(rs, bumped) - b) / abs(b) for rs, b in zip(PW92_RS, base))
+            assert worst > 1e-8, (k, sgn)
