@@ -239,15 +239,21 @@ int flosic_hamiltonian_apply(flosic_ctx* ctx, const double* psi, const double* v
                              const double* V_avg, double* Hpsi, void* stream);
 
 /* Instrumentation (no counterpart in the paper): enable != 0 records a CUDA
- * event pair around every launch of the dominant kernel (the Poisson CG
- * stencil apply) on the stream it runs on.  Errors: ARG, CUDA. */
+ * event pair, on the stream the work runs on, around every launch of the
+ * dominant kernel of the context's Poisson solver: the stencil apply of CG
+ * (FLOSIC_SOLVER_PCG), the residual update of AAR (FLOSIC_SOLVER_AAR), or
+ * one whole inner solve of the Kronecker-product solver, i.e. its
+ * transform passes (FLOSIC_SOLVER_KRON).  Errors: ARG, CUDA. */
 int flosic_profile(flosic_ctx* ctx, int enable);
 
-/* Host array out[4]: [0] summed duration (ms) of the timed launches,
- * [1] number of timed launches, [2] kernels launched by ctx (all kinds),
- * [3] algorithmic bytes of the stencil-apply launches (per active orbital
- * and launch: read z, p_old, q_old and write p, q; 3 arrays on the first
- * iteration of a solve), counted on the device.  Waits for the device.
+/* Host array out[4]: [0] summed duration (ms) of the timed launches (or
+ * inner solves), [1] their number, [2] kernels launched by ctx (all
+ * kinds), [3] the algorithmic work of the timed launches, counted on the
+ * device: for CG and AAR the bytes their stencil sweep must move (CG: per
+ * active orbital and launch, read z, p_old, q_old and write p, q; 3 arrays
+ * on the first iteration of a solve), for the Kronecker-product solver the
+ * flops of its transforms (2 (n_s^2 + n_a^2) per line and pass, n_s and n_a
+ * the even and odd half sizes of the line).  Waits for the device.
  * reset != 0 zeroes the counters. */
 int flosic_profile_read(flosic_ctx* ctx, double* out, int reset);
 
@@ -280,15 +286,20 @@ int flosic_profile_read_overlap(flosic_ctx* ctx, double* out, int reset);
  * are rejected with FLOSIC_ERR_ARG before any work is queued.
  * The first call on a device sets that device up (looks up the device
  * address of the scratch array and uploads the stencil weights); make that
- * first call before any stream capture.  All calls share the one scratch
- * array, so calls that overlap on the GPU (from two host threads or on two
- * streams) race and must be serialised by the caller.  Waits for `stream`.
+ * first call before any stream capture.  That set-up is kept until the
+ * process exits: resetting the device (cudaDeviceReset) after the first
+ * call is not supported.  All calls share the one scratch array, so calls
+ * that overlap on the GPU (from two host threads or on two streams) race
+ * and must be serialised by the caller.  Every call synchronises `stream`:
+ * it reads the number of unconverged orbitals back to the host every 8
+ * iterations and the convergence flags at the end.
  * Errors: ARG, CUDA, NOCONV; the message is in flosic_noalloc_last_error(). */
 int flosic_orbital_poisson_noalloc(int nx, int ny, int nz, double h, const double* origin,
                                    int norb, const double* phi, double* V, double cg_tol,
                                    int max_iter, int* iters, int* conv_flags, void* stream);
 
-/* Message of the last failing flosic_orbital_poisson_noalloc call. */
+/* Message of the last failing flosic_orbital_poisson_noalloc call made
+ * from the calling host thread (one buffer per host thread). */
 const char* flosic_noalloc_last_error(void);
 
 #ifdef __cplusplus

@@ -304,16 +304,20 @@ __global__ void k_na_finish(int norb, const double* orbbase, int* iters, int* co
 std::mutex g_na_mutex;
 double* g_na_ptr[kNaMaxDevices] = {nullptr};
 
-// Once per device, with that device current: the device address of the
-// scratch array (its host-side name is only a stand-in) and the stencil
-// weights in this file's constant bank.
-// message of the last failure; a fixed buffer, so that no call allocates
-char g_na_error[256] = "";
+// Message of the last failure on this host thread: a fixed buffer per
+// thread, so that no call allocates and calls from different host threads
+// (each driving its own GPU) never write the same buffer.
+thread_local char g_na_error[256] = "";
 
 void na_fail(const char* what, const char* detail) {
     snprintf(g_na_error, sizeof g_na_error, "%s%s%s", what, detail ? ": " : "", detail ? detail : "");
 }
 
+// Once per device, with that device current: the device address of the
+// scratch array (its host-side name is only a stand-in) and the stencil
+// weights in this file's constant bank.  The result is kept for the life of
+// the process, so it is not redone if the device's primary context is torn
+// down (cudaDeviceReset) after the first call; that is not supported.
 int na_setup(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
