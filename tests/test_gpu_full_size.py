@@ -9,8 +9,10 @@ Laplacian and boundary map (a property that holds at any size); energies,
 V_avg and the adjoint (FOD gradient, dE/dpsi) against the oracle evaluated
 on the GPU's own phi and V.  Accuracy targets of the mixed path: 1e-6 Ha per
 orbital energy, 1e-6 Ha on potentials, 1e-5 Ha/bohr on FOD gradients; the
-bars below are tighter where the measured errors leave room (U and E_xc
-are float-float / float32 sums whose errors are ~1e-9 / ~1e-8 Ha).
+bars below sit about ten times above the errors measured on GB300 where that
+is tighter (128^3 and 96^3: phi 2.3e-7 relative, S 3e-7, U 3e-16 Ha (a
+float-float sum of the same products), E_xc 1.4e-8 Ha, V_avg 1.6e-7 Ha, FOD
+gradient 1.5e-7 Ha/bohr, dE/dpsi 3.4e-7 relative).
 
 The FOD gradient of the GPU path is also checked against central finite
 differences of its own FP64 energy at 128^3 (Eq. 9; step 1e-4 bohr on eight
@@ -95,7 +97,7 @@ def test_full_size_step(F, orc, record_property, cfg, scale, solver):
         X_ref = dV * np.sum(rho * eps, axis=1)
         err["U"] = max(err["U"], np.max(np.abs(U[off:off + N] - U_ref)))
         err["Exc"] = max(err["Exc"], np.max(np.abs(Exc[off:off + N] - X_ref)))
-        assert err["U"] < 1e-9 and err["Exc"] < 2e-7
+        assert err["U"] < 1e-12 and err["Exc"] < 2e-7
         Vsic = -(Vb + vxc)
         rho_s = np.sum(s.psi[sp] ** 2, axis=0)
         m = rho_s > 1e-12
@@ -113,8 +115,8 @@ def test_full_size_step(F, orc, record_property, cfg, scale, solver):
     err["dpsi"] = np.max(np.abs(dpsi - dp)) / np.max(np.abs(dp))
     for k, v in err.items():
         record_property("err_" + k, float(v))
-    assert err["dfod"] < 1e-5
-    assert err["dpsi"] < 1e-5
+    assert err["dfod"] < 2e-6
+    assert err["dpsi"] < 4e-6
 
 
 def test_full_size_fod_gradient_against_finite_differences(F, record_property):
