@@ -123,13 +123,19 @@ typedef struct {
     int aar_p;            /* AAR: every p-th step is an Anderson step, >= 2
                              (default 6) */
     int boundary;         /* FLOSIC_BC_ISOLATED (default), _PERIODIC, _SLAB */
+    int kron_tensor_cores; /* KRON solver: 1 (default) runs the 1-D transforms
+                             of every spin block whose sides are multiples of
+                             8 and at most 128 on the tensor cores (split
+                             bf16, float32 accumulation); 0 keeps them all on
+                             the CUDA cores (float32) */
 } flosic_options;
 
 typedef struct flosic_ctx flosic_ctx;
 
 /* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
  * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG,
- * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6), BC_ISOLATED.  The KRON solver
+ * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6), BC_ISOLATED,
+ * kron_tensor_cores 1.  The KRON solver
  * requires MIXED and every side <= 256.
  * Returns FLOSIC_ERR_ARG if opt is NULL. */
 int flosic_default_options(flosic_options* opt);
@@ -168,6 +174,24 @@ int flosic_layout(const flosic_ctx* ctx, int64_t* out);
  * FOD).  Waits for `stream` before returning. */
 int flosic_build_flos(flosic_ctx* ctx, const double* psi, const double* fods,
                       double* phi, double* S, double* S_mhalf, void* stream);
+
+/* Orbital mask for sharding the orbital units of one system over several
+ * GPUs (Sec. II.A solves one Poisson problem per orbital; Eq. 1 sums E_SIC
+ * over orbitals and Eq. 13 sums V_avg's numerator over orbitals, so sums
+ * over disjoint orbital subsets add up to the whole).  mask: host array of
+ * one int per orbital (0 or 1, in the context's orbital order) or NULL
+ * (every orbital).  Afterwards flosic_orbital_poisson solves only orbitals
+ * with mask 1 (the others get V = 0, iters 0, conv 1);
+ * flosic_sic_energy_potential gives U = E_xc = 0 to masked orbitals, leaves
+ * them out of E_SIC and of V_avg's numerator (the denominator rho_sigma
+ * still sums every psi of the spin), and caches V^SIC = 0 for them, so
+ * flosic_sic_backward's gradients are those of the unmasked orbitals'
+ * energy terms alone.  Summing V_avg, U, E_xc, E_SIC, dE/dpsi and dE/da
+ * over ranks whose masks partition the orbitals gives the unmasked values.
+ * flosic_build_flos is not masked (every rank builds all FLOs of a spin).
+ * Synchronous.  Errors: ARG (NULL ctx, an entry other than 0 or 1, or a
+ * partial mask with ADJ_EXACT), CUDA. */
+int flosic_set_orbital_mask(flosic_ctx* ctx, const int* mask);
 
 /* Steps a6-a7 (Sec. II.A): per orbital, -Delta_h V_i = 4 pi phi_i^2 with the
  * 12th-order centred Laplacian and, by flosic_options.boundary, Dirichlet

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace flosic {
 
@@ -36,53 +37,6 @@ constexpr int kGRows = 128;                  // MMA M: orbital rows, padded
 constexpr int kGTile = kGRows * kGK * 2;     // one bf16 tile: 16 KB
 constexpr int kGStages = 2;
 constexpr int kGSmem = kGStages * 3 * kGTile + 1024;   // + 1024-byte alignment slack
-constexpr long long kGWaitLimit = 1LL << 24;
-
-__device__ __forceinline__ uint32_t g_smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void g_mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(g_smem_addr(bar)), "r"(count) : "memory");
-}
-
-// true once the phase with the given parity has completed; false after the limit
-__device__ __forceinline__ bool g_mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < kGWaitLimit; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(g_smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, consecutive
-// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                  // leading byte offset (unused by swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
-    d |= (uint64_t)1 << 46;                  // version
-    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor of kind::f16: bf16 A and B (K-major), float32 D.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, int acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc)
-        : "memory");
-}
 
 // the six split pairs (i, j) with i + j <= 2 (0-based), A split i with B split j
 __constant__ int c_pair_a[6] = {0, 0, 1, 0, 2, 1};
@@ -90,20 +44,11 @@ __constant__ int c_pair_b[6] = {0, 1, 0, 2, 0, 1};
 
 // Reads 32 columns of this warp's 32 TMEM lanes and adds them to acc.
 __device__ __forceinline__ void tmem_add32(uint32_t taddr, float* acc) {
-    uint32_t v[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    float v[32];
+    tmem_ld32(taddr, v);
+    tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(v[j]);
+    for (int j = 0; j < 32; ++j) acc[j] += v[j];
 }
 
 template <int NB>   // NB = MMA N / 32 (1 .. 4)
@@ -129,12 +74,12 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
     for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 128)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        g_mbar_init(&mbar[0], 1);
-        g_mbar_init(&mbar[1], 1);
+        tc_mbar_init(&mbar[0], 1);
+        tc_mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_addr(&tmem_base)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_addr(&tmem_base)),
                      "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -155,7 +100,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
     for (int st = 0; st < nst; ++st) {
         const int buf = st & 1;
         if (st >= kGStages) {                        // stage st-2 done: its tile may be overwritten
-            ok = g_mbar_wait(&mbar[buf], phase[buf]) && ok;
+            ok = tc_mbar_wait(&mbar[buf], phase[buf]) && ok;
             phase[buf] ^= 1u;
         }
         unsigned char* tile = base + buf * 3 * kGTile;
@@ -177,7 +122,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t s0 = g_smem_addr(tile);
+            const uint32_t s0 = tc_smem_addr(tile);
             const uint32_t dhi = tmem + (uint32_t)(buf * NN), dx = tmem + (uint32_t)(2 * NN);
 #pragma unroll
             for (int kk = 0; kk < kGK / 16; ++kk) {
@@ -190,12 +135,12 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             g_smem_addr(&mbar[buf]))
+                             tc_smem_addr(&mbar[buf]))
                          : "memory");
         }
         if (st >= 1) {                               // add the previous stage's hi x hi sums
             const int pbuf = buf ^ 1;
-            ok = g_mbar_wait(&mbar[pbuf], phase[pbuf]) && ok;
+            ok = tc_mbar_wait(&mbar[pbuf], phase[pbuf]) && ok;
             ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld is warp-collective
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (ok) {
@@ -208,7 +153,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
     // the last stage (its commit covers every MMA of the CTA): its hi x hi
     // sums, then the cross products
     const int lb = (nst - 1) & 1;
-    ok = g_mbar_wait(&mbar[lb], phase[lb]) && ok;
+    ok = tc_mbar_wait(&mbar[lb], phase[lb]) && ok;
     ok = __all_sync(0xffffffffu, ok);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {

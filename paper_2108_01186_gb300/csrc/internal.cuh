@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a FLO-SIC library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +39,8 @@ struct BlkDesc {
     int per;                    // periodic directions (bit 0 x, 1 y, 2 z)
     long long kq[3];            // Kronecker solver: offsets of Q_d (then Q_d^T) in the matrix table
     long long kl[3];            // and of the eigenvalues of T_d
+    long long kt[3];            // tensor-core transforms: offsets of the split bf16 matrices
+    int tc;                     // 1: this block's transforms run on the tensor cores
 };
 
 // periodic-direction mask of a boundary mode
@@ -108,6 +111,7 @@ struct CgState {
     int* n_oactive;    // [1] number of orbitals with oactive = 1
     int* conv;         // [norb] 1 = converged
     double* prof_bytes;  // [1] algorithmic bytes moved by the stencil-apply launches
+    const int* mask;     // [norb] 1 = this context solves the orbital (see flosic_set_orbital_mask)
 };
 
 struct Workspace {
@@ -129,6 +133,7 @@ struct Workspace {
     double* e_part;        // [nchunk_total][2] energies partials
     double* e_orb;         // [norb][2] U_i, E_xc,i
     int* status;           // [4] device status words
+    int* mask;             // [norb] orbital mask (1 = computed here), all ones by default
     // Poisson
     double *b64, *r64, *p64, *q64;   // FP64 CG vectors / refinement
     float *d32, *r32, *p32, *q32;    // FP32 inner CG vectors
@@ -163,11 +168,17 @@ namespace flosic {
 struct KronPlan {
     float* mat = nullptr;          // per distinct 1-D operator: Q (n x n), then Q^T
     float* lam = nullptr;          // per distinct 1-D operator: eigenvalues (n)
-    long long* items = nullptr;    // [3][nblk + 1] first tile of each block per pass
+    long long* items = nullptr;    // [3][nblk + 1] first tile of each block per pass (CUDA-core kernel)
     long long total[3] = {0, 0, 0};
     int threads[3] = {0, 0, 0};
     size_t smem[3] = {0, 0, 0};
     int grid[3] = {0, 0, 0};
+    int n_simt = 0, n_tc = 0;      // blocks on the CUDA-core and on the tensor-core transforms
+    uint16_t* tc_mat = nullptr;    // per distinct operator of a tensor-core block: split bf16 matrices
+    long long* tc_items = nullptr; // [6][nblk + 1] first tile of each block per pass (tensor-core kernel)
+    void* tc_maps = nullptr;       // [6][nblk] CUtensorMap of each pass's input rows
+    long long tc_total[6] = {0, 0, 0, 0, 0, 0};
+    int tc_grid[6] = {0, 0, 0, 0, 0, 0};
 };
 }  // namespace flosic
 
@@ -190,6 +201,7 @@ struct flosic_ctx {
     flosic::Workspace ws{};
     flosic::Multigrid mg;
     flosic::KronPlan kron;
+    int n_unmasked = 0;                     // orbitals with mask 1
     bool have_forward = false;
     bool have_energy = false;
     std::string err;
@@ -246,6 +258,14 @@ void launch_energy_reduce(const flosic_ctx* c, double* U, double* Exc, double* E
 int kron_max_n();
 cudaError_t setup_kron(flosic_ctx* c);
 void launch_kron_solve(flosic_ctx* c, const float* r, float* d, float* t1, float* t2, cudaStream_t s);
+// its transforms on the tensor cores (kron_tc.cu)
+bool kron_tc_eligible(const BlkDesc& B);
+void kron_tc_pack(int n, const std::vector<double>& Vs, const std::vector<double>& Va, std::vector<uint16_t>& out);
+size_t kron_tc_smem();
+const void* kron_tc_symbol();
+bool kron_tc_map(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, const float* buf);
+long long kron_tc_tiles(const BlkDesc& B, int axis);
+void launch_kron_tc_pass(flosic_ctx* c, int step, float* out, cudaStream_t s);
 // Alternating Anderson-Richardson inner solver (mixed precision)
 template <class T>
 void launch_aar_step(flosic_ctx* c, T* x, T* r, T* f, int k, bool anderson, cudaStream_t s,

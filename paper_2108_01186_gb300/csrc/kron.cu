@@ -24,6 +24,7 @@
 // mixed refinement calls it as its float32 inner solve; the float-float
 // residual around it carries the accuracy to the requested tolerance.
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -460,15 +461,67 @@ __global__ void k_kron_done(int norb, CgState st) {
 
 int kron_max_n() { return kKronMaxN; }
 
+// Tensor-core transforms: the split bf16 matrices, per pass the tile table
+// and the input tensor maps of every tensor-core block (the pass reads the
+// workspace arrays r32, p32, q32 in the order of launch_kron_solve), the
+// kernel's shared-memory limit and one CTA per SM.
+cudaError_t setup_kron_tc(flosic_ctx* c, const std::vector<uint16_t>& tcmat, int sms) {
+    KronPlan& K = c->kron;
+    cudaError_t e = ctx_alloc(c, &K.tc_mat, tcmat.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(K.tc_mat, tcmat.data(), sizeof(uint16_t) * tcmat.size(), cudaMemcpyHostToDevice);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (e == cudaSuccess &&
+        (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+         q != cudaDriverEntryPointSuccess || !fn))
+        e = cudaErrorNotSupported;
+    const float* in_buf[6] = {c->ws.r32, c->ws.p32, c->ws.q32, c->ws.p32, c->ws.q32, c->ws.p32};
+    std::vector<CUtensorMap> maps(6 * (size_t)c->nblk);
+    std::vector<long long> items(6 * (size_t)(c->nblk + 1));
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    for (int st = 0; st < 6 && e == cudaSuccess; ++st) {
+        long long acc = 0;
+        for (int b = 0; b < c->nblk; ++b) {
+            const BlkDesc& B = c->blk[b];
+            items[(size_t)st * (c->nblk + 1) + b] = acc;
+            if (!B.tc) continue;
+            acc += kron_tc_tiles(B, st % 3);
+            if (!kron_tc_map(fn, &maps[(size_t)st * c->nblk + b], B, st % 3, in_buf[st])) e = cudaErrorInvalidValue;
+        }
+        items[(size_t)st * (c->nblk + 1) + c->nblk] = acc;
+        K.tc_total[st] = acc;
+        K.tc_grid[st] = (int)(acc < sms ? (acc > 0 ? acc : 1) : sms);
+    }
+    void* dm = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(CUtensorMap) * maps.size());
+    if (e == cudaSuccess) {
+        c->allocations.push_back(dm);
+        K.tc_maps = dm;
+        e = cudaMemcpy(dm, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = ctx_alloc(c, &K.tc_items, items.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(K.tc_items, items.data(), sizeof(long long) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = ensure_dyn_smem(kron_tc_symbol(), kron_tc_smem());
+    return e;
+}
+
 // Host set-up: for every distinct 1-D operator (n, h, periodic) the
 // eigen-decompositions of its even and odd blocks, the forward and inverse
 // half-size matrices in float32, the eigenvalues (the periodic constant mode
 // set to exactly zero), per-block offsets and the tile counts of the passes.
 cudaError_t setup_kron(flosic_ctx* c) {
     std::map<std::tuple<int, double, int>, std::pair<long long, long long>> seen;
+    std::map<std::tuple<int, double, int>, std::pair<std::vector<double>, std::vector<double>>> vecs;
+    std::map<std::tuple<int, double, int>, long long> tc_seen;
     std::vector<float> mat, lam;
+    std::vector<uint16_t> tcmat;
     KronPlan& K = c->kron;
+    K.n_simt = K.n_tc = 0;
     for (BlkDesc& B : c->blk) {
+        B.tc = (c->opt.kron_tensor_cores && kron_tc_eligible(B)) ? 1 : 0;
+        ++(B.tc ? K.n_tc : K.n_simt);
         const int nd[3] = {B.nx, B.ny, B.nz};
         for (int d = 0; d < 3; ++d) {
             const int n = nd[d];
@@ -531,9 +584,21 @@ cudaError_t setup_kron(flosic_ctx* c) {
                 for (int k = 0; k < na; ++k) lam.push_back((float)Ta[(size_t)k * na + k]);
                 if (periodic) lam[lo + kmin] = 0.f;
                 it = seen.emplace(key, std::make_pair(qo, lo)).first;
+                vecs.emplace(key, std::make_pair(std::move(Vs), std::move(Va)));
             }
             B.kq[d] = it->second.first;
             B.kl[d] = it->second.second;
+            B.kt[d] = 0;
+            if (B.tc) {
+                auto jt = tc_seen.find(key);
+                if (jt == tc_seen.end()) {
+                    const auto& V = vecs.at(key);
+                    const long long to = (long long)tcmat.size();
+                    kron_tc_pack(n, V.first, V.second, tcmat);
+                    jt = tc_seen.emplace(key, to).first;
+                }
+                B.kt[d] = jt->second;
+            }
         }
     }
     cudaError_t e = ctx_alloc(c, &K.mat, mat.size());
@@ -553,7 +618,7 @@ cudaError_t setup_kron(flosic_ctx* c) {
             if (d == 0) g = (B.ny * (long long)B.nz + kKronCols - 1) / kKronCols;
             else if (d == 1) g = (long long)B.nz * ((B.nx + kKronCols - 1) / kKronCols);
             else g = ((long long)B.nx * B.ny + kKronCols - 1) / kKronCols;
-            acc += g * B.N;
+            if (!B.tc) acc += g * B.N;   // tensor-core blocks take no tiles of this kernel
             const int n = d == 0 ? B.nx : (d == 1 ? B.ny : B.nz);
             nmax = n > nmax ? n : nmax;
             const int Rb = kron_rows(n), s8 = round8((n + 1) / 2), a8 = Rb - s8;
@@ -581,6 +646,7 @@ cudaError_t setup_kron(flosic_ctx* c) {
         long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
         K.grid[d] = (int)(grid < K.total[d] ? grid : (K.total[d] > 0 ? K.total[d] : 1));
     }
+    if (e == cudaSuccess && K.n_tc > 0) e = setup_kron_tc(c, tcmat, sms);
     return e;
 }
 
@@ -595,19 +661,27 @@ void launch_kron_solve(flosic_ctx* c, const float* r, float* d, float* t1, float
     a.lam = K.lam;
     a.active = c->ws.cg.active;
     a.flops = c->profiling ? c->ws.cg.prof_bytes : nullptr;
+    // Pass i of the CUDA-core kernel (standard layout throughout: x, y, z
+    // forward, z, y, x inverse) and pass i of the tensor-core kernel (x, y,
+    // z forward, x, y, z inverse with rotating layouts) read and write the
+    // same arrays, each on its own blocks.
     struct Step { int axis, inverse, scale; const float* in; float* out; };
     const Step steps[6] = {{0, 0, 0, r, t1}, {1, 0, 0, t1, t2}, {2, 0, 1, t2, t1},
                            {2, 1, 0, t1, t2}, {1, 1, 0, t2, t1}, {0, 1, 0, t1, d}};
     prof_begin(c, s);
-    for (const Step& st : steps) {
-        a.axis = st.axis;
-        a.inverse = st.inverse;
-        a.scale = st.scale;
-        a.in = st.in;
-        a.out = st.out;
-        a.item0 = K.items + (size_t)st.axis * (c->nblk + 1);
-        k_kron_pass<<<K.grid[st.axis], K.threads[st.axis], K.smem[st.axis], s>>>(a, K.total[st.axis]);
-        note_launch(c);
+    for (int i = 0; i < 6; ++i) {
+        const Step& st = steps[i];
+        if (K.n_simt > 0) {
+            a.axis = st.axis;
+            a.inverse = st.inverse;
+            a.scale = st.scale;
+            a.in = st.in;
+            a.out = st.out;
+            a.item0 = K.items + (size_t)st.axis * (c->nblk + 1);
+            k_kron_pass<<<K.grid[st.axis], K.threads[st.axis], K.smem[st.axis], s>>>(a, K.total[st.axis]);
+            note_launch(c);
+        }
+        if (K.n_tc > 0) launch_kron_tc_pass(c, i, st.out, s);
     }
     prof_end(c, s);
     k_kron_done<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->ws.cg);

@@ -1,0 +1,477 @@
+// The Kronecker-product transforms of the mixed-precision inner Poisson
+// solve on the fifth-generation tensor cores (tcgen05).
+//
+// Sec. II.A writes the finite-difference Laplacian as a Kronecker sum; its
+// inverse is three forward 1-D transforms, a diagonal scaling and three
+// inverse transforms (kron.cu has the algebra and the CUDA-core kernel).
+// Each transform multiplies every line of one direction by a dense matrix:
+// a GEMM with K = the line length, so it belongs on the tensor cores.
+//
+// Layout.  A pass reads its input as rows (one row = one line, its n points
+// contiguous) and writes its output transposed: out[orb][k][row], k the
+// position (or mode) along the line.  The three directions therefore rotate
+// through the passes: the standard [z][y][x] input r becomes [mx][z][y]
+// after the x pass, [my][mx][z] after the y pass, [mz][my][mx] after the z
+// pass (with the scaling), [x][mz][my], [y][x][mz] and finally the standard
+// [z][y][x] after the inverse x, y and z passes.  Every input row is a
+// contiguous run that one tiled bulk copy (TMA, 128-byte swizzle) brings to
+// shared memory; every output store is coalesced (the 32 lanes of a warp
+// own 32 consecutive rows).
+//
+// One CTA per SM streams tiles of 128 rows.  Per tile: the copy engine
+// delivers the rows (float32); the threads fold each row into its even and
+// odd halves (s_k = v_k + v_{n-1-k}, a_k = v_k - v_{n-1-k}: T_d commutes
+// with the reflection, so the transform splits into two half-size
+// products) and write each half as three bf16 terms (v = v1 + v2 + v3, ~24
+// significant bits) in the K-major 128-byte-swizzled operand layout; one
+// thread issues the MMAs (M = 128 rows, N = 64 modes, K = 16 per
+// instruction): the six split products v_i w_j with i + j <= 2 of each
+// half, the v1 w1 product into its own accumulator and the five smaller
+// ones into a second, both in tensor memory (two tile buffers of 256
+// columns); the threads read the accumulators back (tcgen05.ld), add them,
+// apply the scaling (forward z) or the even/odd recombination (inverse) and
+// store.  The copy of the next tile is in flight while a tile is converted,
+// multiplied and stored; the MMAs of a tile run while the previous tile's
+// results are stored.
+//
+// Accuracy: keeping the dominant product in its own short accumulation
+// chain (4 instructions of K = 16 per half) holds the tensor cores'
+// float32 accumulation error to the level of a float32 CUDA-core product,
+// so two refinement rounds still reach 1e-10 at 128^3.
+//
+// Blocks qualify when every side is a multiple of 8 and at most 128 and
+// their offset keeps rows 16-byte aligned; other blocks keep the CUDA-core
+// kernel (kron.cu).  Every mbarrier wait is bounded; a timeout sets bit 4 of
+// status word 3, lets the CTA wait (bounded) for its copies and MMAs in
+// flight, frees its tensor memory and return.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "tcgen05.cuh"
+
+namespace flosic {
+namespace {
+
+constexpr int kTcRows = 128;                      // rows (lines) per tile: MMA M
+constexpr int kTcHalf = 64;                       // half-line length (K) and modes per half (N), padded
+constexpr int kTcThreads = 256;
+constexpr int kTcATile = kTcRows * kTcHalf * 2;   // one split of one half of a tile (bf16): 16 KB
+constexpr int kTcBTile = kTcHalf * kTcHalf * 2;   // one split of one half-matrix (bf16): 8 KB
+constexpr int kTcBox = kTcRows * 32 * 4;          // one copy: 128 rows x 32 points (float32): 16 KB
+constexpr int kTcOffB = 0;                        // 6 half-matrix tiles (2 halves x 3 splits)
+constexpr int kTcOffA = kTcOffB + 6 * kTcBTile;   // 6 operand tiles
+constexpr int kTcOffRaw = kTcOffA + 6 * kTcATile; // up to 4 copies (128 points per row)
+constexpr int kTcSmem = kTcOffRaw + 4 * kTcBox + 1024;   // + 1024-byte alignment slack
+constexpr uint32_t kTcCols = 512;                 // two tile buffers of 256 tensor-memory columns
+constexpr int kTcMatElems = 64 * 64;              // one padded half-matrix
+constexpr int kTcOpElems = 12 * kTcMatElems;      // per operator: 2 directions x 2 halves x 3 splits
+
+__constant__ int c_tc_pa[6] = {0, 0, 1, 0, 2, 1};   // split of the data operand (A) of product p
+__constant__ int c_tc_pb[6] = {0, 1, 0, 2, 0, 1};   // split of the matrix operand (B)
+
+struct KronTcArgs {
+    const BlkDesc* blk;
+    int nblk;
+    const long long* item0;   // [nblk + 1] first tile of each block in this pass
+    const CUtensorMap* maps;  // [nblk] the pass's input rows of each block
+    const uint16_t* mat;      // bf16 split matrices (kTcOpElems per operator)
+    const float* lam;         // eigenvalues per distinct operator
+    float* out;
+    const int* active;
+    double* flops;            // algorithmic flop counter (profiling) or null
+    int* status;
+    int axis, inverse, scale;
+};
+
+struct TcTile {
+    int b, o, q;   // block, orbital within the block, tile within the orbital
+};
+
+__device__ __forceinline__ int tc_side(const BlkDesc& B, int axis) { return axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz); }
+
+__device__ __forceinline__ int tc_tiles_per_orb(const BlkDesc& B, int axis) {
+    const long long R = B.G / tc_side(B, axis);
+    return (int)((R + kTcRows - 1) / kTcRows);
+}
+
+// next item at or after it whose orbital is active (it1 if none); b tracks the block
+__device__ __forceinline__ long long tc_next(const KronTcArgs& a, long long it, long long it1, int& b, TcTile& t) {
+    for (; it < it1; ++it) {
+        while (b + 1 < a.nblk && it >= a.item0[b + 1]) ++b;
+        const BlkDesc& B = a.blk[b];
+        const int tpo = tc_tiles_per_orb(B, a.axis);
+        const long long r = it - a.item0[b];
+        const int o = (int)(r / tpo);
+        if (a.active[B.orb0 + o]) {
+            t.b = b;
+            t.o = o;
+            t.q = (int)(r - (long long)o * tpo);
+            return it;
+        }
+    }
+    return it1;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Writes eight consecutive K values of one half of row r as three bf16
+// splits into the K-major, 128-byte-swizzled operand tiles (chunk c).
+__device__ __forceinline__ void tc_store_chunk(unsigned char* sA, int half, int r, int c, const float* v) {
+    uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        __nv_bfloat16 x1[2], x2[2], x3[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float f = v[2 * p + e];
+            x1[e] = __float2bfloat16_rn(f);
+            const float r1 = f - __bfloat162float(x1[e]);
+            x2[e] = __float2bfloat16_rn(r1);
+            x3[e] = __float2bfloat16_rn(r1 - __bfloat162float(x2[e]));
+        }
+        w1[p] = pack_bf16(x1[0], x1[1]);
+        w2[p] = pack_bf16(x2[0], x2[1]);
+        w3[p] = pack_bf16(x3[0], x3[1]);
+    }
+    const int off = r * 128 + ((c ^ (r & 7)) << 4);
+    unsigned char* base = sA + half * 3 * kTcATile + off;
+    *reinterpret_cast<uint4*>(base) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(base + kTcATile) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    *reinterpret_cast<uint4*>(base + 2 * kTcATile) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+}
+
+// four consecutive points pos..pos+3 (pos a multiple of 4) of row r of the staged copy
+__device__ __forceinline__ float4 tc_raw4(const unsigned char* sR, int r, int pos) {
+    return *reinterpret_cast<const float4*>(sR + (pos >> 5) * kTcBox + r * 128 + ((((pos & 31) >> 2) ^ (r & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long long total) {
+    extern __shared__ unsigned char kt_smem_raw[];
+    __shared__ uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
+    const long long it0 = (long long)blockIdx.x * per_cta;
+    const long long it1 = it0 + per_cta < total ? it0 + per_cta : total;
+    if (it0 >= it1) return;
+    int bsearch = 0;
+    TcTile cur{};
+    long long item = tc_next(a, it0, it1, bsearch, cur);
+    if (item >= it1) return;   // uniform: every thread walks the same items
+
+    unsigned char* sm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(kt_smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sB = sm + kTcOffB;
+    unsigned char* sA = sm + kTcOffA;
+    unsigned char* sR = sm + kTcOffRaw;
+    if (tid == 0) {
+        tc_mbar_init(&bar_tma, 1);
+        tc_mbar_init(&bar_mma, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, kTcCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    auto issue_copy = [&](const TcTile& t) {   // thread 0: the tile's rows, all points
+        const BlkDesc& B = a.blk[t.b];
+        const int n = tc_side(B, a.axis);
+        const long long R = B.G / n;
+        const int nbox = (n + 31) >> 5;
+        const int row0 = (int)((long long)t.o * R + (long long)t.q * kTcRows);
+        tc_mbar_expect_tx(&bar_tma, (uint32_t)(nbox * kTcBox));
+        for (int bx = 0; bx < nbox; ++bx) tc_tma_load_2d(sR + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma);
+    };
+
+    // results of tile t from tensor-memory buffer buf: warp w reads lanes
+    // 32 (w mod 4) .. (the tile's rows) and modes 32 (w / 4) .. of both halves
+    auto epilogue = [&](const TcTile& t, int buf) {
+        const BlkDesc& B = a.blk[t.b];
+        const int n = tc_side(B, a.axis), ns = n >> 1;
+        const long long R = B.G / n;
+        const int r = 32 * (warp & 3) + lane, hc = warp >> 2;
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * 256 + 32 * hc);
+        float e0[32], e1[32], o0[32], o1[32];
+        tmem_ld32(ta, e0);
+        tmem_ld32(ta + 64, e1);
+        tmem_ld32(ta + 128, o0);
+        tmem_ld32(ta + 192, o1);
+        tmem_wait_ld();
+        const long long l = (long long)t.q * kTcRows + r;   // row within the orbital
+        if (l >= R) return;
+        float* dst = a.out + B.off + (long long)t.o * B.G + l;
+        if (!a.inverse) {
+            float lxy = 0.f;
+            const float* lz = a.lam + B.kl[2];
+            if (a.scale) {   // forward z: rows are (my, mx), mx fastest
+                const int mx = (int)(l % B.nx), my = (int)(l / B.nx);
+                lxy = a.lam[B.kl[0] + mx] + a.lam[B.kl[1] + my];
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int m = 32 * hc + j;
+                if (m < ns) {
+                    float ve = e0[j] + e1[j], vo = o0[j] + o1[j];
+                    if (a.scale) {   // (fast division: 2 ulp, far below the solve's accuracy)
+                        const float se = lxy + lz[m], so = lxy + lz[ns + m];
+                        ve = se > 0.f ? __fdividef(ve, se) : 0.f;
+                        vo = so > 0.f ? __fdividef(vo, so) : 0.f;
+                    }
+                    __stcs(dst + (long long)m * R, ve);
+                    __stcs(dst + (long long)(ns + m) * R, vo);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int k = 32 * hc + j;
+                if (k < ns) {
+                    const float S = e0[j] + e1[j], A = o0[j] + o1[j];
+                    __stcs(dst + (long long)k * R, S + A);
+                    __stcs(dst + (long long)(n - 1 - k) * R, S - A);
+                }
+            }
+        }
+    };
+
+    if (tid == 0) issue_copy(cur);
+    uint32_t tma_ph = 0, mma_ph = 0;
+    int loaded_b = -1;
+    bool have_prev = false;
+    TcTile prev{};
+    int prev_buf = 0, ntile = 0;
+    const int r = tid & (kTcRows - 1), kp = tid >> 7;   // converter: row r, K values 32 kp .. 32 kp + 31
+    for (;;) {
+        bool ok = tc_mbar_wait(&bar_tma, tma_ph);
+        tma_ph ^= 1u;
+        if (have_prev) {
+            ok = tc_mbar_wait(&bar_mma, mma_ph) && ok;
+            mma_ph ^= 1u;
+        }
+        if (!ok) atomicOr(&s_abort, 1);
+        const BlkDesc& B = a.blk[cur.b];
+        const int n = tc_side(B, a.axis), ns = n >> 1;
+        // this thread's raw values: forward (v_k, v_{n-4-k..n-1-k}), inverse (c_s[k..], c_a[k..])
+        float4 fr[8], bk[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const int k = 32 * kp + 4 * g;
+            fr[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            bk[g] = fr[g];
+            if (ok && k < ns) {
+                fr[g] = tc_raw4(sR, r, k);
+                bk[g] = tc_raw4(sR, r, a.inverse ? ns + k : n - 4 - k);
+            }
+        }
+        TcTile nxt_t{};
+        const long long nxt = tc_next(a, item + 1, it1, bsearch, nxt_t);
+        tc_fence_before();
+        __syncthreads();   // the staged rows are read; previous results are read from tensor memory
+        if (s_abort) break;
+        if (tid == 0 && nxt < it1) issue_copy(nxt_t);
+        if (cur.b != loaded_b) {   // this block's matrices (the previous tile's MMAs have completed)
+            const uint16_t* src = a.mat + B.kt[a.axis] + (a.inverse ? 6 * kTcMatElems : 0);
+            for (int i = tid; i < 6 * 64 * 8; i += kTcThreads) {
+                const int mt = i >> 9, m = (i >> 3) & 63, c = i & 7;
+                const uint4 v = *reinterpret_cast<const uint4*>(src + mt * kTcMatElems + m * 64 + c * 8);
+                *reinterpret_cast<uint4*>(sB + mt * kTcBTile + m * 128 + ((c ^ (m & 7)) << 4)) = v;
+            }
+            loaded_b = cur.b;
+        }
+        // fold (forward) and split into the operand tiles: chunk c = 4 kp + cc holds K = 8c .. 8c + 7
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            float s8[8], d8[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float4 x = fr[2 * cc + h], y = bk[2 * cc + h];
+                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (a.inverse) {
+                        s8[4 * h + i] = xs[i];
+                        d8[4 * h + i] = ys[i];
+                    } else {
+                        s8[4 * h + i] = xs[i] + ys[3 - i];
+                        d8[4 * h + i] = xs[i] - ys[3 - i];
+                    }
+                }
+            }
+            tc_store_chunk(sA, 0, r, 4 * kp + cc, s8);
+            tc_store_chunk(sA, 1, r, 4 * kp + cc, d8);
+        }
+        tc_fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        const int buf = ntile & 1;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t idesc = umma_idesc_bf16(kTcRows, kTcHalf);
+            const uint32_t a0 = tc_smem_addr(sA), b0 = tc_smem_addr(sB);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t dm = tmem + (uint32_t)(buf * 256 + h * 128);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) {
+                        const uint64_t da = umma_desc_sw128(a0 + (h * 3 + c_tc_pa[p]) * kTcATile + kk * 32);
+                        const uint64_t db = umma_desc_sw128(b0 + (h * 3 + c_tc_pb[p]) * kTcBTile + kk * 32);
+                        if (p == 0) umma_bf16(dm, da, db, idesc, kk != 0);
+                        else umma_bf16(dm + 64, da, db, idesc, (kk | (p - 1)) != 0);
+                    }
+                }
+            }
+            umma_commit(&bar_mma);
+            if (a.flops) {
+                const long long R = B.G / n;
+                const long long rows = R - (long long)cur.q * kTcRows;
+                atomicAdd(a.flops, 4.0 * (double)ns * ns * (double)(rows < kTcRows ? rows : kTcRows));
+            }
+        }
+        if (have_prev) {
+            tc_fence_after();
+            epilogue(prev, prev_buf);
+        }
+        prev = cur;
+        prev_buf = buf;
+        have_prev = true;
+        ++ntile;
+        if (nxt >= it1) break;
+        cur = nxt_t;
+        item = nxt;
+    }
+    if (!s_abort) {   // the last tile (the abort flag is block-uniform here)
+        if (!tc_mbar_wait(&bar_mma, mma_ph)) atomicOr(&s_abort, 1);
+        mma_ph ^= 1u;
+        __syncthreads();
+        if (!s_abort) {
+            tc_fence_after();
+            epilogue(prev, prev_buf);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        atomicOr(a.status + 3, 4);
+        // let the copy and the MMAs this CTA has in flight finish (bounded)
+        tc_mbar_wait(&bar_tma, tma_ph ^ 1u);
+        tc_mbar_wait(&bar_mma, mma_ph ^ 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTcCols);
+    }
+}
+
+uint16_t host_bf16(float f) {   // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double host_bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+}  // namespace
+
+bool kron_tc_eligible(const BlkDesc& B) {
+    const int nd[3] = {B.nx, B.ny, B.nz};
+    for (int d = 0; d < 3; ++d)
+        if (nd[d] < 8 || nd[d] > 2 * kTcHalf || nd[d] % 8 != 0) return false;
+    return B.off % 4 == 0;
+}
+
+// The operator's four half-matrices in the transform kernel's operand form
+// (rows = outputs, K = inputs, padded to 64 x 64), each as three bf16
+// splits of the float64 value: [direction][half][split][64][64].
+//   forward: c_s[m] = sum_k s_k Vs[k][m] / sqrt 2, c_a[m] = sum_k a_k Va[k][m] / sqrt 2
+//   inverse: S_k = sum_m c_s[m] Vs[k][m] / sqrt 2, A_k = sum_m c_a[m] Va[k][m] / sqrt 2
+// (n even, so every even/odd basis vector carries 1/sqrt 2).
+void kron_tc_pack(int n, const std::vector<double>& Vs, const std::vector<double>& Va, std::vector<uint16_t>& out) {
+    const int h = n / 2;
+    const double r2 = std::sqrt(0.5);
+    const size_t o0 = out.size();
+    out.resize(o0 + kTcOpElems, 0);
+    for (int dir = 0; dir < 2; ++dir)
+        for (int half = 0; half < 2; ++half) {
+            const std::vector<double>& V = half == 0 ? Vs : Va;
+            for (int row = 0; row < h; ++row)
+                for (int k = 0; k < h; ++k) {
+                    // forward: row = mode m, k = point; inverse: row = point, k = mode
+                    const double v = (dir == 0 ? V[(size_t)k * h + row] : V[(size_t)row * h + k]) * r2;
+                    const uint16_t b1 = host_bf16((float)v);
+                    const double q1 = v - host_bf16_value(b1);
+                    const uint16_t b2 = host_bf16((float)q1);
+                    const double q2 = q1 - host_bf16_value(b2);
+                    const uint16_t b3 = host_bf16((float)q2);
+                    const uint16_t bs[3] = {b1, b2, b3};
+                    for (int s = 0; s < 3; ++s)
+                        out[o0 + (size_t)((dir * 2 + half) * 3 + s) * kTcMatElems + (size_t)row * 64 + k] = bs[s];
+                }
+        }
+}
+
+size_t kron_tc_smem() { return (size_t)kTcSmem; }
+const void* kron_tc_symbol() { return (const void*)k_kron_tc; }
+
+// Input rows of pass `step` (axis step mod 3) of block B as a 2-D tensor map:
+// n points per row (contiguous), N G / n rows, boxes of 32 points x 128 rows.
+bool kron_tc_map(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, const float* buf) {
+    auto encode = reinterpret_cast<CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                                CUtensorMapInterleave, CUtensorMapSwizzle,
+                                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(encode_fn);
+    const int n = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(B.G / n) * (cuuint64_t)B.N};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)kTcRows};
+    const cuuint32_t estr[2] = {1, 1};
+    void* base = const_cast<float*>(buf) + B.off;
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+long long kron_tc_tiles(const BlkDesc& B, int axis) {
+    const int n = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+    const long long R = B.G / n;
+    return (long long)B.N * ((R + kTcRows - 1) / kTcRows);
+}
+
+void launch_kron_tc_pass(flosic_ctx* c, int step, float* out, cudaStream_t s) {
+    const KronPlan& K = c->kron;
+    KronTcArgs a{};
+    a.blk = c->d_blk;
+    a.nblk = c->nblk;
+    a.item0 = K.tc_items + (size_t)step * (c->nblk + 1);
+    a.maps = reinterpret_cast<const CUtensorMap*>(K.tc_maps) + (size_t)step * c->nblk;
+    a.mat = K.tc_mat;
+    a.lam = K.lam;
+    a.out = out;
+    a.active = c->ws.cg.active;
+    a.flops = c->profiling ? c->ws.cg.prof_bytes : nullptr;
+    a.status = c->ws.status;
+    a.axis = step % 3;
+    a.inverse = step >= 3;
+    a.scale = step == 2;
+    k_kron_tc<<<K.tc_grid[step], kTcThreads, kTcSmem, s>>>(a, K.tc_total[step]);
+    note_launch(c);
+}
+
+}  // namespace flosic

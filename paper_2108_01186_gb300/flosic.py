@@ -28,7 +28,7 @@ ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "f
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
                  "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error",
-                 "flosic_hamiltonian_apply", "flosic_profile_read_overlap")
+                 "flosic_hamiltonian_apply", "flosic_profile_read_overlap", "flosic_set_orbital_mask")
 
 
 class FlosicError(RuntimeError):
@@ -49,7 +49,8 @@ class FlosicOptions(ctypes.Structure):
                 ("rho_min", ctypes.c_double), ("illcond_tol", ctypes.c_double),
                 ("preconditioner", ctypes.c_int), ("solver", ctypes.c_int),
                 ("aar_omega", ctypes.c_double), ("aar_beta", ctypes.c_double),
-                ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("kron_tensor_cores", ctypes.c_int)]
 
 
 _lib = None
@@ -75,6 +76,7 @@ def load_library(path=LIB_PATH):
     L.flosic_sic_energy_potential.argtypes = [vp, vp, vp, vp, d, vp, vp, vp, vp, vp]
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_hamiltonian_apply.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.flosic_set_orbital_mask.argtypes = [vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
     L.flosic_profile_read_overlap.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
@@ -226,6 +228,19 @@ class Context:
         self._check(self._L.flosic_sic_backward(self._h, _ptr(psi), _ptr(fods), _ptr(phi), _ptr(V), _ptr(gE),
                                                 _ptr(dpsi), _ptr(dfod), _stream()))
         return dpsi, dfod
+
+    @_on_device
+    def set_orbital_mask(self, mask=None):
+        """Calls flosic_set_orbital_mask: mask = a sequence of 0/1 per orbital
+        (context order) or None for every orbital."""
+        if mask is None:
+            self._check(self._L.flosic_set_orbital_mask(self._h, None))
+            return
+        m = [int(v) for v in mask]
+        if len(m) != self.norb:
+            raise FlosicError(FLOSIC_ERR_ARG, "mask needs one entry per orbital (%d)" % self.norb)
+        arr = (ctypes.c_int * len(m))(*m)
+        self._check(self._L.flosic_set_orbital_mask(self._h, ctypes.cast(arr, ctypes.c_void_p)))
 
     @_on_device
     def hamiltonian_apply(self, psi, vloc=None, V_avg=None, out=None):
