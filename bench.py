@@ -18,8 +18,12 @@ the float-float refinement, to ||r|| <= 1e-10 ||b||); the line also carries
 the same step with multigrid-preconditioned CG (pcg_path) and with the plain
 float64 path (fp64_path).
 
-Under torchrun (N > 1) every rank runs its own independent system (weak
-scaling, no collective on the data path); value = all orbitals / max time.
+Under torchrun (N > 1) the orbitals of the one 128^3 system are split over
+the ranks by default (--shard orbitals: every rank builds all FLOs, solves
+and scores its own orbitals, and E_SIC, V_avg, the energies and gradients
+are summed over ranks with NCCL; strong scaling, value = the system's
+orbitals / max time); --shard systems gives every rank its own independent
+system instead (weak scaling, value = all orbitals / max time).
 """
 import argparse
 import hashlib
@@ -64,6 +68,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-pcg", action="store_true", help="skip the multigrid-PCG comparison line")
+    p.add_argument("--shard", default="orbitals", choices=["orbitals", "systems"],
+                   help="N > 1: split the orbitals of one system over the ranks (strong scaling; every rank "
+                        "builds all FLOs, solves and scores its own orbitals, sums over ranks) or give every "
+                        "rank its own system (weak scaling)")
+    p.add_argument("--no-tensor-core-transforms", action="store_true",
+                   help="Kronecker solver: keep every 1-D transform on the CUDA cores")
     p.add_argument("--workload", default="128", choices=["128", "192", "uneven", "fodopt", "hamiltonian"],
                    help="128: the 128^3 forward+adjoint step (default); 192: the same step at 192^3 with "
                         "120+120 orbitals; uneven: 64 systems of "
@@ -274,17 +284,22 @@ def run_gpu(args):
     from paper_2108_01186_gb300.flosic import Context
 
     build.build()
+    sharded = world > 1 and args.shard == "orbitals"
+    seed_rank = 0 if sharded else rank   # sharded: one system split over the ranks; else one per rank
     if args.workload == "192":   # the largest workload: 192^3, h=0.15, 120+120 orbitals on 60 atoms
-        s = synth.make_system(192, 0.15, 60, [120, 120], seed=4000 + rank)
+        s = synth.make_system(192, 0.15, 60, [120, 120], seed=4000 + seed_rank)
         workload = WORKLOAD_192
     else:
-        s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + rank)   # each rank: its own system
+        s = synth.make_system(128, 0.2, 16, [32, 32], seed=3000 + seed_rank)
         workload = WORKLOAD
     norb = sum(s.norb)
     prec = 1 if args.precision == "mixed" else 0
     pc = 1 if args.preconditioner == "mg" else 0
     solver = {"pcg": 0, "aar": 1, "kron": 2}[args.solver]
-    ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc, solver=solver)
+    ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc, solver=solver,
+                  kron_tensor_cores=0 if args.no_tensor_core_transforms else 1)
+    shard_step = D.OrbitalShardedStep(ctx) if sharded else None
+    units = world * norb if not sharded else norb   # orbitals the whole job processes per step
     dev = torch.device("cuda", local)
     psi_h = torch.from_numpy(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
     fods_h = torch.from_numpy(np.concatenate([f.ravel() for f in s.fods])).pin_memory()
@@ -294,7 +309,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step(psi, fods):
-        return step_with(ctx, psi, fods, gE)
+        if shard_step is None:
+            return step_with(ctx, psi, fods, gE)
+        out = shard_step.forward(psi, fods, 1.0)
+        dpsi, dfod = shard_step.backward(psi, fods, out["phi"], out["V"], gE)
+        return out["E_sic"], out["V_avg"], dpsi, dfod, out["iters"]
 
     def barrier():
         D.barrier(torch.cuda.synchronize)
@@ -324,7 +343,7 @@ def run_gpu(args):
     ctx.profile(False)
     ms = D.max_over_ranks(ms, dev)
     ms_step = ms / args.steps
-    value = world * norb / (ms_step / 1e3)
+    value = units / (ms_step / 1e3)
 
     # roofline of the dominant kernel (the PCG stencil apply): algorithmic
     # bytes counted on the device per active orbital and launch (read z,
@@ -416,14 +435,14 @@ def run_gpu(args):
             torch.cuda.synchronize()
         barrier()
         te = D.max_over_ranks((time.perf_counter() - t0) / ke, dev)
-        e2e = {"value": world * norb / te, "unit": "solves/s",
+        e2e = {"value": units / te, "unit": "solves/s",
                "h2d_bytes_per_step": int(psi_h.numel() * 8 + fods_h.numel() * 8),
                "d2h_bytes_per_step": int((out_E.numel() + out_V.numel() + out_df.numel() + out_dp.numel()) * 8)}
 
     # the plain float64 path on the same system (the comparison the metric
     # names), and the mixed path's deviation from it
     fp64 = None
-    if prec == 1 and not args.no_fp64:
+    if prec == 1 and not args.no_fp64 and world == 1:
         E_m, Va_m, U_m, X_m = ctx.sic_energy_potential(psi, *step_outputs(ctx, psi, fods)[:2], 1.0)
         ctx64 = Context([s], precision=0, cg_tol=CG_TOL, preconditioner=pc)
         step64 = lambda: step_with(ctx64, psi, fods, gE)
@@ -456,7 +475,7 @@ def run_gpu(args):
     # the same step with the multigrid-preconditioned CG inner solver, and
     # the roofline of its dominant kernel (the HBM-bound stencil apply)
     pcg = None
-    if solver != 0 and prec == 1 and not args.no_pcg:
+    if solver != 0 and prec == 1 and not args.no_pcg and world == 1:
         ctxp = Context([s], precision=1, cg_tol=CG_TOL, preconditioner=1, solver=0)
         for _ in range(2):
             step_with(ctxp, psi, fods, gE)
@@ -494,10 +513,14 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC if args.workload == "128" else METRIC_192, "value": value, "unit": "solves/s",
                 "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": "f32-cg+f64" if prec == 1 else "f64", "data": "synthetic",
                 "config": {"workload": workload, "precision": args.precision, "preconditioner": args.preconditioner,
                            "solver": args.solver,
+                           "parallelism": ("orbitals of one system over %d ranks" % world if sharded
+                                           else "one system per rank"),
+                           "transforms": ("cuda cores" if args.no_tensor_core_transforms else "tensor cores"),
                            "cg_tol": CG_TOL,
                            "l2": "inputs larger than L2 (psi %.2f GB per rank)" % (8e-9 * norb * s.G),
                            "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},

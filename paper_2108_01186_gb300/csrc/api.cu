@@ -61,6 +61,7 @@ int validate_options(const flosic_options& o, std::string& why) {
         why = "the AAR and KRON solvers require MIXED precision";
     else if (o.boundary != FLOSIC_BC_ISOLATED && o.boundary != FLOSIC_BC_PERIODIC && o.boundary != FLOSIC_BC_SLAB)
         why = "bad boundary";
+    else if (o.kron_tensor_cores != 0 && o.kron_tensor_cores != 1) why = "kron_tensor_cores must be 0 or 1";
     else if (o.boundary != FLOSIC_BC_ISOLATED &&
              (o.solver != FLOSIC_SOLVER_KRON || o.adjoint_mode != FLOSIC_ADJ_REUSE_V ||
               o.fod_grad_mode != FLOSIC_GRAD_INTERP))
@@ -223,6 +224,7 @@ int flosic_default_options(flosic_options* opt) {
     opt->aar_m = 7;
     opt->aar_p = 6;
     opt->boundary = FLOSIC_BC_ISOLATED;
+    opt->kron_tensor_cores = 1;
     return FLOSIC_OK;
 }
 
@@ -377,6 +379,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&c->d_bidx, (long long)bidx.size()); A(&c->d_bcoef, 10LL * (long long)bidx.size());
     A(&w.e_part, 2 * chunk); A(&w.e_orb, 2LL * orb);
     A(&w.status, 4);
+    A(&w.mask, orb);
     A(&w.b64, off); A(&w.r64, off);
     if (o.precision == FLOSIC_FP64) {
         A(&w.p64, off); A(&w.q64, off);
@@ -498,6 +501,12 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
+    if (e == cudaSuccess) {   // every orbital computed here until flosic_set_orbital_mask says otherwise
+        const std::vector<int> ones((size_t)orb, 1);
+        e = cudaMemcpy(w.mask, ones.data(), sizeof(int) * orb, cudaMemcpyHostToDevice);
+        g.mask = w.mask;
+        c->n_unmasked = (int)orb;
+    }
     if (e == cudaSuccess) e = cudaMemset(g.prof_bytes, 0, sizeof(double));
     if (e == cudaSuccess) e = upload_stencil_constants();
     if (e == cudaSuccess) e = upload_boundary_constants();
@@ -576,7 +585,9 @@ int flosic_orbital_poisson(flosic_ctx* c, const double* phi, double* V, int warm
     int st[4];
     rc = read_status(c, s, st);
     if (rc) return rc;
-    if (st[3]) return fail(c, FLOSIC_ERR_CUDA, "a stencil copy did not complete (bounded wait expired)");
+    if (st[3])
+        return fail(c, FLOSIC_ERR_CUDA,
+                    "a bulk copy or a tensor-core completion of the Poisson kernels did not arrive (bounded wait expired)");
     if (st[1]) return fail(c, FLOSIC_ERR_NOCONV, "a Poisson solve reached max_iter");
     return FLOSIC_OK;
 }
@@ -592,6 +603,28 @@ int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* 
     launch_energy_reduce(c, U, Exc, E_sic, s);
     c->have_energy = true;
     return check_cuda(c, cudaGetLastError(), "energy kernels");
+}
+
+int flosic_set_orbital_mask(flosic_ctx* c, const int* mask) {
+    if (!c) return FLOSIC_ERR_ARG;
+    std::vector<int> m((size_t)c->norb, 1);
+    int on = c->norb;
+    if (mask) {
+        on = 0;
+        for (int o = 0; o < c->norb; ++o) {
+            if (mask[o] != 0 && mask[o] != 1) return fail(c, FLOSIC_ERR_ARG, "mask entries must be 0 or 1");
+            m[(size_t)o] = mask[o];
+            on += mask[o];
+        }
+        if (on < c->norb && c->opt.adjoint_mode == FLOSIC_ADJ_EXACT)
+            return fail(c, FLOSIC_ERR_ARG, "an orbital mask requires ADJ_REUSE_V");
+    }
+    int rc = check_cuda(c, cudaMemcpy(c->ws.mask, m.data(), sizeof(int) * c->norb, cudaMemcpyHostToDevice),
+                        "cudaMemcpy(mask)");
+    if (rc) return rc;
+    c->n_unmasked = on;
+    c->have_energy = false;   // the cached V^SIC belongs to the previous mask
+    return FLOSIC_OK;
 }
 
 int flosic_hamiltonian_apply(flosic_ctx* c, const double* psi, const double* vloc, const double* V_avg,

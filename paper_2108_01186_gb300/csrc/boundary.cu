@@ -122,9 +122,11 @@ __global__ void __launch_bounds__(256) k_rhs_bulk(const BlkDesc* __restrict__ bl
                                                   const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                   const double* __restrict__ phi, double scale, int want_mom,
                                                   double* __restrict__ b, double* __restrict__ mom_part,
-                                                  double* __restrict__ mom, unsigned* __restrict__ count) {
+                                                  double* __restrict__ mom, unsigned* __restrict__ count,
+                                                  const int* __restrict__ mask) {
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!mask[P.o]) return;   // an orbital this context does not solve (every CTA of it returns)
     const LvlDesc& D = L[P.b];
     const BlkDesc& B = blk[P.b];
     double m[10];
@@ -174,10 +176,12 @@ __global__ void __launch_bounds__(256) k_rhs_bulk_ff(const BlkDesc* __restrict__
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                      const double* __restrict__ phi, double scale, int want_mom,
                                                      float2* __restrict__ b, double* __restrict__ mom_part,
-                                                     double* __restrict__ mom, unsigned* __restrict__ count) {
+                                                     double* __restrict__ mom, unsigned* __restrict__ count,
+                                                     const int* __restrict__ mask) {
     __shared__ double scratch[32];
     __shared__ double wsum[8][10];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!mask[P.o]) return;   // an orbital this context does not solve (every CTA of it returns)
     const LvlDesc& D = L[P.b];
     const BlkDesc& B = blk[P.b];
     ff m[10];
@@ -309,10 +313,11 @@ void launch_rhs(flosic_ctx* c, const double* phi, bool with_bc, double* b, cudaS
     if (ff)
         k_rhs_bulk_ff<<<(unsigned)M.ntiles[0], tb, 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi,
                                                            scale, with_bc ? 1 : 0, reinterpret_cast<float2*>(b),
-                                                           c->ws.mom_part, c->ws.mom, c->ws.cg.count);
+                                                           c->ws.mom_part, c->ws.mom, c->ws.cg.count, c->ws.mask);
     else
         k_rhs_bulk<<<(unsigned)M.ntiles[0], tb, 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, phi, scale,
-                                                        with_bc ? 1 : 0, b, c->ws.mom_part, c->ws.mom, c->ws.cg.count);
+                                                        with_bc ? 1 : 0, b, c->ws.mom_part, c->ws.mom, c->ws.cg.count,
+                                                        c->ws.mask);
     note_launch(c);
     if (!with_bc) return;
     if (c->opt.boundary == FLOSIC_BC_PERIODIC) {   // mixed precision only (validated)

@@ -157,17 +157,20 @@ __device__ __forceinline__ void xyz_of(long long g, int nx, int ny, int& x, int&
 // ---------------------------------------------------------------------------
 // conjugate gradients, batched over orbitals (one CTA per chunk of points)
 // ---------------------------------------------------------------------------
-__global__ void k_cg_reset(int norb, CgState st) {
+// Masked orbitals (mask 0) take no part: inactive from the start, reported
+// converged after 0 iterations; nact = the number of unmasked orbitals.
+__global__ void k_cg_reset(int norb, int nact, CgState st) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o == 0) {
-        *st.n_active = norb;
-        *st.n_oactive = norb;
+        *st.n_active = nact;
+        *st.n_oactive = nact;
     }
     if (o >= norb) return;
-    st.active[o] = 1;
-    st.oactive[o] = 1;
+    const int on = st.mask[o] != 0;
+    st.active[o] = on;
+    st.oactive[o] = on;
     st.iters[o] = 0;
-    st.conv[o] = 0;
+    st.conv[o] = 1 - on;
     st.count[o] = 0;
     st.rz[o] = 0.0;
     st.beta[o] = 0.0;
@@ -488,6 +491,20 @@ __global__ void __launch_bounds__(256) k_residual_zero(const BlkDesc* __restrict
     }
 }
 
+// V = 0 on every orbital the mask leaves out (one CTA per chunk of points).
+__global__ void k_zero_masked(const BlkDesc* __restrict__ blk, const int* __restrict__ chunk_orb,
+                              const int* __restrict__ orb_blk, const int* __restrict__ mask, double* __restrict__ V) {
+    const int o = chunk_orb[blockIdx.x];
+    if (mask[o]) return;
+    const BlkDesc& B = blk[orb_blk[o]];
+    const long long c = (long long)blockIdx.x - (B.chunk0 + (long long)(o - B.orb0) * B.nchunk);
+    const long long base = B.off + (long long)(o - B.orb0) * B.G;
+    for (int k = threadIdx.x; k < kChunk; k += blockDim.x) {
+        const long long g = c * kChunk + k;
+        if (g < B.G) V[base + g] = 0.0;
+    }
+}
+
 __global__ void k_cg_finish(int norb, CgState st, int* out_iters, int* out_conv, int* status) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= norb) return;
@@ -586,7 +603,7 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
     if (!warm && c->opt.precision == FLOSIC_FP64 &&
         check_cuda(c, cudaMemsetAsync(V, 0, sizeof(double) * c->orb_elems, s), "memset V"))
         return FLOSIC_ERR_CUDA;
-    k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, st); note_launch(c);
+    k_cg_reset<<<(c->norb + 255) / 256, 256, 0, s>>>(c->norb, c->n_unmasked, st); note_launch(c);
     if (c->opt.precision == FLOSIC_FP64) {
         if (warm)
             launch_residual12(c, b, V, w.r64, tol2, max_iter, st.active, st.n_active, 1, s);
@@ -656,6 +673,10 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
             launch_correct_ff(c, x, s);
         }
         launch_join_ff(c, x, V, s);
+    }
+    if (c->n_unmasked < c->norb) {
+        k_zero_masked<<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, st.mask, V);
+        note_launch(c);
     }
     return check_cuda(c, cudaGetLastError(), "poisson kernels");
 }

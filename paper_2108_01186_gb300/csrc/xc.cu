@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kChunkThreads)
 k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double* __restrict__ phi, const double* __restrict__ V, double scale,
             double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part,
-            double* __restrict__ vsic) {
+            double* __restrict__ vsic, const int* __restrict__ mask) {
     using R = typename std::conditional<kF32, float, double>::type;
     __shared__ double red[kChunkThreads / 32][kMaxN][2];
     const BlkDesc& B = blk[blockIdx.y];
@@ -54,12 +54,19 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
     for (int k = 0; k < kXcPts; ++k) num[k] = rs[k] = R(0);
     for (int i = 0; i < B.N; ++i) {
         const long long base = B.off + (long long)i * B.G;
+        const bool on = mask[B.orb0 + i] != 0;   // masked: only its psi^2 enters (rho_sigma)
         R u = R(0), ex = R(0);
         ff uff = {0.f, 0.f};   // kF32: rho V as pairs (U to ~1e-13 relative)
 #pragma unroll
         for (int k = 0; k < kXcPts; ++k) {
             const long long g = g0 + threadIdx.x + k * kChunkThreads;
             if (g >= B.G) continue;
+            if (!on) {
+                const R p = kF32 ? (R)d2f(psi[base + g]) : (R)psi[base + g];
+                rs[k] += p * p;
+                vsic[base + g] = 0.0;
+                continue;
+            }
             R f, v, p, eps, vxc;
             if (kF32) {
                 const float2 f2 = d2ff(phi[base + g]), v2 = d2ff(V[base + g]);
@@ -131,10 +138,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
     const dim3 grid(cmax, c->nblk);
     if (c->opt.precision == FLOSIC_MIXED)
         k_xc_energy<true><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                                         c->ws.e_part, c->ws.vsic);
+                                                         c->ws.e_part, c->ws.vsic, c->ws.mask);
     else
         k_xc_energy<false><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                                          c->ws.e_part, c->ws.vsic);
+                                                          c->ws.e_part, c->ws.vsic, c->ws.mask);
     note_launch(c);
 }
 
