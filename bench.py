@@ -259,6 +259,20 @@ def traffic_for(kernel_src):
     return d.get("traffic_bytes_per_launch_scaled")
 
 
+def kron_tc_traffic(n_orb):
+    """DRAM bytes of the six tensor-core transform passes of one solve, from
+    the committed ncu summary (scaled by orbitals), while kron_tc.cu is the
+    source the capture was taken on."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "kron_tc_traffic.json")))
+        src = os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "kron_tc.cu")
+        if d.get("source_sha") != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
+            return None
+        return int(d["traffic_bytes_per_solve"] * n_orb / d["orbitals"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def step_with(ctx, psi, fods, gE):
     """One forward + adjoint step through the public API."""
     phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
@@ -369,30 +383,49 @@ def run_gpu(args):
             "avg_launch_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
             "share_of_step": round(prof["kernel_ms"] / ms, 4)}
     if solver == 2:
-        # the Kronecker solver's six transform passes: float32 FMA-bound dense
-        # 1-D transforms, 2 n flops per point and pass (counted on the device);
-        # peak = the device's SMs x 128 FP32 lanes x 2 flops x its maximum SM clock
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        fmax = (clocks or {}).get("sm_max_mhz") or 2070.0
-        fp32_peak = sms * 128 * 2 * fmax * 1e6 / 1e12
-        tfl = prof["kernel_bytes"] / (prof["kernel_ms"] / 1e3) / 1e12 if prof["kernel_ms"] > 0 else 0.0
-        kt = None   # DRAM bytes per solve from the committed capture, while kron.cu is unchanged
-        try:
-            kd = json.load(open(os.path.join(ROOT, "profiles", "kron_traffic.json")))
-            ksrc = os.path.join(ROOT, "paper_2108_01186_gb300", "csrc", "kron.cu")
-            if (kd.get("source_sha") == hashlib.sha256(open(ksrc, "rb").read()).hexdigest()[:16]
-                    and args.workload == "128"):
-                kt = kd.get("traffic_bytes_per_solve_scaled")
-        except (OSError, ValueError):
-            kt = None
-        roof = {"bound": "alu", "kernel": "k_kron_pass (6 passes per solve)", "achieved": round(tfl, 2),
-                "peak": round(fp32_peak, 1),
-                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, fmax),
-                "unit": "TFLOP/s", "frac": round(tfl / fp32_peak, 4), "traffic": kt,
-                "traffic_per": "solve (6 launches)", "alg_bytes_per_solve": 6 * 8 * norb * s.G,
-                "alg_flops_per_solve": prof["kernel_bytes"] / launches,
-                "avg_solve_ms": prof["kernel_ms"] / launches, "launches": prof["kernel_launches"],
-                "share_of_step": round(prof["kernel_ms"] / ms, 4)}
+        # the Kronecker solver's six transform passes per solve (timed by the
+        # library around each inner solve; algorithmic flops 2 (n_s^2 + n_a^2)
+        # per line and pass counted on the device)
+        n_local = sum(shard_step.mask) if shard_step is not None else norb   # orbitals this rank solves
+        alg_bytes = 6 * 8 * n_local * s.G          # per solve: every pass reads and writes 4 B per point
+        solve_ms = prof["kernel_ms"] / launches
+        flops_solve = prof["kernel_bytes"] / launches
+        gbs = alg_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else 0.0
+        if not args.no_tensor_core_transforms:
+            # tensor-core transforms: HBM-bound (one read and one write of the
+            # float32 field per pass); the tensor pipe executes the six split
+            # products of every half-size transform
+            try:
+                pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                tcp, tcs = float(pk["bf16_tflops"]), "measured"
+            except (OSError, ValueError, KeyError):
+                tcp, tcs = 1900.0, "fallback"
+            roof = {"bound": "hbm", "kernel": "k_kron_tc (6 passes per solve; tcgen05, split bf16)",
+                    "achieved": round(gbs, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": round(gbs / peak, 4),
+                    "traffic": (kron_tc_traffic(n_local) if args.workload == "128" else None),
+                    "traffic_per": "solve (6 launches)", "alg_bytes_per_solve": alg_bytes,
+                    "avg_solve_ms": solve_ms, "launches": prof["kernel_launches"],
+                    "share_of_step": round(prof["kernel_ms"] / ms, 4),
+                    "tensor_pipe": {"executed_tflops": round(6 * flops_solve / (solve_ms / 1e3) / 1e12, 2)
+                                    if solve_ms > 0 else 0.0,
+                                    "peak": tcp, "peak_source": tcs,
+                                    "frac": round(6 * flops_solve / (solve_ms / 1e3) / 1e12 / tcp, 4)
+                                    if solve_ms > 0 else 0.0}}
+        else:
+            # CUDA-core transforms: float32 FMA-bound dense 1-D products; peak =
+            # the device's SMs x 128 FP32 lanes x 2 flops x its maximum SM clock
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            fmax = (clocks or {}).get("sm_max_mhz") or 2070.0
+            fp32_peak = sms * 128 * 2 * fmax * 1e6 / 1e12
+            tfl = flops_solve / (solve_ms / 1e3) / 1e12 if solve_ms > 0 else 0.0
+            roof = {"bound": "alu", "kernel": "k_kron_pass (6 passes per solve)", "achieved": round(tfl, 2),
+                    "peak": round(fp32_peak, 1),
+                    "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, fmax),
+                    "unit": "TFLOP/s", "frac": round(tfl / fp32_peak, 4), "traffic": None,
+                    "alg_bytes_per_solve": alg_bytes, "hbm_achieved_gbs": round(gbs, 1),
+                    "alg_flops_per_solve": flops_solve, "avg_solve_ms": solve_ms,
+                    "launches": prof["kernel_launches"], "share_of_step": round(prof["kernel_ms"] / ms, 4)}
     # the overlap Gram on the tensor cores (mixed path): algorithmic flops
     # 2 N^2 G per spin block against the measured dense bf16 peak, and its
     # float64 reads of psi (8 N G bytes per block) against the HBM peak
@@ -414,9 +447,37 @@ def run_gpu(args):
                    "avg_launch_ms": prof_ov["kernel_ms"] / prof_ov["kernel_launches"],
                    "launches": prof_ov["kernel_launches"]}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: flosic_step_host
+    # (host arrays in, host arrays out, the library's own copies); two host
+    # input sets alternate, so every step copies its inputs, and each call
+    # hands the library the next step's inputs to copy while it computes
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and shard_step is None:
+        psi_h2 = psi_h.clone().pin_memory()
+        fods_h2 = fods_h.clone().pin_memory()
+        ins = [(psi_h, fods_h), (psi_h2, fods_h2)]
+        pin = lambda n, dt=torch.float64: torch.empty(n, dtype=dt).pin_memory()
+        o_E, o_U, o_X = pin(ctx.nsys), pin(ctx.norb), pin(ctx.norb)
+        o_V, o_dp, o_df, o_cv = pin(ctx.vavg_elems), pin(ctx.orb_elems), pin(3 * ctx.norb), pin(ctx.norb, torch.int32)
+        ctx.step_host(psi_h, fods_h, 1.0, 1.0, o_E, o_U, o_X, o_V, o_dp, o_df, o_cv)   # untimed: buffers
+        ke = max(2, min(args.steps, 6))
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(ke):
+            nx = ins[(k + 1) % 2] if k + 1 < ke else (None, None)
+            ctx.step_host(ins[k % 2][0], ins[k % 2][1], 1.0, 1.0, o_E, o_U, o_X, o_V, o_dp, o_df, o_cv,
+                          psi_next=nx[0], fods_next=nx[1])
+        barrier()
+        te = D.max_over_ranks((time.perf_counter() - t0) / ke, dev)
+        e2e = {"value": units / te, "unit": "solves/s", "api": "flosic_step_host (host arrays in and out)",
+               "steps": ke, "ms_per_step": 1e3 * te,
+               "overlap": "each step's input copy runs during the previous step (the first inside the timed region)",
+               "h2d_bytes_per_step": int(psi_h.numel() * 8 + fods_h.numel() * 8),
+               "d2h_bytes_per_step": int((o_E.numel() + o_U.numel() + o_X.numel() + o_V.numel() + o_dp.numel()
+                                          + o_df.numel()) * 8 + o_cv.numel() * 4)}
+        if abs(float(o_E[0]) - float(E[0])) > 1e-6:
+            raise RuntimeError("host-buffer step disagrees with the device step: %r vs %r" % (float(o_E[0]), float(E[0])))
+    elif not args.no_e2e:
         out_E = torch.empty(1, dtype=torch.float64).pin_memory()
         out_V = torch.empty(ctx.vavg_elems, dtype=torch.float64).pin_memory()
         out_df = torch.empty(3 * norb, dtype=torch.float64).pin_memory()

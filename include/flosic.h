@@ -262,6 +262,32 @@ int flosic_sic_backward(flosic_ctx* ctx, const double* psi, const double* fods,
 int flosic_hamiltonian_apply(flosic_ctx* ctx, const double* psi, const double* vloc,
                              const double* V_avg, double* Hpsi, void* stream);
 
+/* One whole step (steps a1-a10) with inputs and outputs in HOST memory:
+ * flosic_build_flos, flosic_orbital_poisson (cold start),
+ * flosic_sic_energy_potential and flosic_sic_backward on device copies
+ * that the context owns (allocated at the first call: two input sets and
+ * the intermediate and output arrays, about 5 orbital-sized float64 arrays).
+ * No counterpart in the paper; it exists so that the host<->device copies
+ * of a step are issued by the library.
+ * In (host): psi [sum N*G], fods [sum N*3] float64; scale (V_avg factor);
+ *   gE (the same upstream factor for every system's E_sic).
+ * Out (host, any may be NULL): E_sic [nsys], U, Exc [orbitals],
+ *   V_avg [sum G], dE_dpsi [sum N*G], dE_dfod [sum N*3] float64,
+ *   conv_flags [orbitals] int32.
+ * psi_next, fods_next (host, both or neither): the inputs of the next
+ *   call; they are copied to the context's second input set on a separate
+ *   stream while this step computes, and the next call that passes exactly
+ *   these pointers uses them without copying again (the caller must not
+ *   change their contents in between).
+ * Host arrays should be page-locked (cudaHostAlloc / pinned) for the copies
+ * to run asynchronously at full speed.  Waits for `stream`; the outputs are
+ * in host memory on return.  Errors: as the four step calls; NOCONV is
+ * returned after the outputs are copied. */
+int flosic_step_host(flosic_ctx* ctx, const double* psi, const double* fods, double scale, double gE,
+                     double* E_sic, double* U, double* Exc, double* V_avg, double* dE_dpsi,
+                     double* dE_dfod, int* conv_flags, const double* psi_next,
+                     const double* fods_next, void* stream);
+
 /* Instrumentation (no counterpart in the paper): enable != 0 records a CUDA
  * event pair, on the stream the work runs on, around every launch of the
  * dominant kernel of the context's Poisson solver: the stencil apply of CG

@@ -36,6 +36,10 @@ cudaError_t alloc(flosic_ctx* c, T** p, long long n) {
 }
 
 void release(flosic_ctx* c) {
+    if (c->hs.copy) cudaStreamDestroy(c->hs.copy);
+    for (cudaEvent_t e : c->hs.copied)
+        if (e) cudaEventDestroy(e);
+    c->hs = flosic_ctx::HostStep{};
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
     for (cudaEvent_t e : c->ov_ev) cudaEventDestroy(e);
@@ -666,6 +670,81 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
         return FLOSIC_OK;
     }
     return check_cuda(c, cudaGetLastError(), "backward kernels");
+}
+
+int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, double scale, double gE,
+                     double* E_sic, double* U, double* Exc, double* V_avg, double* dE_dpsi, double* dE_dfod,
+                     int* conv_flags, const double* psi_next, const double* fods_next, void* stream) {
+    if (!c) return FLOSIC_ERR_ARG;
+    if (!psi_h || !fods_h) return fail(c, FLOSIC_ERR_ARG, "psi and fods are required");
+    if ((psi_next == nullptr) != (fods_next == nullptr))
+        return fail(c, FLOSIC_ERR_ARG, "psi_next and fods_next go together");
+    if (!std::isfinite(scale) || !std::isfinite(gE)) return fail(c, FLOSIC_ERR_ARG, "scale and gE must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto& H = c->hs;
+    const long long orb = c->orb_elems, nf = 3LL * c->norb;
+    if (!H.ready) {
+        cudaError_t e = cudaSuccess;
+        auto A = [&](auto** p, long long n) { if (e == cudaSuccess) e = alloc(c, p, n); };
+        A(&H.psi[0], orb); A(&H.psi[1], orb); A(&H.fods[0], nf); A(&H.fods[1], nf);
+        A(&H.phi, orb); A(&H.V, orb); A(&H.Vavg, c->vavg_elems); A(&H.dpsi, orb); A(&H.dfod, nf);
+        A(&H.E, (long long)c->sys.size()); A(&H.U, c->norb); A(&H.Exc, c->norb); A(&H.gE, (long long)c->sys.size());
+        A(&H.conv, c->norb);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H.copy, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&H.copied[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return check_cuda(c, e, "host-step buffers");
+        H.ready = true;
+    }
+    const size_t bpsi = sizeof(double) * (size_t)orb, bfod = sizeof(double) * (size_t)nf;
+    int rc;
+    // this step's inputs: already on the device when the previous call prefetched them
+    int cur;
+    if (H.pre >= 0 && H.pre_psi == psi_h && H.pre_fods == fods_h) {
+        cur = H.pre;
+        rc = check_cuda(c, cudaStreamWaitEvent(s, H.copied[cur], 0), "cudaStreamWaitEvent");
+        if (rc) return rc;
+    } else {
+        cur = (H.pre >= 0) ? 1 - H.pre : 0;
+        rc = check_cuda(c, cudaMemcpyAsync(H.psi[cur], psi_h, bpsi, cudaMemcpyHostToDevice, s), "copy psi");
+        if (!rc) rc = check_cuda(c, cudaMemcpyAsync(H.fods[cur], fods_h, bfod, cudaMemcpyHostToDevice, s), "copy fods");
+        if (rc) return rc;
+    }
+    H.pre = -1;
+    // the next step's inputs, copied on the copy stream while this step computes
+    if (psi_next) {
+        const int nxt = 1 - cur;
+        rc = check_cuda(c, cudaMemcpyAsync(H.psi[nxt], psi_next, bpsi, cudaMemcpyHostToDevice, H.copy), "prefetch psi");
+        if (!rc)
+            rc = check_cuda(c, cudaMemcpyAsync(H.fods[nxt], fods_next, bfod, cudaMemcpyHostToDevice, H.copy),
+                            "prefetch fods");
+        if (!rc) rc = check_cuda(c, cudaEventRecord(H.copied[nxt], H.copy), "cudaEventRecord");
+        if (rc) return rc;
+        H.pre = nxt;
+        H.pre_psi = psi_next;
+        H.pre_fods = fods_next;
+    }
+    const int nsys = (int)c->sys.size();
+    std::vector<double> g((size_t)nsys, gE);
+    rc = check_cuda(c, cudaMemcpyAsync(H.gE, g.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s), "copy gE");
+    if (rc) return rc;
+    rc = flosic_build_flos(c, H.psi[cur], H.fods[cur], H.phi, nullptr, nullptr, s);
+    if (rc) return rc;
+    rc = flosic_orbital_poisson(c, H.phi, H.V, 0, nullptr, H.conv, s);
+    if (rc && rc != FLOSIC_ERR_NOCONV) return rc;
+    const int prc = rc;
+    rc = flosic_sic_energy_potential(c, H.psi[cur], H.phi, H.V, scale, H.U, H.Exc, H.E, H.Vavg, s);
+    if (rc) return rc;
+    rc = flosic_sic_backward(c, H.psi[cur], H.fods[cur], H.phi, H.V, H.gE, dE_dpsi ? H.dpsi : nullptr,
+                             dE_dfod ? H.dfod : nullptr, s);
+    if (rc) return rc;
+    struct Out { void* h; const void* d; size_t n; };
+    const Out outs[] = {{E_sic, H.E, sizeof(double) * nsys}, {U, H.U, sizeof(double) * c->norb},
+                        {Exc, H.Exc, sizeof(double) * c->norb}, {V_avg, H.Vavg, sizeof(double) * c->vavg_elems},
+                        {dE_dfod, H.dfod, bfod}, {conv_flags, H.conv, sizeof(int) * c->norb}, {dE_dpsi, H.dpsi, bpsi}};
+    for (const Out& o : outs)
+        if (o.h && !rc) rc = check_cuda(c, cudaMemcpyAsync(o.h, o.d, o.n, cudaMemcpyDeviceToHost, s), "copy out");
+    if (!rc) rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return rc ? rc : prc;
 }
 
 int flosic_profile(flosic_ctx* c, int enable) {

@@ -51,79 +51,112 @@ __device__ __forceinline__ void tmem_add32(uint32_t taddr, float* acc) {
     for (int j = 0; j < 32; ++j) acc[j] += v[j];
 }
 
-template <int NB>   // NB = MMA N / 32 (1 .. 4)
-__global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
+// Orbital rows are padded to NN = 32 NB per sub-chunk; with NN <= 64 several
+// point sub-chunks share the 128 MMA rows (P = 128 / NN of them: row q NN + a
+// holds orbital a over the points of sub-chunk q), so no MMA row is padding
+// when N is a multiple of 32 and a stage moves P times as many points.  The
+// MMA then runs N = P NN columns, and only the diagonal blocks (sub-chunk q
+// with itself) are read back: warp w holds rows 32 w .. 32 w + 31, i.e. part
+// of sub-chunk q = 32 w / NN, and reads its block's NN columns from q NN.
+template <int NB>
+__host__ __device__ constexpr int gram_pack() { return (32 * NB <= 64) ? 128 / (32 * NB) : 1; }
+
+template <int NB>   // NB = orbital rows per sub-chunk / 32 (1 .. 4)
+__global__ void __launch_bounds__(256, NB <= 2 ? 2 : 1) k_gram_tc(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
                                                     float* __restrict__ part, const long long* __restrict__ part_off,
                                                     int* __restrict__ status) {
     extern __shared__ unsigned char g_smem_raw[];
     __shared__ uint64_t mbar[kGStages];
     __shared__ uint32_t tmem_base;
-    constexpr int NN = 32 * NB;                      // MMA N (columns of one accumulator)
-    constexpr uint32_t kCols = (3 * NN <= 32) ? 32 : (3 * NN <= 64) ? 64 : (3 * NN <= 128) ? 128
-                               : (3 * NN <= 256) ? 256 : 512;
+    constexpr int NN = 32 * NB;                      // orbital rows per sub-chunk
+    constexpr int P = gram_pack<NB>();               // sub-chunks sharing the 128 rows
+    constexpr int MN = P * NN;                       // MMA N (columns of one accumulator)
+    constexpr int kSub = kGChunk / P;                // points per sub-chunk
+    constexpr uint32_t kCols = (2 * MN <= 128) ? 128 : 256;
     const BlkDesc& B = blk[blockIdx.y];
     const int N = B.N;
     const long long g_begin = (long long)blockIdx.x * kGChunk;
     if (g_begin >= B.G) return;                      // whole CTA
     const long long g_end = min(g_begin + (long long)kGChunk, B.G);
-    const int nst = (int)((g_end - g_begin + kGK - 1) / kGK);
+    const int nst = kSub / kGK;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
-    // zero every tile once: rows N..127 and points past the chunk stay zero
-    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 128)
+    // zero every tile once: padding rows and points past the chunk stay zero
+    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 256)
         reinterpret_cast<uint4*>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         tc_mbar_init(&mbar[0], 1);
         tc_mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_addr(&tmem_base)),
-                     "r"(kCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (warp == 0) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;                 // columns: [0,NN) and [NN,2NN) hi x hi, [2NN,3NN) cross
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    const uint32_t idesc = umma_idesc_bf16(kGRows, NN);
-    uint32_t phase[kGStages] = {0u, 0u};
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;                 // columns: [0,MN) hi x hi of a stage, [MN,2MN) cross
+    // warps 0-3 read the accumulator lanes that hold sub-chunk rows (with
+    // P NN < 128, as for NN = 96, the last rows are padding: not read)
+    const bool reader = warp < 4 && 32 * warp < P * NN;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int q_own = (32 * (warp & 3)) / NN;        // the reading warp's sub-chunk
+    const uint32_t col0 = (uint32_t)(q_own * NN);    // its diagonal block
+    const uint32_t idesc = umma_idesc_bf16(kGRows, MN);
     bool ok = true;
-    float acc[NN];                                   // row 32 warp + lane of the sums
+    float acc[NN];                                   // row 32 warp + lane of its sub-chunk's sums
 #pragma unroll
     for (int j = 0; j < NN; ++j) acc[j] = 0.f;
     const double* pb = psi + B.off;
     const int k = tid & 63;                          // this thread's point within a stage
+    constexpr int kRows = P * NN;                    // rows (q, a) of a stage
+    constexpr int kGroup = 16;                       // loads in flight per thread before converting
     for (int st = 0; st < nst; ++st) {
-        const int buf = st & 1;
-        if (st >= kGStages) {                        // stage st-2 done: its tile may be overwritten
-            ok = tc_mbar_wait(&mbar[buf], phase[buf]) && ok;
-            phase[buf] ^= 1u;
-        }
+        const int buf = st & 1;                      // (the MMAs of stage st - 2 completed at stage st - 1)
         unsigned char* tile = base + buf * 3 * kGTile;
-        const long long g = g_begin + (long long)st * kGK + k;
-        for (int a = tid >> 6; a < N; a += 2) {
-            const double v = (g < g_end) ? pb[(long long)a * B.G + g] : 0.0;
-            const float f = d2f(v);
-            const __nv_bfloat16 b1 = __float2bfloat16_rn(f);
-            const float r1 = f - __bfloat162float(b1);
-            const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
-            const __nv_bfloat16 b3 = __float2bfloat16_rn(r1 - __bfloat162float(b2));
-            const int off = a * 128 + ((((k >> 3) ^ (a & 7))) << 4) + ((k & 7) << 1);
-            *reinterpret_cast<__nv_bfloat16*>(tile + off) = b1;
-            *reinterpret_cast<__nv_bfloat16*>(tile + kGTile + off) = b2;
-            *reinterpret_cast<__nv_bfloat16*>(tile + 2 * kGTile + off) = b3;
+        // thread: point k of every sub-chunk, rows (q, a) = tid / 64 + 4 i
+#pragma unroll 1
+        for (int r0 = tid >> 6; r0 < kRows; r0 += 4 * kGroup) {
+            double v[kGroup];
+#pragma unroll
+            for (int i = 0; i < kGroup; ++i) {
+                const int row = r0 + 4 * i;
+                const int q = row / NN, a = row - q * NN;
+                const long long g = g_begin + (long long)q * kSub + (long long)st * kGK + k;
+                v[i] = (row < kRows && a < N && g < g_end) ? pb[(long long)a * B.G + g] : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < kGroup; ++i) {
+                const int row = r0 + 4 * i;
+                const int q = row / NN, a = row - q * NN;
+                if (row >= kRows || a >= N) continue;
+                const float f = d2f(v[i]);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(f);
+                const float r1 = f - __bfloat162float(b1);
+                const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 b3 = __float2bfloat16_rn(r1 - __bfloat162float(b2));
+                const int off = row * 128 + ((((k >> 3) ^ (row & 7))) << 4) + ((k & 7) << 1);
+                *reinterpret_cast<__nv_bfloat16*>(tile + off) = b1;
+                *reinterpret_cast<__nv_bfloat16*>(tile + kGTile + off) = b2;
+                *reinterpret_cast<__nv_bfloat16*>(tile + 2 * kGTile + off) = b3;
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (st >= 1) {   // the previous stage's hi x hi sums (read before this stage's MMAs restart them)
+            const int pb2 = (st - 1) & 1;
+            ok = tc_mbar_wait(&mbar[pb2], (uint32_t)(((st - 1) >> 1) & 1)) && ok;
+            ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld is warp-collective
+            tc_fence_after();
+            if (ok && reader) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
+            }
+        }
+        tc_fence_proxy_async();
+        tc_fence_before();
         __syncthreads();
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_fence_after();
             const uint32_t s0 = tc_smem_addr(tile);
-            const uint32_t dhi = tmem + (uint32_t)(buf * NN), dx = tmem + (uint32_t)(2 * NN);
+            const uint32_t dhi = tmem, dx = tmem + (uint32_t)MN;
 #pragma unroll
             for (int kk = 0; kk < kGK / 16; ++kk) {
 #pragma unroll
@@ -134,72 +167,67 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const BlkDesc* __restrict__ 
                     else umma_bf16(dx, da, db, idesc, (st | kk | (p - 1)) != 0);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tc_smem_addr(&mbar[buf]))
-                         : "memory");
-        }
-        if (st >= 1) {                               // add the previous stage's hi x hi sums
-            const int pbuf = buf ^ 1;
-            ok = tc_mbar_wait(&mbar[pbuf], phase[pbuf]) && ok;
-            ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld is warp-collective
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (ok) {
-#pragma unroll
-                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(pbuf * NN + 32 * c), acc + 32 * c);
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            umma_commit(&mbar[buf]);
         }
     }
     // the last stage (its commit covers every MMA of the CTA): its hi x hi
     // sums, then the cross products
-    const int lb = (nst - 1) & 1;
-    ok = tc_mbar_wait(&mbar[lb], phase[lb]) && ok;
+    ok = tc_mbar_wait(&mbar[(nst - 1) & 1], (uint32_t)(((nst - 1) >> 1) & 1)) && ok;
     ok = __all_sync(0xffffffffu, ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    tc_fence_after();
+    if (ok && reader) {
 #pragma unroll
-        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(lb * NN + 32 * c), acc + 32 * c);
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
 #pragma unroll
-        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(2 * NN + 32 * c), acc + 32 * c);
-        const int r = warp * 32 + lane;
-        float* out = part + part_off[blockIdx.y] + (long long)blockIdx.x * N * N;
-        if (r < N) {
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)MN + col0 + 32 * c, acc + 32 * c);
+        const int a = warp * 32 + lane - q_own * NN;  // orbital of this row in its sub-chunk
+        float* out = part + part_off[blockIdx.y] + ((long long)blockIdx.x * P + q_own) * N * N;
+        if (a < N) {
 #pragma unroll
             for (int j = 0; j < NN; ++j)
-                if (j < N) out[(long long)r * N + j] = acc[j];
+                if (j < N) out[(long long)a * N + j] = acc[j];
         }
-    } else if (tid == 0) {
+    } else if (!ok && tid == 0) {
         atomicOr(status + 3, 2);                     // an MMA completion did not arrive in time
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
     }
 }
 
-// M[block][e] = sum over the block's chunks of the float32 partials, in
-// float64 and in chunk order.
+// pk = the launch's sub-chunk partials per chunk (set by its widest block).
 __global__ void k_gram_sum(const BlkDesc* __restrict__ blk, const float* __restrict__ part,
-                           const long long* __restrict__ part_off, double* __restrict__ M) {
+                           const long long* __restrict__ part_off, double* __restrict__ M, int pk) {
     const BlkDesc& B = blk[blockIdx.y];
     const int NN2 = B.N * B.N;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NN2) return;
-    const long long nch = (B.G + kGChunk - 1) / kGChunk;
+    const long long nch = ((B.G + kGChunk - 1) / kGChunk) * pk;
     const float* p = part + part_off[blockIdx.y] + e;
     double s = 0.0;
     for (long long q = 0; q < nch; ++q) s += (double)p[q * NN2];
     M[B.moff + e] = s;
 }
 
+// sub-chunk partials per chunk of every block: set by the widest block, whose
+// row width the one launch of the kernel takes for all blocks
+static int gram_launch_pack(const flosic_ctx* c) {
+    int nmax = 0;
+    for (const auto& b : c->blk) nmax = b.N > nmax ? b.N : nmax;
+    const int nb = (nmax + 31) / 32;
+    return nb <= 1 ? gram_pack<1>() : nb == 2 ? gram_pack<2>() : 1;
+}
+
 long long gram_tc_part_elems(const flosic_ctx* c, std::vector<long long>& off) {
     long long total = 0;
     off.clear();
+    const int pk = gram_launch_pack(c);
     for (const auto& b : c->blk) {
         off.push_back(total);
-        total += ((b.G + kGChunk - 1) / kGChunk) * (long long)b.N * b.N;
+        total += ((b.G + kGChunk - 1) / kGChunk) * pk * (long long)b.N * b.N;
     }
     return total;
 }
@@ -233,17 +261,17 @@ void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
         cudaEventRecord(cm->ov_ev[2 * cm->ov_used], s);
         for (const auto& b : c->blk) cm->ov_flops += 2.0 * b.N * b.N * (double)b.G;
     }
-    if (nb <= 1) k_gram_tc<1><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else if (nb == 2) k_gram_tc<2><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else if (nb == 3) k_gram_tc<3><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else k_gram_tc<4><<<grid, 128, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    if (nb <= 1) k_gram_tc<1><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else if (nb == 2) k_gram_tc<2><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else if (nb == 3) k_gram_tc<3><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+    else k_gram_tc<4><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
     note_launch(cm);
     if (timed) {
         cudaEventRecord(cm->ov_ev[2 * cm->ov_used + 1], s);
         ++cm->ov_used;
     }
     const dim3 g2((unsigned)((nmax * nmax + 255) / 256), (unsigned)c->nblk);
-    k_gram_sum<<<g2, 256, 0, s>>>(c->d_blk, part, off, c->ws.M);
+    k_gram_sum<<<g2, 256, 0, s>>>(c->d_blk, part, off, c->ws.M, gram_launch_pack(c));
     note_launch((flosic_ctx*)c);
 }
 

@@ -221,6 +221,22 @@ struct flosic_ctx {
     double ov_ms = 0.0, ov_flops = 0.0;   // timed duration, algorithmic flops (2 N^2 G per block)
     long long ov_launches = 0;
     std::vector<void*> allocations;
+    // flosic_step_host: device copies of the step's inputs (two sets, so
+    // the next step's can arrive while this one computes) and outputs,
+    // allocated at the first call
+    struct HostStep {
+        bool ready = false;
+        double* psi[2] = {nullptr, nullptr};
+        double* fods[2] = {nullptr, nullptr};
+        const double* pre_psi = nullptr;    // host arrays already copied into set `pre`
+        const double* pre_fods = nullptr;
+        int pre = -1;
+        double *phi = nullptr, *V = nullptr, *Vavg = nullptr, *dpsi = nullptr, *dfod = nullptr;
+        double *E = nullptr, *U = nullptr, *Exc = nullptr, *gE = nullptr;
+        int* conv = nullptr;
+        cudaStream_t copy = nullptr;        // host -> device copies of the next step's inputs
+        cudaEvent_t copied[2] = {nullptr, nullptr};
+    } hs;
 };
 
 namespace flosic {
@@ -296,8 +312,10 @@ cudaError_t upload_ff_weights();
 void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,
                     double tol2, double inner_tol2, cudaStream_t s);
 void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
-                        double inner_tol2, cudaStream_t s);
+                        double inner_tol2, bool store_r, cudaStream_t s);
 void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s);
+// Kronecker inner solver: x += d and r -= A d in one sweep (r in pairs over b)
+void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double inner_tol2, cudaStream_t s);
 void launch_join_ff(flosic_ctx* c, const float2* x, double* V, cudaStream_t s);
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
 const void* k_lowdin_symbol();

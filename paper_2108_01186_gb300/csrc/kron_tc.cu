@@ -18,21 +18,19 @@
 // shared memory; every output store is coalesced (the 32 lanes of a warp
 // own 32 consecutive rows).
 //
-// One CTA per SM streams tiles of 128 rows.  Per tile: the copy engine
-// delivers the rows (float32); the threads fold each row into its even and
-// odd halves (s_k = v_k + v_{n-1-k}, a_k = v_k - v_{n-1-k}: T_d commutes
-// with the reflection, so the transform splits into two half-size
-// products) and write each half as three bf16 terms (v = v1 + v2 + v3, ~24
-// significant bits) in the K-major 128-byte-swizzled operand layout; one
-// thread issues the MMAs (M = 128 rows, N = 64 modes, K = 16 per
-// instruction): the six split products v_i w_j with i + j <= 2 of each
-// half, the v1 w1 product into its own accumulator and the five smaller
-// ones into a second, both in tensor memory (two tile buffers of 256
-// columns); the threads read the accumulators back (tcgen05.ld), add them,
-// apply the scaling (forward z) or the even/odd recombination (inverse) and
-// store.  The copy of the next tile is in flight while a tile is converted,
-// multiplied and stored; the MMAs of a tile run while the previous tile's
-// results are stored.
+// One CTA per SM (17 warps) streams tiles of 128 rows.  The copy engine
+// delivers a tile's rows (float32).  Eight converter warps fold each row
+// into its even and odd halves (s_k = v_k + v_{n-1-k}, a_k = v_k - v_{n-1-k}:
+// T_d commutes with the reflection, so the transform splits into two
+// half-size products) and write each half as three bf16 terms
+// (v = v1 + v2 + v3, ~24 significant bits) in the K-major 128-byte-swizzled
+// operand layout; a control warp issues the copies and the MMAs (M = 128
+// rows, N = 64 modes, K = 16 per instruction): the six split products
+// v_i w_j with i + j <= 2 of each half, the v1 w1 product into its own
+// accumulator and the five smaller ones into a second, both in tensor
+// memory (two tile buffers of 256 columns); eight epilogue warps read the
+// accumulators back (tcgen05.ld), add them, apply the scaling (forward z)
+// or the even/odd recombination (inverse) and store.
 //
 // Accuracy: keeping the dominant product in its own short accumulation
 // chain (4 instructions of K = 16 per half) holds the tensor cores'
@@ -58,7 +56,9 @@ namespace {
 
 constexpr int kTcRows = 128;                      // rows (lines) per tile: MMA M
 constexpr int kTcHalf = 64;                       // half-line length (K) and modes per half (N), padded
-constexpr int kTcThreads = 256;
+constexpr int kTcConv = 256;                     // converter threads (warps 1-8: two per row)
+constexpr int kTcEpi = 256;                      // epilogue threads (warps 9-16: two per row)
+constexpr int kTcThreads = 32 + kTcConv + kTcEpi;   // + the control warp
 constexpr int kTcATile = kTcRows * kTcHalf * 2;   // one split of one half of a tile (bf16): 16 KB
 constexpr int kTcBTile = kTcHalf * kTcHalf * 2;   // one split of one half-matrix (bf16): 8 KB
 constexpr int kTcBox = kTcRows * 32 * 4;          // one copy: 128 rows x 32 points (float32): 16 KB
@@ -116,34 +116,18 @@ __device__ __forceinline__ long long tc_next(const KronTcArgs& a, long long it, 
     return it1;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// Writes eight consecutive K values of one half of row r as three bf16
-// splits into the K-major, 128-byte-swizzled operand tiles (chunk c).
-__device__ __forceinline__ void tc_store_chunk(unsigned char* sA, int half, int r, int c, const float* v) {
-    uint32_t w1[4], w2[4], w3[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        __nv_bfloat16 x1[2], x2[2], x3[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float f = v[2 * p + e];
-            x1[e] = __float2bfloat16_rn(f);
-            const float r1 = f - __bfloat162float(x1[e]);
-            x2[e] = __float2bfloat16_rn(r1);
-            x3[e] = __float2bfloat16_rn(r1 - __bfloat162float(x2[e]));
-        }
-        w1[p] = pack_bf16(x1[0], x1[1]);
-        w2[p] = pack_bf16(x2[0], x2[1]);
-        w3[p] = pack_bf16(x3[0], x3[1]);
-    }
-    const int off = r * 128 + ((c ^ (r & 7)) << 4);
-    unsigned char* base = sA + half * 3 * kTcATile + off;
-    *reinterpret_cast<uint4*>(base) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4*>(base + kTcATile) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-    *reinterpret_cast<uint4*>(base + 2 * kTcATile) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+// Three bf16 terms of a pair of floats (f0, f1), each packed as bf16x2 (f0 in
+// the low half): v = v1 + v2 + v3 with v1 = bf16(v), v2 = bf16(v - v1),
+// v3 = bf16(v - v1 - v2) (the differences are exact in float32).
+__device__ __forceinline__ void tc_split2(float f0, float f1, uint32_t& w1, uint32_t& w2, uint32_t& w3) {
+    const __nv_bfloat162 b1 = __floats2bfloat162_rn(f0, f1);
+    w1 = *reinterpret_cast<const uint32_t*>(&b1);
+    const float r0 = f0 - __uint_as_float(w1 << 16), r1 = f1 - __uint_as_float(w1 & 0xffff0000u);
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0, r1);
+    w2 = *reinterpret_cast<const uint32_t*>(&b2);
+    const float q0 = r0 - __uint_as_float(w2 << 16), q1 = r1 - __uint_as_float(w2 & 0xffff0000u);
+    const __nv_bfloat162 b3 = __floats2bfloat162_rn(q0, q1);
+    w3 = *reinterpret_cast<const uint32_t*>(&b3);
 }
 
 // four consecutive points pos..pos+3 (pos a multiple of 4) of row r of the staged copy
@@ -151,20 +135,36 @@ __device__ __forceinline__ float4 tc_raw4(const unsigned char* sR, int r, int po
     return *reinterpret_cast<const float4*>(sR + (pos >> 5) * kTcBox + r * 128 + ((((pos & 31) >> 2) ^ (r & 7)) << 4));
 }
 
+// Warp roles: warp 0 issues the copies and the MMAs (one lane), warps 1-8
+// convert (two threads per row), warps 9-16 drain the accumulators and store
+// (two threads per row).  They meet only at mbarriers, each completing once
+// per tile:
+//   bar_tma      the tile's rows have arrived            (copy engine)
+//   bar_raw      every converter has read them           (8 warp arrivals)
+//   bar_conv[h]  half h's operand tiles are written      (8 warp arrivals)
+//   bar_half[h]  half h's MMAs have completed            (MMA commit)
+//   bar_mma[b]   the tile in tensor-memory buffer b is done (MMA commit)
+//   bar_empty[b] the epilogue has read buffer b          (8 warp arrivals)
+// so the even half's MMAs run while the odd half is converted, the odd
+// half's while the next tile's rows are read, and the stores of one tile
+// while the next is converted.  Every wait sleeps on its mbarrier, gives up
+// after about two seconds or as soon as another warp has given up
+// (s_abort), and the decision is warp-uniform.
 __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long long total) {
     extern __shared__ unsigned char kt_smem_raw[];
-    __shared__ uint64_t bar_tma, bar_mma;
+    __shared__ uint64_t bar_tma, bar_raw, bar_conv[2], bar_half[2], bar_mma[2], bar_empty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
+    __shared__ int s_tma_issued, s_tma_waited, s_mma_issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * per_cta;
     const long long it1 = it0 + per_cta < total ? it0 + per_cta : total;
     if (it0 >= it1) return;
     int bsearch = 0;
-    TcTile cur{};
-    long long item = tc_next(a, it0, it1, bsearch, cur);
-    if (item >= it1) return;   // uniform: every thread walks the same items
+    TcTile first{};
+    const long long item0 = tc_next(a, it0, it1, bsearch, first);
+    if (item0 >= it1) return;   // uniform: every thread walks the same items
 
     unsigned char* sm =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(kt_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -173,8 +173,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     unsigned char* sR = sm + kTcOffRaw;
     if (tid == 0) {
         tc_mbar_init(&bar_tma, 1);
-        tc_mbar_init(&bar_mma, 1);
+        tc_mbar_init(&bar_raw, kTcConv / 32);
+        for (int b = 0; b < 2; ++b) {
+            tc_mbar_init(&bar_conv[b], kTcConv / 32);
+            tc_mbar_init(&bar_half[b], 1);
+            tc_mbar_init(&bar_mma[b], 1);
+            tc_mbar_init(&bar_empty[b], kTcEpi / 32);
+        }
         s_abort = 0;
+        s_tma_issued = s_tma_waited = s_mma_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(&tmem_base, kTcCols);
@@ -183,181 +190,217 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    auto issue_copy = [&](const TcTile& t) {   // thread 0: the tile's rows, all points
-        const BlkDesc& B = a.blk[t.b];
-        const int n = tc_side(B, a.axis);
-        const long long R = B.G / n;
-        const int nbox = (n + 31) >> 5;
-        const int row0 = (int)((long long)t.o * R + (long long)t.q * kTcRows);
-        tc_mbar_expect_tx(&bar_tma, (uint32_t)(nbox * kTcBox));
-        for (int bx = 0; bx < nbox; ++bx) tc_tma_load_2d(sR + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma);
-    };
-
-    // results of tile t from tensor-memory buffer buf: warp w reads lanes
-    // 32 (w mod 4) .. (the tile's rows) and modes 32 (w / 4) .. of both halves
-    auto epilogue = [&](const TcTile& t, int buf) {
-        const BlkDesc& B = a.blk[t.b];
-        const int n = tc_side(B, a.axis), ns = n >> 1;
-        const long long R = B.G / n;
-        const int r = 32 * (warp & 3) + lane, hc = warp >> 2;
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * 256 + 32 * hc);
-        float e0[32], e1[32], o0[32], o1[32];
-        tmem_ld32(ta, e0);
-        tmem_ld32(ta + 64, e1);
-        tmem_ld32(ta + 128, o0);
-        tmem_ld32(ta + 192, o1);
-        tmem_wait_ld();
-        const long long l = (long long)t.q * kTcRows + r;   // row within the orbital
-        if (l >= R) return;
-        float* dst = a.out + B.off + (long long)t.o * B.G + l;
-        if (!a.inverse) {
+    if (warp == 0) {
+        // ---- control: copies and MMAs (lane 0) --------------------------------
+        if (lane == 0) {
+            auto issue_copy = [&](const TcTile& t) {
+                const BlkDesc& B = a.blk[t.b];
+                const int n = tc_side(B, a.axis);
+                const long long R = B.G / n;
+                const int nbox = (n + 31) >> 5;
+                const int row0 = (int)((long long)t.o * R + (long long)t.q * kTcRows);
+                tc_mbar_expect_tx(&bar_tma, (uint32_t)(nbox * kTcBox));
+                for (int bx = 0; bx < nbox; ++bx)
+                    tc_tma_load_2d(sR + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma);
+                ++s_tma_issued;
+            };
+            const uint32_t idesc = umma_idesc_bf16(kTcRows, kTcHalf);
+            const uint32_t a0 = tc_smem_addr(sA), b0 = tc_smem_addr(sB);
+            TcTile cur = first;
+            long long item = item0;
+            int bs = bsearch;
+            issue_copy(cur);
+            for (int t = 0;; ++t) {
+                TcTile nxt_t{};
+                const long long nxt = tc_next(a, item + 1, it1, bs, nxt_t);
+                // the converters have read the rows: the next tile's copy may land
+                if (!tc_mbar_sleep_or_abort(&bar_raw, (uint32_t)(t & 1), &s_abort)) break;
+                s_tma_waited = s_tma_issued;
+                if (nxt < it1) issue_copy(nxt_t);
+                bool ok = true;
+                for (int h = 0; h < 2 && ok; ++h) {
+                    ok = tc_mbar_sleep_or_abort(&bar_conv[h], (uint32_t)(t & 1), &s_abort);
+                    // tensor-memory buffer t & 1 was drained by the epilogue of tile t - 2
+                    if (ok && h == 0 && t >= 2)
+                        ok = tc_mbar_sleep_or_abort(&bar_empty[t & 1], (uint32_t)(((t - 2) >> 1) & 1), &s_abort);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t dm = tmem + (uint32_t)((t & 1) * 256 + h * 128);
+#pragma unroll 1
+                    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                        for (int p = 0; p < 6; ++p) {
+                            const uint64_t da = umma_desc_sw128(a0 + (h * 3 + c_tc_pa[p]) * kTcATile + kk * 32);
+                            const uint64_t db = umma_desc_sw128(b0 + (h * 3 + c_tc_pb[p]) * kTcBTile + kk * 32);
+                            if (p == 0) umma_bf16(dm, da, db, idesc, kk != 0);
+                            else umma_bf16(dm + 64, da, db, idesc, (kk | (p - 1)) != 0);
+                        }
+                    }
+                    umma_commit(&bar_half[h]);
+                }
+                if (!ok) break;
+                umma_commit(&bar_mma[t & 1]);
+                ++s_mma_issued;
+                if (a.flops) {
+                    const BlkDesc& B = a.blk[cur.b];
+                    const int n = tc_side(B, a.axis), ns = n >> 1;
+                    const long long rows = B.G / n - (long long)cur.q * kTcRows;
+                    atomicAdd(a.flops, 4.0 * (double)ns * ns * (double)(rows < kTcRows ? rows : kTcRows));
+                }
+                if (nxt >= it1) break;
+                cur = nxt_t;
+                item = nxt;
+            }
+        }
+        __syncwarp();
+    } else if (warp <= kTcConv / 32) {
+        // ---- converters: rows in, fold, split, operand tiles ---------------
+        const int ct = tid - 32;
+        const int r = ct & (kTcRows - 1), kp = ct >> 7;   // row r, K values 32 kp .. 32 kp + 31
+        const int rsw = r & 7;
+        unsigned char* const arow = sA + r * 128;
+        TcTile cur = first;
+        long long item = item0;
+        int bs = bsearch, loaded_b = -1;
+        for (int t = 0;; ++t) {
+            bool ok = tc_mbar_sleep_or_abort(&bar_tma, (uint32_t)(t & 1), &s_abort);
+            if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
+            const BlkDesc& B = a.blk[cur.b];
+            const int n = tc_side(B, a.axis), ns = n >> 1;
+            float4 fr[8], bk[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int k = 32 * kp + 4 * g;
+                fr[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                bk[g] = fr[g];
+                if (k < ns) {
+                    fr[g] = tc_raw4(sR, r, k);
+                    bk[g] = tc_raw4(sR, r, a.inverse ? ns + k : n - 4 - k);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc_mbar_arrive(&bar_raw);   // the staged rows may be overwritten
+            if (cur.b != loaded_b) {   // this block's matrices, once the last tile's MMAs have completed
+                ok = t < 1 || tc_mbar_sleep_or_abort(&bar_half[1], (uint32_t)((t - 1) & 1), &s_abort);
+                if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
+                const uint16_t* src = a.mat + B.kt[a.axis] + (a.inverse ? 6 * kTcMatElems : 0);
+                for (int i = ct; i < 6 * 64 * 8; i += kTcConv) {
+                    const int mt = i >> 9, m = (i >> 3) & 63, c = i & 7;
+                    const uint4 v = *reinterpret_cast<const uint4*>(src + mt * kTcMatElems + m * 64 + c * 8);
+                    *reinterpret_cast<uint4*>(sB + mt * kTcBTile + m * 128 + ((c ^ (m & 7)) << 4)) = v;
+                }
+                loaded_b = cur.b;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // the last tile's MMAs of this half have read its operand tiles
+                ok = t < 1 || tc_mbar_sleep_or_abort(&bar_half[h], (uint32_t)((t - 1) & 1), &s_abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    s_abort = 1;
+                    break;
+                }
+                unsigned char* const ah = arow + h * 3 * kTcATile;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {   // chunk c = 4 kp + cc holds K = 8c .. 8c + 7
+                    uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float4 x = fr[2 * cc + e], y = bk[2 * cc + e];
+                        const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+                        float v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (a.inverse) v[i] = h == 0 ? xs[i] : ys[i];
+                            else v[i] = h == 0 ? xs[i] + ys[3 - i] : xs[i] - ys[3 - i];
+                        }
+                        tc_split2(v[0], v[1], w1[2 * e], w2[2 * e], w3[2 * e]);
+                        tc_split2(v[2], v[3], w1[2 * e + 1], w2[2 * e + 1], w3[2 * e + 1]);
+                    }
+                    unsigned char* dstc = ah + (((4 * kp + cc) ^ rsw) << 4);
+                    *reinterpret_cast<uint4*>(dstc) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                    *reinterpret_cast<uint4*>(dstc + kTcATile) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+                    *reinterpret_cast<uint4*>(dstc + 2 * kTcATile) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+                }
+                tc_fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc_mbar_arrive(&bar_conv[h]);
+            }
+            if (s_abort) break;
+            TcTile nxt_t{};
+            const long long nxt = tc_next(a, item + 1, it1, bs, nxt_t);
+            if (nxt >= it1) break;
+            cur = nxt_t;
+            item = nxt;
+        }
+    } else {
+        // ---- epilogue: accumulators -> scaling / recombination -> stores -------
+        const int g4 = warp & 3;                                  // TMEM lanes 32 g4 .. = tile rows
+        const int hc = (warp - 1 - kTcConv / 32) >> 2;            // modes 32 hc .. 32 hc + 31
+        const int r = 32 * g4 + lane;
+        TcTile cur = first;
+        long long item = item0;
+        int bs = bsearch;
+        for (int t = 0;; ++t) {
+            const bool ok = tc_mbar_sleep_or_abort(&bar_mma[t & 1], (uint32_t)((t >> 1) & 1), &s_abort);
+            if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
+            tc_fence_after();
+            const BlkDesc& B = a.blk[cur.b];
+            const int n = tc_side(B, a.axis), ns = n >> 1;
+            const long long R = B.G / n;
+            const long long l = (long long)cur.q * kTcRows + r;   // row within the orbital
             float lxy = 0.f;
-            const float* lz = a.lam + B.kl[2];
-            if (a.scale) {   // forward z: rows are (my, mx), mx fastest
+            if (a.scale && l < R) {   // forward z: rows are (my, mx), mx fastest
                 const int mx = (int)(l % B.nx), my = (int)(l / B.nx);
                 lxy = a.lam[B.kl[0] + mx] + a.lam[B.kl[1] + my];
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int m = 32 * hc + j;
-                if (m < ns) {
-                    float ve = e0[j] + e1[j], vo = o0[j] + o1[j];
-                    if (a.scale) {   // (fast division: 2 ulp, far below the solve's accuracy)
-                        const float se = lxy + lz[m], so = lxy + lz[ns + m];
-                        ve = se > 0.f ? __fdividef(ve, se) : 0.f;
-                        vo = so > 0.f ? __fdividef(vo, so) : 0.f;
-                    }
-                    __stcs(dst + (long long)m * R, ve);
-                    __stcs(dst + (long long)(ns + m) * R, vo);
+            const float* lz = a.lam + B.kl[2];
+            const uint32_t ta = tmem + ((uint32_t)(32 * g4) << 16) + (uint32_t)((t & 1) * 256 + 32 * hc);
+            float* const dst = a.out + B.off + (long long)cur.o * B.G + (l < R ? l : 0);
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                float e0[16], e1[16], o0[16], o1[16];
+                tmem_ld16(ta + 16 * c, e0);
+                tmem_ld16(ta + 16 * c + 64, e1);
+                tmem_ld16(ta + 16 * c + 128, o0);
+                tmem_ld16(ta + 16 * c + 192, o1);
+                tmem_wait_ld();
+                if (c == 1) {   // the buffer is read: the MMAs of tile t + 2 may overwrite it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc_mbar_arrive(&bar_empty[t & 1]);
                 }
-            }
-        } else {
+                const int m0 = 32 * hc + 16 * c;
+                if (l < R && m0 < ns) {
+                    float* p1 = dst + (long long)m0 * R;                                   // position m
+                    float* p2 = dst + (long long)(a.inverse ? n - 1 - m0 : ns + m0) * R;   // its partner
+                    const long long s2 = a.inverse ? -R : R;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int k = 32 * hc + j;
-                if (k < ns) {
-                    const float S = e0[j] + e1[j], A = o0[j] + o1[j];
-                    __stcs(dst + (long long)k * R, S + A);
-                    __stcs(dst + (long long)(n - 1 - k) * R, S - A);
-                }
-            }
-        }
-    };
-
-    if (tid == 0) issue_copy(cur);
-    uint32_t tma_ph = 0, mma_ph = 0;
-    int loaded_b = -1;
-    bool have_prev = false;
-    TcTile prev{};
-    int prev_buf = 0, ntile = 0;
-    const int r = tid & (kTcRows - 1), kp = tid >> 7;   // converter: row r, K values 32 kp .. 32 kp + 31
-    for (;;) {
-        bool ok = tc_mbar_wait(&bar_tma, tma_ph);
-        tma_ph ^= 1u;
-        if (have_prev) {
-            ok = tc_mbar_wait(&bar_mma, mma_ph) && ok;
-            mma_ph ^= 1u;
-        }
-        if (!ok) atomicOr(&s_abort, 1);
-        const BlkDesc& B = a.blk[cur.b];
-        const int n = tc_side(B, a.axis), ns = n >> 1;
-        // this thread's raw values: forward (v_k, v_{n-4-k..n-1-k}), inverse (c_s[k..], c_a[k..])
-        float4 fr[8], bk[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const int k = 32 * kp + 4 * g;
-            fr[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-            bk[g] = fr[g];
-            if (ok && k < ns) {
-                fr[g] = tc_raw4(sR, r, k);
-                bk[g] = tc_raw4(sR, r, a.inverse ? ns + k : n - 4 - k);
-            }
-        }
-        TcTile nxt_t{};
-        const long long nxt = tc_next(a, item + 1, it1, bsearch, nxt_t);
-        tc_fence_before();
-        __syncthreads();   // the staged rows are read; previous results are read from tensor memory
-        if (s_abort) break;
-        if (tid == 0 && nxt < it1) issue_copy(nxt_t);
-        if (cur.b != loaded_b) {   // this block's matrices (the previous tile's MMAs have completed)
-            const uint16_t* src = a.mat + B.kt[a.axis] + (a.inverse ? 6 * kTcMatElems : 0);
-            for (int i = tid; i < 6 * 64 * 8; i += kTcThreads) {
-                const int mt = i >> 9, m = (i >> 3) & 63, c = i & 7;
-                const uint4 v = *reinterpret_cast<const uint4*>(src + mt * kTcMatElems + m * 64 + c * 8);
-                *reinterpret_cast<uint4*>(sB + mt * kTcBTile + m * 128 + ((c ^ (m & 7)) << 4)) = v;
-            }
-            loaded_b = cur.b;
-        }
-        // fold (forward) and split into the operand tiles: chunk c = 4 kp + cc holds K = 8c .. 8c + 7
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            float s8[8], d8[8];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float4 x = fr[2 * cc + h], y = bk[2 * cc + h];
-                const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (a.inverse) {
-                        s8[4 * h + i] = xs[i];
-                        d8[4 * h + i] = ys[i];
-                    } else {
-                        s8[4 * h + i] = xs[i] + ys[3 - i];
-                        d8[4 * h + i] = xs[i] - ys[3 - i];
+                    for (int j = 0; j < 16; ++j) {
+                        if (m0 + j < ns) {
+                            float ve = e0[j] + e1[j], vo = o0[j] + o1[j];
+                            if (!a.inverse) {
+                                if (a.scale) {   // (fast division: 2 ulp, far below the solve's accuracy)
+                                    const float se = lxy + lz[m0 + j], so = lxy + lz[ns + m0 + j];
+                                    ve = se > 0.f ? __fdividef(ve, se) : 0.f;
+                                    vo = so > 0.f ? __fdividef(vo, so) : 0.f;
+                                }
+                                __stcs(p1, ve);
+                                __stcs(p2, vo);
+                            } else {
+                                __stcs(p1, ve + vo);
+                                __stcs(p2, ve - vo);
+                            }
+                        }
+                        p1 += R;
+                        p2 += s2;
                     }
                 }
             }
-            tc_store_chunk(sA, 0, r, 4 * kp + cc, s8);
-            tc_store_chunk(sA, 1, r, 4 * kp + cc, d8);
-        }
-        tc_fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        const int buf = ntile & 1;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t idesc = umma_idesc_bf16(kTcRows, kTcHalf);
-            const uint32_t a0 = tc_smem_addr(sA), b0 = tc_smem_addr(sB);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t dm = tmem + (uint32_t)(buf * 256 + h * 128);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-                    for (int p = 0; p < 6; ++p) {
-                        const uint64_t da = umma_desc_sw128(a0 + (h * 3 + c_tc_pa[p]) * kTcATile + kk * 32);
-                        const uint64_t db = umma_desc_sw128(b0 + (h * 3 + c_tc_pb[p]) * kTcBTile + kk * 32);
-                        if (p == 0) umma_bf16(dm, da, db, idesc, kk != 0);
-                        else umma_bf16(dm + 64, da, db, idesc, (kk | (p - 1)) != 0);
-                    }
-                }
-            }
-            umma_commit(&bar_mma);
-            if (a.flops) {
-                const long long R = B.G / n;
-                const long long rows = R - (long long)cur.q * kTcRows;
-                atomicAdd(a.flops, 4.0 * (double)ns * ns * (double)(rows < kTcRows ? rows : kTcRows));
-            }
-        }
-        if (have_prev) {
-            tc_fence_after();
-            epilogue(prev, prev_buf);
-        }
-        prev = cur;
-        prev_buf = buf;
-        have_prev = true;
-        ++ntile;
-        if (nxt >= it1) break;
-        cur = nxt_t;
-        item = nxt;
-    }
-    if (!s_abort) {   // the last tile (the abort flag is block-uniform here)
-        if (!tc_mbar_wait(&bar_mma, mma_ph)) atomicOr(&s_abort, 1);
-        mma_ph ^= 1u;
-        __syncthreads();
-        if (!s_abort) {
-            tc_fence_after();
-            epilogue(prev, prev_buf);
+            TcTile nxt_t{};
+            const long long nxt = tc_next(a, item + 1, it1, bs, nxt_t);
+            if (nxt >= it1) break;
+            cur = nxt_t;
+            item = nxt;
         }
     }
     tc_fence_before();
@@ -365,8 +408,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     if (s_abort && tid == 0) {
         atomicOr(a.status + 3, 4);
         // let the copy and the MMAs this CTA has in flight finish (bounded)
-        tc_mbar_wait(&bar_tma, tma_ph ^ 1u);
-        tc_mbar_wait(&bar_mma, mma_ph ^ 1u);
+        if (s_tma_issued > s_tma_waited) tc_mbar_wait(&bar_tma, (uint32_t)((s_tma_issued - 1) & 1));
+        if (s_mma_issued > 0) {
+            const int last = s_mma_issued - 1;
+            tc_mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1));
+        }
     }
     __syncthreads();
     if (warp == 0) {

@@ -638,11 +638,14 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
         float* p32 = (mg || c->opt.solver != FLOSIC_SOLVER_PCG) ? nullptr : w.p32;
         if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset")) return FLOSIC_ERR_CUDA;
         launch_ff_init(c, b, V, warm, x, p32, tol2, inner_tol2, s);
+        // with the Kronecker solve (which overwrites d), each round ends with one
+        // sweep: x += d and the residual updated from d, r -= A d (b holds r)
+        const bool fused = c->opt.solver == FLOSIC_SOLVER_KRON;
         for (int round = 0; round < 40; ++round) {
-            if (round > 0 || warm) {
+            if ((round > 0 && !fused) || (round == 0 && warm)) {
                 if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
                     return FLOSIC_ERR_CUDA;
-                launch_residual_ff(c, b, x, p32, tol2, inner_tol2, s);
+                launch_residual_ff(c, b, x, p32, tol2, inner_tol2, fused, s);
             }
             const int na = read_count(c, st.n_oactive, s);
             if (na < 0) return FLOSIC_ERR_CUDA;
@@ -670,7 +673,13 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
                     k_cg_pupdate<float><<<nb, T, 0, s>>>(c->d_blk, c->d_chunk_orb, c->d_orb_blk, w.r32, w.p32, st); note_launch(c);
                 }
             }
-            launch_correct_ff(c, x, s);
+            if (fused) {
+                if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
+                    return FLOSIC_ERR_CUDA;
+                launch_update_ff(c, b, x, tol2, inner_tol2, s);
+            } else {
+                launch_correct_ff(c, x, s);
+            }
         }
         launch_join_ff(c, x, V, s);
     }

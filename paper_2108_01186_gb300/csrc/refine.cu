@@ -107,13 +107,15 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
 }
 
 // r = b - A x in pairs on the tiles of the float-float sweep.  Writes
-// r32 = float(r), d32 = 0 (p32 = r32 when given) and starts the next round.
+// r32 = float(r), d32 = 0 (p32 = r32 when given) and starts the next round;
+// with store_r also r itself as pairs over b (each point's r needs only its
+// own b), for the rounds that then update r from the corrections.
 __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                        const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                       const float2* __restrict__ b, const float2* __restrict__ x,
+                                                       float2* __restrict__ b, const float2* __restrict__ x,
                                                        float* __restrict__ r32, float* __restrict__ p32,
                                                        float* __restrict__ d32, double tol2, double inner_tol2,
-                                                       int max_iter, CgState st) {
+                                                       int max_iter, int store_r, CgState st) {
     __shared__ ff plane[kPY][kPX];
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
@@ -127,10 +129,53 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
             // acc = h^2 Delta_h x, so r = b - A x = b + acc / h^2
             const ff r = ff_add(to_ff(b[g]), ff_mul(acc, ih2));
             const float rv = r.h;
+            if (store_r) b[g] = make_float2(r.h, r.l);
             r32[g] = rv;
             d32[g] = 0.f;
             if (p32) p32[g] = rv;
             rrf += rv * rv;
+        },
+        plane);
+    if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[P.o] = 0;
+            start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
+        }
+    }
+}
+
+// One refinement round's update from the float32 correction d of the inner
+// solve: r -= A d (r in pairs, in place: r_{k+1} = b - A x_{k+1} =
+// r_k - A d_k), x += d (pairs), r32 = float(r), and the next round's start.
+// The operand of the sweep is d itself, a float32 field, so the stencil sums
+// run on plain floats.  d is left as it is (neighbouring tiles read it as
+// halo): this serves inner solvers that overwrite d (the Kronecker-product
+// solve), not those that start from d = 0.
+__global__ void __launch_bounds__(256) k_update12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                     const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                     float2* __restrict__ r, float2* __restrict__ x,
+                                                     float* __restrict__ r32, const float* __restrict__ d32,
+                                                     double tol2, double inner_tol2, int max_iter, CgState st) {
+    __shared__ float plane[kPY][kPX];
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    const ff ih2 = to_ff(d2ff(1.0 / (D.h * D.h)));   // once per CTA
+    float rrf = 0.f;
+    ff_sweep12_f(
+        D, P, [&](long long g) { return d32[g]; },
+        [&](long long g, float dc, ff acc) {
+            // acc = h^2 Delta_h d, so r - A d = r + acc / h^2
+            const ff rn = ff_add(to_ff(r[g]), ff_mul(acc, ih2));
+            const float2 xv = x[g];
+            const ff xs = ff_two_sum(xv.x, dc);
+            const ff xn = ff_quick(xs.h, xs.l + xv.y);
+            r[g] = make_float2(rn.h, rn.l);
+            x[g] = make_float2(xn.h, xn.l);
+            r32[g] = rn.h;
+            rrf += rn.h * rn.h;
         },
         plane);
     if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
@@ -203,11 +248,19 @@ void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, 
 }
 
 void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
-                        double inner_tol2, cudaStream_t s) {
+                        double inner_tol2, bool store_r, cudaStream_t s) {
     const Multigrid& M = c->mg;
     k_residual12_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
-        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<const float2*>(b), x, c->ws.r32, p32,
-        c->ws.d32, tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(const_cast<double*>(b)), x,
+        c->ws.r32, p32, c->ws.d32, tol2, inner_tol2, c->opt.max_iter, store_r ? 1 : 0, c->ws.cg);
+    note_launch(c);
+}
+
+void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double inner_tol2, cudaStream_t s) {
+    const Multigrid& M = c->mg;
+    k_update12_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(r), x, c->ws.r32, c->ws.d32,
+        tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
     note_launch(c);
 }
 

@@ -94,7 +94,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* out) {
     for (int j = 0; j < 32; ++j) out[j] = __uint_as_float(v[j]);
 }
 
+// 16 consecutive columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[j] = __uint_as_float(v[j]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// plain arrival (no transaction count) on an mbarrier
+__device__ __forceinline__ void tc_mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_addr(bar)) : "memory");
+}
+
+// bounded wait that also gives up as soon as *abort (shared) becomes nonzero
+__device__ __forceinline__ bool tc_mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+    for (long long i = 0; i < kTcWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tc_smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+// As tc_mbar_wait_or_abort, but each poll may suspend the thread for up to
+// about a microsecond (it resumes as soon as the phase completes), so a
+// waiting warp takes almost no issue slots; gives up after about two
+// seconds.
+__device__ __forceinline__ bool tc_mbar_sleep_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+    for (int i = 0; i < (1 << 21); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tc_smem_addr(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+// named barrier over `count` threads (a multiple of 32) of the CTA
+__device__ __forceinline__ void tc_named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // generic-proxy shared-memory writes become visible to the async proxy (MMA operand reads)

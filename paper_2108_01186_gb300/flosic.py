@@ -28,7 +28,8 @@ ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "f
                  "flosic_layout", "flosic_build_flos", "flosic_orbital_poisson",
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
                  "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error",
-                 "flosic_hamiltonian_apply", "flosic_profile_read_overlap", "flosic_set_orbital_mask")
+                 "flosic_hamiltonian_apply", "flosic_profile_read_overlap", "flosic_set_orbital_mask",
+                 "flosic_step_host")
 
 
 class FlosicError(RuntimeError):
@@ -77,6 +78,7 @@ def load_library(path=LIB_PATH):
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_hamiltonian_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.flosic_set_orbital_mask.argtypes = [vp, vp]
+    L.flosic_step_host.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
     L.flosic_profile_read_overlap.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
@@ -228,6 +230,33 @@ class Context:
         self._check(self._L.flosic_sic_backward(self._h, _ptr(psi), _ptr(fods), _ptr(phi), _ptr(V), _ptr(gE),
                                                 _ptr(dpsi), _ptr(dfod), _stream()))
         return dpsi, dfod
+
+    @_on_device
+    def step_host(self, psi, fods, scale=1.0, gE=1.0, E_sic=None, U=None, Exc=None, V_avg=None, dE_dpsi=None,
+                  dE_dfod=None, conv=None, psi_next=None, fods_next=None):
+        """Calls flosic_step_host: one forward + adjoint step with every array in
+        host memory (contiguous CPU tensors, float64 / int32 for conv; pinned
+        for full-speed copies).  Outputs are filled in place; returns the
+        status (OK or NOCONV)."""
+        def host(t, n, dtype, name):
+            if t is None:
+                return None
+            if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == dtype
+                    and t.is_contiguous() and t.numel() == n):
+                raise FlosicError(FLOSIC_ERR_ARG, "%s: contiguous CPU %s tensor of %d elements" % (name, dtype, n))
+            return ctypes.c_void_p(t.data_ptr())
+        f64 = torch.float64
+        args = [host(psi, self.orb_elems, f64, "psi"), host(fods, 3 * self.norb, f64, "fods")]
+        if args[0] is None or args[1] is None:
+            raise FlosicError(FLOSIC_ERR_ARG, "psi and fods are required")
+        outs = [host(E_sic, self.nsys, f64, "E_sic"), host(U, self.norb, f64, "U"), host(Exc, self.norb, f64, "Exc"),
+                host(V_avg, self.vavg_elems, f64, "V_avg"), host(dE_dpsi, self.orb_elems, f64, "dE_dpsi"),
+                host(dE_dfod, 3 * self.norb, f64, "dE_dfod"), host(conv, self.norb, torch.int32, "conv")]
+        nxt = [host(psi_next, self.orb_elems, f64, "psi_next"), host(fods_next, 3 * self.norb, f64, "fods_next")]
+        rc = self._L.flosic_step_host(self._h, args[0], args[1], float(scale), float(gE), *outs, *nxt, _stream())
+        if rc not in (FLOSIC_OK, FLOSIC_ERR_NOCONV):
+            self._check(rc)
+        return rc
 
     @_on_device
     def set_orbital_mask(self, mask=None):
