@@ -74,6 +74,8 @@ def parse():
                         "rank its own system (weak scaling)")
     p.add_argument("--no-tensor-core-transforms", action="store_true",
                    help="Kronecker solver: keep every 1-D transform on the CUDA cores")
+    p.add_argument("--no-extra-workloads", action="store_true",
+                   help="skip the uneven-batch and 192^3 lines added to the default line")
     p.add_argument("--workload", default="128", choices=["128", "192", "uneven", "fodopt", "hamiltonian"],
                    help="128: the 128^3 forward+adjoint step (default); 192: the same step at 192^3 with "
                         "120+120 orbitals; uneven: 64 systems of "
@@ -567,6 +569,17 @@ def run_gpu(args):
                             "share_of_step": round(pp["kernel_ms"] / (ms_p * kp), 4)}}
         del ctxp
 
+    # the two other real-size workloads, a few timed steps each (after the
+    # 128^3 contexts are released)
+    extra = {}
+    if world == 1 and args.workload == "128" and not args.no_extra_workloads and prec == 1:
+        del ctx
+        torch.cuda.empty_cache()
+        extra["uneven_batch"] = time_uneven(dev, stream, solver, steps=3)
+        torch.cuda.empty_cache()
+        extra["cube192"] = time_192(dev, stream, solver, steps=2)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "128":
         cpu = oracle_sample(s)
@@ -586,11 +599,81 @@ def run_gpu(args):
                            "l2": "inputs larger than L2 (psi %.2f GB per rank)" % (8e-9 * norb * s.G),
                            "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},
                 "roofline": roof, "roofline_overlap": roof_ov, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "fp64_path": fp64,
-                "pcg_path": pcg,
+                "pcg_path": pcg, **extra,
                 "gpu_launches": prof["launches"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _timed(fn, steps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def time_uneven(dev, stream, solver, steps=3):
+    """Forward step of the 64-system uneven batch (48^3..128^3, 2..40
+    orbitals) in one context: solves/s."""
+    import torch
+    from paper_2108_01186_gb300 import synth
+    from paper_2108_01186_gb300.flosic import Context
+    systems = synth.make_uneven_batch(nsys=64, seed_base=2000)
+    norb = sum(sum(x.norb) for x in systems)
+    # blocks on the tensor-core transforms: sides multiples of 8 (<= 128) and a
+    # 16-byte-aligned offset in the packed orbital arrays
+    n_tc, off = 0, 0
+    for x in systems:
+        if x.n % 8 == 0 and x.n <= 128 and off % 4 == 0:
+            n_tc += 1
+        off += x.norb[0] * x.G
+    ctx = Context(systems, precision=1, cg_tol=CG_TOL, preconditioner=1, solver=solver)
+    psi = torch.tensor(np.concatenate([p.ravel() for x in systems for p in x.psi]), device=dev)
+    fods = torch.tensor(np.concatenate([f.ravel() for x in systems for f in x.fods]), device=dev)
+    del systems
+
+    def fwd():
+        phi, _, _ = ctx.build_flos(psi, fods, want_matrices=False)
+        V, _, _ = ctx.orbital_poisson(phi)
+        ctx.sic_energy_potential(psi, phi, V, 1.0)
+
+    ms = _timed(fwd, steps, stream)
+    out = {"metric": "orbital SIC solves/s, uneven batch, forward", "value": norb / (ms / 1e3),
+           "unit": "solves/s", "ms_per_step": ms, "steps": steps,
+           "workload": "64 systems, 48^3..128^3, h 0.15..0.3, 2..40 orbitals (%d orbitals in %d blocks; %d blocks "
+                       "on the tensor-core transforms, the rest on the CUDA-core ones)"
+                       % (norb, ctx.nblk, n_tc)}
+    del ctx, psi, fods
+    return out
+
+
+def time_192(dev, stream, solver, steps=2):
+    """Forward + adjoint step of 192^3, h = 0.15, 120 + 120 orbitals: solves/s."""
+    import torch
+    from paper_2108_01186_gb300 import synth
+    from paper_2108_01186_gb300.flosic import Context
+    s = synth.make_system(192, 0.15, 60, [120, 120], seed=4000)
+    norb = sum(s.norb)
+    ctx = Context([s], precision=1, cg_tol=CG_TOL, preconditioner=1, solver=solver)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi]), device=dev)
+    fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods]), device=dev)
+    del s
+    gE = torch.ones(1, dtype=torch.float64, device=dev)
+    ms = _timed(lambda: step_with(ctx, psi, fods, gE), steps, stream)
+    out = {"metric": "orbital SIC solves/s at 192^3, forward + adjoint", "value": norb / (ms / 1e3),
+           "unit": "solves/s", "ms_per_step": ms, "steps": steps,
+           "workload": WORKLOAD_192,
+           "device_gb_in_use": round((torch.cuda.mem_get_info(dev)[1] - torch.cuda.mem_get_info(dev)[0]) / 1e9, 1)}
+    del ctx, psi, fods
+    return out
 
 
 def run_uneven(args):

@@ -198,18 +198,31 @@ __global__ void __launch_bounds__(256, NB <= 2 ? 2 : 1) k_gram_tc(const BlkDesc*
     }
 }
 
-// pk = the launch's sub-chunk partials per chunk (set by its widest block).
-__global__ void k_gram_sum(const BlkDesc* __restrict__ blk, const float* __restrict__ part,
-                           const long long* __restrict__ part_off, double* __restrict__ M, int pk) {
+// M[block][e] = sum over the block's partials (pk per chunk, pk = the
+// launch's sub-chunk count, set by its widest block) in float64: a CTA takes
+// 32 elements; its 8 warps sum every 8th partial each, and the 8 sums are
+// added in a fixed order.
+__global__ void __launch_bounds__(256) k_gram_sum(const BlkDesc* __restrict__ blk, const float* __restrict__ part,
+                                                  const long long* __restrict__ part_off, double* __restrict__ M,
+                                                  int pk) {
+    __shared__ double red[8][32];
     const BlkDesc& B = blk[blockIdx.y];
     const int NN2 = B.N * B.N;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= NN2) return;
-    const long long nch = ((B.G + kGChunk - 1) / kGChunk) * pk;
-    const float* p = part + part_off[blockIdx.y] + e;
+    const int e = blockIdx.x * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
+    const long long nparts = ((B.G + kGChunk - 1) / kGChunk) * pk;
     double s = 0.0;
-    for (long long q = 0; q < nch; ++q) s += (double)p[q * NN2];
-    M[B.moff + e] = s;
+    if (e < NN2) {
+        const float* p = part + part_off[blockIdx.y] + e;
+#pragma unroll 8
+        for (long long q = w; q < nparts; q += 8) s += (double)p[q * NN2];
+    }
+    red[w][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (w == 0 && e < NN2) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        M[B.moff + e] = t;
+    }
 }
 
 // sub-chunk partials per chunk of every block: set by the widest block, whose
@@ -270,7 +283,7 @@ void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
         cudaEventRecord(cm->ov_ev[2 * cm->ov_used + 1], s);
         ++cm->ov_used;
     }
-    const dim3 g2((unsigned)((nmax * nmax + 255) / 256), (unsigned)c->nblk);
+    const dim3 g2((unsigned)((nmax * nmax + 31) / 32), (unsigned)c->nblk);
     k_gram_sum<<<g2, 256, 0, s>>>(c->d_blk, part, off, c->ws.M, gram_launch_pack(c));
     note_launch((flosic_ctx*)c);
 }

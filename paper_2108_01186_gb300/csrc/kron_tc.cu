@@ -57,8 +57,8 @@ namespace {
 constexpr int kTcRows = 128;                      // rows (lines) per tile: MMA M
 constexpr int kTcHalf = 64;                       // half-line length (K) and modes per half (N), padded
 constexpr int kTcConv = 256;                     // converter threads (warps 1-8: two per row)
-constexpr int kTcEpi = 256;                      // epilogue threads (warps 9-16: two per row)
-constexpr int kTcThreads = 32 + kTcConv + kTcEpi;   // + the control warp
+constexpr int kTcEpi = 128;                      // epilogue threads (warps 9-12: one per row)
+constexpr int kTcThreads = 32 + kTcConv + kTcEpi;   // + the control warp: 13 warps, 128 registers each
 constexpr int kTcATile = kTcRows * kTcHalf * 2;   // one split of one half of a tile (bf16): 16 KB
 constexpr int kTcBTile = kTcHalf * kTcHalf * 2;   // one split of one half-matrix (bf16): 8 KB
 constexpr int kTcBox = kTcRows * 32 * 4;          // one copy: 128 rows x 32 points (float32): 16 KB
@@ -90,6 +90,29 @@ struct KronTcArgs {
 struct TcTile {
     int b, o, q;   // block, orbital within the block, tile within the orbital
 };
+
+// What a warp needs of its tile's block, read once per block change.
+struct TcBlk {
+    int b = -1, n, ns, nx;
+    long long G, R, off;
+    long long kt, kl0, kl1, kl2;
+};
+
+__device__ __forceinline__ void tc_blk_load(TcBlk& k, const BlkDesc* blk, int b, int axis) {
+    if (k.b == b) return;
+    const BlkDesc& B = blk[b];
+    k.b = b;
+    k.n = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+    k.ns = k.n >> 1;
+    k.nx = B.nx;
+    k.G = B.G;
+    k.R = B.G / k.n;
+    k.off = B.off;
+    k.kt = B.kt[axis];
+    k.kl0 = B.kl[0];
+    k.kl1 = B.kl[1];
+    k.kl2 = B.kl[2];
+}
 
 __device__ __forceinline__ int tc_side(const BlkDesc& B, int axis) { return axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz); }
 
@@ -193,12 +216,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     if (warp == 0) {
         // ---- control: copies and MMAs (lane 0) --------------------------------
         if (lane == 0) {
+            TcBlk kc;
             auto issue_copy = [&](const TcTile& t) {
-                const BlkDesc& B = a.blk[t.b];
-                const int n = tc_side(B, a.axis);
-                const long long R = B.G / n;
-                const int nbox = (n + 31) >> 5;
-                const int row0 = (int)((long long)t.o * R + (long long)t.q * kTcRows);
+                tc_blk_load(kc, a.blk, t.b, a.axis);
+                const int nbox = (kc.n + 31) >> 5;
+                const int row0 = (int)((long long)t.o * kc.R + (long long)t.q * kTcRows);
                 tc_mbar_expect_tx(&bar_tma, (uint32_t)(nbox * kTcBox));
                 for (int bx = 0; bx < nbox; ++bx)
                     tc_tma_load_2d(sR + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma);
@@ -262,11 +284,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
         TcTile cur = first;
         long long item = item0;
         int bs = bsearch, loaded_b = -1;
+        TcBlk kb;
         for (int t = 0;; ++t) {
             bool ok = tc_mbar_sleep_or_abort(&bar_tma, (uint32_t)(t & 1), &s_abort);
             if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
-            const BlkDesc& B = a.blk[cur.b];
-            const int n = tc_side(B, a.axis), ns = n >> 1;
+            tc_blk_load(kb, a.blk, cur.b, a.axis);
+            const int n = kb.n, ns = kb.ns;
             float4 fr[8], bk[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
@@ -283,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
             if (cur.b != loaded_b) {   // this block's matrices, once the last tile's MMAs have completed
                 ok = t < 1 || tc_mbar_sleep_or_abort(&bar_half[1], (uint32_t)((t - 1) & 1), &s_abort);
                 if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
-                const uint16_t* src = a.mat + B.kt[a.axis] + (a.inverse ? 6 * kTcMatElems : 0);
+                const uint16_t* src = a.mat + kb.kt + (a.inverse ? 6 * kTcMatElems : 0);
                 for (int i = ct; i < 6 * 64 * 8; i += kTcConv) {
                     const int mt = i >> 9, m = (i >> 3) & 63, c = i & 7;
                     const uint4 v = *reinterpret_cast<const uint4*>(src + mt * kTcMatElems + m * 64 + c * 8);
@@ -335,45 +358,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     } else {
         // ---- epilogue: accumulators -> scaling / recombination -> stores -------
         const int g4 = warp & 3;                                  // TMEM lanes 32 g4 .. = tile rows
-        const int hc = (warp - 1 - kTcConv / 32) >> 2;            // modes 32 hc .. 32 hc + 31
-        const int r = 32 * g4 + lane;
+        const int r = 32 * g4 + lane;                             // one row per thread
         TcTile cur = first;
         long long item = item0;
         int bs = bsearch;
+        TcBlk kb;
         for (int t = 0;; ++t) {
             const bool ok = tc_mbar_sleep_or_abort(&bar_mma[t & 1], (uint32_t)((t >> 1) & 1), &s_abort);
             if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
             tc_fence_after();
-            const BlkDesc& B = a.blk[cur.b];
-            const int n = tc_side(B, a.axis), ns = n >> 1;
-            const long long R = B.G / n;
+            tc_blk_load(kb, a.blk, cur.b, a.axis);
+            const int n = kb.n, ns = kb.ns;
+            const long long R = kb.R;
             const long long l = (long long)cur.q * kTcRows + r;   // row within the orbital
             float lxy = 0.f;
             if (a.scale && l < R) {   // forward z: rows are (my, mx), mx fastest
-                const int mx = (int)(l % B.nx), my = (int)(l / B.nx);
-                lxy = a.lam[B.kl[0] + mx] + a.lam[B.kl[1] + my];
+                const int mx = (int)(l % kb.nx), my = (int)(l / kb.nx);
+                lxy = a.lam[kb.kl0 + mx] + a.lam[kb.kl1 + my];
             }
-            const float* lz = a.lam + B.kl[2];
-            const uint32_t ta = tmem + ((uint32_t)(32 * g4) << 16) + (uint32_t)((t & 1) * 256 + 32 * hc);
-            float* const dst = a.out + B.off + (long long)cur.o * B.G + (l < R ? l : 0);
+            const float* lz = a.lam + kb.kl2;
+            const uint32_t ta = tmem + ((uint32_t)(32 * g4) << 16) + (uint32_t)((t & 1) * 256);
+            float* const dst = a.out + kb.off + (long long)cur.o * kb.G + (l < R ? l : 0);
+            const long long s2 = a.inverse ? -R : R;
+            float* p1 = dst;                                                   // position m
+            float* p2 = dst + (long long)(a.inverse ? n - 1 : ns) * R;         // its partner
 #pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 float e0[16], e1[16], o0[16], o1[16];
                 tmem_ld16(ta + 16 * c, e0);
                 tmem_ld16(ta + 16 * c + 64, e1);
                 tmem_ld16(ta + 16 * c + 128, o0);
                 tmem_ld16(ta + 16 * c + 192, o1);
                 tmem_wait_ld();
-                if (c == 1) {   // the buffer is read: the MMAs of tile t + 2 may overwrite it
+                if (c == 3) {   // the buffer is read: the MMAs of tile t + 2 may overwrite it
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc_mbar_arrive(&bar_empty[t & 1]);
                 }
-                const int m0 = 32 * hc + 16 * c;
+                const int m0 = 16 * c;
                 if (l < R && m0 < ns) {
-                    float* p1 = dst + (long long)m0 * R;                                   // position m
-                    float* p2 = dst + (long long)(a.inverse ? n - 1 - m0 : ns + m0) * R;   // its partner
-                    const long long s2 = a.inverse ? -R : R;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (m0 + j < ns) {
