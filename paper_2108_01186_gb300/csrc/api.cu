@@ -498,6 +498,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.mom_part, 10 * nparts);
     A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
+    A(&g.dmax, orb);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
     if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) e = setup_kron(c);   // sets the blocks' kq, kl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
@@ -505,6 +506,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
+    if (e == cudaSuccess) e = cudaMemset(g.dmax, 0, sizeof(unsigned) * orb);
     if (e == cudaSuccess) {   // every orbital computed here until flosic_set_orbital_mask says otherwise
         const std::vector<int> ones((size_t)orb, 1);
         e = cudaMemcpy(w.mask, ones.data(), sizeof(int) * orb, cudaMemcpyHostToDevice);

@@ -128,99 +128,4 @@ __device__ __forceinline__ void ff_sweep12(const LvlDesc& D, const TilePos& P, L
     }
 }
 
-// The same sweep for a float32 operand: the plane and the z-queue hold
-// plain floats, the six values at distance m are summed exactly (a chain of
-// two-sums, their rounding errors added in float: ~eps^2 of the terms'
-// magnitudes) and the weighted terms accumulated as in the kSloppy form.
-// load(g) -> float; epi(g, centre, lap) with lap = h^2 Delta_h u as a pair.
-template <class Load, class Epi>
-__device__ __forceinline__ void ff_sweep12_f(const LvlDesc& D, const TilePos& P, Load load, Epi epi,
-                                             float (*plane)[kPX]) {
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTileX + tx;
-    const int nthr = kTileX * (kTileY / 2);
-    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
-    const int gx = P.x0 + tx;
-    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
-    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
-    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
-    long long soff[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) {
-        const int e = tid + j * nthr;
-        soff[j] = -1;
-        if (e < kPX * kPY) {
-            const int yy = e / kPX, xx = e - yy * kPX;
-            int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
-            if (D.per & 1) px = wrap_coord(px, D.nx);
-            if (D.per & 2) py = wrap_coord(py, D.ny);
-            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * sy + px;
-        }
-    }
-    float q0[2 * kHalf + 1], q1[2 * kHalf + 1];
-    const bool perz = (D.per & 4) != 0;
-#pragma unroll
-    for (int j = 0; j < 2 * kHalf; ++j) {
-        int zz = P.z0 - kHalf + j;
-        if (perz) zz = wrap_coord(zz, D.nz);
-        const bool okz = zz >= 0 && zz < D.nz;
-        q0[j] = (in0 && okz) ? load(P.base + zz * sz + c0) : 0.f;
-        q1[j] = (in1 && okz) ? load(P.base + zz * sz + c1) : 0.f;
-    }
-    float pre[kSlots];
-#pragma unroll
-    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? load(P.base + P.z0 * sz + soff[j]) : 0.f;
-    ff w[kHalf + 1];
-#pragma unroll
-    for (int m = 0; m <= kHalf; ++m) w[m] = {c_wff[2 * m], c_wff[2 * m + 1]};
-    float* flat = &plane[0][0];
-    for (int z = P.z0; z < P.z1; ++z) {
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) {
-            const int e = tid + j * nthr;
-            if (e < kPX * kPY) flat[e] = pre[j];
-        }
-        {
-            int zz = z + kHalf;
-            if (perz) zz = wrap_coord(zz, D.nz);
-            q0[2 * kHalf] = (in0 && zz < D.nz) ? load(P.base + zz * sz + c0) : 0.f;
-            q1[2 * kHalf] = (in1 && zz < D.nz) ? load(P.base + zz * sz + c1) : 0.f;
-        }
-        __syncthreads();
-        if (z + 1 < P.z1) {
-            const long long pz = P.base + (z + 1) * sz;
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? load(pz + soff[j]) : 0.f;
-        }
-        const int lx = tx + kHalf;
-        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
-        const bool in[2] = {in0, in1};
-        const long long cc[2] = {c0, c1};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float* qk = (k == 0) ? q0 : q1;
-            ff acc = ff_mulf(w[0], qk[kHalf]);
-#pragma unroll
-            for (int m = 1; m <= kHalf; ++m) {
-                ff sm = ff_two_sum(plane[ly[k]][lx - m], plane[ly[k]][lx + m]);
-                float err = sm.l;
-                sm = ff_two_sum(sm.h, plane[ly[k] - m][lx]); err += sm.l;
-                sm = ff_two_sum(sm.h, plane[ly[k] + m][lx]); err += sm.l;
-                sm = ff_two_sum(sm.h, qk[kHalf - m]); err += sm.l;
-                sm = ff_two_sum(sm.h, qk[kHalf + m]); err += sm.l;
-                const ff tm = ff_mul(w[m], ff_quick(sm.h, err));
-                const ff s2 = ff_two_sum(acc.h, tm.h);
-                acc = ff_quick(s2.h, s2.l + (acc.l + tm.l));
-            }
-            if (in[k]) epi(P.base + z * sz + cc[k], qk[kHalf], acc);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 2 * kHalf; ++j) {
-            q0[j] = q0[j + 1];
-            q1[j] = q1[j + 1];
-        }
-    }
-}
-
 }  // namespace flosic

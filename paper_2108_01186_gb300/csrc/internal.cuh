@@ -111,6 +111,7 @@ struct CgState {
     int* n_oactive;    // [1] number of orbitals with oactive = 1
     int* conv;         // [norb] 1 = converged
     double* prof_bytes;  // [1] algorithmic bytes moved by the stencil-apply launches
+    unsigned* dmax;      // [norb] float bits of max |d| of the current correction (refinement update)
     const int* mask;     // [norb] 1 = this context solves the orbital (see flosic_set_orbital_mask)
 };
 
@@ -177,6 +178,7 @@ struct KronPlan {
     uint16_t* tc_mat = nullptr;    // per distinct operator of a tensor-core block: split bf16 matrices
     long long* tc_items = nullptr; // [6][nblk + 1] first tile of each block per pass (tensor-core kernel)
     void* tc_maps = nullptr;       // [6][nblk] CUtensorMap of each pass's input rows
+    void* tc_omaps = nullptr;      // [6][nblk] CUtensorMap of each pass's output lines
     long long tc_total[6] = {0, 0, 0, 0, 0, 0};
     int tc_grid[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -280,6 +282,7 @@ void kron_tc_pack(int n, const std::vector<double>& Vs, const std::vector<double
 size_t kron_tc_smem();
 const void* kron_tc_symbol();
 bool kron_tc_map(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, const float* buf);
+bool kron_tc_map_out(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, float* buf);
 long long kron_tc_tiles(const BlkDesc& B, int axis);
 void launch_kron_tc_pass(flosic_ctx* c, int step, float* out, cudaStream_t s);
 // Alternating Anderson-Richardson inner solver (mixed precision)

@@ -476,8 +476,11 @@ cudaError_t setup_kron_tc(flosic_ctx* c, const std::vector<uint16_t>& tcmat, int
         (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
          q != cudaDriverEntryPointSuccess || !fn))
         e = cudaErrorNotSupported;
+    // the buffers of launch_kron_solve's passes as the refinement calls it
+    // (r = r32, d = d32, scratch p32 and q32)
     const float* in_buf[6] = {c->ws.r32, c->ws.p32, c->ws.q32, c->ws.p32, c->ws.q32, c->ws.p32};
-    std::vector<CUtensorMap> maps(6 * (size_t)c->nblk);
+    float* out_buf[6] = {c->ws.p32, c->ws.q32, c->ws.p32, c->ws.q32, c->ws.p32, c->ws.d32};
+    std::vector<CUtensorMap> maps(12 * (size_t)c->nblk);   // inputs, then outputs
     std::vector<long long> items(6 * (size_t)(c->nblk + 1));
     std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
     for (int st = 0; st < 6 && e == cudaSuccess; ++st) {
@@ -487,7 +490,9 @@ cudaError_t setup_kron_tc(flosic_ctx* c, const std::vector<uint16_t>& tcmat, int
             items[(size_t)st * (c->nblk + 1) + b] = acc;
             if (!B.tc) continue;
             acc += kron_tc_tiles(B, st % 3);
-            if (!kron_tc_map(fn, &maps[(size_t)st * c->nblk + b], B, st % 3, in_buf[st])) e = cudaErrorInvalidValue;
+            if (!kron_tc_map(fn, &maps[(size_t)st * c->nblk + b], B, st % 3, in_buf[st]) ||
+                !kron_tc_map_out(fn, &maps[(size_t)(6 + st) * c->nblk + b], B, st % 3, out_buf[st]))
+                e = cudaErrorInvalidValue;
         }
         items[(size_t)st * (c->nblk + 1) + c->nblk] = acc;
         K.tc_total[st] = acc;
@@ -498,6 +503,7 @@ cudaError_t setup_kron_tc(flosic_ctx* c, const std::vector<uint16_t>& tcmat, int
     if (e == cudaSuccess) {
         c->allocations.push_back(dm);
         K.tc_maps = dm;
+        K.tc_omaps = reinterpret_cast<CUtensorMap*>(dm) + 6 * (size_t)c->nblk;
         e = cudaMemcpy(dm, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = ctx_alloc(c, &K.tc_items, items.size());

@@ -18,19 +18,24 @@
 // shared memory; every output store is coalesced (the 32 lanes of a warp
 // own 32 consecutive rows).
 //
-// One CTA per SM (17 warps) streams tiles of 128 rows.  The copy engine
-// delivers a tile's rows (float32).  Eight converter warps fold each row
-// into its even and odd halves (s_k = v_k + v_{n-1-k}, a_k = v_k - v_{n-1-k}:
-// T_d commutes with the reflection, so the transform splits into two
-// half-size products) and write each half as three bf16 terms
-// (v = v1 + v2 + v3, ~24 significant bits) in the K-major 128-byte-swizzled
-// operand layout; a control warp issues the copies and the MMAs (M = 128
-// rows, N = 64 modes, K = 16 per instruction): the six split products
-// v_i w_j with i + j <= 2 of each half, the v1 w1 product into its own
-// accumulator and the five smaller ones into a second, both in tensor
-// memory (two tile buffers of 256 columns); eight epilogue warps read the
-// accumulators back (tcgen05.ld), add them, apply the scaling (forward z)
-// or the even/odd recombination (inverse) and store.
+// One CTA per SM (13 warps) streams tiles of 128 rows.  The copy engine
+// delivers a tile's rows (float32) into one of two staging buffers, so the
+// next tile's rows are on their way while this one is converted.  Eight
+// converter warps fold each row into its even and odd halves (s_k = v_k +
+// v_{n-1-k}, a_k = v_k - v_{n-1-k}: T_d commutes with the reflection, so the
+// transform splits into two half-size products) and write each half as
+// three bf16 terms (v = v1 + v2 + v3, ~24 significant bits) straight into
+// tensor memory, the MMAs' A operand (row i in lane i); the split matrices
+// stay in shared memory (B operand, K-major, 128-byte swizzle).  A control
+// thread issues the copies and the MMAs (M = 128 rows, N = 64 modes, K = 16
+// per instruction): the six split products v_i w_j with i + j <= 2 of each
+// half, the v1 w1 product into its own accumulator and the five smaller ones
+// into a second.  Four epilogue warps read the accumulators back
+// (tcgen05.ld), add them, apply the scaling (forward z) or the even/odd
+// recombination (inverse), write 16 output lines of 32 rows at a time to
+// shared memory and hand them to the copy engine (tiled bulk stores).
+// Operands in tensor memory leave shared memory only the copies, the
+// matrices and the output staging to carry.
 //
 // Accuracy: keeping the dominant product in its own short accumulation
 // chain (4 instructions of K = 16 per half) holds the tensor cores'
@@ -56,17 +61,20 @@ namespace {
 
 constexpr int kTcRows = 128;                      // rows (lines) per tile: MMA M
 constexpr int kTcHalf = 64;                       // half-line length (K) and modes per half (N), padded
-constexpr int kTcConv = 256;                     // converter threads (warps 1-8: two per row)
-constexpr int kTcEpi = 128;                      // epilogue threads (warps 9-12: one per row)
-constexpr int kTcThreads = 32 + kTcConv + kTcEpi;   // + the control warp: 13 warps, 128 registers each
-constexpr int kTcATile = kTcRows * kTcHalf * 2;   // one split of one half of a tile (bf16): 16 KB
+constexpr int kTcConv = 256;                      // converter threads (warps 1-8: two per row)
+constexpr int kTcEpi = 128;                       // epilogue threads (warps 9-12: one per row)
+constexpr int kTcThreads = 32 + kTcConv + kTcEpi; // + the control warp: 13 warps, 128 registers each
 constexpr int kTcBTile = kTcHalf * kTcHalf * 2;   // one split of one half-matrix (bf16): 8 KB
 constexpr int kTcBox = kTcRows * 32 * 4;          // one copy: 128 rows x 32 points (float32): 16 KB
+constexpr int kTcRaw = 4 * kTcBox;                // one tile's rows (up to 128 points): 64 KB
+constexpr int kTcLines = 16;                      // output lines per bulk store
+constexpr int kTcStage = kTcLines * 32 * 4;       // one bulk store: 16 lines x 32 rows (float32): 2 KB
 constexpr int kTcOffB = 0;                        // 6 half-matrix tiles (2 halves x 3 splits)
-constexpr int kTcOffA = kTcOffB + 6 * kTcBTile;   // 6 operand tiles
-constexpr int kTcOffRaw = kTcOffA + 6 * kTcATile; // up to 4 copies (128 points per row)
-constexpr int kTcSmem = kTcOffRaw + 4 * kTcBox + 1024;   // + 1024-byte alignment slack
-constexpr uint32_t kTcCols = 512;                 // two tile buffers of 256 tensor-memory columns
+constexpr int kTcOffRaw = kTcOffB + 6 * kTcBTile; // two tile buffers of staged rows
+constexpr int kTcOffOut = kTcOffRaw + 2 * kTcRaw; // per epilogue warp: 2 buffers x 2 stores
+constexpr int kTcSmem = kTcOffOut + 4 * 4 * kTcStage + 1024;   // + 1024-byte alignment slack
+constexpr uint32_t kTcCols = 512;                 // tensor-memory columns
+constexpr uint32_t kTcColA = 256;                 // A operands: half h, split s at 256 + 32 (3 h + s)
 constexpr int kTcMatElems = 64 * 64;              // one padded half-matrix
 constexpr int kTcOpElems = 12 * kTcMatElems;      // per operator: 2 directions x 2 halves x 3 splits
 
@@ -78,11 +86,13 @@ struct KronTcArgs {
     int nblk;
     const long long* item0;   // [nblk + 1] first tile of each block in this pass
     const CUtensorMap* maps;  // [nblk] the pass's input rows of each block
+    const CUtensorMap* omaps; // [nblk] the pass's output lines of each block (16 lines x 32 rows)
     const uint16_t* mat;      // bf16 split matrices (kTcOpElems per operator)
     const float* lam;         // eigenvalues per distinct operator
     float* out;
     const int* active;
     double* flops;            // algorithmic flop counter (profiling) or null
+    unsigned* dmax;           // [norb] max |output| per orbital (float bits, atomicMax) or null
     int* status;
     int axis, inverse, scale;
 };
@@ -159,26 +169,28 @@ __device__ __forceinline__ float4 tc_raw4(const unsigned char* sR, int r, int po
 }
 
 // Warp roles: warp 0 issues the copies and the MMAs (one lane), warps 1-8
-// convert (two threads per row), warps 9-16 drain the accumulators and store
-// (two threads per row).  They meet only at mbarriers, each completing once
-// per tile:
-//   bar_tma      the tile's rows have arrived            (copy engine)
-//   bar_raw      every converter has read them           (8 warp arrivals)
-//   bar_conv[h]  half h's operand tiles are written      (8 warp arrivals)
-//   bar_half[h]  half h's MMAs have completed            (MMA commit)
-//   bar_mma[b]   the tile in tensor-memory buffer b is done (MMA commit)
-//   bar_empty[b] the epilogue has read buffer b          (8 warp arrivals)
-// so the even half's MMAs run while the odd half is converted, the odd
-// half's while the next tile's rows are read, and the stores of one tile
-// while the next is converted.  Every wait sleeps on its mbarrier, gives up
-// after about two seconds or as soon as another warp has given up
-// (s_abort), and the decision is warp-uniform.
+// convert (two threads per row: warp w owns tensor-memory lanes
+// 32 (w mod 4) .. + 31, K values 32 kp .. + 31 with kp = (w - 1) / 4),
+// warps 9-12 drain the accumulators and store (one thread per row).  They
+// meet only at mbarriers:
+//   bar_tma[b]   rows of the tile in staging buffer b have arrived  (copy engine)
+//   bar_raw[b]   every converter has read buffer b                   (8 warp arrivals)
+//   bar_conv[h]  half h's operand splits are in tensor memory        (8 warp arrivals)
+//   bar_half[h]  half h's MMAs have completed                        (MMA commit)
+//   bar_mma      the tile's MMAs have completed                      (MMA commit)
+//   bar_empty    the epilogue has read the accumulators              (4 warp arrivals)
+// Tile t's rows land in buffer t mod 2, and the copy of tile t + 2 is issued
+// as soon as tile t's rows are read, so a copy has two tiles' time to land;
+// the even half's MMAs run while the odd half is converted, and the
+// accumulators are read before the next tile's MMAs overwrite them.  Every
+// wait sleeps on its mbarrier, gives up after about two seconds or as soon
+// as another warp has given up (s_abort), and the decision is warp-uniform.
 __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long long total) {
     extern __shared__ unsigned char kt_smem_raw[];
-    __shared__ uint64_t bar_tma, bar_raw, bar_conv[2], bar_half[2], bar_mma[2], bar_empty[2];
+    __shared__ uint64_t bar_tma[2], bar_raw[2], bar_conv[2], bar_half[2], bar_mma, bar_empty;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_abort;
-    __shared__ int s_tma_issued, s_tma_waited, s_mma_issued;
+    __shared__ int s_tma_issued[2], s_mma_issued;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * per_cta;
@@ -192,19 +204,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
     unsigned char* sm =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(kt_smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* sB = sm + kTcOffB;
-    unsigned char* sA = sm + kTcOffA;
     unsigned char* sR = sm + kTcOffRaw;
     if (tid == 0) {
-        tc_mbar_init(&bar_tma, 1);
-        tc_mbar_init(&bar_raw, kTcConv / 32);
         for (int b = 0; b < 2; ++b) {
+            tc_mbar_init(&bar_tma[b], 1);
+            tc_mbar_init(&bar_raw[b], kTcConv / 32);
             tc_mbar_init(&bar_conv[b], kTcConv / 32);
             tc_mbar_init(&bar_half[b], 1);
-            tc_mbar_init(&bar_mma[b], 1);
-            tc_mbar_init(&bar_empty[b], kTcEpi / 32);
+            s_tma_issued[b] = 0;
         }
+        tc_mbar_init(&bar_mma, 1);
+        tc_mbar_init(&bar_empty, kTcEpi / 32);
         s_abort = 0;
-        s_tma_issued = s_tma_waited = s_mma_issued = 0;
+        s_mma_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(&tmem_base, kTcCols);
@@ -217,51 +229,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
         // ---- control: copies and MMAs (lane 0) --------------------------------
         if (lane == 0) {
             TcBlk kc;
-            auto issue_copy = [&](const TcTile& t) {
+            auto issue_copy = [&](const TcTile& t, int buf) {
                 tc_blk_load(kc, a.blk, t.b, a.axis);
                 const int nbox = (kc.n + 31) >> 5;
                 const int row0 = (int)((long long)t.o * kc.R + (long long)t.q * kTcRows);
-                tc_mbar_expect_tx(&bar_tma, (uint32_t)(nbox * kTcBox));
+                unsigned char* dst = sR + buf * kTcRaw;
+                tc_mbar_expect_tx(&bar_tma[buf], (uint32_t)(nbox * kTcBox));
                 for (int bx = 0; bx < nbox; ++bx)
-                    tc_tma_load_2d(sR + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma);
-                ++s_tma_issued;
+                    tc_tma_load_2d(dst + bx * kTcBox, a.maps + t.b, 32 * bx, row0, &bar_tma[buf]);
+                ++s_tma_issued[buf];
             };
             const uint32_t idesc = umma_idesc_bf16(kTcRows, kTcHalf);
-            const uint32_t a0 = tc_smem_addr(sA), b0 = tc_smem_addr(sB);
-            TcTile cur = first;
-            long long item = item0;
+            const uint32_t b0 = tc_smem_addr(sB);
+            // copies run two tiles ahead: tile t (cur), t + 1 (t1, item n1), t + 2 (t2, item n2)
             int bs = bsearch;
-            issue_copy(cur);
+            TcTile cur = first, t1{}, t2{};
+            long long n1 = tc_next(a, item0 + 1, it1, bs, t1);
+            long long n2 = n1 < it1 ? tc_next(a, n1 + 1, it1, bs, t2) : it1;
+            issue_copy(first, 0);
+            if (n1 < it1) issue_copy(t1, 1);
             for (int t = 0;; ++t) {
-                TcTile nxt_t{};
-                const long long nxt = tc_next(a, item + 1, it1, bs, nxt_t);
-                // the converters have read the rows: the next tile's copy may land
-                if (!tc_mbar_sleep_or_abort(&bar_raw, (uint32_t)(t & 1), &s_abort)) break;
-                s_tma_waited = s_tma_issued;
-                if (nxt < it1) issue_copy(nxt_t);
+                // tile t's rows are read: the copy of tile t + 2 may land in their buffer
+                if (!tc_mbar_sleep_or_abort(&bar_raw[t & 1], (uint32_t)((t >> 1) & 1), &s_abort)) break;
+                if (n2 < it1) issue_copy(t2, t & 1);
                 bool ok = true;
                 for (int h = 0; h < 2 && ok; ++h) {
                     ok = tc_mbar_sleep_or_abort(&bar_conv[h], (uint32_t)(t & 1), &s_abort);
-                    // tensor-memory buffer t & 1 was drained by the epilogue of tile t - 2
-                    if (ok && h == 0 && t >= 2)
-                        ok = tc_mbar_sleep_or_abort(&bar_empty[t & 1], (uint32_t)(((t - 2) >> 1) & 1), &s_abort);
+                    // the accumulators were read by the epilogue of tile t - 1
+                    if (ok && h == 0 && t >= 1)
+                        ok = tc_mbar_sleep_or_abort(&bar_empty, (uint32_t)((t - 1) & 1), &s_abort);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t dm = tmem + (uint32_t)((t & 1) * 256 + h * 128);
+                    const uint32_t dm = tmem + (uint32_t)(h * 128);
+                    const uint32_t am = tmem + kTcColA + (uint32_t)(h * 96);
 #pragma unroll 1
                     for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
                         for (int p = 0; p < 6; ++p) {
-                            const uint64_t da = umma_desc_sw128(a0 + (h * 3 + c_tc_pa[p]) * kTcATile + kk * 32);
+                            const uint32_t ta = am + (uint32_t)(32 * c_tc_pa[p] + 8 * kk);
                             const uint64_t db = umma_desc_sw128(b0 + (h * 3 + c_tc_pb[p]) * kTcBTile + kk * 32);
-                            if (p == 0) umma_bf16(dm, da, db, idesc, kk != 0);
-                            else umma_bf16(dm + 64, da, db, idesc, (kk | (p - 1)) != 0);
+                            if (p == 0) umma_bf16_ts(dm, ta, db, idesc, kk != 0);
+                            else umma_bf16_ts(dm + 64, ta, db, idesc, (kk | (p - 1)) != 0);
                         }
                     }
                     umma_commit(&bar_half[h]);
                 }
                 if (!ok) break;
-                umma_commit(&bar_mma[t & 1]);
+                umma_commit(&bar_mma);
                 ++s_mma_issued;
                 if (a.flops) {
                     const BlkDesc& B = a.blk[cur.b];
@@ -269,27 +283,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
                     const long long rows = B.G / n - (long long)cur.q * kTcRows;
                     atomicAdd(a.flops, 4.0 * (double)ns * ns * (double)(rows < kTcRows ? rows : kTcRows));
                 }
-                if (nxt >= it1) break;
-                cur = nxt_t;
-                item = nxt;
+                if (n1 >= it1) break;
+                cur = t1;
+                t1 = t2;
+                n1 = n2;
+                n2 = n1 < it1 ? tc_next(a, n1 + 1, it1, bs, t2) : it1;
             }
         }
         __syncwarp();
     } else if (warp <= kTcConv / 32) {
-        // ---- converters: rows in, fold, split, operand tiles ---------------
-        const int ct = tid - 32;
-        const int r = ct & (kTcRows - 1), kp = ct >> 7;   // row r, K values 32 kp .. 32 kp + 31
-        const int rsw = r & 7;
-        unsigned char* const arow = sA + r * 128;
+        // ---- converters: rows in, fold, split, operand splits in tensor memory --
+        const int qd = warp & 3;                         // tensor-memory lane quadrant
+        const int r = 32 * qd + lane;                    // row of the tile
+        const int kp = (warp - 1) >> 2;                  // K values 32 kp .. 32 kp + 31
+        const uint32_t ta_row = tmem + ((uint32_t)(32 * qd) << 16) + kTcColA + (uint32_t)(16 * kp);
         TcTile cur = first;
         long long item = item0;
         int bs = bsearch, loaded_b = -1;
         TcBlk kb;
         for (int t = 0;; ++t) {
-            bool ok = tc_mbar_sleep_or_abort(&bar_tma, (uint32_t)(t & 1), &s_abort);
+            bool ok = tc_mbar_sleep_or_abort(&bar_tma[t & 1], (uint32_t)((t >> 1) & 1), &s_abort);
             if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
             tc_blk_load(kb, a.blk, cur.b, a.axis);
             const int n = kb.n, ns = kb.ns;
+            const unsigned char* raw = sR + (t & 1) * kTcRaw;
             float4 fr[8], bk[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
@@ -297,34 +314,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
                 fr[g] = make_float4(0.f, 0.f, 0.f, 0.f);
                 bk[g] = fr[g];
                 if (k < ns) {
-                    fr[g] = tc_raw4(sR, r, k);
-                    bk[g] = tc_raw4(sR, r, a.inverse ? ns + k : n - 4 - k);
+                    fr[g] = tc_raw4(raw, r, k);
+                    bk[g] = tc_raw4(raw, r, a.inverse ? ns + k : n - 4 - k);
                 }
             }
             __syncwarp();
-            if (lane == 0) tc_mbar_arrive(&bar_raw);   // the staged rows may be overwritten
+            if (lane == 0) tc_mbar_arrive(&bar_raw[t & 1]);   // the staged rows may be overwritten
+            bool wrote_b = false;
             if (cur.b != loaded_b) {   // this block's matrices, once the last tile's MMAs have completed
                 ok = t < 1 || tc_mbar_sleep_or_abort(&bar_half[1], (uint32_t)((t - 1) & 1), &s_abort);
                 if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
                 const uint16_t* src = a.mat + kb.kt + (a.inverse ? 6 * kTcMatElems : 0);
-                for (int i = ct; i < 6 * 64 * 8; i += kTcConv) {
+                for (int i = tid - 32; i < 6 * 64 * 8; i += kTcConv) {
                     const int mt = i >> 9, m = (i >> 3) & 63, c = i & 7;
                     const uint4 v = *reinterpret_cast<const uint4*>(src + mt * kTcMatElems + m * 64 + c * 8);
                     *reinterpret_cast<uint4*>(sB + mt * kTcBTile + m * 128 + ((c ^ (m & 7)) << 4)) = v;
                 }
                 loaded_b = cur.b;
+                wrote_b = true;
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                // the last tile's MMAs of this half have read its operand tiles
+                // the last tile's MMAs of this half have read its operand splits
                 ok = t < 1 || tc_mbar_sleep_or_abort(&bar_half[h], (uint32_t)((t - 1) & 1), &s_abort);
                 if (!__all_sync(0xffffffffu, ok)) {
                     s_abort = 1;
                     break;
                 }
-                unsigned char* const ah = arow + h * 3 * kTcATile;
+                tc_fence_after();
+                const uint32_t th = ta_row + (uint32_t)(h * 96);
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {   // chunk c = 4 kp + cc holds K = 8c .. 8c + 7
+                for (int cc = 0; cc < 4; ++cc) {   // K = 32 kp + 8 cc .. + 7: columns 16 kp + 4 cc .. + 3
                     uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
@@ -339,12 +359,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
                         tc_split2(v[0], v[1], w1[2 * e], w2[2 * e], w3[2 * e]);
                         tc_split2(v[2], v[3], w1[2 * e + 1], w2[2 * e + 1], w3[2 * e + 1]);
                     }
-                    unsigned char* dstc = ah + (((4 * kp + cc) ^ rsw) << 4);
-                    *reinterpret_cast<uint4*>(dstc) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-                    *reinterpret_cast<uint4*>(dstc + kTcATile) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-                    *reinterpret_cast<uint4*>(dstc + 2 * kTcATile) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+                    tmem_st4(th + (uint32_t)(4 * cc), w1[0], w1[1], w1[2], w1[3]);
+                    tmem_st4(th + (uint32_t)(32 + 4 * cc), w2[0], w2[1], w2[2], w2[3]);
+                    tmem_st4(th + (uint32_t)(64 + 4 * cc), w3[0], w3[1], w3[2], w3[3]);
                 }
-                tc_fence_proxy_async();
+                tmem_wait_st();
+                if (h == 0 && wrote_b) tc_fence_proxy_async();   // the matrices, for the MMAs' reads
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc_mbar_arrive(&bar_conv[h]);
             }
@@ -359,29 +380,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
         // ---- epilogue: accumulators -> scaling / recombination -> stores -------
         const int g4 = warp & 3;                                  // TMEM lanes 32 g4 .. = tile rows
         const int r = 32 * g4 + lane;                             // one row per thread
+        float* const stage = reinterpret_cast<float*>(sm + kTcOffOut + (warp - 1 - kTcConv / 32) * 4 * kTcStage);
         TcTile cur = first;
         long long item = item0;
-        int bs = bsearch;
+        int bs = bsearch, u = 0;   // u: bulk-stored line groups so far (staging buffer u mod 2)
         TcBlk kb;
         for (int t = 0;; ++t) {
-            const bool ok = tc_mbar_sleep_or_abort(&bar_mma[t & 1], (uint32_t)((t >> 1) & 1), &s_abort);
+            const bool ok = tc_mbar_sleep_or_abort(&bar_mma, (uint32_t)(t & 1), &s_abort);
             if (!__all_sync(0xffffffffu, ok)) { s_abort = 1; break; }
             tc_fence_after();
             tc_blk_load(kb, a.blk, cur.b, a.axis);
             const int n = kb.n, ns = kb.ns;
             const long long R = kb.R;
             const long long l = (long long)cur.q * kTcRows + r;   // row within the orbital
+            const int x0 = cur.q * kTcRows + 32 * g4;               // first row of this warp's lines
             float lxy = 0.f;
             if (a.scale && l < R) {   // forward z: rows are (my, mx), mx fastest
                 const int mx = (int)(l % kb.nx), my = (int)(l / kb.nx);
                 lxy = a.lam[kb.kl0 + mx] + a.lam[kb.kl1 + my];
             }
             const float* lz = a.lam + kb.kl2;
-            const uint32_t ta = tmem + ((uint32_t)(32 * g4) << 16) + (uint32_t)((t & 1) * 256);
+            const uint32_t ta = tmem + ((uint32_t)(32 * g4) << 16);
+            float amax = 0.f;   // max |output| of this row (for a.dmax)
             float* const dst = a.out + kb.off + (long long)cur.o * kb.G + (l < R ? l : 0);
-            const long long s2 = a.inverse ? -R : R;
-            float* p1 = dst;                                                   // position m
-            float* p2 = dst + (long long)(a.inverse ? n - 1 : ns) * R;         // its partner
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float e0[16], e1[16], o0[16], o1[16];
@@ -390,34 +411,72 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
                 tmem_ld16(ta + 16 * c + 128, o0);
                 tmem_ld16(ta + 16 * c + 192, o1);
                 tmem_wait_ld();
-                if (c == 3) {   // the buffer is read: the MMAs of tile t + 2 may overwrite it
+                if (c == 3) {   // the accumulators are read: the next tile's MMAs may overwrite them
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) tc_mbar_arrive(&bar_empty[t & 1]);
+                    if (lane == 0) tc_mbar_arrive(&bar_empty);
                 }
                 const int m0 = 16 * c;
-                if (l < R && m0 < ns) {
+                if (m0 >= ns) continue;
+                // lines of output position p1 = m (forward: even mode m; inverse: point m) and
+                // p2 (forward: odd mode ns + m; inverse: point n - 1 - m)
+                float v1[16], v2[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float ve = e0[j] + e1[j], vo = o0[j] + o1[j];
+                    if (!a.inverse) {
+                        if (a.scale) {   // (fast division: 2 ulp, far below the solve's accuracy)
+                            const float se = lxy + lz[m0 + j], so = lxy + lz[ns + m0 + j];
+                            ve = se > 0.f ? __fdividef(ve, se) : 0.f;
+                            vo = so > 0.f ? __fdividef(vo, so) : 0.f;
+                        }
+                        v1[j] = ve;
+                        v2[j] = vo;
+                    } else {
+                        v1[j] = ve + vo;
+                        v2[j] = ve - vo;
+                    }
+                    if (m0 + j < ns) amax = fmaxf(amax, fmaxf(fabsf(v1[j]), fabsf(v2[j])));
+                }
+                if (m0 + kTcLines <= ns) {
+                    // 16 whole lines: stage them (line j of 32 rows) and store in bulk
+                    float* const sb = stage + (u & 1) * 2 * (kTcStage / 4);
+                    if (lane == 0) tc_bulk_wait_read1();   // the store from this buffer two groups ago has read it
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        sb[j * 32 + lane] = v1[j];
+                        sb[kTcStage / 4 + (a.inverse ? 15 - j : j) * 32 + lane] = v2[j];
+                    }
+                    tc_fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (x0 < R) {
+                            const int y0 = cur.o * n;
+                            tc_tma_store_2d(a.omaps + cur.b, x0, y0 + m0, sb);
+                            tc_tma_store_2d(a.omaps + cur.b, x0, y0 + (a.inverse ? n - kTcLines - m0 : ns + m0),
+                                            sb + kTcStage / 4);
+                        }
+                        tc_bulk_commit();
+                    }
+                    ++u;
+                } else if (l < R) {
+                    // a partial group of lines (ns not a multiple of 16): plain stores
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (m0 + j < ns) {
-                            float ve = e0[j] + e1[j], vo = o0[j] + o1[j];
-                            if (!a.inverse) {
-                                if (a.scale) {   // (fast division: 2 ulp, far below the solve's accuracy)
-                                    const float se = lxy + lz[m0 + j], so = lxy + lz[ns + m0 + j];
-                                    ve = se > 0.f ? __fdividef(ve, se) : 0.f;
-                                    vo = so > 0.f ? __fdividef(vo, so) : 0.f;
-                                }
-                                __stcs(p1, ve);
-                                __stcs(p2, vo);
-                            } else {
-                                __stcs(p1, ve + vo);
-                                __stcs(p2, ve - vo);
-                            }
+                            const int k1 = m0 + j, k2 = a.inverse ? n - 1 - m0 - j : ns + m0 + j;
+                            __stcs(dst + (long long)k1 * R, v1[j]);
+                            __stcs(dst + (long long)k2 * R, v2[j]);
                         }
-                        p1 += R;
-                        p2 += s2;
                     }
                 }
+            }
+            if (a.dmax) {   // rows past the orbital's last one hold no output
+                float m = l < R ? amax : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0 && m > 0.f) atomicMax(a.dmax + a.blk[cur.b].orb0 + cur.o, __float_as_uint(m));
             }
             TcTile nxt_t{};
             const long long nxt = tc_next(a, item + 1, it1, bs, nxt_t);
@@ -425,17 +484,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
             cur = nxt_t;
             item = nxt;
         }
+        if (lane == 0) tc_bulk_wait_all();   // the bulk stores have completed
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
     if (s_abort && tid == 0) {
         atomicOr(a.status + 3, 4);
-        // let the copy and the MMAs this CTA has in flight finish (bounded)
-        if (s_tma_issued > s_tma_waited) tc_mbar_wait(&bar_tma, (uint32_t)((s_tma_issued - 1) & 1));
-        if (s_mma_issued > 0) {
-            const int last = s_mma_issued - 1;
-            tc_mbar_wait(&bar_mma[last & 1], (uint32_t)((last >> 1) & 1));
-        }
+        // let the copies and the MMAs this CTA has in flight finish (bounded)
+        for (int b = 0; b < 2; ++b)
+            if (s_tma_issued[b] > 0) tc_mbar_wait(&bar_tma[b], (uint32_t)((s_tma_issued[b] - 1) & 1));
+        if (s_mma_issued > 0) tc_mbar_wait(&bar_mma, (uint32_t)((s_mma_issued - 1) & 1));
     }
     __syncthreads();
     if (warp == 0) {
@@ -517,6 +576,25 @@ bool kron_tc_map(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, 
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output lines of pass `step` of block B as a 2-D tensor map: the output is
+// out[orb][k][row], so R = G / n rows per line (contiguous) and N n lines;
+// boxes of 32 rows x 16 lines, no swizzle (the epilogue stages line-major).
+bool kron_tc_map_out(void* encode_fn, CUtensorMap* map, const BlkDesc& B, int axis, float* buf) {
+    auto encode = reinterpret_cast<CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                                CUtensorMapInterleave, CUtensorMapSwizzle,
+                                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(encode_fn);
+    const int n = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
+    const long long R = B.G / n;
+    const cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)n * (cuuint64_t)B.N};
+    const cuuint64_t strides[1] = {(cuuint64_t)R * sizeof(float)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)kTcLines};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, buf + B.off, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 long long kron_tc_tiles(const BlkDesc& B, int axis) {
     const int n = axis == 0 ? B.nx : (axis == 1 ? B.ny : B.nz);
     const long long R = B.G / n;
@@ -530,11 +608,13 @@ void launch_kron_tc_pass(flosic_ctx* c, int step, float* out, cudaStream_t s) {
     a.nblk = c->nblk;
     a.item0 = K.tc_items + (size_t)step * (c->nblk + 1);
     a.maps = reinterpret_cast<const CUtensorMap*>(K.tc_maps) + (size_t)step * c->nblk;
+    a.omaps = reinterpret_cast<const CUtensorMap*>(K.tc_omaps) + (size_t)step * c->nblk;
     a.mat = K.tc_mat;
     a.lam = K.lam;
     a.out = out;
     a.active = c->ws.cg.active;
     a.flops = c->profiling ? c->ws.cg.prof_bytes : nullptr;
+    a.dmax = step == 5 ? c->ws.cg.dmax : nullptr;   // the correction d: its scale for the refinement update
     a.status = c->ws.status;
     a.axis = step % 3;
     a.inverse = step >= 3;

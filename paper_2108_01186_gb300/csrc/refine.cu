@@ -14,12 +14,21 @@
 // Round structure per orbital:  r = b - A x (pairs) -> stop if
 // r.r <= tol^2 b.b, else a float32 solve of A d = float(r) to
 // max(inner_tol^2 r.r, tol^2 b.b / 4) -> x += d (pairs).
+#include <cmath>
+
 #include "ffsweep.cuh"
 
 namespace flosic {
 
 
-cudaError_t upload_ff_weights() { return upload_ffsweep_weights(); }
+bool ix_weights_match();
+
+// the float-float weights, after checking the update's integer weights
+// against the float64 ones (a mismatch fails the context's creation)
+cudaError_t upload_ff_weights() {
+    if (!ix_weights_match()) return cudaErrorInvalidValue;
+    return upload_ffsweep_weights();
+}
 
 // Last CTA of an orbital, once r.r is known: the outer stop test, else the
 // start of the next float32 solve (its target, active flag and counters).
@@ -145,43 +154,240 @@ __global__ void __launch_bounds__(256) k_residual12_ff(const BlkDesc* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact stencil sums for the refinement update.  The 12th-order weights of
+// the second derivative (Sec. II.A: centred differences, w_m =
+// 2 (-1)^(m+1) (6!)^2 / (m^2 (6-m)! (6+m)!), w_0 = -2 sum w_m) are rationals
+// whose common denominator is 831600, so W_m = 831600 w_m are integers and
+// h^2 Delta_h u = (1 / 831600) sum_m W_m (sum of the six neighbours at
+// distance m).  A float32 field d whose magnitude is below 2^e splits
+// exactly into y = d 2^(28-e) = hi + lo with hi = rint(y) an integer
+// (|hi| <= 2^28) and |lo| <= 1/2: the hi parts are summed and weighted in
+// integers (six of them stay below 2^31, the weighted sum below 2^53), so
+// that part is exact, and the lo parts in float32, an error of a few units
+// of 2^(e-28) / 831600 in h^2 Delta_h d per point -- about 1e-14 of
+// max |d| / h^2, below the float-float sweep's error on smooth fields.
+// ---------------------------------------------------------------------------
+constexpr long long kW12Den = 831600;
+
+__host__ __device__ constexpr long long w12_fact(int n) { return n <= 1 ? 1 : n * w12_fact(n - 1); }
+__host__ __device__ constexpr long long w12_num(int m) {   // 2 (6!)^2 831600, signed
+    return (m % 2 == 1 ? 2 : -2) * w12_fact(6) * w12_fact(6) * kW12Den;
+}
+__host__ __device__ constexpr long long w12_den(int m) { return (long long)m * m * w12_fact(6 - m) * w12_fact(6 + m); }
+// W_m for m >= 1; W_0 of the three-dimensional centre is 3 (-2 sum_m W_m)
+__host__ __device__ constexpr long long w12_int(int m) { return w12_num(m) / w12_den(m); }
+__host__ __device__ constexpr long long w12_centre3() {
+    return -6 * (w12_int(1) + w12_int(2) + w12_int(3) + w12_int(4) + w12_int(5) + w12_int(6));
+}
+static_assert(w12_num(1) % w12_den(1) == 0 && w12_num(2) % w12_den(2) == 0 && w12_num(3) % w12_den(3) == 0 &&
+                  w12_num(4) % w12_den(4) == 0 && w12_num(5) % w12_den(5) == 0 && w12_num(6) % w12_den(6) == 0,
+              "831600 is a common denominator of the 12th-order weights");
+static_assert(w12_centre3() > -(1LL << 24) && w12_int(1) < (1LL << 24), "weights exact in float32");
+
+// Host check of the integer weights against the float64 ones the other
+// stencils use (|W_m / 831600 - w_m| at rounding level).
+bool ix_weights_match() {
+    double w[kHalf + 1];
+    stencil_weights(w);
+    for (int m = 1; m <= kHalf; ++m)
+        if (std::fabs((double)w12_int(m) / (double)kW12Den - w[m]) > 1e-15 * std::fabs(w[m])) return false;
+    return std::fabs((double)w12_centre3() / (double)kW12Den - 3.0 * w[0]) <= 1e-15 * std::fabs(3.0 * w[0]);
+}
+
+struct __align__(8) IxPt {
+    int h;     // rint(y)
+    float l;   // y - rint(y), or y itself when it is not finite
+};
+
+// y = d 2^es (exact) split into hi + lo; a non-finite y keeps hi = 0 and
+// carries inf / NaN in lo, so it reaches the residual.
+__device__ __forceinline__ IxPt ix_split(float d, float s) {
+    const float y = d * s;
+    const float r = rintf(y);
+    const bool fin = fabsf(y) < 536870912.f;   // 2^29
+    return {fin ? __float2int_rn(r) : 0, fin ? y - r : y};
+}
+
+// Per orbital, max |d| over its grid (float bits in st.dmax, atomicMax on
+// the bit patterns of non-negative floats); the update's last CTA of the
+// orbital resets it.  NaN values are skipped here and reach the residual
+// through the split.
+__global__ void __launch_bounds__(256) k_dmax(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                              const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                              const float* __restrict__ d32, CgState st) {
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o]) return;
+    const LvlDesc& D = L[P.b];
+    float m = 0.f;
+    tile_elementwise<float>(D, P, [&](long long g, int n) {
+        if (n == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(d32 + g);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            return;
+        }
+        for (int k = 0; k < n; ++k) m = fmaxf(m, fabsf(d32[g + k]));
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((linear_tid() & 31) == 0 && m > 0.f) atomicMax(st.dmax + P.o, __float_as_uint(m));
+}
+
 // One refinement round's update from the float32 correction d of the inner
 // solve: r -= A d (r in pairs, in place: r_{k+1} = b - A x_{k+1} =
 // r_k - A d_k), x += d (pairs), r32 = float(r), and the next round's start.
-// The operand of the sweep is d itself, a float32 field, so the stencil sums
-// run on plain floats.  d is left as it is (neighbouring tiles read it as
-// halo): this serves inner solvers that overwrite d (the Kronecker-product
-// solve), not those that start from d = 0.
-__global__ void __launch_bounds__(256) k_update12_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+// A d comes from the exact integer sums above, on the tiles of the other
+// 12th-order sweeps (a CTA of 32 x 8 threads owns a 32 x 16 column tile and
+// marches along z: the plane with its 6-point x/y halo staged in shared
+// memory as split values, the 13 z-values of each of its two columns in
+// registers).  d is left as it is (neighbouring tiles read it as halo): this
+// serves inner solvers that overwrite d (the Kronecker-product solve), not
+// those that start from d = 0.
+__global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                      float2* __restrict__ r, float2* __restrict__ x,
                                                      float* __restrict__ r32, const float* __restrict__ d32,
                                                      double tol2, double inner_tol2, int max_iter, CgState st) {
-    __shared__ float plane[kPY][kPX];
+    __shared__ IxPt plane[kPY][kPX];
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
     const LvlDesc& D = L[P.b];
-    const ff ih2 = to_ff(d2ff(1.0 / (D.h * D.h)));   // once per CTA
+    // |d| < 2^(E - 126) with E the biased exponent of max |d|: scale by
+    // 2^es, es = 154 - E (so |y| < 2^28), kept within the normal range
+    const int E = (int)((st.dmax[P.o] >> 23) & 0xffu);
+    const int es = max(-126, min(126, 154 - E));
+    const float s = __uint_as_float((unsigned)(es + 127) << 23);    // 2^es
+    const float is = __uint_as_float((unsigned)(127 - es) << 23);   // 2^-es
+    const ff cf = to_ff(d2ff(ldexp(1.0 / ((double)kW12Den * D.h * D.h), -es)));   // units -> Delta_h d
+    constexpr int kWc = (int)w12_centre3();
+    constexpr int kW1 = (int)w12_int(1), kW2 = (int)w12_int(2), kW3 = (int)w12_int(3);
+    constexpr int kW4 = (int)w12_int(4), kW5 = (int)w12_int(5), kW6 = (int)w12_int(6);
+    const int kW[kHalf + 1] = {kWc, kW1, kW2, kW3, kW4, kW5, kW6};
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTileX + tx;
+    const int nthr = kTileX * (kTileY / 2);
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    const int gx = P.x0 + tx;
+    const int gy0 = P.y0 + ty, gy1 = P.y0 + ty + kTileY / 2;
+    const bool in0 = gx < D.nx && gy0 < D.ny, in1 = gx < D.nx && gy1 < D.ny;
+    const long long c0 = gy0 * sy + gx, c1 = gy1 * sy + gx;
+    int soff[kSlots];   // in-plane offsets of this thread's staged points (-1: outside)
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) {
+        const int e = tid + j * nthr;
+        soff[j] = -1;
+        if (e < kPX * kPY) {
+            const int yy = e / kPX, xx = e - yy * kPX;
+            int px = P.x0 - kHalf + xx, py = P.y0 - kHalf + yy;
+            if (D.per & 1) px = wrap_coord(px, D.nx);
+            if (D.per & 2) py = wrap_coord(py, D.ny);
+            if (px >= 0 && px < D.nx && py >= 0 && py < D.ny) soff[j] = py * D.nx + px;
+        }
+    }
+    IxPt q0[2 * kHalf + 1], q1[2 * kHalf + 1];
+    const bool perz = (D.per & 4) != 0;
+#pragma unroll
+    for (int j = 0; j < 2 * kHalf; ++j) {
+        int zz = P.z0 - kHalf + j;
+        if (perz) zz = wrap_coord(zz, D.nz);
+        const bool okz = zz >= 0 && zz < D.nz;
+        q0[j] = ix_split((in0 && okz) ? d32[P.base + zz * sz + c0] : 0.f, s);
+        q1[j] = ix_split((in1 && okz) ? d32[P.base + zz * sz + c1] : 0.f, s);
+    }
+    float pre[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? d32[P.base + P.z0 * sz + soff[j]] : 0.f;
+    // r and x of this thread's two points, one plane ahead of their use
+    float4 rx0 = make_float4(0.f, 0.f, 0.f, 0.f), rx1 = rx0;   // (r.h, r.l, x.h, x.l)
+    if (in0) {
+        const float2 rv = r[P.base + P.z0 * sz + c0], xv = x[P.base + P.z0 * sz + c0];
+        rx0 = make_float4(rv.x, rv.y, xv.x, xv.y);
+    }
+    if (in1) {
+        const float2 rv = r[P.base + P.z0 * sz + c1], xv = x[P.base + P.z0 * sz + c1];
+        rx1 = make_float4(rv.x, rv.y, xv.x, xv.y);
+    }
+    IxPt* flat = &plane[0][0];
     float rrf = 0.f;
-    ff_sweep12_f(
-        D, P, [&](long long g) { return d32[g]; },
-        [&](long long g, float dc, ff acc) {
-            // acc = h^2 Delta_h d, so r - A d = r + acc / h^2
-            const ff rn = ff_add(to_ff(r[g]), ff_mul(acc, ih2));
-            const float2 xv = x[g];
-            const ff xs = ff_two_sum(xv.x, dc);
-            const ff xn = ff_quick(xs.h, xs.l + xv.y);
-            r[g] = make_float2(rn.h, rn.l);
-            x[g] = make_float2(xn.h, xn.l);
-            r32[g] = rn.h;
-            rrf += rn.h * rn.h;
-        },
-        plane);
+    for (int z = P.z0; z < P.z1; ++z) {
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int e = tid + j * nthr;
+            if (e < kPX * kPY) flat[e] = ix_split(pre[j], s);
+        }
+        {
+            int zz = z + kHalf;
+            if (perz) zz = wrap_coord(zz, D.nz);
+            q0[2 * kHalf] = ix_split((in0 && zz < D.nz) ? d32[P.base + zz * sz + c0] : 0.f, s);
+            q1[2 * kHalf] = ix_split((in1 && zz < D.nz) ? d32[P.base + zz * sz + c1] : 0.f, s);
+        }
+        __syncthreads();
+        float4 nx0 = rx0, nx1 = rx1;
+        if (z + 1 < P.z1) {
+            const long long pz = P.base + (z + 1) * sz;
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? d32[pz + soff[j]] : 0.f;
+            if (in0) {
+                const float2 rv = r[pz + c0], xv = x[pz + c0];
+                nx0 = make_float4(rv.x, rv.y, xv.x, xv.y);
+            }
+            if (in1) {
+                const float2 rv = r[pz + c1], xv = x[pz + c1];
+                nx1 = make_float4(rv.x, rv.y, xv.x, xv.y);
+            }
+        }
+        const int lx = tx + kHalf;
+        const int ly[2] = {ty + kHalf, ty + kTileY / 2 + kHalf};
+        const bool in[2] = {in0, in1};
+        const long long cc[2] = {c0, c1};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const IxPt* qk = (k == 0) ? q0 : q1;
+            long long I = (long long)kW[0] * qk[kHalf].h;
+            float Lo = (float)kW[0] * qk[kHalf].l;
+#pragma unroll
+            for (int m = 1; m <= kHalf; ++m) {
+                const IxPt a = plane[ly[k]][lx - m], b = plane[ly[k]][lx + m];
+                const IxPt c = plane[ly[k] - m][lx], d = plane[ly[k] + m][lx];
+                const IxPt e = qk[kHalf - m], f = qk[kHalf + m];
+                const int hs = ((a.h + b.h) + (c.h + d.h)) + (e.h + f.h);
+                const float ls = ((a.l + b.l) + (c.l + d.l)) + (e.l + f.l);
+                I += (long long)kW[m] * hs;
+                Lo = fmaf((float)kW[m], ls, Lo);
+            }
+            if (in[k]) {
+                const long long g = P.base + z * sz + cc[k];
+                // I + Lo in float-float (I's two leading float parts), times 2^-es / (831600 h^2)
+                const float ih = __ll2float_rn(I);
+                const float il = __ll2float_rn(I - __float2ll_rn(ih)) + Lo;
+                const ff ad = ff_mul(ff_two_sum(ih, il), cf);   // Delta_h d, so r - A d = r + ad
+                const float4 rx = (k == 0) ? rx0 : rx1;
+                const ff rn = ff_add(ff{rx.x, rx.y}, ad);
+                const float dc = (__int2float_rn(qk[kHalf].h) + qk[kHalf].l) * is;   // d at the point (exact)
+                const ff xs = ff_two_sum(rx.z, dc);
+                const ff xn = ff_quick(xs.h, xs.l + rx.w);
+                r[g] = make_float2(rn.h, rn.l);
+                x[g] = make_float2(xn.h, xn.l);
+                r32[g] = rn.h;
+                rrf += rn.h * rn.h;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 2 * kHalf; ++j) {
+            q0[j] = q0[j + 1];
+            q1[j] = q1[j + 1];
+        }
+        rx0 = nx0;
+        rx1 = nx1;
+    }
     if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
+            st.dmax[P.o] = 0u;   // every CTA of the orbital has read it
             start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
         }
     }
@@ -258,7 +464,12 @@ void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* 
 
 void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double inner_tol2, cudaStream_t s) {
     const Multigrid& M = c->mg;
-    k_update12_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+    if (c->kron.n_simt > 0) {   // the tensor-core passes record max |d| themselves
+        k_dmax<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
+                                                                c->ws.d32, c->ws.cg);
+        note_launch(c);
+    }
+    k_update12_ix<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
         c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(r), x, c->ws.r32, c->ws.d32,
         tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
     note_launch(c);
