@@ -527,6 +527,10 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         c->n_tma_blocks = f32 ? setup_tensor_maps(c, w.z32, w.p32, w.q32, 4) : setup_tensor_maps(c, w.z64, w.p64, w.q64, 8);
         cudaGetLastError();   // a refused attribute or entry point only disables the copy-engine path
     }
+    if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) {
+        c->n_utma_blocks = setup_update_maps(c);
+        cudaGetLastError();   // as above: the update then runs with plain loads
+    }
     if (e != cudaSuccess) {
         g_create_error = std::string("workspace set-up: ") + cudaGetErrorString(e);
         release(c);

@@ -71,6 +71,7 @@ struct LvlDesc {
     long long tile0;       // first tile of orbital 0 in this level's tile table
     int ntile;             // tiles per orbital
     int tma;               // level 0: 1 if the stencil operands of this block are TMA-staged
+    int utma;              // level 0: 1 if the refinement update's operands are TMA-staged
     int per;               // level 0: periodic directions (bit 0 x, 1 y, 2 z); 0 on coarse levels
     int tz;                // z-depth of this level's tiles (kTileZ on level 0, kTileZc below)
     // Diagonal weight (units 1/h_l^2) of the 7-point operator at the last
@@ -211,6 +212,8 @@ struct flosic_ctx {
     mutable long long launches = 0;         // kernels launched by this context
     int n_tma_blocks = 0;                   // blocks whose stencil operands the copy engine stages
     void* d_tmaps = nullptr;                // per-block tensor maps of the z buffer (CUtensorMap)
+    int n_utma_blocks = 0;                  // blocks whose refinement-update operands the copy engine stages
+    void* d_umaps = nullptr;                // per-block tensor maps of d, r and x for the update (CUtensorMap)
     // optional CUDA-event timing of the dominant kernel (the CG stencil apply)
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;       // start/stop pairs, recorded in order
@@ -310,6 +313,7 @@ const void* apply12_tma_symbol(bool f32);
 void launch_residual12(flosic_ctx* c, const double* b, const double* x, double* r, double tol2, int max_iter,
                        int* flag, int* counter, int want_bb, cudaStream_t s);
 cudaError_t upload_ff_weights();
+int setup_update_maps(flosic_ctx* c);   // refinement update's tensor maps (refine.cu); blocks on that path
 // mixed precision: float-float refinement around the float32 inner solves
 // (b holds float-float pairs, written so by launch_rhs; x the solution's)
 void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,

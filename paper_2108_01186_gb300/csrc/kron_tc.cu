@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
             const int x0 = cur.q * kTcRows + 32 * g4;               // first row of this warp's lines
             float lxy = 0.f;
             if (a.scale && l < R) {   // forward z: rows are (my, mx), mx fastest
-                const int mx = (int)(l % kb.nx), my = (int)(l / kb.nx);
+                const int li = (int)l, my = li / kb.nx, mx = li - my * kb.nx;
                 lxy = a.lam[kb.kl0 + mx] + a.lam[kb.kl1 + my];
             }
             const float* lz = a.lam + kb.kl2;
@@ -436,7 +436,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_kron_tc(KronTcArgs a, long lo
                         v1[j] = ve + vo;
                         v2[j] = ve - vo;
                     }
-                    if (m0 + j < ns) amax = fmaxf(amax, fmaxf(fabsf(v1[j]), fabsf(v2[j])));
+                }
+                if (a.dmax) {   // (last inverse pass only) a tree of maxima, not a chain
+                    float mj[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float u0 = m0 + j < ns ? fmaxf(fabsf(v1[j]), fabsf(v2[j])) : 0.f;
+                        const float u1 = m0 + j + 8 < ns ? fmaxf(fabsf(v1[j + 8]), fabsf(v2[j + 8])) : 0.f;
+                        mj[j] = fmaxf(u0, u1);
+                    }
+                    amax = fmaxf(amax, fmaxf(fmaxf(fmaxf(mj[0], mj[1]), fmaxf(mj[2], mj[3])),
+                                             fmaxf(fmaxf(mj[4], mj[5]), fmaxf(mj[6], mj[7]))));
                 }
                 if (m0 + kTcLines <= ns) {
                     // 16 whole lines: stage them (line j of 32 rows) and store in bulk

@@ -15,8 +15,12 @@
 // r.r <= tol^2 b.b, else a float32 solve of A d = float(r) to
 // max(inner_tol^2 r.r, tol^2 b.b / 4) -> x += d (pairs).
 #include <cmath>
+#include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "ffsweep.cuh"
+#include "tcgen05.cuh"
 
 namespace flosic {
 
@@ -209,6 +213,21 @@ __device__ __forceinline__ IxPt ix_split(float d, float s) {
     return {fin ? __float2int_rn(r) : 0, fin ? y - r : y};
 }
 
+// I + Lo as a float-float pair (|I| < 2^53): |I| in three pieces of at most 23
+// bits, each turned into a float exactly by the 2^23 bias (integer and float
+// additions only -- no 64-bit conversion, which would run on the float64
+// pipe), summed with a two-sum; Lo is added to the low part (one rounding).
+__device__ __forceinline__ ff ix_to_ff(long long I, float Lo) {
+    const unsigned long long M = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
+    const float f0 = __uint_as_float(0x4B000000u | ((unsigned)M & 0x7fffffu)) - 8388608.f;
+    const float f1 = (__uint_as_float(0x4B000000u | ((unsigned)(M >> 23) & 0x7fffffu)) - 8388608.f) * 8388608.f;
+    const float f2 = (__uint_as_float(0x4B000000u | (unsigned)(M >> 46)) - 8388608.f) * 70368744177664.f;
+    ff v = ff_two_sum(f2, f1);
+    const float sg = I < 0 ? -1.f : 1.f;
+    v = ff_two_sum(sg * v.h, sg * (v.l + f0) + Lo);
+    return v;
+}
+
 // Per orbital, max |d| over its grid (float bits in st.dmax, atomicMax on
 // the bit patterns of non-negative floats); the update's last CTA of the
 // orbital resets it.  NaN values are skipped here and reach the residual
@@ -251,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
     __shared__ IxPt plane[kPY][kPX];
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
-    if (!st.oactive[P.o]) return;
+    if (!st.oactive[P.o] || L[P.b].utma) return;
     const LvlDesc& D = L[P.b];
     // |d| < 2^(E - 126) with E the biased exponent of max |d|: scale by
     // 2^es, es = 154 - E (so |y| < 2^28), kept within the normal range
@@ -360,9 +379,7 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
             if (in[k]) {
                 const long long g = P.base + z * sz + cc[k];
                 // I + Lo in float-float (I's two leading float parts), times 2^-es / (831600 h^2)
-                const float ih = __ll2float_rn(I);
-                const float il = __ll2float_rn(I - __float2ll_rn(ih)) + Lo;
-                const ff ad = ff_mul(ff_two_sum(ih, il), cf);   // Delta_h d, so r - A d = r + ad
+                const ff ad = ff_mul(ix_to_ff(I, Lo), cf);   // Delta_h d, so r - A d = r + ad
                 const float4 rx = (k == 0) ? rx0 : rx1;
                 const ff rn = ff_add(ff{rx.x, rx.y}, ad);
                 const float dc = (__int2float_rn(qk[kHalf].h) + qk[kHalf].l) * is;   // d at the point (exact)
@@ -391,6 +408,229 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
             start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
         }
     }
+}
+
+// The same update with its operands staged by the copy engine (blocks
+// whose rows and offset are 16-byte aligned and that have no periodic
+// direction: the zero fill of the copies is the zero ghost value).  A ring
+// of kURing stages runs ahead of the z-march, each holding the plane z of d
+// with its halo (48 x 28: x0 - 8 keeps the copy 16-byte aligned), d at
+// plane z + 6 (32 x 16, the head of the register z-queues) and r and x at
+// plane z (32 x 16 pairs).  Each plane's d is split once into shared memory
+// (hi, lo; two buffers, so one barrier per plane serves both the split plane
+// and the stage of the plane before); a thread owns the two points (x0 + 2 tx + a, y0 + ty), reads
+// their x-window (14 values) and y-windows as 16-byte pairs and keeps their
+// z-windows in registers.
+constexpr int kUX = 48;                              // staged width: x0 - 8 .. x0 + 39
+constexpr int kUY = kTileY + 2 * kHalf;              // 28: y0 - 6 .. y0 + 21
+constexpr int kUPlane = kUX * kUY;                   // floats of the halo plane
+constexpr int kUCtr = kTileX * kTileY;               // points of a centre tile
+constexpr int kUStage = kUPlane + 5 * kUCtr;         // floats: plane, d head, r pairs, x pairs
+constexpr int kURing = 5;
+constexpr unsigned kUStageBytes = 4u * kUStage;
+
+// the stages, two split planes (one barrier per plane), the stages' mbarriers
+size_t update_tma_smem() { return 4 * (size_t)kURing * kUStage + 2 * sizeof(IxPt) * kUPlane + 8 * kURing + 128; }
+
+__global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+                                                         const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
+                                                         const CUtensorMap* __restrict__ maps,
+                                                         const float* __restrict__ d32, float2* __restrict__ r,
+                                                         float2* __restrict__ x, float* __restrict__ r32,
+                                                         double tol2, double inner_tol2, int max_iter, CgState st,
+                                                         int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char us_raw[];
+    unsigned char* smem = us_raw + ((128 - (tc_smem_addr(us_raw) & 127)) & 127);
+    float* ring = reinterpret_cast<float*>(smem);
+    IxPt* spb = reinterpret_cast<IxPt*>(smem + 4 * (size_t)kURing * kUStage);   // two split planes
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * (size_t)kURing * kUStage + 2 * sizeof(IxPt) * kUPlane);
+    __shared__ double scratch[32];
+    const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
+    if (!st.oactive[P.o] || !L[P.b].utma) return;
+    const LvlDesc& D = L[P.b];
+    const CUtensorMap* mp = maps + 4 * P.b;   // d with halo, d centre, r pairs, x pairs
+    const int oi = P.o - blk[P.b].orb0;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nzt = P.z1 - P.z0;
+    const int E = (int)((st.dmax[P.o] >> 23) & 0xffu);
+    const int es = max(-126, min(126, 154 - E));
+    const float sc = __uint_as_float((unsigned)(es + 127) << 23);   // 2^es
+    const float is = __uint_as_float((unsigned)(127 - es) << 23);   // 2^-es
+    const ff cf = to_ff(d2ff(ldexp(1.0 / ((double)kW12Den * D.h * D.h), -es)));
+    constexpr int kWc = (int)w12_centre3();
+    constexpr int kW1 = (int)w12_int(1), kW2 = (int)w12_int(2), kW3 = (int)w12_int(3);
+    constexpr int kW4 = (int)w12_int(4), kW5 = (int)w12_int(5), kW6 = (int)w12_int(6);
+    const int kW[kHalf + 1] = {kWc, kW1, kW2, kW3, kW4, kW5, kW6};
+    auto issue = [&](int k) {
+        uint64_t* b = bar + (k % kURing);
+        float* sg = ring + (size_t)(k % kURing) * kUStage;
+        const int zz = P.z0 + k;
+        tc_mbar_expect_tx(b, kUStageBytes);
+        tc_tma_load_4d(sg, mp + 0, P.x0 - 8, P.y0 - kHalf, zz, oi, b);
+        tc_tma_load_4d(sg + kUPlane, mp + 1, P.x0, P.y0, zz + kHalf, oi, b);
+        tc_tma_load_4d(sg + kUPlane + kUCtr, mp + 2, 2 * P.x0, P.y0, zz, oi, b);
+        tc_tma_load_4d(sg + kUPlane + 3 * kUCtr, mp + 3, 2 * P.x0, P.y0, zz, oi, b);
+    };
+    if (tid == 0) {
+        for (int k = 0; k < kURing; ++k) tc_mbar_init(bar + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < kURing && k < nzt; ++k) issue(k);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 16 x 16
+    const int gx = P.x0 + 2 * tx, gy = P.y0 + ty;
+    const bool in = gx < D.nx && gy < D.ny;           // nx is a multiple of 4: gx + 1 < nx as well
+    const long long sy = D.nx, sz = (long long)D.nx * D.ny;
+    const long long col = gy * sy + gx;
+    IxPt q0[2 * kHalf + 1], q1[2 * kHalf + 1];        // z-windows of the two points
+#pragma unroll
+    for (int j = 0; j < 2 * kHalf; ++j) {
+        const int zz = P.z0 - kHalf + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (in && zz >= 0 && zz < D.nz) v = *reinterpret_cast<const float2*>(d32 + P.base + zz * sz + col);
+        q0[j] = ix_split(v.x, sc);
+        q1[j] = ix_split(v.y, sc);
+    }
+    float rrf = 0.f;
+    const int ly = ty + kHalf, cx = 2 * tx + 8;       // the points' row and first column in the staged plane
+    for (int k = 0; k < nzt; ++k) {
+        if (!tc_mbar_wait(bar + (k % kURing), (uint32_t)((k / kURing) & 1))) atomicOr(status + 3, 8);
+        const float* sg = ring + (size_t)(k % kURing) * kUStage;
+        IxPt* const sp = spb + (k & 1) * kUPlane;
+        for (int e = tid; e < kUPlane; e += 256) sp[e] = ix_split(sg[e], sc);
+        {
+            const float2 hv = *reinterpret_cast<const float2*>(sg + kUPlane + ty * kTileX + 2 * tx);
+            q0[2 * kHalf] = ix_split(hv.x, sc);
+            q1[2 * kHalf] = ix_split(hv.y, sc);
+        }
+        // the split plane is written, and every thread has finished plane k - 1: its
+        // stage takes plane k - 1 + kURing (the other split plane is free for plane k + 1)
+        __syncthreads();
+        if (tid == 0 && k >= 1 && k - 1 + kURing < nzt) {
+            tc_fence_proxy_async();
+            issue(k - 1 + kURing);
+        }
+        // x-window of row ly, columns cx - 6 .. cx + 7, as 7 pairs
+        IxPt xw[2 * kHalf + 2];
+#pragma unroll
+        for (int k2 = 0; k2 < kHalf + 1; ++k2) {
+            const int4 v = *reinterpret_cast<const int4*>(sp + ly * kUX + cx - kHalf + 2 * k2);
+            xw[2 * k2] = {v.x, __int_as_float(v.y)};
+            xw[2 * k2 + 1] = {v.z, __int_as_float(v.w)};
+        }
+        long long I0 = (long long)kW[0] * q0[kHalf].h, I1 = (long long)kW[0] * q1[kHalf].h;
+        float L0 = (float)kW[0] * q0[kHalf].l, L1 = (float)kW[0] * q1[kHalf].l;
+#pragma unroll
+        for (int m = 1; m <= kHalf; ++m) {
+            const int4 u = *reinterpret_cast<const int4*>(sp + (ly - m) * kUX + cx);   // rows ly -+ m, both columns
+            const int4 w = *reinterpret_cast<const int4*>(sp + (ly + m) * kUX + cx);
+            const int h0 = ((xw[kHalf - m].h + xw[kHalf + m].h) + (u.x + w.x)) + (q0[kHalf - m].h + q0[kHalf + m].h);
+            const int h1 = ((xw[kHalf + 1 - m].h + xw[kHalf + 1 + m].h) + (u.z + w.z)) +
+                           (q1[kHalf - m].h + q1[kHalf + m].h);
+            const float l0 = ((xw[kHalf - m].l + xw[kHalf + m].l) + (__int_as_float(u.y) + __int_as_float(w.y))) +
+                             (q0[kHalf - m].l + q0[kHalf + m].l);
+            const float l1 = ((xw[kHalf + 1 - m].l + xw[kHalf + 1 + m].l) +
+                              (__int_as_float(u.w) + __int_as_float(w.w))) +
+                             (q1[kHalf - m].l + q1[kHalf + m].l);
+            I0 += (long long)kW[m] * h0;
+            I1 += (long long)kW[m] * h1;
+            L0 = fmaf((float)kW[m], l0, L0);
+            L1 = fmaf((float)kW[m], l1, L1);
+        }
+        if (in) {
+            const float4 rv = *reinterpret_cast<const float4*>(sg + kUPlane + kUCtr + ty * 2 * kTileX + 4 * tx);
+            const float4 xv = *reinterpret_cast<const float4*>(sg + kUPlane + 3 * kUCtr + ty * 2 * kTileX + 4 * tx);
+            const long long g = P.base + (P.z0 + k) * sz + col;
+            ff rn[2], xn[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const long long I = a == 0 ? I0 : I1;
+                const float Lo = a == 0 ? L0 : L1;
+                const IxPt qc = a == 0 ? q0[kHalf] : q1[kHalf];
+                const ff ad = ff_mul(ix_to_ff(I, Lo), cf);
+                rn[a] = ff_add(a == 0 ? ff{rv.x, rv.y} : ff{rv.z, rv.w}, ad);
+                const float dc = (__int2float_rn(qc.h) + qc.l) * is;
+                const ff xs = ff_two_sum(a == 0 ? xv.x : xv.z, dc);
+                xn[a] = ff_quick(xs.h, xs.l + (a == 0 ? xv.y : xv.w));
+                rrf += rn[a].h * rn[a].h;
+            }
+            *reinterpret_cast<float4*>(r + g) = make_float4(rn[0].h, rn[0].l, rn[1].h, rn[1].l);
+            *reinterpret_cast<float4*>(x + g) = make_float4(xn[0].h, xn[0].l, xn[1].h, xn[1].l);
+            *reinterpret_cast<float2*>(r32 + g) = make_float2(rn[0].h, rn[1].h);
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * kHalf; ++j) {
+            q0[j] = q0[j + 1];
+            q1[j] = q1[j + 1];
+        }
+    }
+    if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
+        const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
+        if (linear_tid() == 0) {
+            st.count[P.o] = 0;
+            st.dmax[P.o] = 0u;
+            start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
+        }
+    }
+}
+
+// Tensor maps of the update's operands, four per block, each a 4-D view
+// (x, y, z, orbital): d with 48 x 28 boxes and 32 x 16 boxes, and the pair
+// arrays r (b) and x as float32 rows of 2 nx values with 64 x 16 boxes.
+// Blocks with a periodic direction, or whose rows or offset are not
+// 16-byte aligned, keep k_update12_ix (flag utma = 0).  Returns the number
+// of blocks on the copy-engine path.
+int setup_update_maps(flosic_ctx* c) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return 0;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    std::vector<CUtensorMap> maps(4 * (size_t)c->nblk);
+    std::vector<LvlDesc>& L0 = c->mg.h_lvl[0];
+    int n_ok = 0;
+    for (int b = 0; b < c->nblk; ++b) {
+        const BlkDesc& B = c->blk[b];
+        L0[b].utma = 0;
+        if (B.nx % 4 != 0 || B.off % 4 != 0 || B.per != 0) continue;
+        const cuuint64_t dims[4] = {(cuuint64_t)B.nx, (cuuint64_t)B.ny, (cuuint64_t)B.nz, (cuuint64_t)B.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)B.nx * 4, (cuuint64_t)B.nx * B.ny * 4, (cuuint64_t)B.G * 4};
+        const cuuint64_t dims2[4] = {2 * (cuuint64_t)B.nx, (cuuint64_t)B.ny, (cuuint64_t)B.nz, (cuuint64_t)B.N};
+        const cuuint64_t strides2[3] = {(cuuint64_t)B.nx * 8, (cuuint64_t)B.nx * B.ny * 8, (cuuint64_t)B.G * 8};
+        const cuuint32_t box_halo[4] = {(cuuint32_t)kUX, (cuuint32_t)kUY, 1, 1};
+        const cuuint32_t box_ctr[4] = {(cuuint32_t)kTileX, (cuuint32_t)kTileY, 1, 1};
+        const cuuint32_t box_pair[4] = {2 * (cuuint32_t)kTileX, (cuuint32_t)kTileY, 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        float* d = c->ws.d32 + B.off;
+        float* rb = reinterpret_cast<float*>(c->ws.b64 + B.off);
+        float* xb = reinterpret_cast<float*>(c->ws.r64 + B.off);
+        bool ok = true;
+        auto enc = [&](CUtensorMap* m, void* base, const cuuint64_t* dm, const cuuint64_t* sd, const cuuint32_t* bx) {
+            return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dm, sd, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        };
+        ok = enc(&maps[4 * b + 0], d, dims, strides, box_halo) && enc(&maps[4 * b + 1], d, dims, strides, box_ctr) &&
+             enc(&maps[4 * b + 2], rb, dims2, strides2, box_pair) && enc(&maps[4 * b + 3], xb, dims2, strides2, box_pair);
+        if (!ok) continue;
+        L0[b].utma = 1;
+        ++n_ok;
+    }
+    if (n_ok == 0) return 0;
+    void* dm = nullptr;
+    if (cudaMalloc(&dm, sizeof(CUtensorMap) * maps.size()) != cudaSuccess) return 0;
+    c->allocations.push_back(dm);
+    if (cudaMemcpy(dm, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_update12_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)update_tma_smem()) != cudaSuccess ||
+        cudaMemcpy(c->mg.d_lvl[0], L0.data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice) != cudaSuccess) {
+        for (auto& D : L0) D.utma = 0;
+        cudaMemcpy(c->mg.d_lvl[0], L0.data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice);
+        return 0;
+    }
+    c->d_umaps = dm;
+    return n_ok;
 }
 
 // x += d32 in pairs for the orbitals still refining.
@@ -469,10 +709,18 @@ void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double i
                                                                 c->ws.d32, c->ws.cg);
         note_launch(c);
     }
-    k_update12_ix<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
-        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(r), x, c->ws.r32, c->ws.d32,
-        tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
-    note_launch(c);
+    if (c->n_utma_blocks > 0) {   // blocks whose operands the copy engine stages
+        k_update12_tma<<<(unsigned)M.ntiles[0], dim3(kTileX / 2, kTileY), update_tma_smem(), s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_umaps, c->ws.d32,
+            reinterpret_cast<float2*>(r), x, c->ws.r32, tol2, inner_tol2, c->opt.max_iter, c->ws.cg, c->ws.status);
+        note_launch(c);
+    }
+    if (c->n_utma_blocks < c->nblk) {   // the rest: plain loads
+        k_update12_ix<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+            c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(r), x, c->ws.r32, c->ws.d32,
+            tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
+        note_launch(c);
+    }
 }
 
 void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s) {

@@ -46,6 +46,16 @@ __device__ __forceinline__ void tc_tma_load_2d(void* dst, const CUtensorMap* map
         : "memory");
 }
 
+// 4-D tiled bulk copy global -> shared (x, y, z, orbital), completion counted in bytes on bar
+__device__ __forceinline__ void tc_tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                               uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+            tc_smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc_smem_addr(bar))
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, consecutive
 // 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
