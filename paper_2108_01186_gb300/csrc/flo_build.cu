@@ -464,28 +464,30 @@ __device__ void mm(int N, const double* A, bool ta, const double* Bm, bool tb, d
 }
 
 // Cyclic Jacobi eigen-decomposition of the symmetric matrix S (N x N,
-// row-major, shared memory), round-robin ordering so that the N/2 rotations
-// of a round are disjoint and run in parallel.  On exit S is diagonal (the
-// eigenvalues) and U holds the eigenvectors as columns.  Stops when the
-// squared off-diagonal norm is at most tol times the squared diagonal one,
-// or after max_sweeps sweeps.  T = float runs the rounds in float32.
+// row-major with row stride ld, shared memory), round-robin ordering so that
+// the N/2 rotations of a round are disjoint and run in parallel.  On exit S
+// is diagonal (the eigenvalues) and U (stride ld) holds the eigenvectors as
+// columns.  Stops when the squared off-diagonal norm is at most tol times
+// the squared diagonal one, or after max_sweeps sweeps.  T = float runs the
+// rounds in float32.  A row stride of N + 1 keeps the column updates (lanes
+// over rows) free of shared-memory bank conflicts.
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <class T>
-__device__ void jacobi_eig_t(int N, T* S, T* U, double tol, int max_sweeps) {
+__device__ void jacobi_eig_t(int N, int ld, T* S, T* U, double tol, int max_sweeps) {
     __shared__ int rp[kMaxN / 2], rq[kMaxN / 2];
     __shared__ T rc[kMaxN / 2], rs[kMaxN / 2];
     __shared__ double scratch[32];
     const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[e] = (e / N == e % N) ? T(1) : T(0);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[(e / N) * ld + e % N] = (e / N == e % N) ? T(1) : T(0);
     __syncthreads();
     const int N2 = N + (N & 1);
     const int m = N2 - 1;
     for (int sweep = 0; sweep < max_sweeps && N > 1; ++sweep) {
         T off = T(0), dg = T(0);
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-            const T v = S[e];
+            const T v = S[(e / N) * ld + e % N];
             if (e / N == e % N) dg += v * v; else off += v * v;
         }
         const double offs = block_sum(off, scratch);
@@ -505,9 +507,9 @@ __device__ void jacobi_eig_t(int N, T* S, T* U, double tol, int max_sweeps) {
                 if (p > q) { const int tmp = p; p = q; q = tmp; }
                 T c = T(1), sn = T(0);
                 if (q < N) {
-                    const T apq = S[p * N + q];
+                    const T apq = S[p * ld + q];
                     if (fabs(apq) > tiny) {
-                        const T th = (S[q * N + q] - S[p * N + p]) / (T(2) * apq);
+                        const T th = (S[q * ld + q] - S[p * ld + p]) / (T(2) * apq);
                         const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                         c = rsq(tt * tt + T(1));
                         sn = tt * c;
@@ -525,9 +527,9 @@ __device__ void jacobi_eig_t(int N, T* S, T* U, double tol, int max_sweeps) {
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
                 const T c = rc[t], sn = rs[t];
-                const T a = S[p * N + k], b = S[q * N + k];
-                S[p * N + k] = c * a - sn * b;
-                S[q * N + k] = sn * a + c * b;
+                const T a = S[p * ld + k], b = S[q * ld + k];
+                S[p * ld + k] = c * a - sn * b;
+                S[q * ld + k] = sn * a + c * b;
             }
             __syncthreads();
             for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // columns p, q
@@ -535,20 +537,20 @@ __device__ void jacobi_eig_t(int N, T* S, T* U, double tol, int max_sweeps) {
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
                 const T c = rc[t], sn = rs[t];
-                T a = S[k * N + p], b = S[k * N + q];
-                S[k * N + p] = c * a - sn * b;
-                S[k * N + q] = sn * a + c * b;
-                a = U[k * N + p];
-                b = U[k * N + q];
-                U[k * N + p] = c * a - sn * b;
-                U[k * N + q] = sn * a + c * b;
+                T a = S[k * ld + p], b = S[k * ld + q];
+                S[k * ld + p] = c * a - sn * b;
+                S[k * ld + q] = sn * a + c * b;
+                a = U[k * ld + p];
+                b = U[k * ld + q];
+                U[k * ld + p] = c * a - sn * b;
+                U[k * ld + q] = sn * a + c * b;
             }
             __syncthreads();
         }
     }
 }
 
-__device__ void jacobi_eig(int N, double* S, double* U) { jacobi_eig_t<double>(N, S, U, 1e-30, 40); }
+__device__ void jacobi_eig(int N, double* S, double* U) { jacobi_eig_t<double>(N, N, S, U, 1e-30, 40); }
 
 // Blocks of up to this many orbitals take the two-stage eigen-solver in the
 // mixed path (its four N x N work matrices fit in shared memory).
@@ -619,16 +621,20 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
         if (S_out) S_out[mo + e] = Ssh[e];
     }
     __syncthreads();
+    const int ldp = N + 1;   // padded row stride of the Jacobi matrices
+    double* Sd = Ssh;        // the diagonalised S (eigenvalues on its diagonal), row stride ldS
+    int ldS = N;
     if (two_stage) {
-        double* U64 = Ssh + N * N;   // shared: U, V (float64), S and U in float32
-        double* V64 = U64 + N * N;
-        float* S32 = reinterpret_cast<float*>(V64 + N * N);
-        float* U32 = S32 + N * N;
+        double* U64 = Ssh + N * N;   // shared: U (float64), V (float64, padded), then S and U
+        double* V64 = U64 + N * N;   // in float32 (padded), whose space later holds S (float64, padded)
+        double* Sp = V64 + N * ldp;
+        float* S32 = reinterpret_cast<float*>(Sp);
+        float* U32 = S32 + N * ldp;
         double* Y = w.tmp + w.mat_elems + mo;
-        for (int e = threadIdx.x; e < N * N; e += blockDim.x) S32[e] = d2f(Ssh[e]);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) S32[(e / N) * ldp + e % N] = d2f(Ssh[e]);
         __syncthreads();
-        jacobi_eig_t<float>(N, S32, U32, 1e-11, 12);
-        for (int e = threadIdx.x; e < N * N; e += blockDim.x) U64[e] = f2d(U32[e]);
+        jacobi_eig_t<float>(N, ldp, S32, U32, 1e-11, 12);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) U64[e] = f2d(U32[(e / N) * ldp + e % N]);
         __syncthreads();
         for (int it = 0; it < 2; ++it) {   // U <- U (3I - U^T U) / 2
             mm(N, U64, true, U64, false, X);
@@ -643,18 +649,26 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
         mm(N, U64, true, X, false, Y);      // Y = U^T S U
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // exact symmetry
             const int i = e / N, j = e % N;
-            Ssh[e] = (i == j) ? Y[e] : 0.5 * (Y[e] + Y[j * N + i]);
+            Sp[i * ldp + j] = (i == j) ? Y[e] : 0.5 * (Y[e] + Y[j * N + i]);
         }
         __syncthreads();
-        jacobi_eig_t<double>(N, Ssh, V64, 1e-30, 40);
-        mm(N, U64, false, V64, false, U);   // U = U V
+        jacobi_eig_t<double>(N, ldp, Sp, V64, 1e-30, 40);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // U = U V
+            const int i = e / N, j = e % N;
+            double sum = 0.0;
+            for (int k = 0; k < N; ++k) sum += U64[i * N + k] * V64[k * ldp + j];
+            U[e] = sum;
+        }
+        __syncthreads();
+        Sd = Sp;
+        ldS = ldp;
     } else {
         jacobi_eig(N, Ssh, U);
     }
     double* lam = w.lam + B.orb0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        lam[i] = Ssh[i * N + i];
-        il[i] = rsqrt(fmax(Ssh[i * N + i], 1e-300));
+        lam[i] = Sd[i * ldS + i];
+        il[i] = rsqrt(fmax(Sd[i * ldS + i], 1e-300));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -682,7 +696,8 @@ static bool lowdin_two_stage(const flosic_ctx* c) {
 
 size_t lowdin_smem(const flosic_ctx* c) {
     const size_t n2 = (size_t)max_block_n(c) * max_block_n(c);
-    return lowdin_two_stage(c) ? n2 * (3 * sizeof(double) + 2 * sizeof(float)) : n2 * sizeof(double);
+    const size_t np = (size_t)max_block_n(c) * (max_block_n(c) + 1);   // a padded matrix
+    return lowdin_two_stage(c) ? 2 * n2 * sizeof(double) + 2 * np * sizeof(double) : n2 * sizeof(double);
 }
 
 void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream_t s) {
