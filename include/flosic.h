@@ -278,11 +278,20 @@ int flosic_hamiltonian_apply(flosic_ctx* ctx, const double* psi, const double* v
  *   call; they are copied to the context's second input set on a separate
  *   stream while this step computes, and the next call that passes exactly
  *   these pointers uses them without copying again (the caller must not
- *   change their contents in between).
+ *   change their contents in between).  With them, the call also starts
+ *   the next step's FLO build and Poisson solve on `stream` once this
+ *   step's outputs are final, while those outputs travel to the host on a
+ *   second stream; the next call that passes exactly these pointers finds
+ *   that work done and only adds the energies and the adjoint (with its own
+ *   scale and gE).  Any other call on the context in between discards it
+ *   (the next step is then computed in full).  Work of the next step may
+ *   still be running on `stream` when this call returns.  A failure of the
+ *   started FLO build or solve is reported by the next call, which repeats
+ *   them; only a CUDA error is returned at once.
  * Host arrays should be page-locked (cudaHostAlloc / pinned) for the copies
- * to run asynchronously at full speed.  Waits for `stream`; the outputs are
- * in host memory on return.  Errors: as the four step calls; NOCONV is
- * returned after the outputs are copied. */
+ * to run asynchronously at full speed.  The outputs are in host memory on
+ * return.  Errors: as the four step calls; NOCONV is returned after the
+ * outputs are copied. */
 int flosic_step_host(flosic_ctx* ctx, const double* psi, const double* fods, double scale, double gE,
                      double* E_sic, double* U, double* Exc, double* V_avg, double* dE_dpsi,
                      double* dE_dfod, int* conv_flags, const double* psi_next,

@@ -37,8 +37,10 @@ cudaError_t alloc(flosic_ctx* c, T** p, long long n) {
 
 void release(flosic_ctx* c) {
     if (c->hs.copy) cudaStreamDestroy(c->hs.copy);
+    if (c->hs.copy_out) cudaStreamDestroy(c->hs.copy_out);
     for (cudaEvent_t e : c->hs.copied)
         if (e) cudaEventDestroy(e);
+    if (c->hs.done) cudaEventDestroy(c->hs.done);
     c->hs = flosic_ctx::HostStep{};
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     c->prof_ev.clear();
@@ -562,6 +564,7 @@ int flosic_layout(const flosic_ctx* c, int64_t* out) {
 int flosic_build_flos(flosic_ctx* c, const double* psi, const double* fods, double* phi, double* S,
                       double* S_mhalf, void* stream) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     if (!psi || !fods || !phi) return fail(c, FLOSIC_ERR_ARG, "psi, fods and phi are required");
     cudaStream_t s = (cudaStream_t)stream;
     c->have_forward = false;
@@ -584,6 +587,7 @@ int flosic_build_flos(flosic_ctx* c, const double* psi, const double* fods, doub
 int flosic_orbital_poisson(flosic_ctx* c, const double* phi, double* V, int warm_start, int* iters,
                            int* conv_flags, void* stream) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     if (!phi || !V) return fail(c, FLOSIC_ERR_ARG, "phi and V are required");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
@@ -606,6 +610,7 @@ int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* 
                                 double scale, double* U, double* Exc, double* E_sic, double* V_avg,
                                 void* stream) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     if (!psi || !phi || !V) return fail(c, FLOSIC_ERR_ARG, "psi, phi and V are required");
     if (!std::isfinite(scale)) return fail(c, FLOSIC_ERR_ARG, "scale must be finite");
     cudaStream_t s = (cudaStream_t)stream;
@@ -617,6 +622,7 @@ int flosic_sic_energy_potential(flosic_ctx* c, const double* psi, const double* 
 
 int flosic_set_orbital_mask(flosic_ctx* c, const int* mask) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     std::vector<int> m((size_t)c->norb, 1);
     int on = c->norb;
     if (mask) {
@@ -640,6 +646,7 @@ int flosic_set_orbital_mask(flosic_ctx* c, const int* mask) {
 int flosic_hamiltonian_apply(flosic_ctx* c, const double* psi, const double* vloc, const double* V_avg,
                              double* Hpsi, void* stream) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     if (!psi || !Hpsi) return fail(c, FLOSIC_ERR_ARG, "psi and Hpsi are required");
     if (Hpsi == psi) return fail(c, FLOSIC_ERR_ARG, "Hpsi must not overlap psi");
     launch_hamiltonian(c, psi, vloc, V_avg, Hpsi, (cudaStream_t)stream);
@@ -650,6 +657,7 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
                         const double* V, const double* gE, double* dE_dpsi, double* dE_dfod,
                         void* stream) {
     if (!c) return FLOSIC_ERR_ARG;
+    c->hs.fwd_valid = false;   // the workspace changes: a started next step is void
     if (!psi || !fods || !phi || !V || !gE) return fail(c, FLOSIC_ERR_ARG, "psi, fods, phi, V, gE are required");
     if (!c->have_forward) return fail(c, FLOSIC_ERR_ARG, "no forward step recorded on this context");
     cudaStream_t s = (cudaStream_t)stream;
@@ -695,17 +703,24 @@ int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, d
         A(&H.psi[0], orb); A(&H.psi[1], orb); A(&H.fods[0], nf); A(&H.fods[1], nf);
         A(&H.phi, orb); A(&H.V, orb); A(&H.Vavg, c->vavg_elems); A(&H.dpsi, orb); A(&H.dfod, nf);
         A(&H.E, (long long)c->sys.size()); A(&H.U, c->norb); A(&H.Exc, c->norb); A(&H.gE, (long long)c->sys.size());
-        A(&H.conv, c->norb);
+        A(&H.conv[0], c->norb); A(&H.conv[1], c->norb);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H.copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H.copy_out, cudaStreamNonBlocking);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&H.copied[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H.done, cudaEventDisableTiming);
         if (e != cudaSuccess) return check_cuda(c, e, "host-step buffers");
         H.ready = true;
     }
     const size_t bpsi = sizeof(double) * (size_t)orb, bfod = sizeof(double) * (size_t)nf;
     int rc;
-    // this step's inputs: already on the device when the previous call prefetched them
+    // this step's inputs: already on the device when the previous call prefetched
+    // them, and its FLO build and Poisson solve already done when that call
+    // started them (same host arrays, nothing else run on the context since)
     int cur;
-    if (H.pre >= 0 && H.pre_psi == psi_h && H.pre_fods == fods_h) {
+    const bool prefetched = H.pre >= 0 && H.pre_psi == psi_h && H.pre_fods == fods_h;
+    const bool have_fwd = prefetched && H.fwd_valid && H.fwd_psi == psi_h && H.fwd_fods == fods_h;
+    H.fwd_valid = false;
+    if (prefetched) {
         cur = H.pre;
         rc = check_cuda(c, cudaStreamWaitEvent(s, H.copied[cur], 0), "cudaStreamWaitEvent");
         if (rc) return rc;
@@ -717,8 +732,8 @@ int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, d
     }
     H.pre = -1;
     // the next step's inputs, copied on the copy stream while this step computes
+    const int nxt = 1 - cur;
     if (psi_next) {
-        const int nxt = 1 - cur;
         rc = check_cuda(c, cudaMemcpyAsync(H.psi[nxt], psi_next, bpsi, cudaMemcpyHostToDevice, H.copy), "prefetch psi");
         if (!rc)
             rc = check_cuda(c, cudaMemcpyAsync(H.fods[nxt], fods_next, bfod, cudaMemcpyHostToDevice, H.copy),
@@ -733,23 +748,53 @@ int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, d
     std::vector<double> g((size_t)nsys, gE);
     rc = check_cuda(c, cudaMemcpyAsync(H.gE, g.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s), "copy gE");
     if (rc) return rc;
-    rc = flosic_build_flos(c, H.psi[cur], H.fods[cur], H.phi, nullptr, nullptr, s);
-    if (rc) return rc;
-    rc = flosic_orbital_poisson(c, H.phi, H.V, 0, nullptr, H.conv, s);
-    if (rc && rc != FLOSIC_ERR_NOCONV) return rc;
-    const int prc = rc;
+    int prc, ci;
+    if (have_fwd) {
+        prc = H.fwd_rc;
+        ci = H.fwd_conv;
+    } else {
+        ci = 0;
+        rc = flosic_build_flos(c, H.psi[cur], H.fods[cur], H.phi, nullptr, nullptr, s);
+        if (rc) return rc;
+        rc = flosic_orbital_poisson(c, H.phi, H.V, 0, nullptr, H.conv[ci], s);
+        if (rc && rc != FLOSIC_ERR_NOCONV) return rc;
+        prc = rc;
+    }
     rc = flosic_sic_energy_potential(c, H.psi[cur], H.phi, H.V, scale, H.U, H.Exc, H.E, H.Vavg, s);
     if (rc) return rc;
     rc = flosic_sic_backward(c, H.psi[cur], H.fods[cur], H.phi, H.V, H.gE, dE_dpsi ? H.dpsi : nullptr,
                              dE_dfod ? H.dfod : nullptr, s);
     if (rc) return rc;
+    // the outputs go to the host on their own stream ...
+    rc = check_cuda(c, cudaEventRecord(H.done, s), "cudaEventRecord");
+    if (!rc) rc = check_cuda(c, cudaStreamWaitEvent(H.copy_out, H.done, 0), "cudaStreamWaitEvent");
+    if (rc) return rc;
     struct Out { void* h; const void* d; size_t n; };
     const Out outs[] = {{E_sic, H.E, sizeof(double) * nsys}, {U, H.U, sizeof(double) * c->norb},
                         {Exc, H.Exc, sizeof(double) * c->norb}, {V_avg, H.Vavg, sizeof(double) * c->vavg_elems},
-                        {dE_dfod, H.dfod, bfod}, {conv_flags, H.conv, sizeof(int) * c->norb}, {dE_dpsi, H.dpsi, bpsi}};
+                        {dE_dfod, H.dfod, bfod}, {conv_flags, H.conv[ci], sizeof(int) * c->norb},
+                        {dE_dpsi, H.dpsi, bpsi}};
     for (const Out& o : outs)
-        if (o.h && !rc) rc = check_cuda(c, cudaMemcpyAsync(o.h, o.d, o.n, cudaMemcpyDeviceToHost, s), "copy out");
-    if (!rc) rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        if (o.h && !rc) rc = check_cuda(c, cudaMemcpyAsync(o.h, o.d, o.n, cudaMemcpyDeviceToHost, H.copy_out), "copy out");
+    if (rc) return rc;
+    // ... while the compute stream starts the next step's FLO build and Poisson
+    // solve on its prefetched inputs (they read neither this step's outputs nor
+    // its input set, and write the other convergence-flag set)
+    if (psi_next) {
+        rc = check_cuda(c, cudaStreamWaitEvent(s, H.copied[nxt], 0), "cudaStreamWaitEvent");
+        if (rc) return rc;
+        int frc = flosic_build_flos(c, H.psi[nxt], H.fods[nxt], H.phi, nullptr, nullptr, s);
+        if (!frc) frc = flosic_orbital_poisson(c, H.phi, H.V, 0, nullptr, H.conv[1 - ci], s);
+        if (frc == FLOSIC_ERR_CUDA) return frc;
+        if (!frc || frc == FLOSIC_ERR_NOCONV) {   // otherwise the next call repeats it and reports
+            H.fwd_valid = true;
+            H.fwd_psi = psi_next;
+            H.fwd_fods = fods_next;
+            H.fwd_rc = frc;
+            H.fwd_conv = 1 - ci;
+        }
+    }
+    rc = check_cuda(c, cudaStreamSynchronize(H.copy_out), "cudaStreamSynchronize");
     return rc ? rc : prc;
 }
 

@@ -238,9 +238,18 @@ struct flosic_ctx {
         int pre = -1;
         double *phi = nullptr, *V = nullptr, *Vavg = nullptr, *dpsi = nullptr, *dfod = nullptr;
         double *E = nullptr, *U = nullptr, *Exc = nullptr, *gE = nullptr;
-        int* conv = nullptr;
+        int* conv[2] = {nullptr, nullptr};  // convergence flags of the step computed in set k
         cudaStream_t copy = nullptr;        // host -> device copies of the next step's inputs
+        cudaStream_t copy_out = nullptr;    // device -> host copies of a step's outputs
         cudaEvent_t copied[2] = {nullptr, nullptr};
+        cudaEvent_t done = nullptr;         // a step's outputs are final
+        // the next step's FLO build and Poisson solve, started by the previous
+        // call on its prefetched inputs (valid until another call uses the context)
+        bool fwd_valid = false;
+        const double* fwd_psi = nullptr;
+        const double* fwd_fods = nullptr;
+        int fwd_rc = 0;                     // the solve's return code (OK or NOCONV)
+        int fwd_conv = 0;                   // its flags' set
     } hs;
 };
 

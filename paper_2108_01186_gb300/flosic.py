@@ -237,7 +237,10 @@ class Context:
         """Calls flosic_step_host: one forward + adjoint step with every array in
         host memory (contiguous CPU tensors, float64 / int32 for conv; pinned
         for full-speed copies).  Outputs are filled in place; returns the
-        status (OK or NOCONV)."""
+        status (OK or NOCONV).  With psi_next/fods_next the library copies
+        them during this step and starts their FLO build and Poisson solve
+        while this step's outputs are copied out; the next call with exactly
+        those tensors picks that work up."""
         def host(t, n, dtype, name):
             if t is None:
                 return None

@@ -70,3 +70,42 @@ def test_host_step_prefetch_and_pageable_memory(F):
     assert ctx.step_host(psi.clone(), fods.clone(), psi_next=psi, fods_next=fods2, E_sic=pg["E_sic"]) == 0
     assert ctx.step_host(psi, fods, E_sic=pg["E_sic"]) == 0
     assert torch.equal(pg["E_sic"], ref1["E_sic"])
+
+
+def test_host_step_pipelined_next_step_equals_the_device_calls(F):
+    """With psi_next/fods_next the call starts the next step's FLO build and
+    Poisson solve; the next call (its own scale and gE) must return exactly
+    what the device calls return, over a chain of calls."""
+    s = synth.make_system(24, 0.4, 2, [3, 2], seed=8)
+    ctx = F.Context([s], precision=F.MIXED, cg_tol=1e-10, solver=F.SOLVER_KRON)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
+    fods = [torch.tensor(np.concatenate([f.ravel() for f in s.fods])).pin_memory()]
+    fods += [(fods[0] + 0.01 * k).pin_memory() for k in (1, 2, 3)]
+    params = [(1.0, 1.0), (0.5, 2.0), (0.75, -1.5), (1.0, 0.25)]
+    outs = [_host(ctx) for _ in fods]
+    for k in range(len(fods)):
+        nxt = dict(psi_next=psi, fods_next=fods[k + 1]) if k + 1 < len(fods) else {}
+        rc = ctx.step_host(psi, fods[k], params[k][0], params[k][1], **outs[k], **nxt)
+        assert rc == F.FLOSIC_OK
+    for k in range(len(fods)):
+        ref = _device_step(ctx, psi, fods[k], *params[k])
+        for name, v in ref.items():
+            assert torch.equal(outs[k][name], v.to(outs[k][name].dtype)), (k, name)
+
+
+def test_host_step_started_next_step_is_dropped_by_other_calls(F):
+    """A device-pointer call between two host steps changes the workspace:
+    the started next step must not be used (the next call recomputes)."""
+    s = synth.make_system(24, 0.4, 2, [3, 2], seed=8)
+    ctx = F.Context([s], precision=F.MIXED, cg_tol=1e-10, solver=F.SOLVER_KRON)
+    psi = torch.tensor(np.concatenate([p.ravel() for p in s.psi])).pin_memory()
+    fods = torch.tensor(np.concatenate([f.ravel() for f in s.fods])).pin_memory()
+    fods2 = (fods + 0.02).pin_memory()
+    a, b = _host(ctx), _host(ctx)
+    assert ctx.step_host(psi, fods, **a, psi_next=psi, fods_next=fods2) == F.FLOSIC_OK
+    # another system state through the device calls (moved FODs)
+    ctx.forward(psi.cuda(), (fods - 0.03).cuda())
+    assert ctx.step_host(psi, fods2, **b) == F.FLOSIC_OK
+    ref = _device_step(ctx, psi, fods2, 1.0, 1.0)
+    for name, v in ref.items():
+        assert torch.equal(b[name], v.to(b[name].dtype)), name
