@@ -474,41 +474,62 @@ __device__ void mm(int N, const double* A, bool ta, const double* Bm, bool tb, d
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
-template <class T>
+template <class T, bool kFloatAngle = false>
 __device__ void jacobi_eig_t(int N, int ld, T* S, T* U, double tol, int max_sweeps) {
     __shared__ int rp[kMaxN / 2], rq[kMaxN / 2];
     __shared__ T rc[kMaxN / 2], rs[kMaxN / 2];
     __shared__ double scratch[32];
     const T tiny = sizeof(T) == 4 ? T(1e-30) : T(1e-300);
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) U[(e / N) * ld + e % N] = (e / N == e % N) ? T(1) : T(0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < N; i += nw)
+        for (int k = lane; k < N; k += 32) U[i * ld + k] = (i == k) ? T(1) : T(0);
     __syncthreads();
     const int N2 = N + (N & 1);
     const int m = N2 - 1;
+    const int np = N2 / 2;
     for (int sweep = 0; sweep < max_sweeps && N > 1; ++sweep) {
         T off = T(0), dg = T(0);
-        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-            const T v = S[(e / N) * ld + e % N];
-            if (e / N == e % N) dg += v * v; else off += v * v;
-        }
+        for (int i = warp; i < N; i += nw)
+            for (int k = lane; k < N; k += 32) {
+                const T v = S[i * ld + k];
+                if (i == k) dg += v * v; else off += v * v;
+            }
         const double offs = block_sum(off, scratch);
         const double dgs = block_sum(dg, scratch);
         if (offs <= tol * dgs) break;
         for (int round = 0; round < m; ++round) {
-            if (threadIdx.x < N2 / 2) {
+            if (threadIdx.x < np) {
                 const int t = threadIdx.x;
-                int p, q;
+                int p, q;   // the round-robin pairing of round `round` (round + t < 2m, no division)
                 if (t == 0) {
                     p = 0;
-                    q = round % m + 1;
+                    q = round + 1;
                 } else {
-                    p = (round + t) % m + 1;
-                    q = (round - t + m) % m + 1;
+                    p = round + t;
+                    if (p >= m) p -= m;
+                    ++p;
+                    q = round - t + m;
+                    if (q >= m) q -= m;
+                    ++q;
                 }
                 if (p > q) { const int tmp = p; p = q; q = tmp; }
                 T c = T(1), sn = T(0);
                 if (q < N) {
                     const T apq = S[p * ld + q];
-                    if (fabs(apq) > tiny) {
+                    if constexpr (kFloatAngle) {
+                        // a nearly diagonal float64 matrix: the angle in float32 (relative error
+                        // ~1e-7 leaves ~1e-7 of S_pq, removed by the next sweep), c and s from it in
+                        // float64, so the rotation is orthogonal to float64 rounding
+                        const float apf = (float)apq, dqf = (float)(S[q * ld + q] - S[p * ld + p]);
+                        if (fabsf(apf) > 1e-30f) {
+                            const float th = dqf / (2.f * apf), at = fabsf(th);
+                            float tf = at > 1e15f ? 0.5f / at : 1.f / (at + sqrtf(th * th + 1.f));
+                            if (th < 0.f) tf = -tf;
+                            const T tt = (T)tf;
+                            c = rsq(tt * tt + T(1));
+                            sn = tt * c;
+                        }
+                    } else if (fabs(apq) > tiny) {
                         const T th = (S[q * ld + q] - S[p * ld + p]) / (T(2) * apq);
                         const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                         c = rsq(tt * tt + T(1));
@@ -521,29 +542,30 @@ __device__ void jacobi_eig_t(int N, int ld, T* S, T* U, double tol, int max_swee
                 rs[t] = (q < N) ? sn : T(0);
             }
             __syncthreads();
-            const int np = N2 / 2;
-            for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // rows p, q
-                const int t = e / N, k = e % N;
+            for (int t = warp; t < np; t += nw) {   // rows p, q
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
                 const T c = rc[t], sn = rs[t];
-                const T a = S[p * ld + k], b = S[q * ld + k];
-                S[p * ld + k] = c * a - sn * b;
-                S[q * ld + k] = sn * a + c * b;
+                for (int k = lane; k < N; k += 32) {
+                    const T a = S[p * ld + k], b = S[q * ld + k];
+                    S[p * ld + k] = c * a - sn * b;
+                    S[q * ld + k] = sn * a + c * b;
+                }
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < np * N; e += blockDim.x) {   // columns p, q
-                const int t = e / N, k = e % N;
+            for (int t = warp; t < np; t += nw) {   // columns p, q
                 const int p = rp[t], q = rq[t];
                 if (p == q) continue;
                 const T c = rc[t], sn = rs[t];
-                T a = S[k * ld + p], b = S[k * ld + q];
-                S[k * ld + p] = c * a - sn * b;
-                S[k * ld + q] = sn * a + c * b;
-                a = U[k * ld + p];
-                b = U[k * ld + q];
-                U[k * ld + p] = c * a - sn * b;
-                U[k * ld + q] = sn * a + c * b;
+                for (int k = lane; k < N; k += 32) {
+                    T a = S[k * ld + p], b = S[k * ld + q];
+                    S[k * ld + p] = c * a - sn * b;
+                    S[k * ld + q] = sn * a + c * b;
+                    a = U[k * ld + p];
+                    b = U[k * ld + q];
+                    U[k * ld + p] = c * a - sn * b;
+                    U[k * ld + q] = sn * a + c * b;
+                }
             }
             __syncthreads();
         }
@@ -652,7 +674,7 @@ __global__ void __launch_bounds__(512) k_lowdin(const BlkDesc* __restrict__ blk,
             Sp[i * ldp + j] = (i == j) ? Y[e] : 0.5 * (Y[e] + Y[j * N + i]);
         }
         __syncthreads();
-        jacobi_eig_t<double>(N, ldp, Sp, V64, 1e-30, 40);
+        jacobi_eig_t<double, true>(N, ldp, Sp, V64, 1e-30, 40);
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {   // U = U V
             const int i = e / N, j = e % N;
             double sum = 0.0;
