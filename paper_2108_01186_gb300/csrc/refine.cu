@@ -228,6 +228,26 @@ __device__ __forceinline__ ff ix_to_ff(long long I, float Lo) {
     return v;
 }
 
+// ix_split without the finiteness test, for sums taken in unsigned (wrapping)
+// integers: a non-finite y still carries inf / NaN in lo, and its saturated
+// integer part only wraps the integer sum, which lo then overrides.
+__device__ __forceinline__ IxPt ix_split_w(float d, float s) {
+    const float y = d * s;
+    const float r = rintf(y);
+    return {__float2int_rn(r), y - r};
+}
+
+// ix_to_ff for |I| < 2^53 from I + 2^53 (non-negative): the pieces of 23, 23
+// and 8 bits each exact as floats, the bias removed from the top piece.
+__device__ __forceinline__ ff ix_to_ff_b(long long I, float Lo) {
+    const unsigned long long M = (unsigned long long)I + (1ull << 53);
+    const float f0 = __uint_as_float(0x4B000000u | ((unsigned)M & 0x7fffffu)) - 8388608.f;
+    const float f1 = (__uint_as_float(0x4B000000u | ((unsigned)(M >> 23) & 0x7fffffu)) - 8388608.f) * 8388608.f;
+    const float f2 = (__uint_as_float(0x4B000000u | (unsigned)(M >> 46)) - 8388736.f) * 70368744177664.f;
+    const ff v = ff_two_sum(f2, f1);
+    return ff_two_sum(v.h, (v.l + f0) + Lo);
+}
+
 // Per orbital, max |d| over its grid (float bits in st.dmax, atomicMax on
 // the bit patterns of non-negative floats); the update's last CTA of the
 // orbital resets it.  NaN values are skipped here and reach the residual
@@ -482,86 +502,93 @@ __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restri
     const bool in = gx < D.nx && gy < D.ny;           // nx is a multiple of 4: gx + 1 < nx as well
     const long long sy = D.nx, sz = (long long)D.nx * D.ny;
     const long long col = gy * sy + gx;
-    IxPt q0[2 * kHalf + 1], q1[2 * kHalf + 1];        // z-windows of the two points
+    // z-windows of the two points as rings of 13 registers: plane z - 6 + j of
+    // step k sits in slot (k + j) mod 13, so nothing moves between planes (the
+    // z-loop is unrolled by 13 to make every slot index a constant)
+    constexpr int kQ = 2 * kHalf + 1;
+    IxPt q0[kQ], q1[kQ];
 #pragma unroll
     for (int j = 0; j < 2 * kHalf; ++j) {
         const int zz = P.z0 - kHalf + j;
         float2 v = make_float2(0.f, 0.f);
         if (in && zz >= 0 && zz < D.nz) v = *reinterpret_cast<const float2*>(d32 + P.base + zz * sz + col);
-        q0[j] = ix_split(v.x, sc);
-        q1[j] = ix_split(v.y, sc);
+        q0[j] = ix_split_w(v.x, sc);
+        q1[j] = ix_split_w(v.y, sc);
     }
     float rrf = 0.f;
     const int ly = ty + kHalf, cx = 2 * tx + 8;       // the points' row and first column in the staged plane
-    for (int k = 0; k < nzt; ++k) {
-        if (!tc_mbar_wait(bar + (k % kURing), (uint32_t)((k / kURing) & 1))) atomicOr(status + 3, 8);
-        const float* sg = ring + (size_t)(k % kURing) * kUStage;
-        IxPt* const sp = spb + (k & 1) * kUPlane;
-        for (int e = tid; e < kUPlane; e += 256) sp[e] = ix_split(sg[e], sc);
-        {
-            const float2 hv = *reinterpret_cast<const float2*>(sg + kUPlane + ty * kTileX + 2 * tx);
-            q0[2 * kHalf] = ix_split(hv.x, sc);
-            q1[2 * kHalf] = ix_split(hv.y, sc);
-        }
-        // the split plane is written, and every thread has finished plane k - 1: its
-        // stage takes plane k - 1 + kURing (the other split plane is free for plane k + 1)
-        __syncthreads();
-        if (tid == 0 && k >= 1 && k - 1 + kURing < nzt) {
-            tc_fence_proxy_async();
-            issue(k - 1 + kURing);
-        }
-        // x-window of row ly, columns cx - 6 .. cx + 7, as 7 pairs
-        IxPt xw[2 * kHalf + 2];
+    for (int k0 = 0; k0 < nzt; k0 += kQ) {
 #pragma unroll
-        for (int k2 = 0; k2 < kHalf + 1; ++k2) {
-            const int4 v = *reinterpret_cast<const int4*>(sp + ly * kUX + cx - kHalf + 2 * k2);
-            xw[2 * k2] = {v.x, __int_as_float(v.y)};
-            xw[2 * k2 + 1] = {v.z, __int_as_float(v.w)};
-        }
-        long long I0 = (long long)kW[0] * q0[kHalf].h, I1 = (long long)kW[0] * q1[kHalf].h;
-        float L0 = (float)kW[0] * q0[kHalf].l, L1 = (float)kW[0] * q1[kHalf].l;
-#pragma unroll
-        for (int m = 1; m <= kHalf; ++m) {
-            const int4 u = *reinterpret_cast<const int4*>(sp + (ly - m) * kUX + cx);   // rows ly -+ m, both columns
-            const int4 w = *reinterpret_cast<const int4*>(sp + (ly + m) * kUX + cx);
-            const int h0 = ((xw[kHalf - m].h + xw[kHalf + m].h) + (u.x + w.x)) + (q0[kHalf - m].h + q0[kHalf + m].h);
-            const int h1 = ((xw[kHalf + 1 - m].h + xw[kHalf + 1 + m].h) + (u.z + w.z)) +
-                           (q1[kHalf - m].h + q1[kHalf + m].h);
-            const float l0 = ((xw[kHalf - m].l + xw[kHalf + m].l) + (__int_as_float(u.y) + __int_as_float(w.y))) +
-                             (q0[kHalf - m].l + q0[kHalf + m].l);
-            const float l1 = ((xw[kHalf + 1 - m].l + xw[kHalf + 1 + m].l) +
-                              (__int_as_float(u.w) + __int_as_float(w.w))) +
-                             (q1[kHalf - m].l + q1[kHalf + m].l);
-            I0 += (long long)kW[m] * h0;
-            I1 += (long long)kW[m] * h1;
-            L0 = fmaf((float)kW[m], l0, L0);
-            L1 = fmaf((float)kW[m], l1, L1);
-        }
-        if (in) {
-            const float4 rv = *reinterpret_cast<const float4*>(sg + kUPlane + kUCtr + ty * 2 * kTileX + 4 * tx);
-            const float4 xv = *reinterpret_cast<const float4*>(sg + kUPlane + 3 * kUCtr + ty * 2 * kTileX + 4 * tx);
-            const long long g = P.base + (P.z0 + k) * sz + col;
-            ff rn[2], xn[2];
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const long long I = a == 0 ? I0 : I1;
-                const float Lo = a == 0 ? L0 : L1;
-                const IxPt qc = a == 0 ? q0[kHalf] : q1[kHalf];
-                const ff ad = ff_mul(ix_to_ff(I, Lo), cf);
-                rn[a] = ff_add(a == 0 ? ff{rv.x, rv.y} : ff{rv.z, rv.w}, ad);
-                const float dc = (__int2float_rn(qc.h) + qc.l) * is;
-                const ff xs = ff_two_sum(a == 0 ? xv.x : xv.z, dc);
-                xn[a] = ff_quick(xs.h, xs.l + (a == 0 ? xv.y : xv.w));
-                rrf += rn[a].h * rn[a].h;
+        for (int u = 0; u < kQ; ++u) {
+            const int k = k0 + u;
+            if (k >= nzt) break;
+            if (!tc_mbar_wait(bar + (k % kURing), (uint32_t)((k / kURing) & 1))) atomicOr(status + 3, 8);
+            const float* sg = ring + (size_t)(k % kURing) * kUStage;
+            IxPt* const sp = spb + (k & 1) * kUPlane;
+            for (int e = tid; e < kUPlane; e += 256) sp[e] = ix_split_w(sg[e], sc);
+            {
+                const float2 hv = *reinterpret_cast<const float2*>(sg + kUPlane + ty * kTileX + 2 * tx);
+                q0[(u + 2 * kHalf) % kQ] = ix_split_w(hv.x, sc);
+                q1[(u + 2 * kHalf) % kQ] = ix_split_w(hv.y, sc);
             }
-            *reinterpret_cast<float4*>(r + g) = make_float4(rn[0].h, rn[0].l, rn[1].h, rn[1].l);
-            *reinterpret_cast<float4*>(x + g) = make_float4(xn[0].h, xn[0].l, xn[1].h, xn[1].l);
-            *reinterpret_cast<float2*>(r32 + g) = make_float2(rn[0].h, rn[1].h);
-        }
+            // the split plane is written, and every thread has finished plane k - 1: its
+            // stage takes plane k - 1 + kURing (the other split plane is free for plane k + 1)
+            __syncthreads();
+            if (tid == 0 && k >= 1 && k - 1 + kURing < nzt) {
+                tc_fence_proxy_async();
+                issue(k - 1 + kURing);
+            }
+            // x-window of row ly, columns cx - 6 .. cx + 7, as 7 pairs
+            IxPt xw[2 * kHalf + 2];
 #pragma unroll
-        for (int j = 0; j < 2 * kHalf; ++j) {
-            q0[j] = q0[j + 1];
-            q1[j] = q1[j + 1];
+            for (int k2 = 0; k2 < kHalf + 1; ++k2) {
+                const int4 v = *reinterpret_cast<const int4*>(sp + ly * kUX + cx - kHalf + 2 * k2);
+                xw[2 * k2] = {v.x, __int_as_float(v.y)};
+                xw[2 * k2 + 1] = {v.z, __int_as_float(v.w)};
+            }
+            const IxPt c0 = q0[(u + kHalf) % kQ], c1 = q1[(u + kHalf) % kQ];
+            long long I0 = (long long)kW[0] * c0.h, I1 = (long long)kW[0] * c1.h;
+            float L0 = (float)kW[0] * c0.l, L1 = (float)kW[0] * c1.l;
+#pragma unroll
+            for (int m = 1; m <= kHalf; ++m) {
+                const int4 uu = *reinterpret_cast<const int4*>(sp + (ly - m) * kUX + cx);   // rows ly -+ m
+                const int4 ww = *reinterpret_cast<const int4*>(sp + (ly + m) * kUX + cx);
+                const IxPt a0 = q0[(u + kHalf - m) % kQ], b0 = q0[(u + kHalf + m) % kQ];
+                const IxPt a1 = q1[(u + kHalf - m) % kQ], b1 = q1[(u + kHalf + m) % kQ];
+                const unsigned h0 = (((unsigned)xw[kHalf - m].h + (unsigned)xw[kHalf + m].h) +
+                                     ((unsigned)uu.x + (unsigned)ww.x)) + ((unsigned)a0.h + (unsigned)b0.h);
+                const unsigned h1 = (((unsigned)xw[kHalf + 1 - m].h + (unsigned)xw[kHalf + 1 + m].h) +
+                                     ((unsigned)uu.z + (unsigned)ww.z)) + ((unsigned)a1.h + (unsigned)b1.h);
+                const float l0 = ((xw[kHalf - m].l + xw[kHalf + m].l) +
+                                  (__int_as_float(uu.y) + __int_as_float(ww.y))) + (a0.l + b0.l);
+                const float l1 = ((xw[kHalf + 1 - m].l + xw[kHalf + 1 + m].l) +
+                                  (__int_as_float(uu.w) + __int_as_float(ww.w))) + (a1.l + b1.l);
+                I0 += (long long)kW[m] * (int)h0;
+                I1 += (long long)kW[m] * (int)h1;
+                L0 = fmaf((float)kW[m], l0, L0);
+                L1 = fmaf((float)kW[m], l1, L1);
+            }
+            if (in) {
+                const float4 rv = *reinterpret_cast<const float4*>(sg + kUPlane + kUCtr + ty * 2 * kTileX + 4 * tx);
+                const float4 xv = *reinterpret_cast<const float4*>(sg + kUPlane + 3 * kUCtr + ty * 2 * kTileX + 4 * tx);
+                const long long g = P.base + (P.z0 + k) * sz + col;
+                ff rn[2], xn[2];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const long long I = a == 0 ? I0 : I1;
+                    const float Lo = a == 0 ? L0 : L1;
+                    const IxPt qc = a == 0 ? c0 : c1;
+                    const ff ad = ff_mul(ix_to_ff_b(I, Lo), cf);
+                    rn[a] = ff_add(a == 0 ? ff{rv.x, rv.y} : ff{rv.z, rv.w}, ad);
+                    const float dc = (__int2float_rn(qc.h) + qc.l) * is;
+                    const ff xs = ff_two_sum(a == 0 ? xv.x : xv.z, dc);
+                    xn[a] = ff_quick(xs.h, xs.l + (a == 0 ? xv.y : xv.w));
+                    rrf += rn[a].h * rn[a].h;
+                }
+                *reinterpret_cast<float4*>(r + g) = make_float4(rn[0].h, rn[0].l, rn[1].h, rn[1].l);
+                *reinterpret_cast<float4*>(x + g) = make_float4(xn[0].h, xn[0].l, xn[1].h, xn[1].l);
+                *reinterpret_cast<float2*>(r32 + g) = make_float2(rn[0].h, rn[1].h);
+            }
         }
     }
     if (tile_arrive(rrf, st.part, blockIdx.x, st.count + P.o, D.ntile, scratch)) {
