@@ -503,6 +503,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&g.dmax, orb);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
     if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) e = setup_kron(c);   // sets the blocks' kq, kl
+    for (BlkDesc& B : c->blk) B.gtma = (o.precision == FLOSIC_MIXED && gram_async_eligible(B)) ? 1 : 0;
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_orb_blk, c->h_orb_blk.data(), sizeof(int) * c->norb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_chunk_orb, chunk_orb.data(), sizeof(int) * chunk, cudaMemcpyHostToDevice);

@@ -42,6 +42,20 @@ constexpr int kGSmem = kGStages * 3 * kGTile + 1024;   // + 1024-byte alignment 
 __constant__ int c_pair_a[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int c_pair_b[6] = {0, 1, 0, 2, 0, 1};
 
+// Three bf16 terms of a pair of floats (f0, f1), each packed as bf16x2 (f0 in
+// the low half): v = v1 + v2 + v3 with v1 = bf16(v), v2 = bf16(v - v1),
+// v3 = bf16(v - v1 - v2) (the differences are exact in float32).
+__device__ __forceinline__ void gram_split2(float f0, float f1, uint32_t& w1, uint32_t& w2, uint32_t& w3) {
+    const __nv_bfloat162 b1 = __floats2bfloat162_rn(f0, f1);
+    w1 = *reinterpret_cast<const uint32_t*>(&b1);
+    const float r0 = f0 - __uint_as_float(w1 << 16), r1 = f1 - __uint_as_float(w1 & 0xffff0000u);
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0, r1);
+    w2 = *reinterpret_cast<const uint32_t*>(&b2);
+    const float q0 = r0 - __uint_as_float(w2 << 16), q1 = r1 - __uint_as_float(w2 & 0xffff0000u);
+    const __nv_bfloat162 b3 = __floats2bfloat162_rn(q0, q1);
+    w3 = *reinterpret_cast<const uint32_t*>(&b3);
+}
+
 // Reads 32 columns of this warp's 32 TMEM lanes and adds them to acc.
 __device__ __forceinline__ void tmem_add32(uint32_t taddr, float* acc) {
     float v[32];
@@ -74,6 +88,7 @@ __global__ void __launch_bounds__(256, NB <= 2 ? 2 : 1) k_gram_tc(const BlkDesc*
     constexpr int kSub = kGChunk / P;                // points per sub-chunk
     constexpr uint32_t kCols = (2 * MN <= 128) ? 128 : 256;
     const BlkDesc& B = blk[blockIdx.y];
+    if (B.gtma) return;                              // k_gram_tma's block
     const int N = B.N;
     const long long g_begin = (long long)blockIdx.x * kGChunk;
     if (g_begin >= B.G) return;                      // whole CTA
@@ -198,6 +213,163 @@ __global__ void __launch_bounds__(256, NB <= 2 ? 2 : 1) k_gram_tc(const BlkDesc*
     }
 }
 
+// The same sums with the float64 psi tiles brought to shared memory by
+// asynchronous copies (cp.async, 16 bytes each; blocks whose G and offset are
+// even, so every piece is 16-byte aligned): a ring of kGRing stages, the copies
+// of stage st + 1 in flight while stage st is converted and multiplied, rows
+// past N and points past G zero-filled by the copy.  The warps convert rows
+// from shared memory (lane l: points 2l, 2l + 1 of one row) into the same
+// K-major swizzled bf16 tiles, so no thread waits on a global load.  MMAs,
+// read-back and partials as in k_gram_tc.
+constexpr int kGRing = 2;
+constexpr int kGStage = kGRows * kGK * 8;                    // float64 rows of a stage: 64 KB
+constexpr int kGAsyncSmem = kGRing * kGStage + kGStages * 3 * kGTile + 1024;
+
+__device__ __forceinline__ void gram_cp16(void* dst, const void* src, int bytes) {   // bytes 0 or 16
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc_smem_addr(dst)), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void gram_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void gram_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+template <int NB>
+__global__ void __launch_bounds__(256, 1) k_gram_async(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
+                                                       float* __restrict__ part,
+                                                       const long long* __restrict__ part_off,
+                                                       int* __restrict__ status) {
+    extern __shared__ unsigned char g_smem_raw[];
+    __shared__ uint64_t mbar[kGStages];
+    __shared__ uint32_t tmem_base;
+    constexpr int NN = 32 * NB;
+    constexpr int P = gram_pack<NB>();
+    constexpr int MN = P * NN;
+    constexpr int kSub = kGChunk / P;
+    constexpr uint32_t kCols = (2 * MN <= 128) ? 128 : 256;
+    constexpr int kRows = P * NN;                    // rows (q, a) of a stage
+    const BlkDesc& B = blk[blockIdx.y];
+    if (!B.gtma) return;                             // k_gram_tc's block
+    const int N = B.N;
+    const long long g_begin = (long long)blockIdx.x * kGChunk;
+    if (g_begin >= B.G) return;
+    const int nst = kSub / kGK;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* tiles = base;                                  // kGStages x 3 bf16 tiles
+    double* ring = reinterpret_cast<double*>(base + kGStages * 3 * kGTile);
+    const double* pb = psi + B.off;
+    // stage st: 16-byte piece c (points 2c, 2c + 1) of row (q, a) = tid / 32 + 8 i, c = lane
+    auto issue = [&](int st) {
+        double* dst = ring + (size_t)(st % kGRing) * kRows * kGK;
+#pragma unroll 4
+        for (int row = warp; row < kRows; row += 8) {
+            const int q = row / NN, a = row - q * NN;
+            const long long g = g_begin + (long long)q * kSub + (long long)st * kGK + 2 * lane;
+            const bool in = a < N && g < B.G;   // G even: the pair g, g + 1 is inside or outside together
+            gram_cp16(dst + (size_t)row * kGK + 2 * lane, in ? pb + (long long)a * B.G + g : pb, in ? 16 : 0);
+        }
+    };
+    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 256)   // padding rows stay zero
+        reinterpret_cast<uint4*>(tiles)[i] = make_uint4(0u, 0u, 0u, 0u);
+    issue(0);
+    gram_cp_commit();
+    if (tid == 0) {
+        for (int k = 0; k < kGStages; ++k) tc_mbar_init(&mbar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const bool reader = warp < 4 && 32 * warp < P * NN;
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int q_own = (32 * (warp & 3)) / NN;
+    const uint32_t col0 = (uint32_t)(q_own * NN);
+    const uint32_t idesc = umma_idesc_bf16(kGRows, MN);
+    bool ok = true;
+    float acc[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[j] = 0.f;
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        unsigned char* tile = tiles + buf * 3 * kGTile;
+        // the next stage's copies go into the slot of stage st - 1 (converted in the last iteration)
+        if (st + 1 < nst) issue(st + 1);
+        gram_cp_commit();
+        gram_cp_wait<1>();   // this thread's copies of stage st have landed
+        __syncthreads();     // everyone's
+        const double* rows = ring + (size_t)(st % kGRing) * kRows * kGK;
+        // warp w converts rows w, w + 8, ...: lane l takes points 2l, 2l + 1
+        // (one 16-byte shared load), writes their three bf16 pairs (4 bytes each)
+        // at K = 2l in the swizzled row (16-byte chunk l / 4, word l mod 4)
+#pragma unroll 4
+        for (int row = warp; row < kRows; row += 8) {
+            const double2 v = *reinterpret_cast<const double2*>(rows + (size_t)row * kGK + 2 * lane);
+            uint32_t w1, w2, w3;
+            gram_split2(d2f(v.x), d2f(v.y), w1, w2, w3);
+            const int off = row * 128 + (((lane >> 2) ^ (row & 7)) << 4) + ((lane & 3) << 2);
+            *reinterpret_cast<uint32_t*>(tile + off) = w1;
+            *reinterpret_cast<uint32_t*>(tile + kGTile + off) = w2;
+            *reinterpret_cast<uint32_t*>(tile + 2 * kGTile + off) = w3;
+        }
+        if (st >= 1) {   // the previous stage's hi x hi sums (read before this stage's MMAs restart them)
+            const int pb2 = (st - 1) & 1;
+            ok = tc_mbar_wait(&mbar[pb2], (uint32_t)(((st - 1) >> 1) & 1)) && ok;
+            ok = __all_sync(0xffffffffu, ok);
+            tc_fence_after();
+            if (ok && reader) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
+            }
+        }
+        tc_fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();   // the bf16 tiles are written; ring slot st mod kGRing is free
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t s0 = tc_smem_addr(tile);
+            const uint32_t dhi = tmem, dx = tmem + (uint32_t)MN;
+#pragma unroll
+            for (int kk = 0; kk < kGK / 16; ++kk) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint64_t da = umma_desc_sw128(s0 + c_pair_a[p] * kGTile + kk * 32);
+                    const uint64_t db = umma_desc_sw128(s0 + c_pair_b[p] * kGTile + kk * 32);
+                    if (p == 0) umma_bf16(dhi, da, db, idesc, kk != 0);
+                    else umma_bf16(dx, da, db, idesc, (st | kk | (p - 1)) != 0);
+                }
+            }
+            umma_commit(&mbar[buf]);
+        }
+    }
+    gram_cp_wait<0>();
+    ok = tc_mbar_wait(&mbar[(nst - 1) & 1], (uint32_t)(((nst - 1) >> 1) & 1)) && ok;
+    ok = __all_sync(0xffffffffu, ok);
+    tc_fence_after();
+    if (ok && reader) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)MN + col0 + 32 * c, acc + 32 * c);
+        const int a = warp * 32 + lane - q_own * NN;
+        float* out = part + part_off[blockIdx.y] + ((long long)blockIdx.x * P + q_own) * N * N;
+        if (a < N) {
+#pragma unroll
+            for (int j = 0; j < NN; ++j)
+                if (j < N) out[(long long)a * N + j] = acc[j];
+        }
+    } else if (!ok && tid == 0) {
+        atomicOr(status + 3, 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
 // M[block][e] = sum over the block's partials (pk per chunk, pk = the
 // launch's sub-chunk count, set by its widest block) in float64: a CTA takes
 // 32 elements; its 8 warps sum every 8th partial each, and the 8 sums are
@@ -250,8 +422,15 @@ cudaError_t setup_gram_tc() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)k_gram_async<1>, kGAsyncSmem);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)k_gram_async<2>, kGAsyncSmem);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)k_gram_async<3>, kGAsyncSmem);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)k_gram_async<4>, kGAsyncSmem);
     return e;
 }
+
+// blocks whose psi rows the asynchronous-copy kernel can take (16-byte pieces)
+bool gram_async_eligible(const BlkDesc& B) { return B.G % 2 == 0 && B.off % 2 == 0; }
 
 void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
     long long gmax = 0;
@@ -274,11 +453,22 @@ void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
         cudaEventRecord(cm->ov_ev[2 * cm->ov_used], s);
         for (const auto& b : c->blk) cm->ov_flops += 2.0 * b.N * b.N * (double)b.G;
     }
-    if (nb <= 1) k_gram_tc<1><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else if (nb == 2) k_gram_tc<2><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else if (nb == 3) k_gram_tc<3><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    else k_gram_tc<4><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-    note_launch(cm);
+    int n_async = 0;
+    for (const auto& b : c->blk) n_async += b.gtma;
+    if (n_async > 0) {   // blocks with 16-byte aligned rows: copies staged asynchronously
+        if (nb <= 1) k_gram_async<1><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 2) k_gram_async<2><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 3) k_gram_async<3><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else k_gram_async<4><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        note_launch(cm);
+    }
+    if (n_async < c->nblk) {   // the others: thread loads
+        if (nb <= 1) k_gram_tc<1><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 2) k_gram_tc<2><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 3) k_gram_tc<3><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else k_gram_tc<4><<<grid, 256, kGSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        note_launch(cm);
+    }
     if (timed) {
         cudaEventRecord(cm->ov_ev[2 * cm->ov_used + 1], s);
         ++cm->ov_used;

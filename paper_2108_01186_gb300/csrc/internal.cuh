@@ -41,6 +41,7 @@ struct BlkDesc {
     long long kl[3];            // and of the eigenvalues of T_d
     long long kt[3];            // tensor-core transforms: offsets of the split bf16 matrices
     int tc;                     // 1: this block's transforms run on the tensor cores
+    int gtma;                   // 1: the overlap Gram's psi tiles are staged by the copy engine
 };
 
 // periodic-direction mask of a boundary mode
@@ -306,6 +307,7 @@ int aar_max_m();
 // tensor-core overlap Gram (mixed precision)
 long long gram_tc_part_elems(const flosic_ctx* c, std::vector<long long>& off);
 cudaError_t setup_gram_tc();
+bool gram_async_eligible(const BlkDesc& B);   // the overlap Gram's asynchronous-copy kernel takes B
 void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s);
 // SC_AvgSIC Hamiltonian apply: H psi = -1/2 Delta_h psi + (v_loc + V_avg) psi
 void launch_hamiltonian(const flosic_ctx* c, const double* psi, const double* vloc, const double* vavg,
