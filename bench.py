@@ -314,6 +314,14 @@ def run_gpu(args):
     solver = {"pcg": 0, "aar": 1, "kron": 2}[args.solver]
     ctx = Context([s], precision=prec, cg_tol=CG_TOL, preconditioner=pc, solver=solver,
                   kron_tensor_cores=0 if args.no_tensor_core_transforms else 1)
+    paths = ctx.block_paths()
+    if args.no_tensor_core_transforms:
+        transforms_desc = "cuda cores"
+    else:   # the autotuner's pick per block shape (tensor cores or CUDA cores, timed at context creation)
+        ntc = sum(p["tensor_core_transforms"] for p in paths)
+        transforms_desc = ("tensor cores (autotuned)" if ntc == len(paths) else
+                           "cuda cores (autotuned)" if ntc == 0 else "mixed (autotuned, %d of %d blocks on tensor cores)"
+                           % (ntc, len(paths)))
     shard_step = D.OrbitalShardedStep(ctx) if sharded else None
     units = world * norb if not sharded else norb   # orbitals the whole job processes per step
     dev = torch.device("cuda", local)
@@ -598,7 +606,7 @@ def run_gpu(args):
                            "solver": args.solver,
                            "parallelism": ("orbitals of one system over %d ranks" % world if sharded
                                            else "one system per rank"),
-                           "transforms": ("cuda cores" if args.no_tensor_core_transforms else "tensor cores"),
+                           "transforms": transforms_desc,
                            "cg_tol": CG_TOL,
                            "l2": "inputs larger than L2 (psi %.2f GB per rank)" % (8e-9 * norb * s.G),
                            "cg_iters_per_orbital_mean": float(np.mean(iters_sum) / args.steps)},

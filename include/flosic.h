@@ -128,6 +128,14 @@ typedef struct {
                              8 and at most 128 on the tensor cores (split
                              bf16, float32 accumulation); 0 keeps them all on
                              the CUDA cores (float32) */
+    int autotune;         /* KRON solver with kron_tensor_cores 1: 1 (default)
+                             times, at context creation, one inner solve of
+                             each distinct block shape (nx, ny, nz, N) that
+                             qualifies for the tensor cores with the tensor-
+                             core and with the CUDA-core transforms, and keeps
+                             the faster per shape (flosic_block_paths reports
+                             the choice); 0 takes the tensor cores wherever
+                             they qualify */
 } flosic_options;
 
 typedef struct flosic_ctx flosic_ctx;
@@ -135,7 +143,7 @@ typedef struct flosic_ctx flosic_ctx;
 /* Fills *opt with the defaults: MIXED, cg_tol 1e-10, max_iter 20000,
  * GRAD_INTERP, ADJ_REUSE_V, rho_min 1e-30, illcond_tol 1e-10, PC_MG,
  * SOLVER_PCG (AAR parameters 0.6, 0.6, 7, 6), BC_ISOLATED,
- * kron_tensor_cores 1.  The KRON solver
+ * kron_tensor_cores 1, autotune 1.  The KRON solver
  * requires MIXED and every side <= 256.
  * Returns FLOSIC_ERR_ARG if opt is NULL. */
 int flosic_default_options(flosic_options* opt);
@@ -159,6 +167,14 @@ const char* flosic_last_error(const flosic_ctx* ctx);
  * blocks), [3] elements of the N x N matrix arrays (sum N*N), [4] spin
  * blocks, [5] systems. */
 int flosic_layout(const flosic_ctx* ctx, int64_t* out);
+
+/* The kernel paths of every spin block (host array out[blocks], blocks in
+ * the packed order), no counterpart in the paper: bit 0 = its Kronecker
+ * transforms run on the tensor cores (KRON solver; the autotuner's pick
+ * when autotune is 1), bit 1 = its refinement update is staged by the copy
+ * engine, bit 2 = its overlap Gram stages psi with asynchronous copies
+ * (MIXED).  Errors: ARG. */
+int flosic_block_paths(const flosic_ctx* ctx, int* out);
 
 /* Steps a1-a5 (Sec. II.B, Eqs. 6-8, Loewdin of Sec. I.B):
  *   psi_a(a_i), grad psi_a(a_i) by tricubic Lagrange interpolation,

@@ -68,6 +68,7 @@ int validate_options(const flosic_options& o, std::string& why) {
     else if (o.boundary != FLOSIC_BC_ISOLATED && o.boundary != FLOSIC_BC_PERIODIC && o.boundary != FLOSIC_BC_SLAB)
         why = "bad boundary";
     else if (o.kron_tensor_cores != 0 && o.kron_tensor_cores != 1) why = "kron_tensor_cores must be 0 or 1";
+    else if (o.autotune != 0 && o.autotune != 1) why = "autotune must be 0 or 1";
     else if (o.boundary != FLOSIC_BC_ISOLATED &&
              (o.solver != FLOSIC_SOLVER_KRON || o.adjoint_mode != FLOSIC_ADJ_REUSE_V ||
               o.fod_grad_mode != FLOSIC_GRAD_INTERP))
@@ -231,6 +232,7 @@ int flosic_default_options(flosic_options* opt) {
     opt->aar_p = 6;
     opt->boundary = FLOSIC_BC_ISOLATED;
     opt->kron_tensor_cores = 1;
+    opt->autotune = 1;
     return FLOSIC_OK;
 }
 
@@ -534,6 +536,8 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         c->n_utma_blocks = setup_update_maps(c);
         cudaGetLastError();   // as above: the update then runs with plain loads
     }
+    if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON && o.kron_tensor_cores && o.autotune)
+        e = kron_autotune(c);
     if (e != cudaSuccess) {
         g_create_error = std::string("workspace set-up: ") + cudaGetErrorString(e);
         release(c);
@@ -559,6 +563,17 @@ int flosic_layout(const flosic_ctx* c, int64_t* out) {
     out[3] = c->mat_elems;
     out[4] = c->nblk;
     out[5] = (int64_t)c->sys.size();
+    return FLOSIC_OK;
+}
+
+int flosic_block_paths(const flosic_ctx* c, int* out) {
+    if (!c || !out) return FLOSIC_ERR_ARG;
+    const std::vector<LvlDesc>& L0 = c->mg.h_lvl[0];
+    for (int b = 0; b < c->nblk; ++b) {
+        const BlkDesc& B = c->blk[b];
+        const bool kron = c->opt.solver == FLOSIC_SOLVER_KRON;
+        out[b] = (kron && B.tc ? 1 : 0) | (kron && (int)L0.size() > b && L0[b].utma ? 2 : 0) | (B.gtma ? 4 : 0);
+    }
     return FLOSIC_OK;
 }
 

@@ -179,6 +179,7 @@ struct KronPlan {
     int n_simt = 0, n_tc = 0;      // blocks on the CUDA-core and on the tensor-core transforms
     uint16_t* tc_mat = nullptr;    // per distinct operator of a tensor-core block: split bf16 matrices
     long long* tc_items = nullptr; // [6][nblk + 1] first tile of each block per pass (tensor-core kernel)
+    std::vector<int> tc_force;     // [nblk] host: 0 = CUDA-core transforms even if eligible (autotuner)
     void* tc_maps = nullptr;       // [6][nblk] CUtensorMap of each pass's input rows
     void* tc_omaps = nullptr;      // [6][nblk] CUtensorMap of each pass's output lines
     long long tc_total[6] = {0, 0, 0, 0, 0, 0};
@@ -291,6 +292,9 @@ cudaError_t setup_kron(flosic_ctx* c);
 void launch_kron_solve(flosic_ctx* c, const float* r, float* d, float* t1, float* t2, cudaStream_t s);
 // its transforms on the tensor cores (kron_tc.cu)
 bool kron_tc_eligible(const BlkDesc& B);
+// times the tensor-core and CUDA-core transforms per distinct eligible block
+// shape and re-plans the solver with the faster per shape (kron.cu)
+cudaError_t kron_autotune(flosic_ctx* c);
 void kron_tc_pack(int n, const std::vector<double>& Vs, const std::vector<double>& Va, std::vector<uint16_t>& out);
 size_t kron_tc_smem();
 const void* kron_tc_symbol();

@@ -25,6 +25,7 @@
 // residual around it carries the accuracy to the requested tolerance.
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -526,7 +527,9 @@ cudaError_t setup_kron(flosic_ctx* c) {
     KronPlan& K = c->kron;
     K.n_simt = K.n_tc = 0;
     for (BlkDesc& B : c->blk) {
-        B.tc = (c->opt.kron_tensor_cores && kron_tc_eligible(B)) ? 1 : 0;
+        const int bi = (int)(&B - c->blk.data());
+        const bool forced_off = !K.tc_force.empty() && K.tc_force[bi] == 0;
+        B.tc = (c->opt.kron_tensor_cores && kron_tc_eligible(B) && !forced_off) ? 1 : 0;
         ++(B.tc ? K.n_tc : K.n_simt);
         const int nd[3] = {B.nx, B.ny, B.nz};
         for (int d = 0; d < 3; ++d) {
@@ -654,6 +657,93 @@ cudaError_t setup_kron(flosic_ctx* c) {
     }
     if (e == cudaSuccess && K.n_tc > 0) e = setup_kron_tc(c, tcmat, sms);
     return e;
+}
+
+// Autotuner of the transforms: per distinct shape (nx, ny, nz, N, periodic
+// sides) of the blocks that qualify for the tensor cores, one inner solve of
+// one block of that shape is timed (CUDA events, after a warm-up solve, three
+// solves averaged, zero input: the transforms' cost does not depend on the
+// values) with every qualifying block on the tensor cores and again with
+// every block on the CUDA cores; each shape keeps the faster, and the solver
+// is planned once more with those choices.  Runs once, at context creation.
+cudaError_t kron_autotune(flosic_ctx* c) {
+    KronPlan& K = c->kron;
+    std::map<std::array<long long, 5>, std::vector<int>> groups;
+    for (int b = 0; b < c->nblk; ++b) {
+        const BlkDesc& B = c->blk[b];
+        if (kron_tc_eligible(B)) groups[{B.nx, B.ny, B.nz, B.N, B.per}].push_back(b);
+    }
+    if (groups.empty()) return cudaSuccess;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int* dflags = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&dflags, sizeof(int) * (size_t)c->norb * groups.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws.r32, 0, sizeof(float) * (size_t)c->orb_elems, s);
+    // per group: only the first block's orbitals active
+    std::vector<int> hflags((size_t)c->norb * groups.size(), 0);
+    {
+        size_t gi = 0;
+        for (const auto& g : groups) {
+            const BlkDesc& B = c->blk[g.second[0]];
+            for (int o = 0; o < B.N; ++o) hflags[gi * c->norb + B.orb0 + o] = 1;
+            ++gi;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(dflags, hflags.data(), sizeof(int) * hflags.size(), cudaMemcpyHostToDevice);
+    std::vector<float> t_tc(groups.size(), 0.f), t_cc(groups.size(), 0.f);
+    auto plan = [&](int force) {   // force 1: every qualifying block on the tensor cores; 0: none
+        K.tc_force.assign((size_t)c->nblk, force);
+        cudaError_t r = setup_kron(c);
+        if (r == cudaSuccess)
+            r = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
+        return r;
+    };
+    auto time_groups = [&](std::vector<float>& t) {
+        cudaError_t r = cudaSuccess;
+        for (size_t gi = 0; gi < groups.size() && r == cudaSuccess; ++gi) {
+            for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
+                if (rep == 1) r = cudaEventRecord(e0, s);
+                if (r == cudaSuccess)
+                    r = cudaMemcpyAsync(c->ws.cg.active, dflags + gi * c->norb, sizeof(int) * c->norb,
+                                        cudaMemcpyDeviceToDevice, s);
+                if (r == cudaSuccess) launch_kron_solve(c, c->ws.r32, c->ws.d32, c->ws.p32, c->ws.q32, s);
+            }
+            if (r == cudaSuccess) r = cudaEventRecord(e1, s);
+            if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+            t[gi] = ms / 3.f;
+        }
+        return r;
+    };
+    if (e == cudaSuccess) e = plan(1);
+    if (e == cudaSuccess) e = time_groups(t_tc);
+    if (e == cudaSuccess) e = plan(0);
+    if (e == cudaSuccess) e = time_groups(t_cc);
+    // the choices, then the final plan
+    std::vector<int> force((size_t)c->nblk, 1);
+    {
+        size_t gi = 0;
+        for (const auto& g : groups) {
+            const int keep_tc = (e != cudaSuccess || t_tc[gi] <= t_cc[gi]) ? 1 : 0;
+            for (int b : g.second) force[(size_t)b] = keep_tc;
+            ++gi;
+        }
+    }
+    if (s) cudaStreamSynchronize(s);
+    cudaGetLastError();
+    K.tc_force = force;
+    cudaError_t f = setup_kron(c);
+    if (f == cudaSuccess) f = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
+    if (f == cudaSuccess) f = cudaMemset(c->ws.cg.dmax, 0, sizeof(unsigned) * c->norb);
+    if (dflags) cudaFree(dflags);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    return f;   // a failed timing keeps the tensor cores; only the final plan's failure is an error
 }
 
 // d = A^{-1} r for the active orbitals (float32); t1, t2 are scratch arrays

@@ -29,7 +29,7 @@ ABI_FUNCTIONS = ("flosic_default_options", "flosic_create", "flosic_destroy", "f
                  "flosic_sic_energy_potential", "flosic_sic_backward", "flosic_profile",
                  "flosic_profile_read", "flosic_orbital_poisson_noalloc", "flosic_noalloc_last_error",
                  "flosic_hamiltonian_apply", "flosic_profile_read_overlap", "flosic_set_orbital_mask",
-                 "flosic_step_host")
+                 "flosic_step_host", "flosic_block_paths")
 
 
 class FlosicError(RuntimeError):
@@ -51,7 +51,7 @@ class FlosicOptions(ctypes.Structure):
                 ("preconditioner", ctypes.c_int), ("solver", ctypes.c_int),
                 ("aar_omega", ctypes.c_double), ("aar_beta", ctypes.c_double),
                 ("aar_m", ctypes.c_int), ("aar_p", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("kron_tensor_cores", ctypes.c_int)]
+                ("kron_tensor_cores", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 _lib = None
@@ -78,6 +78,7 @@ def load_library(path=LIB_PATH):
     L.flosic_sic_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_hamiltonian_apply.argtypes = [vp, vp, vp, vp, vp, vp]
     L.flosic_set_orbital_mask.argtypes = [vp, vp]
+    L.flosic_block_paths.argtypes = [vp, vp]
     L.flosic_step_host.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.flosic_profile.argtypes = [vp, i]
     L.flosic_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i]
@@ -260,6 +261,15 @@ class Context:
         if rc not in (FLOSIC_OK, FLOSIC_ERR_NOCONV):
             self._check(rc)
         return rc
+
+    def block_paths(self):
+        """Calls flosic_block_paths: per spin block (packed order) a dict of the
+        kernel paths the context took (tensor-core transforms, copy-engine
+        refinement update, asynchronous-copy overlap Gram)."""
+        out = (ctypes.c_int * self.nblk)()
+        self._check(self._L.flosic_block_paths(self._h, ctypes.cast(out, ctypes.c_void_p)))
+        return [dict(tensor_core_transforms=bool(v & 1), tma_update=bool(v & 2), async_gram=bool(v & 4))
+                for v in out]
 
     @_on_device
     def set_orbital_mask(self, mask=None):

@@ -42,6 +42,7 @@ def test_default_options(lib):
     assert o.precision == F.MIXED and o.cg_tol == 1e-10 and o.preconditioner == F.PC_MG
     assert o.solver == F.SOLVER_PCG and (o.aar_omega, o.aar_beta, o.aar_m, o.aar_p) == (0.6, 0.6, 7, 6)
     assert o.kron_tensor_cores == 1
+    assert o.autotune == 1
     assert lib.flosic_default_options(None) == F.FLOSIC_ERR_ARG
 
 

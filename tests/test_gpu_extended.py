@@ -219,3 +219,36 @@ def test_kron_batch_mixing_tensor_core_and_cuda_core_blocks(F, orc):
         got = Vn[off:off + len(ph) * G].reshape(len(ph), G)
         assert np.max(np.abs(got - Vref)) < 1e-9 * np.max(np.abs(Vref))
         off += len(ph) * G
+
+
+def test_autotuner_picks_a_path_per_shape_and_keeps_parity(F, orc):
+    """The autotuner (default) times each qualifying block shape on the tensor
+    cores and on the CUDA cores and keeps the faster: a block is reported on
+    the tensor cores only if it qualifies, without the tuner every qualifying
+    block is, and the tuned context's potentials match the oracle."""
+    specs = [(40, 40, 40, 0.3, 2, 11), (21, 21, 21, 0.42, 4, 12), (32, 24, 16, 0.35, 3, 13), (8, 8, 8, 0.5, 2, 14)]
+    sysds, grids, phis = [], [], []
+    for nx, ny, nz, h, norb, seed in specs:
+        sd, g = _grid_dict(nx, ny, nz, h, norb)
+        sysds.append(sd)
+        grids.append(g)
+        phis.append(_gauss_orbitals(g, norb, seed))
+    off, eligible = 0, []
+    for nx, ny, nz, h, norb, seed in specs:
+        eligible.append(all(n % 8 == 0 and n <= 128 for n in (nx, ny, nz)) and off % 4 == 0)
+        off += norb * nx * ny * nz
+    tuned = F.Context(sysds, precision=F.MIXED, cg_tol=1e-11, solver=F.SOLVER_KRON)
+    plain = F.Context(sysds, precision=F.MIXED, cg_tol=1e-11, solver=F.SOLVER_KRON, autotune=0)
+    for p, q, el in zip(tuned.block_paths(), plain.block_paths(), eligible):
+        assert q["tensor_core_transforms"] == el
+        assert (not p["tensor_core_transforms"]) or el
+    V, iters, conv = tuned.orbital_poisson(_flat(phis))
+    assert np.all(_np(conv) == 1)
+    Vn = _np(V)
+    off = 0
+    for g, ph in zip(grids, phis):
+        G = g[0] * g[1] * g[2]
+        Vref, _ = orc.poisson(ph ** 2, g, tol=1e-13)
+        got = Vn[off:off + len(ph) * G].reshape(len(ph), G)
+        assert np.max(np.abs(got - Vref)) < 1e-9 * np.max(np.abs(Vref))
+        off += len(ph) * G
