@@ -233,18 +233,23 @@ __device__ __forceinline__ void gram_cp_commit() { asm volatile("cp.async.commit
 template <int K> __device__ __forceinline__ void gram_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
 template <int NB>
-__global__ void __launch_bounds__(256, 1) k_gram_async(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
+__global__ void __launch_bounds__(288, 1) k_gram_async(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
                                                        float* __restrict__ part,
                                                        const long long* __restrict__ part_off,
                                                        int* __restrict__ status) {
     extern __shared__ unsigned char g_smem_raw[];
-    __shared__ uint64_t mbar[kGStages];
+    // conv_full[b]: bf16 tile b written (8 converter warps); mma_done[b]: the MMAs
+    // of the stage in tile b / per-stage accumulator b completed (commit);
+    // hi_free[b]: accumulator b read back (4 reader warps)
+    __shared__ uint64_t conv_full[2], mma_done[2], hi_free[2];
     __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_abort;
+    __shared__ int s_mma_issued;
     constexpr int NN = 32 * NB;
     constexpr int P = gram_pack<NB>();
     constexpr int MN = P * NN;
     constexpr int kSub = kGChunk / P;
-    constexpr uint32_t kCols = (2 * MN <= 128) ? 128 : 256;
+    constexpr uint32_t kCols = 512;                  // two per-stage accumulators + the cross one
     constexpr int kRows = P * NN;                    // rows (q, a) of a stage
     const BlkDesc& B = blk[blockIdx.y];
     if (!B.gtma) return;                             // k_gram_tc's block
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_async(const BlkDesc* __restrict
     unsigned char* tiles = base;                                  // kGStages x 3 bf16 tiles
     double* ring = reinterpret_cast<double*>(base + kGStages * 3 * kGTile);
     const double* pb = psi + B.off;
-    // stage st: 16-byte piece c (points 2c, 2c + 1) of row (q, a) = tid / 32 + 8 i, c = lane
+    // stage st: 16-byte piece `lane` (points 2 lane, 2 lane + 1) of rows warp, warp + 8, ...
     auto issue = [&](int st) {
         double* dst = ring + (size_t)(st % kGRing) * kRows * kGK;
 #pragma unroll 4
@@ -269,12 +274,20 @@ __global__ void __launch_bounds__(256, 1) k_gram_async(const BlkDesc* __restrict
             gram_cp16(dst + (size_t)row * kGK + 2 * lane, in ? pb + (long long)a * B.G + g : pb, in ? 16 : 0);
         }
     };
-    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += 256)   // padding rows stay zero
+    for (int i = tid; i < kGStages * 3 * kGTile / 16; i += blockDim.x)   // padding rows stay zero
         reinterpret_cast<uint4*>(tiles)[i] = make_uint4(0u, 0u, 0u, 0u);
-    issue(0);
-    gram_cp_commit();
+    if (warp < 8) {
+        issue(0);
+        gram_cp_commit();
+    }
     if (tid == 0) {
-        for (int k = 0; k < kGStages; ++k) tc_mbar_init(&mbar[k], 1);
+        for (int k = 0; k < 2; ++k) {
+            tc_mbar_init(&conv_full[k], 8);
+            tc_mbar_init(&mma_done[k], 1);
+            tc_mbar_init(&hi_free[k], 4);
+        }
+        s_abort = 0;
+        s_mma_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(&tmem_base, kCols);
@@ -282,87 +295,116 @@ __global__ void __launch_bounds__(256, 1) k_gram_async(const BlkDesc* __restrict
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const bool reader = warp < 4 && 32 * warp < P * NN;
-    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-    const int q_own = (32 * (warp & 3)) / NN;
-    const uint32_t col0 = (uint32_t)(q_own * NN);
-    const uint32_t idesc = umma_idesc_bf16(kGRows, MN);
+    const uint32_t dcross = tmem + (uint32_t)(2 * MN);
     bool ok = true;
-    float acc[NN];
+    if (warp == 8) {
+        // ---- MMA issue (lane 0): per stage, six split products per 16-point K step
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16(kGRows, MN);
+            for (int st = 0; st < nst && ok; ++st) {
+                const int b = st & 1;
+                ok = tc_mbar_sleep_or_abort(&conv_full[b], (uint32_t)((st >> 1) & 1), &s_abort);
+                // per-stage accumulator b was read back (stage st - 2)
+                if (ok && st >= 2) ok = tc_mbar_sleep_or_abort(&hi_free[b], (uint32_t)(((st - 2) >> 1) & 1), &s_abort);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t s0 = tc_smem_addr(tiles + b * 3 * kGTile);
+                const uint32_t dhi = tmem + (uint32_t)(b * MN);
 #pragma unroll
-    for (int j = 0; j < NN; ++j) acc[j] = 0.f;
-    for (int st = 0; st < nst; ++st) {
-        const int buf = st & 1;
-        unsigned char* tile = tiles + buf * 3 * kGTile;
-        // the next stage's copies go into the slot of stage st - 1 (converted in the last iteration)
-        if (st + 1 < nst) issue(st + 1);
-        gram_cp_commit();
-        gram_cp_wait<1>();   // this thread's copies of stage st have landed
-        __syncthreads();     // everyone's
-        const double* rows = ring + (size_t)(st % kGRing) * kRows * kGK;
-        // warp w converts rows w, w + 8, ...: lane l takes points 2l, 2l + 1
-        // (one 16-byte shared load), writes their three bf16 pairs (4 bytes each)
-        // at K = 2l in the swizzled row (16-byte chunk l / 4, word l mod 4)
-#pragma unroll 4
-        for (int row = warp; row < kRows; row += 8) {
-            const double2 v = *reinterpret_cast<const double2*>(rows + (size_t)row * kGK + 2 * lane);
-            uint32_t w1, w2, w3;
-            gram_split2(d2f(v.x), d2f(v.y), w1, w2, w3);
-            const int off = row * 128 + (((lane >> 2) ^ (row & 7)) << 4) + ((lane & 3) << 2);
-            *reinterpret_cast<uint32_t*>(tile + off) = w1;
-            *reinterpret_cast<uint32_t*>(tile + kGTile + off) = w2;
-            *reinterpret_cast<uint32_t*>(tile + 2 * kGTile + off) = w3;
+                for (int kk = 0; kk < kGK / 16; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) {
+                        const uint64_t da = umma_desc_sw128(s0 + c_pair_a[p] * kGTile + kk * 32);
+                        const uint64_t db = umma_desc_sw128(s0 + c_pair_b[p] * kGTile + kk * 32);
+                        if (p == 0) umma_bf16(dhi, da, db, idesc, kk != 0);   // restarts every stage
+                        else umma_bf16(dcross, da, db, idesc, (st | kk | (p - 1)) != 0);
+                    }
+                }
+                umma_commit(&mma_done[b]);
+                ++s_mma_issued;
+            }
+            if (!ok) s_abort = 1;
         }
-        if (st >= 1) {   // the previous stage's hi x hi sums (read before this stage's MMAs restart them)
-            const int pb2 = (st - 1) & 1;
-            ok = tc_mbar_wait(&mbar[pb2], (uint32_t)(((st - 1) >> 1) & 1)) && ok;
-            ok = __all_sync(0xffffffffu, ok);
+        __syncwarp();
+    } else {
+        // ---- converters (warps 0-7); warps 0-3 also read the accumulators back
+        const bool reader = warp < 4 && 32 * warp < P * NN;
+        const bool rwarp = warp < 4;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const int q_own = (32 * (warp & 3)) / NN;
+        const uint32_t col0 = (uint32_t)(q_own * NN);
+        float acc[NN];
+#pragma unroll
+        for (int j = 0; j < NN; ++j) acc[j] = 0.f;
+        auto read_back = [&](int st) {   // stage st's per-stage sums into acc, then release them
+            const int b = st & 1;
+            bool r = tc_mbar_sleep_or_abort(&mma_done[b], (uint32_t)((st >> 1) & 1), &s_abort);
+            r = __all_sync(0xffffffffu, r);
             tc_fence_after();
+            if (r && reader) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)(b * MN) + col0 + 32 * c, acc + 32 * c);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc_mbar_arrive(&hi_free[b]);
+            return r;
+        };
+        // Every converter warp runs every iteration and every named barrier (a warp
+        // that finds s_abort set only skips the work), so no barrier can hang.
+        for (int st = 0; st < nst; ++st) {
+            const int b = st & 1;
+            tc_named_sync(1, 256);   // every converter is done with stage st - 1: its ring slot is free
+            if (st + 1 < nst) issue(st + 1);
+            gram_cp_commit();
+            gram_cp_wait<1>();       // this thread's copies of stage st have landed
+            tc_named_sync(1, 256);   // everyone's
+            if (s_abort) continue;
+            // tile b was last read by the MMAs of stage st - 2
+            bool w = st < 2 || tc_mbar_sleep_or_abort(&mma_done[b], (uint32_t)(((st - 2) >> 1) & 1), &s_abort);
+            if (!__all_sync(0xffffffffu, w)) { s_abort = 1; continue; }
+            tc_fence_after();
+            unsigned char* tile = tiles + b * 3 * kGTile;
+            const double* rows = ring + (size_t)(st % kGRing) * kRows * kGK;
+#pragma unroll 4
+            for (int row = warp; row < kRows; row += 8) {
+                const double2 v = *reinterpret_cast<const double2*>(rows + (size_t)row * kGK + 2 * lane);
+                uint32_t w1, w2, w3;
+                gram_split2(d2f(v.x), d2f(v.y), w1, w2, w3);
+                const int off = row * 128 + (((lane >> 2) ^ (row & 7)) << 4) + ((lane & 3) << 2);
+                *reinterpret_cast<uint32_t*>(tile + off) = w1;
+                *reinterpret_cast<uint32_t*>(tile + kGTile + off) = w2;
+                *reinterpret_cast<uint32_t*>(tile + 2 * kGTile + off) = w3;
+            }
+            tc_fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc_mbar_arrive(&conv_full[b]);
+            if (rwarp && st >= 1 && !read_back(st - 1)) s_abort = 1;
+        }
+        gram_cp_wait<0>();
+        ok = !s_abort;
+        if (ok && rwarp) {
+            ok = read_back(nst - 1);   // the last stage: its commit covers every MMA of the CTA
             if (ok && reader) {
 #pragma unroll
-                for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
-            }
-        }
-        tc_fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();   // the bf16 tiles are written; ring slot st mod kGRing is free
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t s0 = tc_smem_addr(tile);
-            const uint32_t dhi = tmem, dx = tmem + (uint32_t)MN;
+                for (int c = 0; c < NB; ++c) tmem_add32(dcross + lane_off + col0 + 32 * c, acc + 32 * c);
+                const int a = warp * 32 + lane - q_own * NN;
+                float* out = part + part_off[blockIdx.y] + ((long long)blockIdx.x * P + q_own) * N * N;
+                if (a < N) {
 #pragma unroll
-            for (int kk = 0; kk < kGK / 16; ++kk) {
-#pragma unroll
-                for (int p = 0; p < 6; ++p) {
-                    const uint64_t da = umma_desc_sw128(s0 + c_pair_a[p] * kGTile + kk * 32);
-                    const uint64_t db = umma_desc_sw128(s0 + c_pair_b[p] * kGTile + kk * 32);
-                    if (p == 0) umma_bf16(dhi, da, db, idesc, kk != 0);
-                    else umma_bf16(dx, da, db, idesc, (st | kk | (p - 1)) != 0);
+                    for (int j = 0; j < NN; ++j)
+                        if (j < N) out[(long long)a * N + j] = acc[j];
                 }
             }
-            umma_commit(&mbar[buf]);
         }
-    }
-    gram_cp_wait<0>();
-    ok = tc_mbar_wait(&mbar[(nst - 1) & 1], (uint32_t)(((nst - 1) >> 1) & 1)) && ok;
-    ok = __all_sync(0xffffffffu, ok);
-    tc_fence_after();
-    if (ok && reader) {
-#pragma unroll
-        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + col0 + 32 * c, acc + 32 * c);
-#pragma unroll
-        for (int c = 0; c < NB; ++c) tmem_add32(tmem + lane_off + (uint32_t)MN + col0 + 32 * c, acc + 32 * c);
-        const int a = warp * 32 + lane - q_own * NN;
-        float* out = part + part_off[blockIdx.y] + ((long long)blockIdx.x * P + q_own) * N * N;
-        if (a < N) {
-#pragma unroll
-            for (int j = 0; j < NN; ++j)
-                if (j < N) out[(long long)a * N + j] = acc[j];
-        }
-    } else if (!ok && tid == 0) {
-        atomicOr(status + 3, 2);
+        if (!ok && tid == 0) atomicOr(status + 3, 2);   // an MMA completion did not arrive in time
     }
     tc_fence_before();
+    __syncthreads();
+    if (s_abort && tid == 0 && s_mma_issued > 0) {   // let the MMAs in flight finish (bounded)
+        const int last = s_mma_issued - 1;
+        tc_mbar_wait(&mma_done[last & 1], (uint32_t)((last >> 1) & 1));
+    }
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -456,10 +498,10 @@ void launch_gram_tc(const flosic_ctx* c, const double* psi, cudaStream_t s) {
     int n_async = 0;
     for (const auto& b : c->blk) n_async += b.gtma;
     if (n_async > 0) {   // blocks with 16-byte aligned rows: copies staged asynchronously
-        if (nb <= 1) k_gram_async<1><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-        else if (nb == 2) k_gram_async<2><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-        else if (nb == 3) k_gram_async<3><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
-        else k_gram_async<4><<<grid, 256, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        if (nb <= 1) k_gram_async<1><<<grid, 288, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 2) k_gram_async<2><<<grid, 288, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else if (nb == 3) k_gram_async<3><<<grid, 288, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
+        else k_gram_async<4><<<grid, 288, kGAsyncSmem, s>>>(c->d_blk, psi, part, off, c->ws.status);
         note_launch(cm);
     }
     if (n_async < c->nblk) {   // the others: thread loads
