@@ -395,7 +395,8 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
         A(&w.d32, off); A(&w.r32, off); A(&w.p32, off); A(&w.q32, off);
     }
     if (o.adjoint_mode == FLOSIC_ADJ_EXACT) A(&w.veff, off);
-    A(&w.vsic, off);
+    if (uses_wbar(c)) A(&w.wbar, off);   // the only per-point adjoint input the mixed path needs
+    else A(&w.vsic, off);
     // level 0 (the fine grid) always, coarser multigrid levels when asked for:
     // coarsen each block while every side is >= 6
     Multigrid& M = c->mg;
@@ -678,7 +679,7 @@ int flosic_sic_backward(flosic_ctx* c, const double* psi, const double* fods, co
     if (!c->have_forward) return fail(c, FLOSIC_ERR_ARG, "no forward step recorded on this context");
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->have_energy) launch_xc_energy(c, psi, phi, V, 1.0, nullptr, s);   // V^SIC only
-    const double* Vsrc = c->ws.vsic;
+    const double* Vsrc = c->ws.vsic;   // null on the mixed path with V reused: wbar holds V^SIC phi
     if (c->opt.adjoint_mode == FLOSIC_ADJ_EXACT) {
         int rc = check_cuda(c, cudaMemsetAsync(c->ws.status, 0, 4 * sizeof(int), s), "memset status");
         if (rc) return rc;

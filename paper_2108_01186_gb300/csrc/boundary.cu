@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_rhs_bulk(const BlkDesc* __restrict__ bl
 // pairs (rho = phi^2 to ~48 bits) and the moments are accumulated as pairs,
 // so they match the float64 pass to ~1e-13 while no float64 operation runs
 // per grid point.
-__global__ void __launch_bounds__(256) k_rhs_bulk_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+__global__ void __launch_bounds__(256, 3) k_rhs_bulk_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                      const double* __restrict__ phi, double scale, int want_mom,
                                                      float2* __restrict__ b, double* __restrict__ mom_part,
@@ -189,24 +189,46 @@ __global__ void __launch_bounds__(256) k_rhs_bulk_ff(const BlkDesc* __restrict__
     for (int k = 0; k < 10; ++k) m[k] = {0.f, 0.f};
     const ff sc = to_ff(d2ff(scale)), hz = to_ff(d2ff(B.h));
     const int x = P.x0 + threadIdx.x;
+    const long long plane = (long long)D.ny * D.nx;
+    constexpr int kZU = 8;   // z loads a thread has in flight before their products
     for (int k = 0; k < 2; ++k) {
         const int y = P.y0 + threadIdx.y + k * (kTileY / 2);
         if (x >= D.nx || y >= D.ny) continue;
-        ff s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
-        ff Z = to_ff(d2ff(B.oz + B.h * P.z0 - B.cz));
-        for (int z = P.z0; z < P.z1; ++z) {
-            const long long g = P.base + ((long long)z * D.ny + y) * D.nx + x;
-            const float2 f = d2ff(phi[g]);
-            const float ph = f.x * f.x;
-            const ff rho = ff_quick(ph, fmaf(f.x, f.x, -ph) + 2.f * f.x * f.y);
-            const ff bv = ff_mul(sc, rho);
-            b[g] = make_float2(bv.h, bv.l);
-            const ff t = ff_mul(rho, Z);
-            s0 = ff_add(s0, rho);
-            s1 = ff_add(s1, t);
-            s2 = ff_add(s2, ff_mul(t, Z));
-            Z = ff_add(Z, hz);
+        // q_n = sum rho k^n over the column's points, k = z - z0 = 0, 1, ...
+        // (non-negative terms, so the pairs need no renormalisation per point);
+        // the z-moments about the centre follow once per column below.
+        ff q0 = {0.f, 0.f}, q1 = {0.f, 0.f}, q2 = {0.f, 0.f};
+        float kf = 0.f;
+        long long g = P.base + ((long long)P.z0 * D.ny + y) * D.nx + x;
+        for (int z = P.z0; z < P.z1; z += kZU, g += kZU * plane) {
+            double pv[kZU];
+#pragma unroll
+            for (int u = 0; u < kZU; ++u) pv[u] = (z + u < P.z1) ? __ldcs(phi + g + u * plane) : 0.0;
+#pragma unroll
+            for (int u = 0; u < kZU; ++u) {
+                if (z + u >= P.z1) break;
+                const float2 f = d2ff(pv[u]);
+                const float ph = f.x * f.x;
+                const ff rho = ff_quick(ph, fmaf(f.x, f.x, -ph) + 2.f * f.x * f.y);
+                const ff bv = ff_mul(sc, rho);
+                __stcs(b + g + u * plane, make_float2(bv.h, bv.l));
+                const float t1 = rho.h * kf, e1 = fmaf(rho.l, kf, fmaf(rho.h, kf, -t1));   // rho k
+                const float t2 = t1 * kf, e2 = fmaf(e1, kf, fmaf(t1, kf, -t2));            // rho k^2
+                q0 = ff_acc(q0, rho.h, rho.l);
+                q1 = ff_acc(q1, t1, e1);
+                q2 = ff_acc(q2, t2, e2);
+                kf += 1.f;
+            }
         }
+        // Z = Z0 + h k:  S0 = q0, S1 = Z0 q0 + h q1, S2 = Z0 (Z0 q0 + 2 h q1) + h^2 q2
+        q0 = ff_quick(q0.h, q0.l);
+        q1 = ff_quick(q1.h, q1.l);
+        q2 = ff_quick(q2.h, q2.l);
+        const ff Z0 = to_ff(d2ff(B.oz + B.h * P.z0 - B.cz));
+        const ff hq1 = ff_mul(hz, q1), z0q0 = ff_mul(Z0, q0);
+        const ff s0 = q0;
+        const ff s1 = ff_add(z0q0, hq1);
+        const ff s2 = ff_add(ff_mul(Z0, ff_add(z0q0, ff_mulf(hq1, 2.f))), ff_mul(ff_mul(hz, hz), q2));
         const ff X = to_ff(d2ff(B.ox + B.h * x - B.cx)), Y = to_ff(d2ff(B.oy + B.h * y - B.cy));
         const ff sxx = ff_mul(ff_mul(X, X), s0), syy = ff_mul(ff_mul(Y, Y), s0);
         const ff r2 = ff_add(ff_add(sxx, syy), s2);

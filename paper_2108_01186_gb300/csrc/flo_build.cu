@@ -198,6 +198,30 @@ struct LoadPhibar {
     }
 };
 
+// The same Phibar from wbar_i = V_i^SIC phi_i, which the mixed-precision
+// energy pass stores as float32 when the adjoint reuses V (4 bytes a point
+// instead of phi and V^SIC, 16).
+struct LoadWbar {
+    const float* w;
+    const double* gE;
+    __device__ __forceinline__ double operator()(const BlkDesc& B, int i, long long g) const {
+        return gE[B.sys] * 2.0 * B.dV * (double)w[B.off + (long long)i * B.G + g];
+    }
+    struct F {
+        const float* w;
+        long long G;
+        float coef;
+        __device__ __forceinline__ float operator()(int i, long long g) const { return coef * w[(long long)i * G + g]; }
+        using Raw = float;
+        __device__ __forceinline__ Raw raw(int i, long long g) const { return __ldcs(w + (long long)i * G + g); }
+        __device__ __forceinline__ static Raw zero() { return 0.f; }
+        __device__ __forceinline__ float cvt(Raw r) const { return coef * r; }
+    };
+    __device__ __forceinline__ F bindf(const BlkDesc& B) const {
+        return F{w + B.off, B.G, (float)(gE[B.sys] * 2.0 * B.dV)};
+    }
+};
+
 // TC: arithmetic of the products and of the sum within one 16-point k tile.
 // float (mixed precision): float32 operands from the bound loaders, tile sums
 // accumulated as float-float pairs, one float64 addition per matrix element
@@ -281,111 +305,138 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
         }
 }
 
-// Mixed-precision variant of k_contract: 64-point steps whose operand values
-// (float32 from the bound loaders) are fetched into registers while the
-// previous step is multiplied; float sums of 16-point sub-tiles are
-// two-summed into (sum, low) pairs as in k_contract.
+// Mixed-precision variant of k_contract for N <= 16 RM: 64-point steps whose
+// operand values (float32 from the bound loaders) are fetched into registers
+// while the previous step is multiplied.  The step's A and B tiles are staged
+// as [point][orbital] rows of float4 groups (group index XOR-swizzled by the
+// point so the 16-byte stores of consecutive points hit distinct banks).
+// Output tiles of 4 x 4 per thread: the CTA's 256 threads form KG = 256 /
+// (NP/4)^2 groups, each holding the whole NP x NP product for every KG-th
+// point of a step, so a point costs each thread two 16-byte shared loads for
+// 16 FMAs.  Float sums of up to 16 points are two-summed into (sum, low)
+// pairs; the groups' pairs are added at the end in a fixed order.
 template <int RM, class LA, class LB>
-__global__ void __launch_bounds__(256, RM <= 2 ? 3 : 1) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
-                                                    double* __restrict__ part, long long mat_elems) {
+__global__ void __launch_bounds__(256, RM <= 2 ? 2 : 1) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
+                                                       double* __restrict__ part, long long mat_elems) {
     constexpr int KT = 64;
     constexpr int NP = 16 * RM;
-    constexpr int PER = KT * NP / 256;   // values per thread and operand per step
-    __shared__ float As[KT][NP + 1];
-    __shared__ float Bs[KT][NP + 1];
+    constexpr int C4 = NP / 4;                 // float4 groups per staged row
+    constexpr int L = C4 * C4;                 // threads per group (one 4 x 4 output tile each)
+    constexpr int KG = 256 / L;                // groups
+    constexpr int KPG = KT / KG;               // points per group and step
+    constexpr int SUB = KPG < 16 ? KPG : 16;   // points per float sub-sum
+    constexpr int PC = C4 / 4;                 // float4 groups a thread stages per operand
+    static_assert(L * KG == 256 && PC >= 1, "tile shape");
+    constexpr int kStage = 2 * KT * NP;                  // floats of the A and B tiles
+    constexpr int kRed = (KG > 1 ? (KG / 2) : 0) * L * 32;   // floats of the group reduction
+    __shared__ __align__(16) float sm[kStage > kRed ? kStage : kRed];
+    float4* As4 = reinterpret_cast<float4*>(sm);
+    float4* Bs4 = As4 + KT * C4;
     const BlkDesc& B = blk[blockIdx.y];
     const int N = B.N;
     const long long G = B.G;
     const int kp = blockIdx.x;
     const long long kb = G * kp / kparts, ke = G * (kp + 1) / kparts;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x;
     const auto fa = la.bindf(B);
     const auto fb = lb.bindf(B);
-    // element t of a step: orbital (tid >> 6) + 4 t, point tid & 63 (coalesced along the points).
-    // RM <= 2: the next step's float64 loads stay raw in registers while this
-    // step is multiplied and are converted when they are staged; RM = 4 (16
-    // values per operand and thread) converts them as they arrive.
-    constexpr bool kRaw = RM <= 2;
-    const int kk0 = tid & (KT - 1), i0 = tid >> 6;
     using FA = std::remove_const_t<decltype(fa)>;
     using FB = std::remove_const_t<decltype(fb)>;
-    using RA = std::conditional_t<kRaw, typename FA::Raw, float>;
-    using RB = std::conditional_t<kRaw, typename FB::Raw, float>;
-    RA pa[PER];
-    RB pb[PER];
+    // staging: point kk0 of the step, float4 groups c0 + 4 m (orbitals 4 (c0 + 4 m) + j)
+    const int kk0 = tid & (KT - 1), c0 = tid >> 6;
+    typename FA::Raw pa[PC][4];
+    typename FB::Raw pb[PC][4];
     auto fetch = [&](long long k0) {
         const long long g = k0 + kk0;
+        const bool gin = g < ke;
 #pragma unroll
-        for (int t = 0; t < PER; ++t) {
-            const int i = i0 + 4 * t;
-            const bool ok = (i < N) && (g < ke);
-            if constexpr (kRaw) {
-                pa[t] = ok ? fa.raw(i, g) : FA::zero();
-                pb[t] = ok ? fb.raw(i, g) : FB::zero();
-            } else {
-                pa[t] = ok ? fa(i, g) : 0.f;
-                pb[t] = ok ? fb(i, g) : 0.f;
+        for (int m = 0; m < PC; ++m)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * (c0 + 4 * m) + j;
+                const bool ok = gin && i < N;
+                pa[m][j] = ok ? fa.raw(i, g) : FA::zero();
+                pb[m][j] = ok ? fb.raw(i, g) : FB::zero();
             }
-        }
     };
-    float acc[RM][RM], acl[RM][RM];
+    // compute: group kg takes points kg + KG t of each step; tile rows 4 rg.., columns 4 cg..
+    const int kg = tid / L, li = tid % L, rg = li % C4, cg = li / C4;
+    float acc[4][4], acl[4][4];
 #pragma unroll
-    for (int r = 0; r < RM; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < RM; ++q) acc[r][q] = acl[r][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[r][q] = acl[r][q] = 0.f;
     if (kb < ke) fetch(kb);
     for (long long k0 = kb; k0 < ke; k0 += KT) {
-        __syncthreads();
+        __syncthreads();   // the previous step's tiles are read
 #pragma unroll
-        for (int t = 0; t < PER; ++t) {
-            if constexpr (kRaw) {
-                As[kk0][i0 + 4 * t] = fa.cvt(pa[t]);
-                Bs[kk0][i0 + 4 * t] = fb.cvt(pb[t]);
-            } else {
-                As[kk0][i0 + 4 * t] = pa[t];
-                Bs[kk0][i0 + 4 * t] = pb[t];
-            }
+        for (int m = 0; m < PC; ++m) {
+            const int c = c0 + 4 * m, cs = c ^ (kk0 & (C4 - 1));
+            As4[kk0 * C4 + cs] = make_float4(fa.cvt(pa[m][0]), fa.cvt(pa[m][1]), fa.cvt(pa[m][2]), fa.cvt(pa[m][3]));
+            Bs4[kk0 * C4 + cs] = make_float4(fb.cvt(pb[m][0]), fb.cvt(pb[m][1]), fb.cvt(pb[m][2]), fb.cvt(pb[m][3]));
         }
         __syncthreads();
         if (k0 + KT < ke) fetch(k0 + KT);
 #pragma unroll
-        for (int sub = 0; sub < KT / 16; ++sub) {
-            float tacc[RM][RM];
+        for (int s0 = 0; s0 < KPG; s0 += SUB) {
+            float t[4][4];
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < RM; ++q) tacc[r][q] = 0.f;
+                for (int q = 0; q < 4; ++q) t[r][q] = 0.f;
 #pragma unroll 4
-            for (int kk = sub * 16; kk < sub * 16 + 16; ++kk) {
-                float a[RM], bv[RM];
+            for (int u = s0; u < s0 + SUB; ++u) {
+                const int kk = kg + KG * u;
+                const float4 a = As4[kk * C4 + (rg ^ (kk & (C4 - 1)))];
+                const float4 b = Bs4[kk * C4 + (cg ^ (kk & (C4 - 1)))];
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int r = 0; r < RM; ++r) a[r] = As[kk][ty + 16 * r];
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < RM; ++q) bv[q] = Bs[kk][tx + 16 * q];
-#pragma unroll
-                for (int r = 0; r < RM; ++r)
-#pragma unroll
-                    for (int q = 0; q < RM; ++q) tacc[r][q] = fmaf(a[r], bv[q], tacc[r][q]);
+                    for (int q = 0; q < 4; ++q) t[r][q] = fmaf(av[r], bv[q], t[r][q]);
             }
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < RM; ++q) {   // two-sum into the pair
-                    const float a = acc[r][q], b = tacc[r][q];
-                    const float s2 = a + b, bb = s2 - a;
-                    acl[r][q] += (a - (s2 - bb)) + (b - bb);
+                for (int q = 0; q < 4; ++q) {   // two-sum into the pair
+                    const float x = acc[r][q], y = t[r][q];
+                    const float s2 = x + y, bb = s2 - x;
+                    acl[r][q] += (x - (s2 - bb)) + (y - bb);
                     acc[r][q] = s2;
                 }
         }
     }
+    // groups KG/2.. hand their pairs to groups 0..KG/2-1, and so on (fixed order)
+    float2* red = reinterpret_cast<float2*>(sm);
+#pragma unroll 1
+    for (int half = KG / 2; half >= 1; half /= 2) {
+        __syncthreads();
+        if (kg >= half && kg < 2 * half) {
 #pragma unroll
-    for (int r = 0; r < RM; ++r)
-#pragma unroll
-        for (int q = 0; q < RM; ++q) {
-            const int i = ty + 16 * r, j = tx + 16 * q;
-            if (i < N && j < N)
-                part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = f2d(acc[r][q]) + f2d(acl[r][q]);
+            for (int e = 0; e < 16; ++e)
+                red[(e * half + kg - half) * L + li] = make_float2(acc[e >> 2][e & 3], acl[e >> 2][e & 3]);
         }
+        __syncthreads();
+        if (kg < half) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float2 o = red[(e * half + kg) * L + li];
+                const ff s = ff_add(ff{acc[e >> 2][e & 3], acl[e >> 2][e & 3]}, ff{o.x, o.y});
+                acc[e >> 2][e & 3] = s.h;
+                acl[e >> 2][e & 3] = s.l;
+            }
+        }
+    }
+    if (kg == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * rg + r, j = 4 * cg + q;
+                if (i < N && j < N)
+                    part[(long long)kp * mat_elems + B.moff + (long long)i * N + j] = f2d(acc[r][q]) + f2d(acl[r][q]);
+            }
+    }
 }
 
 // out[e] = sum_kp part[kp][e] in a fixed order
@@ -408,10 +459,11 @@ template <class LA, class LB>
 static void contract(const flosic_ctx* c, LA la, LB lb, double* out, cudaStream_t s) {
     const int nmax = max_block_n(c);
     const bool f32 = (c->opt.precision == FLOSIC_MIXED);
-    int kparts = c->kparts;   // one wave: 4 CTAs per SM, 3 for the raw-prefetch float kernels
-    if (f32 && nmax <= 32) {
-        const int k3 = (3 * c->num_sms + c->nblk - 1) / c->nblk;
-        kparts = k3 < 1 ? 1 : (k3 < kparts ? k3 : kparts);
+    int kparts = c->kparts;   // one wave: 4 CTAs per SM, 2 for the float kernels (1 at N > 32)
+    if (f32 && nmax <= 64) {
+        const int per_sm = nmax <= 32 ? 2 : 1;
+        const int k2 = (per_sm * c->num_sms + c->nblk - 1) / c->nblk;
+        kparts = k2 < 1 ? 1 : (k2 < kparts ? k2 : kparts);
     }
     const dim3 grid(kparts, c->nblk);
     double* part = c->ws.mat_part;
@@ -439,9 +491,11 @@ void launch_gram(const flosic_ctx* c, const double* psi, cudaStream_t s) {
         contract(c, LoadPsi{psi}, LoadPsi{psi}, c->ws.M, s);
 }
 
+// Vsrc: V^SIC in float64, or null when the energy pass stored wbar instead
 void launch_backward_contract(const flosic_ctx* c, const double* psi, const double* phi,
                               const double* vsic, const double* gE, cudaStream_t s) {
-    contract(c, LoadPhibar{phi, vsic, gE}, LoadPsi{psi}, c->ws.P, s);
+    if (!vsic) contract(c, LoadWbar{c->ws.wbar, gE}, LoadPsi{psi}, c->ws.P, s);
+    else contract(c, LoadPhibar{phi, vsic, gE}, LoadPsi{psi}, c->ws.P, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -731,15 +785,16 @@ void launch_lowdin(const flosic_ctx* c, double* S_out, double* Q_out, cudaStream
 // ---------------------------------------------------------------------------
 // out_j(g) = sum_k E_jk X_k(g): small matrix times a tall operand, per block
 // ---------------------------------------------------------------------------
-struct LoadPhibarPsi {   // rows 0..N-1: Phibar; rows N..2N-1: psi
-    LoadPhibar pb;
+template <class PB>
+struct LoadPhibarPsi {   // rows 0..N-1: Phibar (PB: LoadPhibar or LoadWbar); rows N..2N-1: psi
+    PB pb;
     const double* psi;
     __device__ __forceinline__ double operator()(const BlkDesc& B, int k, long long g) const {
         if (k < B.N) return pb(B, k, g);
         return psi[B.off + (long long)(k - B.N) * B.G + g];
     }
     struct F {
-        LoadPhibar::F pb;
+        typename PB::F pb;
         const double* psi;
         long long G;
         int N;
@@ -820,52 +875,85 @@ __global__ void __launch_bounds__(256) k_smallmat(const BlkDesc* __restrict__ bl
     }
 }
 
-// Raw operand loaders of the row-tile kernel below: load() issues the
-// float64 loads of X_k(g) and returns them untouched (so the next k group
-// can be in flight while the current one is multiplied); cvt() forms the
-// float32 value with integer-op conversions.
-struct RawPsi {
-    static constexpr int kGroup = 16;   // k values fetched ahead
+// Row loaders of the row-tile kernel below, one per segment of rows of X
+// (rows() of them per block): load() issues the float64 (or float32) load of
+// X_k(g) and returns it untouched, so the next group of k can be in flight
+// while the current one is multiplied; cvt() forms the float32 value with
+// integer-op conversions.
+template <int KU>
+struct RowsPsi {   // psi_k
+    static constexpr int kGroup = KU;   // k values fetched ahead
     using Raw = double;
     const double* p;
     struct Bound {
         const double* p;
         long long G;
+        int n;
+        __device__ __forceinline__ int rows() const { return n; }
         __device__ __forceinline__ Raw load(int k, long long g) const { return __ldcs(p + (long long)k * G + g); }
-        __device__ __forceinline__ float cvt(int, Raw r) const { return d2f(r); }
+        __device__ __forceinline__ float cvt(Raw r) const { return d2f(r); }
     };
     __device__ __forceinline__ static Raw zero() { return 0.0; }
-    __device__ __forceinline__ Bound bind(const BlkDesc& B) const { return Bound{p + B.off, B.G}; }
+    __device__ __forceinline__ Bound bind(const BlkDesc& B) const { return Bound{p + B.off, B.G, B.N}; }
 };
 
-// rows k < N: Phibar_k = coef V_k^SIC phi_k (two loads); rows N..2N-1: psi
-struct RawPhibarPsi {
-    static constexpr int kGroup = 8;
+// Phibar_k = coef V_k^SIC phi_k from float64 phi and V^SIC (two loads)
+struct RowsPhibar {
+    static constexpr int kGroup = 4;
     using Raw = double2;
     const double* phi;
     const double* vsic;
     const double* gE;
-    const double* psi;
     struct Bound {
-        const double *phi, *vsic, *psi;
+        const double *phi, *vsic;
         long long G;
-        int N;
+        int n;
         float coef;
+        __device__ __forceinline__ int rows() const { return n; }
         __device__ __forceinline__ Raw load(int k, long long g) const {
-            if (k < N) {
-                const long long e = (long long)k * G + g;
-                return make_double2(__ldcs(phi + e), __ldcs(vsic + e));
-            }
-            return make_double2(__ldcs(psi + (long long)(k - N) * G + g), 0.0);
+            const long long e = (long long)k * G + g;
+            return make_double2(__ldcs(phi + e), __ldcs(vsic + e));
         }
-        __device__ __forceinline__ float cvt(int k, Raw r) const {
-            return (k < N) ? coef * d2f(r.y) * d2f(r.x) : d2f(r.x);
-        }
+        __device__ __forceinline__ float cvt(Raw r) const { return coef * d2f(r.y) * d2f(r.x); }
     };
     __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
     __device__ __forceinline__ Bound bind(const BlkDesc& B) const {
-        return Bound{phi + B.off, vsic + B.off, psi + B.off, B.G, B.N, (float)(gE[B.sys] * 2.0 * B.dV)};
+        return Bound{phi + B.off, vsic + B.off, B.G, B.N, (float)(gE[B.sys] * 2.0 * B.dV)};
     }
+};
+
+// Phibar_k = coef wbar_k (wbar = V^SIC phi stored as float32 by the energy pass)
+struct RowsWbar {
+    static constexpr int kGroup = 8;
+    using Raw = float;
+    const float* w;
+    const double* gE;
+    struct Bound {
+        const float* w;
+        long long G;
+        int n;
+        float coef;
+        __device__ __forceinline__ int rows() const { return n; }
+        __device__ __forceinline__ Raw load(int k, long long g) const { return __ldcs(w + (long long)k * G + g); }
+        __device__ __forceinline__ float cvt(Raw r) const { return coef * r; }
+    };
+    __device__ __forceinline__ static Raw zero() { return 0.f; }
+    __device__ __forceinline__ Bound bind(const BlkDesc& B) const {
+        return Bound{w + B.off, B.G, B.N, (float)(gE[B.sys] * 2.0 * B.dV)};
+    }
+};
+
+// no rows (a single-segment product)
+struct RowsNone {
+    static constexpr int kGroup = 1;
+    using Raw = float;
+    struct Bound {
+        __device__ __forceinline__ int rows() const { return 0; }
+        __device__ __forceinline__ Raw load(int, long long) const { return 0.f; }
+        __device__ __forceinline__ float cvt(Raw r) const { return r; }
+    };
+    __device__ __forceinline__ static Raw zero() { return 0.f; }
+    __device__ __forceinline__ Bound bind(const BlkDesc&) const { return Bound{}; }
 };
 
 constexpr int kRowTile = 256;     // points per tile of the row-tile kernel (one per thread)
@@ -874,16 +962,21 @@ constexpr int kRowMaxK = 64;      // K = mult N it takes (N <= 32, mult <= 2)
 // out_j(g) = sum_k E_jk X_k(g) for blocks with N <= NJ <= 32 (mixed
 // precision): one point per thread with all N outputs in registers, E (as
 // float, transposed) in shared memory for the whole block, so a k step is
-// NJ/4 broadcast 16-byte shared loads and NJ FMAs per point.  Persistent
-// CTAs walk a contiguous range of the (block, 256-point tile) items; the raw
-// loads of the next k group (or of the next tile's first group) are issued
-// before the current group is multiplied.
-template <int NJ, class RX>
+// NJ/4 broadcast 16-byte shared loads and NJ FMAs per point.  The rows of X
+// come in two segments (R1: k < K1, R2: the K2 rows after them; R2 may be
+// empty), each fetched in groups of its own kGroup with its own load type, so
+// no group mixes two kinds of rows.  Persistent CTAs walk a contiguous range
+// of the (block, 256-point tile) items; the loads of the next group (of the
+// same segment, the other segment or the next tile) are issued before the
+// current group is multiplied.
+template <int NJ, class R1, class R2>
 __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __restrict__ blk, int nblk,
                                                                long long total, const double* __restrict__ E,
-                                                               int mult, RX rx, double* __restrict__ out) {
-    constexpr int KU = RX::kGroup;
-    __shared__ float4 es4[(kRowMaxK + 16) * (NJ / 4)];   // [k][j] rows, zero for k >= K
+                                                               int mult, R1 r1, R2 r2, double* __restrict__ out) {
+    constexpr int KU1 = R1::kGroup, KU2 = R2::kGroup;
+    constexpr bool kTwo = !std::is_same<R2, RowsNone>::value;
+    constexpr int kRows = kRowMaxK + KU1 + KU2;   // staged rows of E: both segments, each padded to its groups
+    __shared__ float4 es4[kRows * (NJ / 4)];      // [row][j], zero past a segment's rows
     float* es = reinterpret_cast<float*>(es4);
     const long long per_cta = (total + gridDim.x - 1) / gridDim.x;
     const long long it0 = (long long)blockIdx.x * per_cta;
@@ -902,47 +995,83 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
     long long item = it0;
     while (item < it1) {
         const BlkDesc& B = blk[b];
-        const int N = B.N, K = mult * N;
-        const int ngroup = (K + KU - 1) / KU;
+        const auto f1 = r1.bind(B);
+        const auto f2 = r2.bind(B);
+        const int K1 = f1.rows(), K2 = f2.rows(), K = mult * B.N;   // K1 + K2 = K
+        const int ng1 = (K1 + KU1 - 1) / KU1, ng2 = kTwo ? (K2 + KU2 - 1) / KU2 : 0;
+        const int s2 = ng1 * KU1;   // first staged row of segment 2
         const long long ntile = (B.G + kRowTile - 1) / kRowTile;
         const long long item_end = (base + ntile < it1) ? base + ntile : it1;
         {   // E of this block, transposed, as float
             const double* Eb = E + (long long)mult * B.moff;
             __syncthreads();   // the previous block's products are done with es
-            for (int e = tid; e < ngroup * KU * NJ; e += kRowTile) {
-                const int k = e / NJ, j = e - k * NJ;
-                es[e] = (j < N && k < K) ? d2f(Eb[(long long)j * K + k]) : 0.f;
+            for (int e = tid; e < (s2 + ng2 * KU2) * NJ; e += kRowTile) {
+                const int row = e / NJ, j = e - row * NJ;
+                const int k = row < s2 ? row : K1 + (row - s2);           // column of E
+                const bool ok = j < B.N && (row < s2 ? row < K1 : row - s2 < K2);
+                es[e] = ok ? d2f(Eb[(long long)j * K + k]) : 0.f;
             }
             __syncthreads();
         }
-        const auto fx = rx.bind(B);
-        typename RX::Raw raw[KU];
-        auto fetch = [&](long long tl, int grp) {
+        typename R1::Raw raw1[KU1];
+        typename R2::Raw raw2[KU2];
+        auto fetch1 = [&](long long tl, int grp) {
             const long long g = tl * kRowTile + tid;
 #pragma unroll
-            for (int u = 0; u < KU; ++u) {
-                const int k = grp * KU + u;
-                raw[u] = (g < B.G && k < K) ? fx.load(k, g) : RX::zero();
+            for (int u = 0; u < KU1; ++u) {
+                const int k = grp * KU1 + u;
+                raw1[u] = (g < B.G && k < K1) ? f1.load(k, g) : R1::zero();
             }
         };
-        fetch(item - base, 0);
+        auto fetch2 = [&](long long tl, int grp) {
+            const long long g = tl * kRowTile + tid;
+#pragma unroll
+            for (int u = 0; u < KU2; ++u) {
+                const int k = grp * KU2 + u;
+                raw2[u] = (g < B.G && k < K2) ? f2.load(k, g) : R2::zero();
+            }
+        };
+        if (ng1 > 0) fetch1(item - base, 0);
+        else if (ng2 > 0) fetch2(item - base, 0);
         for (; item < item_end; ++item) {
-            const long long g = (item - base) * kRowTile + tid;
+            const long long tl = item - base, g = tl * kRowTile + tid;
+            const bool more = item + 1 < item_end;
             float acc[NJ];
 #pragma unroll
             for (int j = 0; j < NJ; ++j) acc[j] = 0.f;
-            for (int grp = 0; grp < ngroup; ++grp) {
-                float x[KU];
+            for (int grp = 0; grp < ng1; ++grp) {
+                float x[KU1];
 #pragma unroll
-                for (int u = 0; u < KU; ++u) x[u] = fx.cvt(grp * KU + u, raw[u]);
-                if (grp + 1 < ngroup) fetch(item - base, grp + 1);
-                else if (item + 1 < item_end) fetch(item + 1 - base, 0);
-                const float4* er = es4 + (long long)grp * KU * (NJ / 4);
+                for (int u = 0; u < KU1; ++u) x[u] = f1.cvt(raw1[u]);
+                const bool same = grp + 1 < ng1;   // next: this segment, the other one or the next tile
+                if (same || (ng2 == 0 && more)) fetch1(same ? tl : tl + 1, same ? grp + 1 : 0);
+                else if (ng2 > 0) fetch2(tl, 0);
 #pragma unroll
-                for (int u = 0; u < KU; ++u) {
+                for (int u = 0; u < KU1; ++u) {
+                    const float4* er = es4 + (long long)(grp * KU1 + u) * (NJ / 4);
 #pragma unroll
                     for (int q = 0; q < NJ / 4; ++q) {
-                        const float4 ev = er[u * (NJ / 4) + q];
+                        const float4 ev = er[q];
+                        acc[4 * q + 0] = fmaf(ev.x, x[u], acc[4 * q + 0]);
+                        acc[4 * q + 1] = fmaf(ev.y, x[u], acc[4 * q + 1]);
+                        acc[4 * q + 2] = fmaf(ev.z, x[u], acc[4 * q + 2]);
+                        acc[4 * q + 3] = fmaf(ev.w, x[u], acc[4 * q + 3]);
+                    }
+                }
+            }
+            for (int grp = 0; kTwo && grp < ng2; ++grp) {
+                float x[KU2];
+#pragma unroll
+                for (int u = 0; u < KU2; ++u) x[u] = f2.cvt(raw2[u]);
+                const bool same = grp + 1 < ng2;
+                if (same || (ng1 == 0 && more)) fetch2(same ? tl : tl + 1, same ? grp + 1 : 0);
+                else if (more) fetch1(tl + 1, 0);
+#pragma unroll
+                for (int u = 0; u < KU2; ++u) {
+                    const float4* er = es4 + (long long)(s2 + grp * KU2 + u) * (NJ / 4);
+#pragma unroll
+                    for (int q = 0; q < NJ / 4; ++q) {
+                        const float4 ev = er[q];
                         acc[4 * q + 0] = fmaf(ev.x, x[u], acc[4 * q + 0]);
                         acc[4 * q + 1] = fmaf(ev.y, x[u], acc[4 * q + 1]);
                         acc[4 * q + 2] = fmaf(ev.z, x[u], acc[4 * q + 2]);
@@ -954,7 +1083,7 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
                 double* o = out + B.off + g;
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
-                    if (j < N) __stcs(o + (long long)j * B.G, f2d(acc[j]));
+                    if (j < B.N) __stcs(o + (long long)j * B.G, f2d(acc[j]));
             }
         }
         base += ntile;
@@ -962,17 +1091,19 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
     }
 }
 
-template <class RX>
-static bool smallmat_rows(const flosic_ctx* c, const double* E, int mult, RX rx, double* out, cudaStream_t s) {
+// R2 = RowsNone: a single segment (K2 = 0)
+template <class R1, class R2>
+static bool smallmat_rows(const flosic_ctx* c, const double* E, int mult, R1 r1, R2 r2, double* out,
+                          cudaStream_t s) {
     const int nmax = max_block_n(c);
     if (c->opt.precision != FLOSIC_MIXED || nmax > 32 || mult * nmax > kRowMaxK) return false;
     long long total = 0;
     for (const auto& b : c->blk) total += (b.G + kRowTile - 1) / kRowTile;
     const long long wave = 2LL * c->num_sms;   // one wave of 2 CTAs per SM
     const unsigned grid = (unsigned)(total < wave ? total : wave);
-    if (nmax <= 8) k_smallmat_rows<8><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
-    else if (nmax <= 16) k_smallmat_rows<16><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
-    else k_smallmat_rows<32><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, rx, out);
+    if (nmax <= 8) k_smallmat_rows<8><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, r1, r2, out);
+    else if (nmax <= 16) k_smallmat_rows<16><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, r1, r2, out);
+    else k_smallmat_rows<32><<<grid, kRowTile, 0, s>>>(c->d_blk, c->nblk, total, E, mult, r1, r2, out);
     note_launch(c);
     return true;
 }
@@ -1001,7 +1132,7 @@ static void smallmat(const flosic_ctx* c, const double* E, int mult, LX lx, doub
 }
 
 void launch_flo_apply(const flosic_ctx* c, const double* psi, double* phi, cudaStream_t s) {
-    if (!smallmat_rows(c, c->ws.C, 1, RawPsi{psi}, phi, s)) smallmat(c, c->ws.C, 1, LoadPsi{psi}, phi, s);
+    if (!smallmat_rows(c, c->ws.C, 1, RowsPsi<16>{psi}, RowsNone{}, phi, s)) smallmat(c, c->ws.C, 1, LoadPsi{psi}, phi, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1097,9 +1228,11 @@ __global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __r
 
 void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, const double* vsic,
                    const double* gE, const double* fods, double* dpsi, cudaStream_t s) {
-    if (!smallmat_rows(c, c->ws.E2, 2, RawPhibarPsi{phi, vsic, gE, psi}, dpsi, s)) {
-        LoadPhibarPsi lx{LoadPhibar{phi, vsic, gE}, psi};
-        smallmat(c, c->ws.E2, 2, lx, dpsi, s);
+    if (!vsic) {   // the energy pass stored wbar = V^SIC phi (mixed precision)
+        if (!smallmat_rows(c, c->ws.E2, 2, RowsWbar{c->ws.wbar, gE}, RowsPsi<8>{psi}, dpsi, s))
+            smallmat(c, c->ws.E2, 2, LoadPhibarPsi<LoadWbar>{LoadWbar{c->ws.wbar, gE}, psi}, dpsi, s);
+    } else if (!smallmat_rows(c, c->ws.E2, 2, RowsPhibar{phi, vsic, gE}, RowsPsi<8>{psi}, dpsi, s)) {
+        smallmat(c, c->ws.E2, 2, LoadPhibarPsi<LoadPhibar>{LoadPhibar{phi, vsic, gE}, psi}, dpsi, s);
     }
     k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
                                                                  c->ws.vbar, fods, dpsi); note_launch(c);

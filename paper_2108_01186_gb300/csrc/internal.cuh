@@ -141,7 +141,9 @@ struct Workspace {
     double *b64, *r64, *p64, *q64;   // FP64 CG vectors / refinement
     float *d32, *r32, *p32, *q32;    // FP32 inner CG vectors
     double* veff;                    // exact adjoint: zero-boundary solve, then its V^SIC
-    double* vsic;                    // V_i^SIC = -(V_i + v_xc,i) of the last energy pass
+    double* vsic;                    // V_i^SIC = -(V_i + v_xc,i) of the last energy pass (float64
+                                     // path, or the exact adjoint's input)
+    float* wbar;                     // mixed path, V reused in the adjoint: V_i^SIC phi_i as float
     double *z64, *p64b;              // multigrid PCG (FP64): z = M r, V-cycle scratch
     float *z32, *p32b;               // multigrid PCG (FP32)
     CgState cg;
@@ -256,6 +258,13 @@ struct flosic_ctx {
 };
 
 namespace flosic {
+
+// Mixed precision with V reused in the adjoint: the energy pass stores
+// wbar_i = V_i^SIC phi_i (float32), all the adjoint reads per point besides
+// psi; otherwise V_i^SIC itself (float64).
+inline bool uses_wbar(const flosic_ctx* c) {
+    return c->opt.precision == FLOSIC_MIXED && c->opt.adjoint_mode == FLOSIC_ADJ_REUSE_V;
+}
 
 // ---- launchers implemented in the .cu files ----------------------------
 // FLO build (flo_build.cu)
@@ -512,6 +521,15 @@ __device__ __forceinline__ ff ff_sum6(ff a, ff b, ff c, ff d, ff e, ff f) {
 __device__ __forceinline__ ff ff_addf(ff a, float b) {
     const ff s = ff_two_sum(a.h, b);
     return ff_quick(s.h, s.l + a.l);
+}
+// Running sum of pairs (th, tl) with |tl| small against |th|: exact
+// two-sum of the high parts, the low parts and its rounding error gathered in
+// a.l without renormalising; after n terms the error is ~n 2^-48 sum |terms|
+// (relative to the sum itself when the terms share a sign).  Renormalise with
+// ff_quick at the end.
+__device__ __forceinline__ ff ff_acc(ff a, float th, float tl) {
+    const ff s = ff_two_sum(a.h, th);
+    return {s.h, a.l + (s.l + tl)};
 }
 __device__ __forceinline__ ff ff_mulf(ff a, float b) {   // pair times float
     const float p = a.h * b;

@@ -34,13 +34,14 @@ __device__ __forceinline__ double warp_sum_ff(float v) {
 // summed as float-float pairs, the functional, V^SIC and V_avg in float32;
 // per-orbital sums are float-float within a warp, float64 across warps.
 // Otherwise float64 throughout.
-// Also stores V_i^SIC = -(V_i + v_xc,i) for the reverse mode.
+// Also stores, for the reverse mode, V_i^SIC = -(V_i + v_xc,i) (vsic, float64)
+// or wbar_i = V_i^SIC phi_i (wbar, float32; kF32 only); either may be null.
 template <bool kF32>
 __global__ void __launch_bounds__(kChunkThreads)
 k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double* __restrict__ phi, const double* __restrict__ V, double scale,
             double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part,
-            double* __restrict__ vsic, const int* __restrict__ mask) {
+            double* __restrict__ vsic, float* __restrict__ wbar, const int* __restrict__ mask) {
     using R = typename std::conditional<kF32, float, double>::type;
     __shared__ double red[kChunkThreads / 32][kMaxN][2];
     const BlkDesc& B = blk[blockIdx.y];
@@ -64,7 +65,8 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             if (!on) {
                 const R p = kF32 ? (R)d2f(psi[base + g]) : (R)psi[base + g];
                 rs[k] += p * p;
-                vsic[base + g] = 0.0;
+                if (vsic) vsic[base + g] = 0.0;
+                if (kF32 && wbar) wbar[base + g] = 0.f;
                 continue;
             }
             R f, v, p, eps, vxc;
@@ -75,7 +77,8 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
                 p = d2f(psi[base + g]);
                 const float ph = f2.x * f2.x;
                 const ff rho2 = ff_quick(ph, fmaf(f2.x, f2.x, -ph) + 2.f * f2.x * f2.y);
-                uff = ff_add(uff, ff_mul(rho2, to_ff(v2)));
+                const float pv = rho2.h * v2.x;   // rho V as an unnormalised pair
+                uff = ff_acc(uff, pv, fmaf(rho2.h, v2.y, fmaf(rho2.l, v2.x, fmaf(rho2.h, v2.x, -pv))));
                 float ef, vf;
                 lsda_pol_f(f * f, (float)rmin, ef, vf);
                 eps = ef;
@@ -93,14 +96,18 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             u += rho * v;
             ex += rho * eps;
             const R vs = -(v + vxc);
-            if (kF32) vsic[base + g] = f2d((float)vs);
-            else vsic[base + g] = (double)vs;
+            if (kF32) {
+                if (vsic) vsic[base + g] = f2d((float)vs);
+                if (wbar) __stcs(wbar + base + g, (float)vs * (float)f);
+            } else {
+                vsic[base + g] = (double)vs;
+            }
             num[k] += rho * vs;
             rs[k] += p * p;
         }
         double us, es;
         if (kF32) {
-            us = ff_to_double(warp_sum(uff));
+            us = ff_to_double(warp_sum(ff_quick(uff.h, uff.l)));
             es = warp_sum_ff((float)ex);
         } else {
             us = warp_sum((double)u);
@@ -138,10 +145,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
     const dim3 grid(cmax, c->nblk);
     if (c->opt.precision == FLOSIC_MIXED)
         k_xc_energy<true><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                                         c->ws.e_part, c->ws.vsic, c->ws.mask);
+                                                         c->ws.e_part, c->ws.vsic, c->ws.wbar, c->ws.mask);
     else
         k_xc_energy<false><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
-                                                          c->ws.e_part, c->ws.vsic, c->ws.mask);
+                                                          c->ws.e_part, c->ws.vsic, nullptr, c->ws.mask);
     note_launch(c);
 }
 
