@@ -369,6 +369,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.vals, me); A(&w.grads, 3 * me); A(&w.rho_a, orb); A(&w.T, me); A(&w.M, me);
     A(&w.S, me); A(&w.Q, me); A(&w.C, me); A(&w.U, me); A(&w.lam, orb); A(&w.P, me);
     A(&w.vbar, me); A(&w.tmp, 4 * me); A(&w.E2, 2 * me);
+    A(&w.node_idx, 64LL * orb); A(&w.node_wt, 64LL * orb);
     A(&w.mat_part, (long long)c->kparts * me);
     if (o.solver == FLOSIC_SOLVER_AAR) {
         float *fp = nullptr, *X = nullptr, *F = nullptr;
@@ -503,7 +504,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&w.mom_part, 10 * nparts);
     A(&g.part, nparts); A(&g.part2, nparts); A(&g.count, orb); A(&g.active, orb); A(&g.oactive, orb);
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
-    A(&g.dmax, orb);
+    A(&g.dmax, orb); A(&g.xz, orb);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
     if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) e = setup_kron(c);   // sets the blocks' kq, kl
     for (BlkDesc& B : c->blk) B.gtma = (o.precision == FLOSIC_MIXED && gram_async_eligible(B)) ? 1 : 0;
@@ -513,6 +514,7 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sys_orb0, sys_orb0.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g.count, 0, sizeof(unsigned) * orb);
     if (e == cudaSuccess) e = cudaMemset(g.dmax, 0, sizeof(unsigned) * orb);
+    if (e == cudaSuccess) e = cudaMemset(g.xz, 0, sizeof(int) * orb);
     if (e == cudaSuccess) {   // every orbital computed here until flosic_set_orbital_mask says otherwise
         const std::vector<int> ones((size_t)orb, 1);
         e = cudaMemcpy(w.mask, ones.data(), sizeof(int) * orb, cudaMemcpyHostToDevice);
@@ -782,9 +784,12 @@ int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, d
     rc = flosic_sic_backward(c, H.psi[cur], H.fods[cur], H.phi, H.V, H.gE, dE_dpsi ? H.dpsi : nullptr,
                              dE_dfod ? H.dfod : nullptr, s);
     if (rc) return rc;
-    // the outputs go to the host on their own stream ...
+    // the outputs go to the host on their own stream, once the next step's
+    // inputs have arrived (the next FLO build waits for those; the outputs
+    // have the whole next forward step to travel) ...
     rc = check_cuda(c, cudaEventRecord(H.done, s), "cudaEventRecord");
     if (!rc) rc = check_cuda(c, cudaStreamWaitEvent(H.copy_out, H.done, 0), "cudaStreamWaitEvent");
+    if (!rc && psi_next) rc = check_cuda(c, cudaStreamWaitEvent(H.copy_out, H.copied[nxt], 0), "cudaStreamWaitEvent");
     if (rc) return rc;
     struct Out { void* h; const void* d; size_t n; };
     const Out outs[] = {{E_sic, H.E, sizeof(double) * nsys}, {U, H.U, sizeof(double) * c->norb},

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(256, 3) k_rhs_bulk_ff(const BlkDesc* __restric
                                                      double* __restrict__ mom, unsigned* __restrict__ count,
                                                      const int* __restrict__ mask) {
     __shared__ double scratch[32];
-    __shared__ double wsum[8][10];
+    __shared__ float2 red[10][256];   // per-thread moment pairs
+    __shared__ float2 red2[10][16];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!mask[P.o]) return;   // an orbital this context does not solve (every CTA of it returns)
     const LvlDesc& D = L[P.b];
@@ -245,17 +246,23 @@ __global__ void __launch_bounds__(256, 3) k_rhs_bulk_ff(const BlkDesc* __restric
         m[9] = ff_add(m[9], ff_mulf(ff_mul(Y, s1), 3.f));
     }
     if (!want_mom) return;
-    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
+    // CTA sums of the ten pairs in a fixed order: 16 threads per moment add
+    // 16 values each, then one thread per moment adds their 16 partials
+    const int tid = linear_tid();
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        const ff v = warp_sum(m[k]);
-        if (lane == 0) wsum[wid][k] = ff_to_double(v);
+    for (int k = 0; k < 10; ++k) red[k][tid] = make_float2(m[k].h, m[k].l);
+    __syncthreads();
+    if (tid < 160) {
+        const int k = tid >> 4, p = tid & 15;
+        ff v = to_ff(red[k][p]);
+        for (int q = 1; q < 16; ++q) v = ff_add(v, to_ff(red[k][p + 16 * q]));
+        red2[k][p] = make_float2(v.h, v.l);
     }
     __syncthreads();
     if (tid < 10) {
-        double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += wsum[w][tid];
-        mom_part[(long long)blockIdx.x * 10 + tid] = s;
+        ff v = to_ff(red2[tid][0]);
+        for (int q = 1; q < 16; ++q) v = ff_add(v, to_ff(red2[tid][q]));
+        mom_part[(long long)blockIdx.x * 10 + tid] = ff_to_double(v);
     }
     __syncthreads();
     gather_moments(P, D, B, mom_part, mom, count, scratch);
@@ -284,11 +291,15 @@ __global__ void k_rhs_bc(const BlkDesc* __restrict__ blk, int b, const int* __re
         float2* rp = reinterpret_cast<float2*>(rhs);
         for (int i = 0; i < B.N; ++i) {
             const float2* mo = mom_ff + i * 10;
-            ff acc = {0.f, 0.f};
+            ff acc = {0.f, 0.f};   // unnormalised products gathered by ff_acc (error ~2^-44 sum |terms|)
 #pragma unroll
-            for (int k = 0; k < 10; ++k) acc = ff_add(acc, ff_mul(to_ff(mo[k]), cf[k]));
+            for (int k = 0; k < 10; ++k) {
+                const float2 m = mo[k];
+                const float p = m.x * cf[k].h;
+                acc = ff_acc(acc, p, fmaf(m.x, cf[k].l, fmaf(m.y, cf[k].h, fmaf(m.x, cf[k].h, -p))));
+            }
             const long long idx = B.off + (long long)i * B.G + g;
-            const ff v = ff_add(to_ff(rp[idx]), acc);
+            const ff v = ff_add(to_ff(rp[idx]), ff_quick(acc.h, acc.l));
             rp[idx] = make_float2(v.h, v.l);
         }
     } else {

@@ -379,27 +379,28 @@ __global__ void __launch_bounds__(256, RM <= 2 ? 2 : 1) k_contract_f(const BlkDe
         if (k0 + KT < ke) fetch(k0 + KT);
 #pragma unroll
         for (int s0 = 0; s0 < KPG; s0 += SUB) {
-            float t[4][4];
+            float2 t[4][2];   // columns (0, 1) and (2, 3) of each row: packed FMAs
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) t[r][q] = 0.f;
+            for (int r = 0; r < 4; ++r) t[r][0] = t[r][1] = make_float2(0.f, 0.f);
 #pragma unroll 4
             for (int u = s0; u < s0 + SUB; ++u) {
                 const int kk = kg + KG * u;
                 const float4 a = As4[kk * C4 + (rg ^ (kk & (C4 - 1)))];
                 const float4 b = Bs4[kk * C4 + (cg ^ (kk & (C4 - 1)))];
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) t[r][q] = fmaf(av[r], bv[q], t[r][q]);
+                for (int r = 0; r < 4; ++r) {
+                    const float2 ar = make_float2(av[r], av[r]);
+                    t[r][0] = __ffma2_rn(ar, b01, t[r][0]);
+                    t[r][1] = __ffma2_rn(ar, b23, t[r][1]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {   // two-sum into the pair
-                    const float x = acc[r][q], y = t[r][q];
+                    const float x = acc[r][q], y = (q & 1) ? t[r][q >> 1].y : t[r][q >> 1].x;
                     const float s2 = x + y, bb = s2 - x;
                     acl[r][q] += (x - (s2 - bb)) + (y - bb);
                     acc[r][q] = s2;
@@ -1036,9 +1037,9 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
         for (; item < item_end; ++item) {
             const long long tl = item - base, g = tl * kRowTile + tid;
             const bool more = item + 1 < item_end;
-            float acc[NJ];
+            float2 acc[NJ / 2];   // outputs (2j, 2j + 1): two FMAs per packed instruction
 #pragma unroll
-            for (int j = 0; j < NJ; ++j) acc[j] = 0.f;
+            for (int j = 0; j < NJ / 2; ++j) acc[j] = make_float2(0.f, 0.f);
             for (int grp = 0; grp < ng1; ++grp) {
                 float x[KU1];
 #pragma unroll
@@ -1049,13 +1050,12 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
 #pragma unroll
                 for (int u = 0; u < KU1; ++u) {
                     const float4* er = es4 + (long long)(grp * KU1 + u) * (NJ / 4);
+                    const float2 xu = make_float2(x[u], x[u]);
 #pragma unroll
                     for (int q = 0; q < NJ / 4; ++q) {
                         const float4 ev = er[q];
-                        acc[4 * q + 0] = fmaf(ev.x, x[u], acc[4 * q + 0]);
-                        acc[4 * q + 1] = fmaf(ev.y, x[u], acc[4 * q + 1]);
-                        acc[4 * q + 2] = fmaf(ev.z, x[u], acc[4 * q + 2]);
-                        acc[4 * q + 3] = fmaf(ev.w, x[u], acc[4 * q + 3]);
+                        acc[2 * q] = __ffma2_rn(make_float2(ev.x, ev.y), xu, acc[2 * q]);
+                        acc[2 * q + 1] = __ffma2_rn(make_float2(ev.z, ev.w), xu, acc[2 * q + 1]);
                     }
                 }
             }
@@ -1069,13 +1069,12 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
 #pragma unroll
                 for (int u = 0; u < KU2; ++u) {
                     const float4* er = es4 + (long long)(s2 + grp * KU2 + u) * (NJ / 4);
+                    const float2 xu = make_float2(x[u], x[u]);
 #pragma unroll
                     for (int q = 0; q < NJ / 4; ++q) {
                         const float4 ev = er[q];
-                        acc[4 * q + 0] = fmaf(ev.x, x[u], acc[4 * q + 0]);
-                        acc[4 * q + 1] = fmaf(ev.y, x[u], acc[4 * q + 1]);
-                        acc[4 * q + 2] = fmaf(ev.z, x[u], acc[4 * q + 2]);
-                        acc[4 * q + 3] = fmaf(ev.w, x[u], acc[4 * q + 3]);
+                        acc[2 * q] = __ffma2_rn(make_float2(ev.x, ev.y), xu, acc[2 * q]);
+                        acc[2 * q + 1] = __ffma2_rn(make_float2(ev.z, ev.w), xu, acc[2 * q + 1]);
                     }
                 }
             }
@@ -1083,7 +1082,7 @@ __global__ void __launch_bounds__(kRowTile, 2) k_smallmat_rows(const BlkDesc* __
                 double* o = out + B.off + g;
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
-                    if (j < B.N) __stcs(o + (long long)j * B.G, f2d(acc[j]));
+                    if (j < B.N) __stcs(o + (long long)j * B.G, f2d((j & 1) ? acc[j >> 1].y : acc[j >> 1].x));
             }
         }
         base += ntile;
@@ -1199,29 +1198,57 @@ void launch_backward_small(const flosic_ctx* c, double* dE_dfod, cudaStream_t s)
     k_backward_small<<<c->nblk, 512, 0, s>>>(c->d_blk, c->ws, dE_dfod); note_launch(c);
 }
 
+// The 64 tricubic interpolation nodes of every FOD (one thread per FOD and
+// node): grid index within the orbital (-1 outside a Dirichlet box) and
+// weight L_x L_y L_z.
+__global__ void k_interp_nodes(const BlkDesc* __restrict__ blk, const int* __restrict__ orb_blk, int norb,
+                               const double* __restrict__ fods, int* __restrict__ node_idx,
+                               double* __restrict__ node_wt) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 64LL * norb) return;
+    const int f = (int)(t >> 6), node = (int)(t & 63);
+    const BlkDesc& B = blk[orb_blk[f]];
+    const double* fp = fods + (B.fod_off + (f - B.orb0)) * 3;
+    const double fa[3] = {fp[0], fp[1], fp[2]};
+    const Cell c = cell_of(B, fa);
+    const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
+    int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
+    if (B.per) wrap_node(B, qx, qy, qz);
+    const bool in = !(qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz);
+    node_idx[t] = in ? (qz * B.ny + qy) * B.nx + qx : -1;
+    node_wt[t] = c.L[0][e] * c.L[1][bb] * c.L[2][cc];
+}
+
 // psibar_a(node) += sum_i vbar_ia L(a_i, node): one warp per orbital a,
-// FODs in sequence (deterministic).
+// FODs in sequence (deterministic); the next FOD's nodes, weights and
+// coefficient are loaded before this FOD's read-modify-writes.
 __global__ void k_interp_scatter(const BlkDesc* __restrict__ blk, const int* __restrict__ orb_blk,
                                  int norb, const double* __restrict__ vbar,
-                                 const double* __restrict__ fods, double* __restrict__ dpsi) {
+                                 const int* __restrict__ node_idx, const double* __restrict__ node_wt,
+                                 double* __restrict__ dpsi) {
     const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (o >= norb) return;
     const BlkDesc& B = blk[orb_blk[o]];
     const int a = o - B.orb0;
     double* u = dpsi + B.off + (long long)a * B.G;
+    int ix0 = 0, ix1 = 0;
+    double w0 = 0.0, w1 = 0.0, coef = 0.0;
+    auto load = [&](int i) {
+        const long long t = 64LL * (B.orb0 + i);
+        ix0 = node_idx[t + lane];
+        ix1 = node_idx[t + 32 + lane];
+        w0 = node_wt[t + lane];
+        w1 = node_wt[t + 32 + lane];
+        coef = vbar[B.moff + i * B.N + a];
+    };
+    if (B.N > 0) load(0);
     for (int i = 0; i < B.N; ++i) {
-        const double coef = vbar[B.moff + i * B.N + a];
-        const double* f = fods + (B.fod_off + i) * 3;
-        const double fa[3] = {f[0], f[1], f[2]};
-        const Cell c = cell_of(B, fa);
-        for (int node = lane; node < 64; node += 32) {
-            const int e = node & 3, bb = (node >> 2) & 3, cc = node >> 4;
-            int qx = c.i0[0] - 1 + e, qy = c.i0[1] - 1 + bb, qz = c.i0[2] - 1 + cc;
-            if (B.per) wrap_node(B, qx, qy, qz);
-            if (qx < 0 || qx >= B.nx || qy < 0 || qy >= B.ny || qz < 0 || qz >= B.nz) continue;
-            u[((long long)qz * B.ny + qy) * B.nx + qx] += coef * c.L[0][e] * c.L[1][bb] * c.L[2][cc];
-        }
+        const int j0 = ix0, j1 = ix1;
+        const double v0 = coef * w0, v1 = coef * w1;
+        if (i + 1 < B.N) load(i + 1);
+        if (j0 >= 0) u[j0] += v0;
+        if (j1 >= 0) u[j1] += v1;
         __syncwarp();
     }
 }
@@ -1234,8 +1261,12 @@ void launch_psibar(const flosic_ctx* c, const double* psi, const double* phi, co
     } else if (!smallmat_rows(c, c->ws.E2, 2, RowsPhibar{phi, vsic, gE}, RowsPsi<8>{psi}, dpsi, s)) {
         smallmat(c, c->ws.E2, 2, LoadPhibarPsi<LoadPhibar>{LoadPhibar{phi, vsic, gE}, psi}, dpsi, s);
     }
-    k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb,
-                                                                 c->ws.vbar, fods, dpsi); note_launch(c);
+    k_interp_nodes<<<(unsigned)((64LL * c->norb + 255) / 256), 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb, fods,
+                                                                            c->ws.node_idx, c->ws.node_wt);
+    note_launch(c);
+    k_interp_scatter<<<(c->norb * 32 + 255) / 256, 256, 0, s>>>(c->d_blk, c->d_orb_blk, c->norb, c->ws.vbar,
+                                                                 c->ws.node_idx, c->ws.node_wt, dpsi);
+    note_launch(c);
 }
 
 }  // namespace flosic

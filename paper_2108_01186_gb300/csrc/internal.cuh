@@ -114,6 +114,7 @@ struct CgState {
     int* conv;         // [norb] 1 = converged
     double* prof_bytes;  // [1] algorithmic bytes moved by the stencil-apply launches
     unsigned* dmax;      // [norb] float bits of max |d| of the current correction (refinement update)
+    int* xz;             // [norb] 1 = the refinement's x is zero and not stored (cold Kronecker start)
     const int* mask;     // [norb] 1 = this context solves the orbital (see flosic_set_orbital_mask)
 };
 
@@ -121,6 +122,8 @@ struct Workspace {
     // FLO build (N x N per block, packed like S)
     double *vals, *grads, *rho_a, *T, *M, *S, *Q, *C, *U, *lam, *P;
     double *vbar;          // [sum N*N] adjoint of psi at the FODs
+    int* node_idx;         // [norb][64] grid index of each FOD's interpolation nodes (-1: outside)
+    double* node_wt;       // [norb][64] their tricubic weights
     double* tmp;           // [4][sum N*N] scratch of the small kernels
     double* E2;            // [sum 2 N*N] [C^T | D] of the reverse apply
     long long mat_elems;   // sum N*N
@@ -340,13 +343,14 @@ cudaError_t upload_ff_weights();
 int setup_update_maps(flosic_ctx* c);   // refinement update's tensor maps (refine.cu); blocks on that path
 // mixed precision: float-float refinement around the float32 inner solves
 // (b holds float-float pairs, written so by launch_rhs; x the solution's)
-void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,
-                    double tol2, double inner_tol2, cudaStream_t s);
+void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, bool keep_zero, float2* x,
+                    float* p32, double tol2, double inner_tol2, cudaStream_t s);
 void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* p32, double tol2,
                         double inner_tol2, bool store_r, cudaStream_t s);
 void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s);
 // Kronecker inner solver: x += d and r -= A d in one sweep (r in pairs over b)
-void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double inner_tol2, cudaStream_t s);
+void launch_update_ff(flosic_ctx* c, double* r, float2* x, bool x_zero, double tol2, double inner_tol2,
+                      cudaStream_t s);
 void launch_join_ff(flosic_ctx* c, const float2* x, double* V, cudaStream_t s);
 void stencil_weights(double* w);   // 12th-order weights w_0..w_6
 const void* k_lowdin_symbol();
@@ -447,25 +451,18 @@ __device__ __forceinline__ double f2d(float f) {
     const unsigned e11 = (e == 255u) ? 2047u : e + 896u;
     return __hiloint2double((int)(sign | (e11 << 20) | (m >> 3)), (int)(m << 29));
 }
-// float(n) for 0 <= n < 2^29 without a conversion instruction: n = a 2^23 + b
-__device__ __forceinline__ float u29_to_float(unsigned n) {
-    const float a = __uint_as_float(0x4B000000u | (n >> 23)) - 8388608.f;
-    const float b = __uint_as_float(0x4B000000u | (n & 0x7fffffu)) - 8388608.f;
-    return fmaf(a, 8388608.f, b);
-}
-// v = hi + lo, hi = d2f(v), lo = v - hi rounded to float (~48 significant bits)
+// v = hi + lo, hi = d2f(v), lo = v - hi rounded to float (~48 significant bits).
+// The 29 bits d2f drops, sign-extended from their top bit, are v - hi in
+// units of 2^(e - 1075) (negative when hi was rounded up); one integer-to-float
+// conversion and a scale by that power of two (with v's sign) give lo.
 __device__ __forceinline__ float2 d2ff(double v) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
     const float h = d2f(v);
     const int ev = (int)((u >> 52) & 0x7ffu);
-    const unsigned low = (unsigned)u & 0x1fffffffu;             // the 29 dropped bits
-    const bool up = low >= (1u << 28);                          // h was rounded away from zero
-    const unsigned mag = up ? (1u << 29) - low : low;
-    const int pe = ev - 1075 + 127;                             // 2^(ev - 1075) as a float exponent
-    float lo = 0.f;
-    if (pe >= 1 && pe <= 254) lo = u29_to_float(mag) * __uint_as_float((unsigned)pe << 23);
-    if (up) lo = -lo;
-    if (u >> 63) lo = -lo;
+    const int rem = (int)((unsigned)u << 3) >> 3;                 // the 29 dropped bits, signed
+    const unsigned pe = (unsigned)(ev - 1075 + 127);              // 2^(ev - 1075) as a float exponent
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const float lo = (pe - 1u < 254u) ? __int2float_rn(rem) * __uint_as_float((pe << 23) | sign) : 0.f;
     return make_float2(h, lo);
 }
 // hi + lo in float64 (one float64 addition)

@@ -637,10 +637,11 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
         float2* x = reinterpret_cast<float2*>(w.r64);
         float* p32 = (mg || c->opt.solver != FLOSIC_SOLVER_PCG) ? nullptr : w.p32;
         if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset")) return FLOSIC_ERR_CUDA;
-        launch_ff_init(c, b, V, warm, x, p32, tol2, inner_tol2, s);
         // with the Kronecker solve (which overwrites d), each round ends with one
-        // sweep: x += d and the residual updated from d, r -= A d (b holds r)
+        // sweep: x += d and the residual updated from d, r -= A d (b holds r);
+        // a cold start then stores neither x = 0 nor d = 0
         const bool fused = c->opt.solver == FLOSIC_SOLVER_KRON;
+        launch_ff_init(c, b, V, warm, fused && !warm, x, p32, tol2, inner_tol2, s);
         for (int round = 0; round < 40; ++round) {
             if ((round > 0 && !fused) || (round == 0 && warm)) {
                 if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
@@ -676,7 +677,7 @@ int run_poisson(flosic_ctx* c, double* b, double* V, bool warm, cudaStream_t s) 
             if (fused) {
                 if (check_cuda(c, cudaMemsetAsync(st.n_active, 0, sizeof(int), s), "memset"))
                     return FLOSIC_ERR_CUDA;
-                launch_update_ff(c, b, x, tol2, inner_tol2, s);
+                launch_update_ff(c, b, x, round == 0 && !warm, tol2, inner_tol2, s);
             } else {
                 launch_correct_ff(c, x, s);
             }

@@ -62,13 +62,16 @@ __device__ __forceinline__ void start_round(CgState& st, int o, double rr, doubl
 // Start of the refinement: b arrives in pairs (from the right-hand-side
 // pass), x = warm start (pairs) or 0; b.b per orbital.  Without a warm start
 // the residual is b itself: r32 = float(b), d32 = 0 (p32 = r32 when given)
-// and the first float32 solve starts here.
+// and the first float32 solve starts here.  keep_zero (cold start of a solver
+// that overwrites d, the Kronecker solve): neither x nor d is stored; xz marks
+// x as zero until the first update writes it.
 __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                  const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                  const float2* __restrict__ b, const double* __restrict__ V,
                                                  float2* __restrict__ x, float* __restrict__ r32,
                                                  float* __restrict__ p32, float* __restrict__ d32, int warm,
-                                                 double tol2, double inner_tol2, int max_iter, CgState st) {
+                                                 int keep_zero, double tol2, double inner_tol2, int max_iter,
+                                                 CgState st) {
     __shared__ double scratch[32];
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     if (!st.oactive[P.o]) return;
@@ -88,10 +91,12 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
                 *reinterpret_cast<float4*>(x + g + 2) = make_float4(e.x, e.y, f.x, f.y);
             } else {
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4*>(x + g) = z4;
-                *reinterpret_cast<float4*>(x + g + 2) = z4;
+                if (!keep_zero) {
+                    *reinterpret_cast<float4*>(x + g) = z4;
+                    *reinterpret_cast<float4*>(x + g + 2) = z4;
+                    *reinterpret_cast<float4*>(d32 + g) = z4;
+                }
                 *reinterpret_cast<float4*>(r32 + g) = bh;
-                *reinterpret_cast<float4*>(d32 + g) = z4;
                 if (p32) *reinterpret_cast<float4*>(p32 + g) = bh;
             }
             return;
@@ -102,9 +107,11 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
             if (warm) {
                 x[g + k] = d2ff(V[g + k]);
             } else {
-                x[g + k] = make_float2(0.f, 0.f);
+                if (!keep_zero) {
+                    x[g + k] = make_float2(0.f, 0.f);
+                    d32[g + k] = 0.f;
+                }
                 r32[g + k] = bh;
-                d32[g + k] = 0.f;
                 if (p32) p32[g + k] = bh;
             }
         }
@@ -114,6 +121,7 @@ __global__ void __launch_bounds__(256) k_ff_init(const BlkDesc* __restrict__ blk
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
             st.bb[P.o] = sum;
+            st.xz[P.o] = (!warm && keep_zero) ? 1 : 0;
             if (!warm) start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
         }
     }
@@ -282,6 +290,8 @@ __global__ void __launch_bounds__(256) k_dmax(const BlkDesc* __restrict__ blk, c
 // registers).  d is left as it is (neighbouring tiles read it as halo): this
 // serves inner solvers that overwrite d (the Kronecker-product solve), not
 // those that start from d = 0.
+// kXZ: the first update after a cold start that stored no x (x = 0, not read)
+template <bool kXZ>
 __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                      float2* __restrict__ r, float2* __restrict__ x,
@@ -339,13 +349,15 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
 #pragma unroll
     for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? d32[P.base + P.z0 * sz + soff[j]] : 0.f;
     // r and x of this thread's two points, one plane ahead of their use
+    constexpr bool xz = kXZ;
+    const float2 f0 = make_float2(0.f, 0.f);
     float4 rx0 = make_float4(0.f, 0.f, 0.f, 0.f), rx1 = rx0;   // (r.h, r.l, x.h, x.l)
     if (in0) {
-        const float2 rv = r[P.base + P.z0 * sz + c0], xv = x[P.base + P.z0 * sz + c0];
+        const float2 rv = r[P.base + P.z0 * sz + c0], xv = xz ? f0 : x[P.base + P.z0 * sz + c0];
         rx0 = make_float4(rv.x, rv.y, xv.x, xv.y);
     }
     if (in1) {
-        const float2 rv = r[P.base + P.z0 * sz + c1], xv = x[P.base + P.z0 * sz + c1];
+        const float2 rv = r[P.base + P.z0 * sz + c1], xv = xz ? f0 : x[P.base + P.z0 * sz + c1];
         rx1 = make_float4(rv.x, rv.y, xv.x, xv.y);
     }
     IxPt* flat = &plane[0][0];
@@ -369,11 +381,11 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
 #pragma unroll
             for (int j = 0; j < kSlots; ++j) pre[j] = (soff[j] >= 0) ? d32[pz + soff[j]] : 0.f;
             if (in0) {
-                const float2 rv = r[pz + c0], xv = x[pz + c0];
+                const float2 rv = r[pz + c0], xv = xz ? f0 : x[pz + c0];
                 nx0 = make_float4(rv.x, rv.y, xv.x, xv.y);
             }
             if (in1) {
-                const float2 rv = r[pz + c1], xv = x[pz + c1];
+                const float2 rv = r[pz + c1], xv = xz ? f0 : x[pz + c1];
                 nx1 = make_float4(rv.x, rv.y, xv.x, xv.y);
             }
         }
@@ -424,7 +436,8 @@ __global__ void __launch_bounds__(256, 2) k_update12_ix(const BlkDesc* __restric
         const double sum = tile_gather(st.part, P.first, D.ntile, scratch);
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
-            st.dmax[P.o] = 0u;   // every CTA of the orbital has read it
+            st.dmax[P.o] = 0u;   // every CTA of the orbital has read it (and xz)
+            st.xz[P.o] = 0;      // x is stored now
             start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
         }
     }
@@ -452,6 +465,7 @@ constexpr unsigned kUStageBytes = 4u * kUStage;
 // the stages, two split planes (one barrier per plane), the stages' mbarriers
 size_t update_tma_smem() { return 4 * (size_t)kURing * kUStage + 2 * sizeof(IxPt) * kUPlane + 8 * kURing + 128; }
 
+template <bool kXZ>
 __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                          const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                          const CUtensorMap* __restrict__ maps,
@@ -472,6 +486,7 @@ __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restri
     const int oi = P.o - blk[P.b].orb0;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nzt = P.z1 - P.z0;
+    constexpr bool xz = kXZ;   // x is zero and not stored yet: its tiles are not copied
     const int E = (int)((st.dmax[P.o] >> 23) & 0xffu);
     const int es = max(-126, min(126, 154 - E));
     const float sc = __uint_as_float((unsigned)(es + 127) << 23);   // 2^es
@@ -485,11 +500,11 @@ __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restri
         uint64_t* b = bar + (k % kURing);
         float* sg = ring + (size_t)(k % kURing) * kUStage;
         const int zz = P.z0 + k;
-        tc_mbar_expect_tx(b, kUStageBytes);
+        tc_mbar_expect_tx(b, xz ? kUStageBytes - 8u * kUCtr : kUStageBytes);
         tc_tma_load_4d(sg, mp + 0, P.x0 - 8, P.y0 - kHalf, zz, oi, b);
         tc_tma_load_4d(sg + kUPlane, mp + 1, P.x0, P.y0, zz + kHalf, oi, b);
         tc_tma_load_4d(sg + kUPlane + kUCtr, mp + 2, 2 * P.x0, P.y0, zz, oi, b);
-        tc_tma_load_4d(sg + kUPlane + 3 * kUCtr, mp + 3, 2 * P.x0, P.y0, zz, oi, b);
+        if (!xz) tc_tma_load_4d(sg + kUPlane + 3 * kUCtr, mp + 3, 2 * P.x0, P.y0, zz, oi, b);
     };
     if (tid == 0) {
         for (int k = 0; k < kURing; ++k) tc_mbar_init(bar + k, 1);
@@ -570,7 +585,8 @@ __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restri
             }
             if (in) {
                 const float4 rv = *reinterpret_cast<const float4*>(sg + kUPlane + kUCtr + ty * 2 * kTileX + 4 * tx);
-                const float4 xv = *reinterpret_cast<const float4*>(sg + kUPlane + 3 * kUCtr + ty * 2 * kTileX + 4 * tx);
+                const float4 xv = xz ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                     : *reinterpret_cast<const float4*>(sg + kUPlane + 3 * kUCtr + ty * 2 * kTileX + 4 * tx);
                 const long long g = P.base + (P.z0 + k) * sz + col;
                 ff rn[2], xn[2];
 #pragma unroll
@@ -596,6 +612,7 @@ __global__ void __launch_bounds__(256, 2) k_update12_tma(const BlkDesc* __restri
         if (linear_tid() == 0) {
             st.count[P.o] = 0;
             st.dmax[P.o] = 0u;
+            st.xz[P.o] = 0;
             start_round(st, P.o, sum, tol2, inner_tol2, max_iter);
         }
     }
@@ -649,7 +666,9 @@ int setup_update_maps(flosic_ctx* c) {
     if (cudaMalloc(&dm, sizeof(CUtensorMap) * maps.size()) != cudaSuccess) return 0;
     c->allocations.push_back(dm);
     if (cudaMemcpy(dm, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaFuncSetAttribute((const void*)k_update12_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute((const void*)k_update12_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)update_tma_smem()) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_update12_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)update_tma_smem()) != cudaSuccess ||
         cudaMemcpy(c->mg.d_lvl[0], L0.data(), sizeof(LvlDesc) * c->nblk, cudaMemcpyHostToDevice) != cudaSuccess) {
         for (auto& D : L0) D.utma = 0;
@@ -692,9 +711,16 @@ __global__ void __launch_bounds__(256) k_correct_ff(const BlkDesc* __restrict__ 
 // V = x (pairs joined into float64), every orbital.
 __global__ void __launch_bounds__(256) k_join_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                  const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
-                                                 const float2* __restrict__ x, double* __restrict__ V) {
+                                                 const float2* __restrict__ x, const int* __restrict__ xz,
+                                                 double* __restrict__ V) {
     const TilePos P = tile_pos(blk, L, tiles, orb_blk, blockIdx.x);
     const LvlDesc& D = L[P.b];
+    if (xz[P.o]) {   // never updated (no solve needed): V = 0
+        tile_elementwise<float>(D, P, [&](long long g, int n) {
+            for (int k = 0; k < n; ++k) V[g + k] = 0.0;
+        });
+        return;
+    }
     tile_elementwise<float>(D, P, [&](long long g, int n) {
         if (n == 4) {   // aligned group of four points: 16-byte accesses
             const float4 a = *reinterpret_cast<const float4*>(x + g);
@@ -711,12 +737,12 @@ __global__ void __launch_bounds__(256) k_join_ff(const BlkDesc* __restrict__ blk
 static dim3 tile_threads() { return dim3(kTileX, kTileY / 2); }
 
 // x is the solution in pairs (float2 per point), p32 may be null.
-void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, float2* x, float* p32,
-                    double tol2, double inner_tol2, cudaStream_t s) {
+void launch_ff_init(flosic_ctx* c, const double* b, const double* V, bool warm, bool keep_zero, float2* x,
+                    float* p32, double tol2, double inner_tol2, cudaStream_t s) {
     const Multigrid& M = c->mg;
-    k_ff_init<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
-                                                               reinterpret_cast<const float2*>(b), V, x, c->ws.r32, p32, c->ws.d32, warm ? 1 : 0, tol2,
-                                                               inner_tol2, c->opt.max_iter, c->ws.cg);
+    k_ff_init<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+        c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<const float2*>(b), V, x, c->ws.r32, p32,
+        c->ws.d32, warm ? 1 : 0, keep_zero ? 1 : 0, tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
     note_launch(c);
 }
 
@@ -729,7 +755,9 @@ void launch_residual_ff(flosic_ctx* c, const double* b, const float2* x, float* 
     note_launch(c);
 }
 
-void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double inner_tol2, cudaStream_t s) {
+// x_zero: the first update after a cold start that stored no x
+void launch_update_ff(flosic_ctx* c, double* r, float2* x, bool x_zero, double tol2, double inner_tol2,
+                      cudaStream_t s) {
     const Multigrid& M = c->mg;
     if (c->kron.n_simt > 0) {   // the tensor-core passes record max |d| themselves
         k_dmax<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk,
@@ -737,13 +765,15 @@ void launch_update_ff(flosic_ctx* c, double* r, float2* x, double tol2, double i
         note_launch(c);
     }
     if (c->n_utma_blocks > 0) {   // blocks whose operands the copy engine stages
-        k_update12_tma<<<(unsigned)M.ntiles[0], dim3(kTileX / 2, kTileY), update_tma_smem(), s>>>(
+        auto kern = x_zero ? k_update12_tma<true> : k_update12_tma<false>;
+        kern<<<(unsigned)M.ntiles[0], dim3(kTileX / 2, kTileY), update_tma_smem(), s>>>(
             c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, (const CUtensorMap*)c->d_umaps, c->ws.d32,
             reinterpret_cast<float2*>(r), x, c->ws.r32, tol2, inner_tol2, c->opt.max_iter, c->ws.cg, c->ws.status);
         note_launch(c);
     }
     if (c->n_utma_blocks < c->nblk) {   // the rest: plain loads
-        k_update12_ix<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
+        auto kern = x_zero ? k_update12_ix<true> : k_update12_ix<false>;
+        kern<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(
             c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, reinterpret_cast<float2*>(r), x, c->ws.r32, c->ws.d32,
             tol2, inner_tol2, c->opt.max_iter, c->ws.cg);
         note_launch(c);
@@ -760,7 +790,7 @@ void launch_correct_ff(flosic_ctx* c, float2* x, cudaStream_t s) {
 void launch_join_ff(flosic_ctx* c, const float2* x, double* V, cudaStream_t s) {
     const Multigrid& M = c->mg;
     k_join_ff<<<(unsigned)M.ntiles[0], tile_threads(), 0, s>>>(c->d_blk, M.d_lvl[0], M.d_tiles[0], c->d_orb_blk, x,
-                                                               V);
+                                                               c->ws.cg.xz, V);
     note_launch(c);
 }
 

@@ -12,7 +12,10 @@
 
 namespace flosic {
 
-constexpr int kXcPts = kChunk / kChunkThreads;   // points per thread
+// 256 threads per chunk, 4 points each (64 threads with 16 points each, which
+// shares the per-orbital warp sums among more points, measured 1.9x slower)
+constexpr int kXcThreads = kChunkThreads;
+constexpr int kXcPts = kChunk / kXcThreads;   // points per thread
 
 // Warp sum of float partials carried as a float-float pair (two-sum per
 // level), returned in float64.
@@ -37,13 +40,13 @@ __device__ __forceinline__ double warp_sum_ff(float v) {
 // Also stores, for the reverse mode, V_i^SIC = -(V_i + v_xc,i) (vsic, float64)
 // or wbar_i = V_i^SIC phi_i (wbar, float32; kF32 only); either may be null.
 template <bool kF32>
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kXcThreads)
 k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
             const double* __restrict__ phi, const double* __restrict__ V, double scale,
             double rho_min, double* __restrict__ Vavg, double* __restrict__ e_part,
             double* __restrict__ vsic, float* __restrict__ wbar, const int* __restrict__ mask) {
     using R = typename std::conditional<kF32, float, double>::type;
-    __shared__ double red[kChunkThreads / 32][kMaxN][2];
+    __shared__ double red[kXcThreads / 32][kMaxN][2];
     const BlkDesc& B = blk[blockIdx.y];
     const int c = blockIdx.x;
     if (c >= B.nchunk) return;
@@ -60,7 +63,7 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
         ff uff = {0.f, 0.f};   // kF32: rho V as pairs (U to ~1e-13 relative)
 #pragma unroll
         for (int k = 0; k < kXcPts; ++k) {
-            const long long g = g0 + threadIdx.x + k * kChunkThreads;
+            const long long g = g0 + threadIdx.x + k * kXcThreads;
             if (g >= B.G) continue;
             if (!on) {
                 const R p = kF32 ? (R)d2f(psi[base + g]) : (R)psi[base + g];
@@ -121,7 +124,7 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
     if (Vavg) {
 #pragma unroll
         for (int k = 0; k < kXcPts; ++k) {
-            const long long g = g0 + threadIdx.x + k * kChunkThreads;
+            const long long g = g0 + threadIdx.x + k * kXcThreads;
             if (g >= B.G) continue;
             if (kF32)
                 Vavg[B.voff + g] = (rs[k] > rmin) ? f2d((float)scale * ((float)num[k] / (float)rs[k])) : 0.0;
@@ -133,7 +136,7 @@ k_xc_energy(const BlkDesc* __restrict__ blk, const double* __restrict__ psi,
     for (int e = threadIdx.x; e < 2 * B.N; e += blockDim.x) {
         const int i = e >> 1, q = e & 1;
         double s = 0.0;
-        for (int w = 0; w < kChunkThreads / 32; ++w) s += red[w][i][q];
+        for (int w = 0; w < kXcThreads / 32; ++w) s += red[w][i][q];
         e_part[(B.chunk0 + (long long)i * B.nchunk + c) * 2 + q] = s;
     }
 }
@@ -144,10 +147,10 @@ void launch_xc_energy(const flosic_ctx* c, const double* psi, const double* phi,
     for (const auto& b : c->blk) cmax = b.nchunk > cmax ? b.nchunk : cmax;
     const dim3 grid(cmax, c->nblk);
     if (c->opt.precision == FLOSIC_MIXED)
-        k_xc_energy<true><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
+        k_xc_energy<true><<<grid, kXcThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
                                                          c->ws.e_part, c->ws.vsic, c->ws.wbar, c->ws.mask);
     else
-        k_xc_energy<false><<<grid, kChunkThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
+        k_xc_energy<false><<<grid, kXcThreads, 0, s>>>(c->d_blk, psi, phi, V, scale, c->opt.rho_min, Vavg,
                                                           c->ws.e_part, c->ws.vsic, nullptr, c->ws.mask);
     note_launch(c);
 }
