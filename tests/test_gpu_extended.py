@@ -74,6 +74,31 @@ def test_kron_isolated_poisson_parity(F, orc):
     assert its.max() <= 6
 
 
+def test_kron_cold_start_zero_orbital_and_repeat(F, orc):
+    # A cold start of the Kronecker refinement stores neither x = 0 nor d = 0:
+    # an orbital with phi = 0 needs no solve and must come out V = 0 exactly,
+    # and a second cold solve on the same context (workspace holding the first
+    # one's x and d) must give the same potentials bit for bit.
+    s = synth.make_system(24, 0.4, 2, [3, 2], seed=33)
+    fl = [orc.build_flos(s.psi[sp], s.fods[sp], s.grid) for sp in range(2)]
+    phis = [fl[0]["phi"].copy(), fl[1]["phi"].copy()]
+    phis[0][1] = 0.0
+    ctx = _ctx(F, [s], 0)
+    phi = _flat(phis)
+    V1, _, conv1 = ctx.orbital_poisson(phi)
+    V1 = _np(V1).copy()
+    assert np.all(_np(conv1) == 1)
+    assert np.all(V1[s.G:2 * s.G] == 0.0)
+    off = 0
+    for sp, N in enumerate(s.norb):
+        Vref, _ = orc.poisson(phis[sp] ** 2, s.grid, tol=1e-13)
+        got = V1[off * s.G:(off + N) * s.G].reshape(N, s.G)
+        assert np.max(np.abs(got - Vref)) < 1e-8 * np.max(np.abs(Vref)), sp
+        off += N
+    V2, _, _ = ctx.orbital_poisson(phi)
+    assert np.array_equal(_np(V2), V1)
+
+
 @pytest.mark.parametrize("bc", [1, 2])
 def test_extended_poisson_parity(F, orc, bc):
     name = BC_NAMES[bc]
