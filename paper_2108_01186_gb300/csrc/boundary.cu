@@ -115,6 +115,10 @@ __device__ __forceinline__ void gather_moments(const TilePos& P, const LvlDesc& 
     }
 }
 
+// packed two-lane a - b and -a (exact: a product with -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+
 // Pass 1 over the tiles: b = scale * phi^2 and (for the multipole boundary)
 // the l <= 2 moments of phi^2 per orbital.  Per column (x, y) the z-sums
 // S0 = sum rho, S1 = sum rho Z, S2 = sum rho Z^2 give all ten moments.
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(256) k_rhs_bulk(const BlkDesc* __restrict__ bl
 // pairs (rho = phi^2 to ~48 bits) and the moments are accumulated as pairs,
 // so they match the float64 pass to ~1e-13 while no float64 operation runs
 // per grid point.
-__global__ void __launch_bounds__(256, 3) k_rhs_bulk_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
+__global__ void __launch_bounds__(256, 2) k_rhs_bulk_ff(const BlkDesc* __restrict__ blk, const LvlDesc* __restrict__ L,
                                                      const int4* __restrict__ tiles, const int* __restrict__ orb_blk,
                                                      const double* __restrict__ phi, double scale, int want_mom,
                                                      float2* __restrict__ b, double* __restrict__ mom_part,
@@ -191,41 +195,77 @@ __global__ void __launch_bounds__(256, 3) k_rhs_bulk_ff(const BlkDesc* __restric
     const ff sc = to_ff(d2ff(scale)), hz = to_ff(d2ff(B.h));
     const int x = P.x0 + threadIdx.x;
     const long long plane = (long long)D.ny * D.nx;
-    constexpr int kZU = 8;   // z loads a thread has in flight before their products
-    for (int k = 0; k < 2; ++k) {
-        const int y = P.y0 + threadIdx.y + k * (kTileY / 2);
-        if (x >= D.nx || y >= D.ny) continue;
-        // q_n = sum rho k^n over the column's points, k = z - z0 = 0, 1, ...
-        // (non-negative terms, so the pairs need no renormalisation per point);
-        // the z-moments about the centre follow once per column below.
-        ff q0 = {0.f, 0.f}, q1 = {0.f, 0.f}, q2 = {0.f, 0.f};
-        float kf = 0.f;
-        long long g = P.base + ((long long)P.z0 * D.ny + y) * D.nx + x;
+    constexpr int kZU = 4;   // z loads per column a thread has in flight before their products
+    // The thread's two columns (x, y_0) and (x, y_0 + 8) side by side: lane a
+    // of every float2 is column a, and each float operation of the pair
+    // arithmetic runs on both columns at once (packed two-lane instructions,
+    // the same IEEE operations per lane as the one-column form).
+    // q_n = sum rho k^n over a column's points, k = z - z0 = 0, 1, ...
+    // (non-negative terms, so the pairs need no renormalisation per point);
+    // the z-moments about the centre follow once per column below.
+    const int yc[2] = {P.y0 + (int)threadIdx.y, P.y0 + (int)threadIdx.y + kTileY / 2};
+    const bool inc[2] = {x < D.nx && yc[0] < D.ny, x < D.nx && yc[1] < D.ny};
+    float2 q0h = make_float2(0.f, 0.f), q0l = q0h, q1h = q0h, q1l = q0h, q2h = q0h, q2l = q0h;
+    if (inc[0] || inc[1]) {
+        const float2 sch = make_float2(sc.h, sc.h), scl = make_float2(sc.l, sc.l), two = make_float2(2.f, 2.f);
+        const long long dy = (long long)(kTileY / 2) * D.nx;   // column 1 lies 8 rows after column 0
+        float2 kf = make_float2(0.f, 0.f);
+        const float2 one = make_float2(1.f, 1.f);
+        long long g = P.base + ((long long)P.z0 * D.ny + yc[0]) * D.nx + x;
         for (int z = P.z0; z < P.z1; z += kZU, g += kZU * plane) {
-            double pv[kZU];
+            double pv0[kZU], pv1[kZU];
 #pragma unroll
-            for (int u = 0; u < kZU; ++u) pv[u] = (z + u < P.z1) ? __ldcs(phi + g + u * plane) : 0.0;
+            for (int u = 0; u < kZU; ++u) {
+                pv0[u] = (inc[0] && z + u < P.z1) ? __ldcs(phi + g + u * plane) : 0.0;
+                pv1[u] = (inc[1] && z + u < P.z1) ? __ldcs(phi + g + dy + u * plane) : 0.0;
+            }
 #pragma unroll
             for (int u = 0; u < kZU; ++u) {
                 if (z + u >= P.z1) break;
-                const float2 f = d2ff(pv[u]);
-                const float ph = f.x * f.x;
-                const ff rho = ff_quick(ph, fmaf(f.x, f.x, -ph) + 2.f * f.x * f.y);
-                const ff bv = ff_mul(sc, rho);
-                __stcs(b + g + u * plane, make_float2(bv.h, bv.l));
-                const float t1 = rho.h * kf, e1 = fmaf(rho.l, kf, fmaf(rho.h, kf, -t1));   // rho k
-                const float t2 = t1 * kf, e2 = fmaf(e1, kf, fmaf(t1, kf, -t2));            // rho k^2
-                q0 = ff_acc(q0, rho.h, rho.l);
-                q1 = ff_acc(q1, t1, e1);
-                q2 = ff_acc(q2, t2, e2);
-                kf += 1.f;
+                const float2 f0 = d2ff(pv0[u]), f1 = d2ff(pv1[u]);
+                const float2 fx = make_float2(f0.x, f1.x), fy = make_float2(f0.y, f1.y);
+                // rho = phi^2 as pairs
+                const float2 ph = __fmul2_rn(fx, fx);
+                const float2 pe = __fadd2_rn(__ffma2_rn(fx, fx, neg2(ph)), __fmul2_rn(__fmul2_rn(two, fx), fy));
+                const float2 rh = __fadd2_rn(ph, pe);
+                const float2 rl = sub2(pe, sub2(rh, ph));
+                // b = sc rho
+                const float2 bp = __fmul2_rn(sch, rh);
+                float2 be = __ffma2_rn(sch, rh, neg2(bp));
+                be = __ffma2_rn(sch, rl, be);
+                be = __ffma2_rn(scl, rh, be);
+                const float2 bh = __fadd2_rn(bp, be);
+                const float2 bl = sub2(be, sub2(bh, bp));
+                if (inc[0]) __stcs(b + g + u * plane, make_float2(bh.x, bl.x));
+                if (inc[1]) __stcs(b + g + dy + u * plane, make_float2(bh.y, bl.y));
+                // rho k and rho k^2 as unnormalised pairs
+                const float2 t1 = __fmul2_rn(rh, kf);
+                const float2 e1 = __ffma2_rn(rl, kf, __ffma2_rn(rh, kf, neg2(t1)));
+                const float2 t2 = __fmul2_rn(t1, kf);
+                const float2 e2 = __ffma2_rn(e1, kf, __ffma2_rn(t1, kf, neg2(t2)));
+                // q += term: exact two-sum of the high parts, the rest gathered in the low part
+                auto acc = [&](float2& qh, float2& ql, float2 th, float2 tl) {
+                    const float2 sh = __fadd2_rn(qh, th);
+                    const float2 bb = sub2(sh, qh);
+                    const float2 er = __fadd2_rn(sub2(qh, sub2(sh, bb)), sub2(th, bb));
+                    ql = __fadd2_rn(ql, __fadd2_rn(er, tl));
+                    qh = sh;
+                };
+                acc(q0h, q0l, rh, rl);
+                acc(q1h, q1l, t1, e1);
+                acc(q2h, q2l, t2, e2);
+                kf = __fadd2_rn(kf, one);
             }
         }
+    }
+    const ff Z0 = to_ff(d2ff(B.oz + B.h * P.z0 - B.cz));
+    for (int k = 0; k < 2; ++k) {
+        if (!inc[k]) continue;
+        const int y = yc[k];
         // Z = Z0 + h k:  S0 = q0, S1 = Z0 q0 + h q1, S2 = Z0 (Z0 q0 + 2 h q1) + h^2 q2
-        q0 = ff_quick(q0.h, q0.l);
-        q1 = ff_quick(q1.h, q1.l);
-        q2 = ff_quick(q2.h, q2.l);
-        const ff Z0 = to_ff(d2ff(B.oz + B.h * P.z0 - B.cz));
+        const ff q0 = ff_quick(k ? q0h.y : q0h.x, k ? q0l.y : q0l.x);
+        const ff q1 = ff_quick(k ? q1h.y : q1h.x, k ? q1l.y : q1l.x);
+        const ff q2 = ff_quick(k ? q2h.y : q2h.x, k ? q2l.y : q2l.x);
         const ff hq1 = ff_mul(hz, q1), z0q0 = ff_mul(Z0, q0);
         const ff s0 = q0;
         const ff s1 = ff_add(z0q0, hq1);
