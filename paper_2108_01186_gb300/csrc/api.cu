@@ -50,6 +50,7 @@ void release(flosic_ctx* c) {
     c->allocations.clear();
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     c->h_pinned = nullptr;
+    c->h_pinned_dev = nullptr;
 }
 
 int validate_options(const flosic_options& o, std::string& why) {
@@ -139,18 +140,38 @@ int setup_tensor_maps(flosic_ctx* c, const void* zbuf, const void* pbuf, const v
 int read_status(flosic_ctx* c, cudaStream_t s, int* st4) {
     int rc = check_cuda(c, cudaGetLastError(), "kernel launch");
     if (rc) return rc;
-    rc = check_cuda(c, cudaMemcpyAsync(c->h_pinned, c->ws.status, 4 * sizeof(int), cudaMemcpyDeviceToHost, s),
-                    "cudaMemcpyAsync(status)");
+    rc = check_cuda(c, fetch_words(c, c->ws.status, 4, s), "status read");
     if (rc) return rc;
     rc = check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (rc) return rc;
-    for (int k = 0; k < 4; ++k) st4[k] = c->h_pinned[k];
+    for (int k = 0; k < 4; ++k) st4[k] = reinterpret_cast<volatile int*>(c->h_pinned)[k];
     prof_collect(c);
     return FLOSIC_OK;
 }
 }  // namespace
 
 namespace flosic {
+
+__global__ void k_put_words(const int* __restrict__ src, int n, int* dst) {
+    if ((int)threadIdx.x < n) reinterpret_cast<volatile int*>(dst)[threadIdx.x] = src[threadIdx.x];
+    __threadfence_system();
+}
+
+cudaError_t fetch_words(const flosic_ctx* c, const int* src, int n, cudaStream_t s) {
+    if (!c->h_pinned_dev) return cudaMemcpyAsync(c->h_pinned, src, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+    k_put_words<<<1, 32, 0, s>>>(src, n, c->h_pinned_dev);
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_doubles(double* dst, int n, double v) {
+    for (int i = threadIdx.x; i < n; i += 32) dst[i] = v;
+}
+
+void fill_doubles(const flosic_ctx* c, double* dst, int n, double v, cudaStream_t s) {
+    k_fill_doubles<<<1, 32, 0, s>>>(dst, n, v);
+    note_launch(c);
+}
 void prof_collect(flosic_ctx* c) {
     for (int k = 0; k < c->prof_used; ++k) {
         float ms = 0.f;
@@ -506,6 +527,10 @@ int flosic_create(flosic_ctx** out, const flosic_system* sys, int nsys, const fl
     A(&g.iters, orb); A(&g.n_active, 1); A(&g.n_oactive, 1); A(&g.conv, orb); A(&g.prof_bytes, 1);
     A(&g.dmax, orb); A(&g.xz, orb);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 16 * sizeof(int));
+    if (e == cudaSuccess && cudaHostGetDevicePointer((void**)&c->h_pinned_dev, c->h_pinned, 0) != cudaSuccess) {
+        c->h_pinned_dev = nullptr;   // not mapped: status reads take cudaMemcpyAsync
+        cudaGetLastError();
+    }
     if (e == cudaSuccess && o.solver == FLOSIC_SOLVER_KRON) e = setup_kron(c);   // sets the blocks' kq, kl
     for (BlkDesc& B : c->blk) B.gtma = (o.precision == FLOSIC_MIXED && gram_async_eligible(B)) ? 1 : 0;
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blk, c->blk.data(), sizeof(BlkDesc) * c->nblk, cudaMemcpyHostToDevice);
@@ -764,8 +789,10 @@ int flosic_step_host(flosic_ctx* c, const double* psi_h, const double* fods_h, d
         H.pre_fods = fods_next;
     }
     const int nsys = (int)c->sys.size();
-    std::vector<double> g((size_t)nsys, gE);
-    rc = check_cuda(c, cudaMemcpyAsync(H.gE, g.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, s), "copy gE");
+    // gE for every system by a kernel (a host copy could queue behind the
+    // prefetch on the copy engine)
+    fill_doubles(c, H.gE, nsys, gE, s);
+    rc = check_cuda(c, cudaGetLastError(), "gE fill");
     if (rc) return rc;
     int prc, ci;
     if (have_fwd) {

@@ -216,6 +216,7 @@ struct flosic_ctx {
     bool have_energy = false;
     std::string err;
     int* h_pinned = nullptr;                // small pinned host buffer
+    int* h_pinned_dev = nullptr;            // its device view (mapped), or null
     mutable long long launches = 0;         // kernels launched by this context
     int n_tma_blocks = 0;                   // blocks whose stencil operands the copy engine stages
     void* d_tmaps = nullptr;                // per-block tensor maps of the z buffer (CUtensorMap)
@@ -265,6 +266,14 @@ namespace flosic {
 // Mixed precision with V reused in the adjoint: the energy pass stores
 // wbar_i = V_i^SIC phi_i (float32), all the adjoint reads per point besides
 // psi; otherwise V_i^SIC itself (float64).
+// Copies n status words from device memory to the context's pinned host
+// buffer on stream s: through its mapping by a one-warp kernel when the
+// buffer is mapped (no copy engine, so the read does not queue behind a large
+// transfer another stream has in flight), else by cudaMemcpyAsync.
+cudaError_t fetch_words(const flosic_ctx* c, const int* src, int n, cudaStream_t s);
+// Fills n doubles of device memory with v on stream s (a one-warp kernel).
+void fill_doubles(const flosic_ctx* c, double* dst, int n, double v, cudaStream_t s);
+
 inline bool uses_wbar(const flosic_ctx* c) {
     return c->opt.precision == FLOSIC_MIXED && c->opt.adjoint_mode == FLOSIC_ADJ_REUSE_V;
 }

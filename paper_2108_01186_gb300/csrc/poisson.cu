@@ -514,12 +514,10 @@ __global__ void k_cg_finish(int norb, CgState st, int* out_iters, int* out_conv,
 }
 
 static int read_count(flosic_ctx* c, const int* dptr, cudaStream_t s) {
-    if (check_cuda(c, cudaMemcpyAsync(c->h_pinned, dptr, sizeof(int), cudaMemcpyDeviceToHost, s),
-                   "cudaMemcpyAsync") != FLOSIC_OK)
-        return -1;
+    if (check_cuda(c, fetch_words(c, dptr, 1, s), "count read") != FLOSIC_OK) return -1;
     if (check_cuda(c, cudaStreamSynchronize(s), "cudaStreamSynchronize") != FLOSIC_OK) return -1;
     prof_collect(c);
-    return c->h_pinned[0];
+    return reinterpret_cast<volatile int*>(c->h_pinned)[0];
 }
 
 static void launch_residual_zero(flosic_ctx* c, const double* b, double* r, double tol2, int* flag, int* counter,
