@@ -449,7 +449,7 @@ def run_gpu(args):
         sec = prof_ov["kernel_ms"] / 1e3
         tflops = prof_ov["flops"] / sec / 1e12
         ov_bytes = prof_ov["kernel_launches"] * sum(8.0 * n * s.G for n in s.norb)
-        roof_ov = {"bound": "latency", "kernel": "k_gram_tc (split-BF16 tcgen05)",
+        roof_ov = {"bound": "latency", "kernel": "k_gram_async (split-BF16 tcgen05)",
                    "achieved": round(tflops, 3), "peak": tc_peak, "peak_source": tc_src, "unit": "TFLOP/s",
                    "frac": round(tflops / tc_peak, 5),
                    "hbm_achieved_gbs": round(ov_bytes / sec / 1e9, 1),
