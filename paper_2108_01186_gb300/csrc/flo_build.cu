@@ -313,7 +313,8 @@ __global__ void __launch_bounds__(256) k_contract(const BlkDesc* __restrict__ bl
 // Output tiles of 4 x 4 per thread: the CTA's 256 threads form KG = 256 /
 // (NP/4)^2 groups, each holding the whole NP x NP product for every KG-th
 // point of a step, so a point costs each thread two 16-byte shared loads for
-// 16 FMAs.  Float sums of up to 16 points are two-summed into (sum, low)
+// 16 FMAs (8 packed two-lane instructions).  Float sums of up to 16 points are
+// two-summed into (sum, low)
 // pairs; the groups' pairs are added at the end in a fixed order.
 template <int RM, class LA, class LB>
 __global__ void __launch_bounds__(256, RM <= 2 ? 2 : 1) k_contract_f(const BlkDesc* __restrict__ blk, int kparts, LA la, LB lb,
