@@ -964,10 +964,10 @@ constexpr int kRowMaxK = 64;      // K = mult N it takes (N <= 32, mult <= 2)
 // out_j(g) = sum_k E_jk X_k(g) for blocks with N <= NJ <= 32 (mixed
 // precision): one point per thread with all N outputs in registers, E (as
 // float, transposed) in shared memory for the whole block, so a k step is
-// NJ/4 broadcast 16-byte shared loads and NJ FMAs per point.  The rows of X
-// come in two segments (R1: k < K1, R2: the K2 rows after them; R2 may be
-// empty), each fetched in groups of its own kGroup with its own load type, so
-// no group mixes two kinds of rows.  Persistent CTAs walk a contiguous range
+// NJ/4 broadcast 16-byte shared loads and NJ FMAs per point (NJ/2 packed
+// two-lane instructions).  The rows of X come in two segments (R1: k < K1,
+// R2: the K2 rows after them; R2 may be empty), each fetched in groups of its
+// own kGroup with its own load type, so no group mixes two kinds of rows.  Persistent CTAs walk a contiguous range
 // of the (block, 256-point tile) items; the loads of the next group (of the
 // same segment, the other segment or the next tile) are issued before the
 // current group is multiplied.
